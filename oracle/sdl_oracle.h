@@ -1,0 +1,96 @@
+/*
+ * sdl_oracle.h -- plain FP64 CPU oracle for split-and-merge dictionary learning.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / --impl reference legs of bench.py may load this library.  The
+ * product path (the CUDA library under paper_1403_4781_gb300/) never links,
+ * imports or calls it, and this code shares nothing with that path.
+ *
+ * Notation follows the paper (Mukherjee & Seelamantula, "A split-and-merge
+ * dictionary learning algorithm for sparse representation", arXiv 1403.4781):
+ *   Y  in R^{m x N}  training signals, one signal per column      (Sec. 2)
+ *   D  in R^{m x K}  dictionary with unit-norm atoms d_j           (Def. 1, Sec. 2)
+ *   X  in R^{K x N}  s-sparse coefficient columns                  (Sec. 2)
+ * Storage: every matrix is column-major with the m entries of one signal or
+ * one atom contiguous (Y[i*m + r], D[j*m + r]).  Sparse coefficient columns are
+ * stored in ELL form: idx[i*s + k] (atom index, -1 pads), val[i*s + k].
+ *
+ * Every function is a direct transcription of a definition; none is blocked,
+ * fused or reordered.  Return value: 0 ok, 1 invalid argument, 2 Cholesky
+ * breakdown after the ridge retry.
+ */
+#ifndef SDL_ORACLE_H
+#define SDL_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Orthogonal matching pursuit (Sec. 1 and the error-constrained form of
+ * Sec. 3.2.2), one signal at a time:
+ *   r = y, S = {}; while |S| < s and ||r||_2 > eps:
+ *     j* = argmax_{j not in S} |d_j^T r|  (lowest index wins a tie);
+ *     stop if that maximum is 0 or d_j* is numerically inside span(D_S);
+ *     S = S u {j*};  x_S = argmin ||y - D_S x||_2;  r = y - D_S x_S.
+ * Outputs per signal i: idx/val [s] in selection order, nnz, resid2 = ||r||^2,
+ * gap[s] = top-two gap of |d_j^T r| among unselected atoms at each step
+ * (+inf where no step was taken).  resid2 and gap may be NULL. */
+int orc_omp(const double *D, int m, int K, const double *Y, int64_t n, int s,
+            double eps, int32_t *idx, double *val, int32_t *nnz,
+            double *resid2, double *gap, int nthreads);
+
+/* Method of optimal directions (Sec. 1): D = Y X^T (X X^T)^{-1} over the used
+ * atoms U (atoms with at least one signal); atoms outside U keep Dprev.  If the
+ * Cholesky factor of A_UU = (X X^T)_UU breaks down it is retried once with
+ * A_UU + lambda I, lambda = 1e-10 tr(A_UU)/|U|.  normalise != 0 then scales
+ * every column to unit norm (Sec. 3.1), keeping Dprev for a zero column.
+ * usage[K] (may be NULL) receives the number of signals using each atom;
+ * ridge (may be NULL) receives 1 when the ridge retry was taken. */
+int orc_mod(const double *Y, int m, int64_t n, const int32_t *idx,
+            const double *val, int s, const double *Dprev, int K, int normalise,
+            double *Dout, int32_t *usage, int *ridge);
+
+/* Alternating minimisation (Sec. 1, "standard approach"): for it in 0..iters-1
+ * { X = OMP(D, Y, s, eps); rmse[it] = ||Y - D X||_F / sqrt(m n); D = MOD(Y, X) }.
+ * D is the initial dictionary on entry and the trained one on exit.
+ * xfro receives ||X||_F of the last coding pass.  idx/val/nnz (may be NULL)
+ * receive that last coding.  rmse may be NULL. */
+int orc_train(const double *Y, int m, int64_t n, double *D, int K, int s,
+              double eps, int iters, double *rmse, double *xfro,
+              int32_t *idx, double *val, int32_t *nnz, int nthreads);
+
+/* Algorithm 1 step 1: Yp[:, i] = Y[:, perm[i]] (the random partition is the
+ * permutation followed by contiguous subsets given by offsets). */
+int orc_split(const double *Y, int m, int64_t N, const int64_t *perm, double *Yp);
+
+/* Algorithm 1 step 2: subset t = columns offsets[t] .. offsets[t+1]-1 of Y is
+ * trained independently with K1 atoms and sparsity s1.  Dloc is [L][K1][m]
+ * (init on entry, trained on exit); xfro[L]; rmse [L][iters] (may be NULL). */
+int orc_local_train(const double *Y, int m, const int64_t *offsets, int L,
+                    double *Dloc, int K1, int s1, double eps, int iters,
+                    double *xfro, double *rmse, int nthreads);
+
+/* Algorithm 1 step 3: Ytilde = [ xfro[0] D^(0) ... xfro[L-1] D^(L-1) ]
+ * (m x K1 L); D is initialised with the normalised columns Ytilde[:, pick[j]]
+ * and trained on Ytilde with K atoms and sparsity s2.  D is [K][m] out.
+ * Ytilde_out [K1 L][m] may be NULL. */
+int orc_merge(const double *Dloc, const double *xfro, int m, int K1, int L,
+              const int32_t *pick, int K, int s2, double eps, int iters,
+              double *D, double *rmse, double *Ytilde_out, int nthreads);
+
+/* ||Y - D X||_F^2 and ||Y||_F^2 with X in ELL form (Table 1's MSE_train is
+ * 20 log10 of the square root of their ratio). */
+int orc_residual(const double *Y, int m, int64_t n, const double *D, int K,
+                 const int32_t *idx, const double *val, int s,
+                 double *res2, double *y2);
+
+/* Atom recovery (Sec. 3.1): number of atoms d_i of D0 with some atom of D
+ * such that |d_i^T dhat_j| >= thresh. */
+int orc_recovery(const double *D0, int K0, const double *D, int K, int m,
+                 double thresh, int *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
