@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark: split-and-merge dictionary learning (Algorithm 1) on one GB300.
+
+One step = the whole hot path on the split-and-merge FP32 workload
+(m=64, K=256, s=6, N=200,000 synthetic signals from a K=256 ground-truth
+dictionary with noise 0.01; L=100 subsets of 2,000; local K1=256, s1=2, 20
+MOD/OMP iterations, all subsets in one batched launch per kernel; merge of the
+25,600 scaled local atoms to K=256 with s2=3 over 20 iterations; final OMP
+coding of all N signals with s=6 and the MSE of Table 1):
+split gather -> initial atoms -> local training -> scaled stack + merge
+training -> final coding -> residual.
+
+metric: OMP-coded signals per second (local + merge + final codings per step
+divided by the step time); the train-to-RMSE time and the RMSE reached are
+reported beside it.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sdl_inputs as si  # noqa: E402
+
+METRIC = "OMP signals/sec and train-to-RMSE time, chosen vs plain form on 1 GB300"
+UNIT = "signals/s"
+WORKLOAD = "splitmerge_fp32_m64_K256_s6_N200000_L100x2000_iters20+20"
+
+# Nominal FP64 rate of the part (recipe table: 1.25 TFLOP/s); with 152 SMs at the
+# 2,070 MHz maximum clock this is 2 DFMA per clock per SM (152*2*2*2.07e9 = 1.259e12).
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
+# FP32 CUDA-core rate: 152 SMs x 128 FFMA/clock x 2 flops x 2.07 GHz.
+FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------ clocks ------
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    mhz.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(mhz)) if mhz else None, "sm_max_mhz": mx,
+                "samples": len(mhz), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ workload ------
+def counts(p):
+    """OMP-coded signals per step: local passes, merge passes, final coding."""
+    local = p.iters_local * p.N
+    merge = p.iters_merge * p.K1 * p.L
+    return local + merge + p.N
+
+
+def algorithmic_work(p):
+    """Per-step algorithmic flops of each kernel family (unit figures x units)."""
+    m, K, K1, L = p.m, p.K, p.K1, p.L
+    nm = p.K1 * p.L
+    def omp_flops(K_, s_):          # 2mK (alpha0) + K s (s+1) (Batch-OMP updates)
+        return 2 * m * K_ + K_ * s_ * (s_ + 1)
+    return {
+        "chol_fp64": ("alu", p.iters_local * L * K1 ** 3 / 3 + p.iters_merge * K ** 3 / 3),
+        "solve_fp64": ("alu", p.iters_local * L * 2 * K1 ** 2 * m + p.iters_merge * 2 * K ** 2 * m),
+        "omp": ("alu", p.iters_local * p.N * omp_flops(K1, p.s1) + p.iters_merge * nm * omp_flops(K, p.s2)
+                + p.N * omp_flops(K, p.s)),
+        "gram": ("alu", p.iters_local * L * 2 * K1 * K1 * m + p.iters_merge * 2 * K * K * m),
+    }
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_1403_4781_gb300 as sdl
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    p = si.config1()
+    Y_h = torch.from_numpy(p.Y).pin_memory()
+    perm_h = torch.from_numpy(p.perm).pin_memory()
+    picks_h = torch.from_numpy(p.picks.reshape(-1)).pin_memory()
+    mpick_h = torch.from_numpy(p.mpick).pin_memory()
+    Y, perm = Y_h.to(dev), perm_h.to(dev)
+    picks, mpick = picks_h.to(dev), mpick_h.to(dev)
+    ctx = sdl.context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(Y, perm, picks, mpick):
+        Yp = sdl.split(Y, perm)
+        Dl = sdl.init_dict(Yp, picks).view(p.L, p.K1, p.m)
+        xfro, _ = sdl.local_train(Yp, p.offsets, Dl, p.s1, p.iters_local, with_rmse=False)
+        D, _ = sdl.merge(Dl, xfro, mpick, p.K, p.s2, p.iters_merge, with_rmse=False)
+        idx, val, nnz, _ = sdl.omp(D, Y, p.s, with_resid=False)
+        out2 = sdl.residual(Y, D, idx, val)
+        return D, out2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(Y, perm, picks, mpick)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    # ---- device-resident timed region (per-step events; L2 flushed between steps)
+    ctx.profile(True)
+    ctx.profile_reset()
+    launches0 = ctx.launch_count()
+    ms = []
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            D, out2 = step(Y, perm, picks, mpick)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    barrier()
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clocks = clk.summary()
+    total_ms = float(sum(ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    r2, y2 = out2.cpu().tolist()
+    n_sig = counts(p)
+    value = world * n_sig * args.steps / (total_ms / 1e3)
+
+    # ---- end to end: pinned host inputs -> device, step, result -> host, every step
+    D_host = torch.empty((p.K, p.m), dtype=torch.float32).pin_memory()
+    out_host = torch.empty((2,), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Yd = Y_h.to(dev, non_blocking=True)
+        permd = perm_h.to(dev, non_blocking=True)
+        picksd = picks_h.to(dev, non_blocking=True)
+        mpickd = mpick_h.to(dev, non_blocking=True)
+        Dd, o2 = step(Yd, permd, picksd, mpickd)
+        D_host.copy_(Dd, non_blocking=True)
+        out_host.copy_(o2, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = float(sum(e2e_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    h2d = sum(t.numel() * t.element_size() for t in (Y_h, perm_h, picks_h, mpick_h))
+    d2h = D_host.numel() * 4 + 16
+
+    # ---- roofline of the dominant kernel (device time measured inside the timed region)
+    work = algorithmic_work(p)
+    dom = max(prof.items(), key=lambda kv: kv[1][2])
+    name, (nl, ncalls, kms) = dom
+    roof = None
+    if name in work:
+        kind, flops_step = work[name]
+        peak = FP64_PEAK_FLOPS if "fp64" in name else FP32_PEAK_FLOPS
+        achieved = flops_step * args.steps / (kms / 1e3)
+        roof = {"kernel": name, "bound": kind, "achieved": achieved / 1e12,
+                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": ("nominal FP64 1.25 TFLOP/s = 152 SMs x 2 DFMA/clk x 2.07 GHz"
+                                if "fp64" in name else "152 SMs x 128 FFMA/clk x 2.07 GHz"),
+                "share_of_step": kms / total_ms, "launches": nl}
+    kernels = {k: {"ms_per_step": v[2] / args.steps, "launches_per_step": v[0] / args.steps}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded; Sec. 3.1 data model, sizes of the split-and-merge FP32 config)",
+        "config": {"workload": WORKLOAD, "m": p.m, "K": p.K, "N": p.N, "L": p.L, "n": int(p.N // p.L),
+                   "K1": p.K1, "s": p.s, "s1": p.s1, "s2": p.s2, "iters_local": p.iters_local,
+                   "iters_merge": p.iters_merge, "form": "plain (FP32 CUDA-core OMP, FP64 MOD)",
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "signals_per_step": n_sig,
+        "train_to_rmse_s": total_ms / args.steps / 1e3,
+        "rmse_final": float(np.sqrt(r2 / (p.m * p.N))),
+        "mse_train_db": float(10 * np.log10(r2 / y2)),
+        "e2e": {"value": world * n_sig * args.steps / (e2e_total / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernels": kernels,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(p, Y_h.numpy())
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ CPU oracle ------
+def _oracle_sample(p, Y, n_sub, final_n, merge_iters):
+    """Run the oracle on a bounded sample of the workload: local training of the
+    first n_sub subsets (all iterations), a merge of their stacked atoms, and the
+    final coding of final_n signals.  Returns (coded signals, seconds, threads)."""
+    import oracle
+    th = oracle.default_threads()
+    Yp = Y[p.perm[: p.offsets[n_sub]]].astype(np.float64)
+    off = p.offsets[: n_sub + 1]
+    Dl = np.stack([Yp[q] / np.linalg.norm(Yp[q], axis=1, keepdims=True) for q in p.picks[:n_sub]])
+    t0 = time.perf_counter()
+    loc = oracle.local_train(Yp, off, Dl, p.s1, p.iters_local, nthreads=th)
+    pick = np.random.default_rng(0).choice(n_sub * p.K1, p.K, replace=False).astype(np.int32)
+    mer = oracle.merge(loc["D"], loc["xfro"], pick, p.K, p.s2, merge_iters, nthreads=th)
+    oracle.omp(mer["D"], Y[:final_n].astype(np.float64), p.s, nthreads=th)
+    dt = time.perf_counter() - t0
+    coded = p.iters_local * int(off[-1]) + merge_iters * n_sub * p.K1 + final_n
+    return coded, dt, th
+
+
+def cpu_baseline(p, Y):
+    coded, dt, th = _oracle_sample(p, Y, n_sub=24, final_n=20_000, merge_iters=2)
+    return {"value": coded / dt, "unit": UNIT, "cores": th, "kind": "oracle",
+            "sample": f"24 of 100 subsets x {p.iters_local} local iterations, merge of their "
+                      f"{24 * p.K1} atoms x 2 iterations, final coding of 20,000 signals "
+                      f"({coded} coded signals in {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p = si.config1()
+    Y = p.Y
+    for _ in range(args.warmup):
+        _oracle_sample(p, Y, n_sub=2, final_n=2000, merge_iters=1)
+    tot_coded, tot_s, th = 0, 0.0, 1
+    for _ in range(args.steps):
+        coded, dt, th = _oracle_sample(p, Y, n_sub=4, final_n=8000, merge_iters=4)
+        tot_coded += coded
+        tot_s += dt
+    value = tot_coded / tot_s
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "form": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                         "sample": "per step: 4 subsets x 20 local iterations, merge of their 1,024 "
+                                   "atoms x 4 iterations, final coding of 8,000 signals"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * sdl.h -- C ABI of the GB300 (sm_103a) split-and-merge dictionary-learning library.
+ *
+ * The library implements the data-parallel hot path of "A split-and-merge
+ * dictionary learning algorithm for sparse representation" (Mukherjee and
+ * Seelamantula, arXiv 1403.4781): OMP sparse coding (Sec. 1; error-constrained
+ * form Sec. 3.2.2), the MOD dictionary update with column renormalisation
+ * (Sec. 1, Sec. 3.1), and Algorithm 1 (split, independent local training,
+ * scaled-stack merge).
+ *
+ * Conventions shared by every call
+ *  - Matrices are column-major with one signal or one atom contiguous:
+ *    Y in R^{m x n} is n*m elements, signal i at Y + i*m; D in R^{m x K} is K*m
+ *    elements, atom j at D + j*m.  Sparse codes are ELL: idx[i*s + k] (atom,
+ *    -1 pads, selection order), val[i*s + k], nnz[i].
+ *  - "device" pointers must be addresses in the context device's memory (e.g.
+ *    torch tensors); "host" pointers are ordinary CPU memory.  The caller owns
+ *    every buffer it passes; the library never frees or retains them beyond the
+ *    call.  Device pointers must be 16-byte aligned.
+ *  - Element type: SDL_PREC_F64 uses double for D, Y, val and resid2; the other
+ *    precisions use float.  Accumulators of the MOD normal equations and their
+ *    Cholesky factor / solve are always FP64.
+ *  - Every call enqueues its kernels on the context's stream and returns a
+ *    status.  Calls that can report a device-side condition (Cholesky breakdown)
+ *    synchronise that stream before returning.  A call may grow the context's
+ *    device workspace (cudaMalloc, synchronising) the first time it sees a
+ *    larger shape.
+ *  - Errors: SDL_EINVAL for a null pointer, a bad size or option (message via
+ *    sdl_last_error); SDL_ENOTPD when the MOD normal equations of some subset
+ *    are not positive definite even after the ridge retry (that subset's atoms
+ *    keep their previous values); SDL_ECUDA for a CUDA runtime error;
+ *    SDL_ENOMEM when the workspace cannot be allocated.  On SDL_EINVAL nothing
+ *    is launched.
+ */
+#ifndef SDL_H
+#define SDL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SDL_OK = 0,
+  SDL_EINVAL = 1,
+  SDL_ENOTPD = 2,
+  SDL_ETIMEOUT = 3,
+  SDL_ECUDA = 4,
+  SDL_ENOMEM = 5
+} sdl_status;
+
+typedef enum {
+  /* FP64 data and FP64 arithmetic everywhere. */
+  SDL_PREC_F64 = 0,
+  /* FP32 data; correlations, Gram and the OMP loop in FP32 (CUDA cores);
+     coefficients recomputed on the support with one refinement step. */
+  SDL_PREC_F32 = 1,
+  /* FP32 data; correlations and Gram from BF16 operands on the tensor cores
+     with FP32 accumulation; coefficients recomputed in FP32 on the support
+     with one refinement step. */
+  SDL_PREC_BF16 = 2
+} sdl_precision;
+
+typedef struct sdl_ctx sdl_ctx;
+
+/* Create a context on CUDA device `device` that enqueues on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *ctx receives the handle. */
+sdl_status sdl_create(sdl_ctx **ctx, int device, void *stream);
+/* Free the context's workspace and the handle (NULL is accepted). */
+sdl_status sdl_destroy(sdl_ctx *ctx);
+/* Change the stream later calls enqueue on. */
+sdl_status sdl_set_stream(sdl_ctx *ctx, void *stream);
+/* Text of the last error on this context ("" if none).  Owned by the context. */
+const char *sdl_last_error(const sdl_ctx *ctx);
+/* Bytes of device workspace the context currently holds. */
+size_t sdl_workspace_bytes(const sdl_ctx *ctx);
+
+/* OMP sparse coding (Sec. 1; stop rule of Sec. 3.2.2).  For every signal y_i:
+ * r = y_i, S = {}; while |S| < s and ||r||_2 > eps: add the unselected atom with
+ * the largest |d_j^T r| (lowest index on ties) unless that value is 0 or the atom
+ * lies numerically in span(D_S); x_S = argmin ||y_i - D_S x||.  Computed in the
+ * Batch-OMP form (progressive Cholesky of the Gram submatrix), after which the
+ * coefficients are recomputed on the support with one refinement step.
+ *   D      device, K atoms of length m (unit norm expected; not checked)
+ *   Y      device, n signals of length m
+ *   s      1 <= s <= min(m, K, 32);  eps >= 0 (0 = pure sparsity stop)
+ *   idx    device int32 [n][s] out;  val device [n][s] out;  nnz device int32 [n] out
+ *   resid2 device [n] out, ||y_i - D x_i||^2, may be NULL
+ * Limits: 1 <= m <= 256, 1 <= K <= 1024, n >= 0 (n = 0 launches nothing). */
+sdl_status sdl_omp(sdl_ctx *ctx, sdl_precision prec, const void *D, int m, int K,
+                   const void *Y, int64_t n, int s, double eps, int32_t *idx, void *val,
+                   int32_t *nnz, void *resid2);
+
+/* Batched OMP (Algorithm 1 step 2's coding stage): subset t = signals
+ * offsets[t] .. offsets[t+1]-1 of Y is coded against its own dictionary
+ * D + t*K*m.  offsets is HOST int64 [L+1], non-decreasing, offsets[0] = 0.
+ * Outputs are indexed by the global signal index as in sdl_omp. */
+sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int m, int K,
+                           const void *Y, const int64_t *offsets, int L, int s, double eps,
+                           int32_t *idx, void *val, int32_t *nnz, void *resid2);
+
+/* MOD dictionary update (Sec. 1) with renormalisation (Sec. 3.1):
+ * D_U = B_U A_UU^{-1} with A = X X^T, B = Y X^T accumulated in FP64 from the ELL
+ * codes, U = atoms used by at least one signal.  A_UU is factored by FP64
+ * Cholesky; on breakdown (a squared pivot <= 1e-12 of its diagonal) it is
+ * retried once with A_UU + lambda I, lambda = 1e-10 tr(A_UU)/|U|.  Used atoms are
+ * scaled to unit norm; unused atoms and atoms whose solution is zero keep their
+ * value from D.
+ *   Y device [n][m];  idx/val device [n][s] (val of the data type);
+ *   D device [K][m], in: previous dictionary, out: updated dictionary
+ *   usage device int32 [K] out (signals per atom), may be NULL. */
+sdl_status sdl_mod_update(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t n,
+                          const int32_t *idx, const void *val, int s, void *D, int K,
+                          int32_t *usage);
+
+/* Batched MOD: subset t uses signals offsets[t]..offsets[t+1]-1 and updates
+ * D + t*K*m.  offsets is HOST int64 [L+1].  usage device int32 [L][K] or NULL. */
+sdl_status sdl_mod_update_batched(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m,
+                                  const int64_t *offsets, int L, const int32_t *idx,
+                                  const void *val, int s, void *D, int K, int32_t *usage);
+
+/* Algorithm 1 step 1: Yp[:, i] = Y[:, perm[i]].  perm device int64 [N], a
+ * permutation of 0..N-1 drawn by the caller; consecutive ranges of Yp given by
+ * the caller's offsets are the random subsets. */
+sdl_status sdl_split(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t N,
+                     const int64_t *perm, void *Yp);
+
+/* Initial atoms (Sec. 3.1: atoms taken from training vectors): column c of the
+ * output is Y[:, pick[c]] scaled to unit norm, or, where pick[c] < 0, fill[c]
+ * scaled to unit norm.  pick device int64 [count]; fill device [count][m] or
+ * NULL (then every pick must be >= 0); D device [count][m] out. */
+sdl_status sdl_init_dict(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t nY,
+                         const int64_t *pick, const void *fill, int64_t count, void *D);
+
+/* Algorithm 1 step 2: every subset t (signals offsets[t]..offsets[t+1]-1 of Y,
+ * offsets HOST int64 [L+1], every subset non-empty) is trained independently
+ * for `iters` rounds of { X = OMP(D^(t), Y^(t), s1, eps); D^(t) = MOD(Y^(t), X) }.
+ *   D_local device [L][K1][m]: initial atoms in, trained atoms out
+ *   xfro    device double [L] out: ||X^(t)||_F of the last coding pass
+ *   rmse    device double [L][iters] out, ||Y^(t) - D^(t) X^(t)||_F / sqrt(m n_t)
+ *           of each coding pass; may be NULL. */
+sdl_status sdl_local_train(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m,
+                           const int64_t *offsets, int L, int K1, int s1, double eps, int iters,
+                           void *D_local, double *xfro, double *rmse);
+
+/* Algorithm 1 step 3: Ytilde = [ xfro[0] D^(0) ... xfro[L-1] D^(L-1) ] (m x K1 L);
+ * D starts from the unit-normalised columns Ytilde[:, pick[j]] and is trained on
+ * Ytilde for `iters` rounds with sparsity s2.
+ *   D_local device [L][K1][m];  xfro device double [L];  pick device int32 [K]
+ *   D device [K][m] out;  rmse device double [iters] out or NULL. */
+sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, const double *xfro,
+                     int m, int K1, int L, const int32_t *pick, int K, int s2, double eps,
+                     int iters, void *D, double *rmse);
+
+/* Table 1's MSE_train ingredients: out2 device double [2] receives
+ * ||Y - D X||_F^2 and ||Y||_F^2 for ELL codes X. */
+sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t n,
+                        const void *D, int K, const int32_t *idx, const void *val, int s,
+                        double *out2);
+
+/* Atom recovery (Sec. 3.1): count device int32 [1] receives the number of atoms
+ * of D0 (K0 x m) for which some atom of D (K x m) has |d0_i^T d_j| >= thresh. */
+sdl_status sdl_recovery(sdl_ctx *ctx, sdl_precision prec, const void *D0, int K0, const void *D,
+                        int K, int m, double thresh, int32_t *count);
+
+/* Instrumentation (the paper has no counterpart; it serves the roofline
+ * measurements): while enabled, every kernel launcher the context runs is
+ * bracketed by a pair of CUDA events recorded on the context's stream and
+ * accumulated per kernel name ("omp", "gram", "mod_accum", "chol_fp64",
+ * "solve_fp64", "normalise", ...).  Reading resolves the events, which
+ * synchronises on them.  Entry names are owned by the context and stay valid
+ * until the next sdl_profile_reset or sdl_destroy. */
+sdl_status sdl_profile_enable(sdl_ctx *ctx, int on);
+/* Drop the accumulated entries (pending events are resolved first). */
+sdl_status sdl_profile_reset(sdl_ctx *ctx);
+/* Number of distinct entries; -1 for a NULL context. */
+int sdl_profile_count(sdl_ctx *ctx);
+/* Entry i: kernel name, kernels launched, launcher calls, total milliseconds. */
+sdl_status sdl_profile_entry(sdl_ctx *ctx, int i, const char **name, int64_t *launches,
+                             int64_t *calls, double *total_ms);
+/* Kernels this context has launched since creation (profiling on or off). */
+int64_t sdl_launch_count(const sdl_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDL_H */

@@ -1,0 +1,652 @@
+// C ABI entry points: argument checks, workspace, and the host-side order of
+// kernels for OMP (Sec. 1), MOD (Sec. 1), and Algorithm 1 (split, local
+// training, scaled-stack merge).  Every kernel runs on the context's stream.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "sdl_internal.cuh"
+
+namespace sdl {
+
+sdl_status set_error(sdl_ctx *ctx, sdl_status st, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+sdl_status check_cuda(sdl_ctx *ctx, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return SDL_OK;
+  return set_error(ctx, SDL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void ws_reset(sdl_ctx *ctx) { ctx->ws.used = 0; }
+
+static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Make sure the workspace holds `bytes`; regrowth synchronises the stream.
+static sdl_status ws_reserve(sdl_ctx *ctx, size_t bytes) {
+  ws_reset(ctx);
+  if (bytes <= ctx->ws.cap) return SDL_OK;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return check_cuda(ctx, e, "workspace sync");
+  if (ctx->ws.base) cudaFree(ctx->ws.base);
+  ctx->ws.base = nullptr;
+  ctx->ws.cap = 0;
+  size_t want = bytes + bytes / 8;
+  e = cudaMalloc(&ctx->ws.base, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws.base = nullptr;
+    return set_error(ctx, SDL_ENOMEM, "cannot allocate " + std::to_string(want) + " bytes of workspace");
+  }
+  ctx->ws.cap = want;
+  return SDL_OK;
+}
+
+void *ws_alloc(sdl_ctx *ctx, size_t bytes) {
+  const size_t b = round256(bytes ? bytes : 1);
+  if (ctx->ws.used + b > ctx->ws.cap) return nullptr;
+  void *p = ctx->ws.base + ctx->ws.used;
+  ctx->ws.used += b;
+  return p;
+}
+
+TilePlan make_tiles(const int64_t *offsets, int L, int tile) {
+  TilePlan p;
+  p.tile_start.resize((size_t)L + 1);
+  int64_t acc = 0;
+  for (int t = 0; t < L; ++t) {
+    p.tile_start[t] = (int32_t)acc;
+    acc += (offsets[t + 1] - offsets[t] + tile - 1) / tile;
+  }
+  p.tile_start[L] = (int32_t)acc;
+  p.total_tiles = acc;
+  return p;
+}
+
+namespace {
+
+// Run one launcher; count its kernels and, when profiling is on, bracket it
+// with a pair of events on the context stream.
+template <class F>
+cudaError_t timed(sdl_ctx *ctx, const char *name, int nkernels, F &&launch) {
+  ctx->launches += nkernels;
+  if (!ctx->prof.on) return launch();
+  Prof &P = ctx->prof;
+  int entry = -1;
+  for (size_t q = 0; q < P.entries.size(); ++q)
+    if (P.entries[q].name == name) { entry = (int)q; break; }
+  if (entry < 0) {
+    P.entries.push_back(ProfEntry{name, 0, 0, 0.0});
+    entry = (int)P.entries.size() - 1;
+  }
+  cudaEvent_t ev[2];
+  for (int q = 0; q < 2; ++q) {
+    if (!P.pool.empty()) { ev[q] = P.pool.back(); P.pool.pop_back(); }
+    else if (cudaEventCreate(&ev[q]) != cudaSuccess) return cudaGetLastError();
+  }
+  cudaEventRecord(ev[0], ctx->stream);
+  cudaError_t e = launch();
+  cudaEventRecord(ev[1], ctx->stream);
+  P.entries[entry].launches += nkernels;
+  P.entries[entry].calls += 1;
+  P.pending.push_back(ProfPending{entry, ev[0], ev[1]});
+  return e;
+}
+
+// Resolve pending event pairs into per-kernel totals (synchronises on them).
+void prof_resolve(sdl_ctx *ctx) {
+  Prof &P = ctx->prof;
+  for (auto &q : P.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(q.e1) == cudaSuccess && cudaEventElapsedTime(&ms, q.e0, q.e1) == cudaSuccess)
+      P.entries[q.entry].ms += ms;
+    P.pool.push_back(q.e0);
+    P.pool.push_back(q.e1);
+  }
+  P.pending.clear();
+  cudaGetLastError();
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool aligned16(const void *p) { return p && ((uintptr_t)p & 15u) == 0; }
+
+#define SDL_REQUIRE(cond, msg) \
+  do {                         \
+    if (!(cond)) return set_error(ctx, SDL_EINVAL, msg); \
+  } while (0)
+
+#define SDL_CUDA(expr, what)                                    \
+  do {                                                          \
+    cudaError_t e_ = (expr);                                    \
+    if (e_ != cudaSuccess) return check_cuda(ctx, e_, what);    \
+  } while (0)
+
+sdl_status check_prec(sdl_ctx *ctx, sdl_precision prec) {
+  if (prec == SDL_PREC_F64 || prec == SDL_PREC_F32) return SDL_OK;
+  if (prec == SDL_PREC_BF16)
+    return set_error(ctx, SDL_EINVAL, "SDL_PREC_BF16 is not available in this build");
+  return set_error(ctx, SDL_EINVAL, "unknown precision");
+}
+
+sdl_status check_offsets(sdl_ctx *ctx, const int64_t *offsets, int L, bool nonempty) {
+  SDL_REQUIRE(offsets != nullptr, "offsets is NULL");
+  SDL_REQUIRE(L >= 1, "L must be >= 1");
+  SDL_REQUIRE(offsets[0] == 0, "offsets[0] must be 0");
+  for (int t = 0; t < L; ++t) {
+    SDL_REQUIRE(offsets[t + 1] >= offsets[t], "offsets must be non-decreasing");
+    if (nonempty) SDL_REQUIRE(offsets[t + 1] > offsets[t], "every subset must be non-empty");
+  }
+  SDL_REQUIRE(offsets[L] < ((int64_t)1 << 31), "at most 2^31-1 signals per call");
+  return SDL_OK;
+}
+
+// Device copy of offsets and of a tile plan (pageable host -> device).
+sdl_status upload_plan(sdl_ctx *ctx, const int64_t *offsets, int L, int tile, int64_t **d_off,
+                       int32_t **d_tiles, int64_t *total_tiles) {
+  TilePlan p = make_tiles(offsets, L, tile);
+  if (p.total_tiles >= ((int64_t)1 << 31)) return set_error(ctx, SDL_EINVAL, "too many tiles");
+  if (d_off) {
+    *d_off = static_cast<int64_t *>(ws_alloc(ctx, sizeof(int64_t) * (L + 1)));
+    SDL_CUDA(cudaMemcpyAsync(*d_off, offsets, sizeof(int64_t) * (L + 1), cudaMemcpyHostToDevice,
+                             ctx->stream), "upload offsets");
+  }
+  *d_tiles = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (L + 1)));
+  SDL_CUDA(cudaMemcpyAsync(*d_tiles, p.tile_start.data(), sizeof(int32_t) * (L + 1),
+                           cudaMemcpyHostToDevice, ctx->stream), "upload tiles");
+  *total_tiles = p.total_tiles;
+  // the pageable source vector dies here: make the copy complete first
+  SDL_CUDA(cudaStreamSynchronize(ctx->stream), "upload sync");
+  return SDL_OK;
+}
+
+size_t elem_size(sdl_precision prec) { return prec == SDL_PREC_F64 ? 8 : 4; }
+
+// Workspace bytes of one OMP pass over L dictionaries.
+size_t omp_ws_bytes(sdl_precision prec, int L, int K) {
+  return round256(elem_size(prec) * (size_t)L * K * K) + 2 * round256(sizeof(int64_t) * (L + 1));
+}
+
+size_t mod_ws_bytes(int L, int K, int m, int64_t n, int s) {
+  size_t b = 0;
+  b += round256(sizeof(int64_t) * (L + 1)) + round256(sizeof(int32_t) * (L + 1));
+  b += round256(sizeof(int32_t) * (size_t)L * K);          // cursor
+  b += round256(sizeof(int32_t) * (size_t)L * (K + 1));    // ptr
+  b += 2 * round256(sizeof(int32_t) * (size_t)(n * s + 1));  // lsig, lslot
+  b += 2 * round256(sizeof(double) * (size_t)L * K * K);   // A, Lf
+  b += round256(sizeof(double) * (size_t)L * K * m);       // B
+  b += round256(sizeof(int32_t) * (size_t)L);              // status
+  b += round256(sizeof(int32_t) * (size_t)L * K);          // usage scratch
+  b += round256(sizeof(int32_t) * 4);                      // status max
+  return b;
+}
+
+// Carve the MOD scratch (after ws_reserve); offsets/tiles are uploaded here.
+sdl_status mod_prepare(sdl_ctx *ctx, ModArgs &a, const int64_t *offsets_h, int L, int K, int m,
+                       int s, int32_t *usage, int32_t **status_max) {
+  int64_t *d_off = nullptr;
+  int32_t *d_tiles = nullptr;
+  int64_t tiles = 0;
+  sdl_status st = upload_plan(ctx, offsets_h, L, mod_tile_signals(), &d_off, &d_tiles, &tiles);
+  if (st != SDL_OK) return st;
+  const int64_t n = offsets_h[L];
+  a.offsets = d_off;
+  a.tile_start = d_tiles;
+  a.total_tiles = tiles;
+  a.n = n;
+  a.L = L; a.m = m; a.K = K; a.s = s;
+  a.cursor = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)L * K));
+  a.ptr = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)L * (K + 1)));
+  a.lsig = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)(n * s + 1)));
+  a.lslot = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)(n * s + 1)));
+  a.A = static_cast<double *>(ws_alloc(ctx, sizeof(double) * (size_t)L * K * K));
+  a.Lf = static_cast<double *>(ws_alloc(ctx, sizeof(double) * (size_t)L * K * K));
+  a.B = static_cast<double *>(ws_alloc(ctx, sizeof(double) * (size_t)L * K * m));
+  a.status = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)L));
+  int32_t *us = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)L * K));
+  a.usage = usage ? usage : us;
+  *status_max = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
+  if (!a.cursor || !a.ptr || !a.lsig || !a.lslot || !a.A || !a.Lf || !a.B || !a.status || !us ||
+      !*status_max)
+    return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  return SDL_OK;
+}
+
+// Read back the worst MOD status of the last launch (synchronises).
+sdl_status mod_status(sdl_ctx *ctx, const int32_t *status, int L, int32_t *d_max) {
+  SDL_CUDA(timed(ctx, "status", 1, [&] { return launch_status_max(status, L, d_max, ctx->stream); }),
+           "status reduce");
+  SDL_CUDA(cudaMemcpyAsync(ctx->h_status, d_max, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
+           "status read");
+  SDL_CUDA(cudaStreamSynchronize(ctx->stream), "status sync");
+  if (*ctx->h_status >= 2)
+    return set_error(ctx, SDL_ENOTPD,
+                     "MOD normal equations not positive definite after the ridge retry");
+  return SDL_OK;
+}
+
+sdl_status check_omp_shape(sdl_ctx *ctx, int m, int K, int s, double eps) {
+  SDL_REQUIRE(m >= 1 && m <= kMaxM, "m must be in [1, 256]");
+  SDL_REQUIRE(K >= 1 && K <= kMaxK, "K must be in [1, 1024]");
+  SDL_REQUIRE(s >= 1 && s <= kMaxS && s <= m && s <= K, "s must be in [1, min(m, K, 32)]");
+  SDL_REQUIRE(eps >= 0.0 && isfinite(eps), "eps must be finite and >= 0");
+  return SDL_OK;
+}
+
+// Workspace of one training loop (Sec. 1, standard approach) over L subsets.
+template <typename T>
+size_t train_ws_bytes(int L, int K, int m, int64_t n, int s, int iters) {
+  return omp_ws_bytes(sizeof(T) == 8 ? SDL_PREC_F64 : SDL_PREC_F32, L, K) + mod_ws_bytes(L, K, m, n, s) +
+         round256(sizeof(int32_t) * (size_t)n * s) + round256(sizeof(T) * (size_t)n * s) +
+         round256(sizeof(int32_t) * (size_t)n) + round256(sizeof(T) * (size_t)n) +
+         round256(sizeof(int32_t) * (size_t)(iters + 1)) + 4096;
+}
+
+// One training loop over L independent subsets; the workspace must already hold
+// train_ws_bytes().  Per round: Gram, OMP, per-subset RMSE (and ||X||_F on the
+// last round), MOD.  Synchronises once at the end to report a breakdown.
+template <typename T>
+sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, int L, int K, int s,
+                     double eps, int iters, T *D, double *xfro, double *rmse) {
+  const int64_t n = offsets[L];
+  sdl_status st;
+  OmpArgs oa{};
+  int64_t *d_off = nullptr;
+  int32_t *d_tiles = nullptr;
+  int64_t tiles = 0;
+  if ((st = upload_plan(ctx, offsets, L, omp_tile_signals(), &d_off, &d_tiles, &tiles)) != SDL_OK)
+    return st;
+  T *G = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)L * K * K));
+  int32_t *idx = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * s));
+  T *val = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)n * s));
+  int32_t *nnz = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n));
+  T *res2 = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)n));
+  int32_t *worst = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)(iters + 1)));
+  if (!G || !idx || !val || !nnz || !res2 || !worst)
+    return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  oa.D = D; oa.G = G; oa.Y = Y; oa.offsets = d_off; oa.tile_start = d_tiles; oa.total_tiles = tiles;
+  oa.L = L; oa.m = m; oa.K = K; oa.s = s; oa.eps = eps;
+  oa.idx = idx; oa.val = val; oa.nnz = nnz; oa.resid2 = res2;
+  ModArgs ma{};
+  int32_t *d_max = nullptr;
+  if ((st = mod_prepare(ctx, ma, offsets, L, K, m, s, nullptr, &d_max)) != SDL_OK) return st;
+  ma.Y = Y; ma.idx = idx; ma.val = val; ma.D = D;
+  SDL_CUDA(cudaMemsetAsync(ma.status, 0, sizeof(int32_t) * L, ctx->stream), "status clear");
+  SDL_CUDA(cudaMemsetAsync(worst, 0, sizeof(int32_t) * (iters + 1), ctx->stream), "status clear");
+  if (xfro) SDL_CUDA(cudaMemsetAsync(xfro, 0, sizeof(double) * L, ctx->stream), "xfro clear");
+  cudaStream_t sm = ctx->stream;
+  for (int it = 0; it < iters; ++it) {
+    SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
+    cudaError_t e = timed(ctx, "omp", 1, [&] { return launch_omp<T>(oa, ctx->num_sms, sm); });
+    if (e == cudaErrorInvalidConfiguration)
+      return set_error(ctx, SDL_EINVAL, "shape too large for the OMP kernel's shared memory");
+    SDL_CUDA(e, "omp");
+    SDL_CUDA(timed(ctx, "subset_stats", 1, [&] {
+               return launch_subset_stats<T>(res2, val, d_off, L, m, s, rmse ? rmse + it : nullptr, iters,
+                                             it == iters - 1 ? xfro : nullptr, sm);
+             }), "subset stats");
+    SDL_CUDA(timed(ctx, "mod_accum", ma.total_tiles > 0 ? 4 : 2,
+                   [&] { return launch_mod_accum<T>(ma, sm); }), "mod accumulate");
+    SDL_CUDA(timed(ctx, "chol_fp64", 1, [&] { return launch_mod_chol(ma, sm); }), "cholesky");
+    SDL_CUDA(timed(ctx, "solve_fp64", 1, [&] { return launch_mod_solve(ma, ctx->num_sms, sm); }), "solve");
+    SDL_CUDA(timed(ctx, "normalise", 1, [&] { return launch_mod_normalise<T>(ma, sm); }), "normalise");
+    SDL_CUDA(timed(ctx, "status", 1, [&] { return launch_status_max(ma.status, L, worst + it, sm); }),
+             "status");
+  }
+  if (iters > 0) return mod_status(ctx, worst, iters, d_max);
+  return SDL_OK;
+}
+
+}  // namespace
+}  // namespace sdl
+
+using namespace sdl;
+
+extern "C" {
+
+sdl_status sdl_create(sdl_ctx **out, int device, void *stream) {
+  if (!out) return SDL_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return SDL_EINVAL;
+  }
+  sdl_ctx *ctx = new sdl_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  DeviceGuard g(device);
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return SDL_ECUDA;
+  }
+  *out = ctx;
+  return SDL_OK;
+}
+
+sdl_status sdl_destroy(sdl_ctx *ctx) {
+  if (!ctx) return SDL_OK;
+  {
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    prof_resolve(ctx);
+    for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    if (ctx->ws.base) cudaFree(ctx->ws.base);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  }
+  delete ctx;
+  return SDL_OK;
+}
+
+sdl_status sdl_set_stream(sdl_ctx *ctx, void *stream) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return SDL_OK;
+}
+
+const char *sdl_last_error(const sdl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t sdl_workspace_bytes(const sdl_ctx *ctx) { return ctx ? ctx->ws.cap : 0; }
+
+sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int m, int K, const void *Y,
+                           const int64_t *offsets, int L, int s, double eps, int32_t *idx, void *val,
+                           int32_t *nnz, void *resid2) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  if ((st = check_omp_shape(ctx, m, K, s, eps)) != SDL_OK) return st;
+  if ((st = check_offsets(ctx, offsets, L, false)) != SDL_OK) return st;
+  const int64_t n = offsets[L];
+  if (n == 0) return SDL_OK;
+  SDL_REQUIRE(aligned16(D) && aligned16(Y) && aligned16(idx) && aligned16(val) && aligned16(nnz) &&
+                  (resid2 == nullptr || aligned16(resid2)),
+              "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  if ((st = ws_reserve(ctx, omp_ws_bytes(prec, L, K) + 1024)) != SDL_OK) return st;
+  OmpArgs a{};
+  int64_t *d_off = nullptr;
+  int32_t *d_tiles = nullptr;
+  int64_t tiles = 0;
+  if ((st = upload_plan(ctx, offsets, L, omp_tile_signals(), &d_off, &d_tiles, &tiles)) != SDL_OK)
+    return st;
+  void *G = ws_alloc(ctx, elem_size(prec) * (size_t)L * K * K);
+  if (!G) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  a.D = D; a.G = G; a.Y = Y; a.offsets = d_off; a.tile_start = d_tiles; a.total_tiles = tiles;
+  a.L = L; a.m = m; a.K = K; a.s = s; a.eps = eps;
+  a.idx = idx; a.val = val; a.nnz = nnz; a.resid2 = resid2;
+  if (prec == SDL_PREC_F64) {
+    SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<double>(static_cast<const double *>(D), m, K, L, static_cast<double *>(G),
+                                 ctx->stream); }), "gram");
+    cudaError_t e = timed(ctx, "omp", 1, [&] { return launch_omp<double>(a, ctx->num_sms, ctx->stream); });
+    if (e == cudaErrorInvalidConfiguration)
+      return set_error(ctx, SDL_EINVAL, "shape too large for the FP64 OMP kernel's shared memory");
+    SDL_CUDA(e, "omp");
+  } else {
+    SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<float>(static_cast<const float *>(D), m, K, L, static_cast<float *>(G),
+                                ctx->stream); }), "gram");
+    cudaError_t e = timed(ctx, "omp", 1, [&] { return launch_omp<float>(a, ctx->num_sms, ctx->stream); });
+    if (e == cudaErrorInvalidConfiguration)
+      return set_error(ctx, SDL_EINVAL, "shape too large for the OMP kernel's shared memory");
+    SDL_CUDA(e, "omp");
+  }
+  return SDL_OK;
+}
+
+sdl_status sdl_omp(sdl_ctx *ctx, sdl_precision prec, const void *D, int m, int K, const void *Y, int64_t n,
+                   int s, double eps, int32_t *idx, void *val, int32_t *nnz, void *resid2) {
+  if (!ctx) return SDL_EINVAL;
+  if (n < 0) return set_error(ctx, SDL_EINVAL, "n must be >= 0");
+  const int64_t offsets[2] = {0, n};
+  return sdl_omp_batched(ctx, prec, D, m, K, Y, offsets, 1, s, eps, idx, val, nnz, resid2);
+}
+
+sdl_status sdl_mod_update_batched(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m,
+                                  const int64_t *offsets, int L, const int32_t *idx, const void *val,
+                                  int s, void *D, int K, int32_t *usage) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  SDL_REQUIRE(m >= 1 && m <= kMaxM, "m must be in [1, 256]");
+  SDL_REQUIRE(K >= 1 && K <= kMaxK, "K must be in [1, 1024]");
+  SDL_REQUIRE(s >= 1 && s <= kMaxS, "s must be in [1, 32]");
+  if ((st = check_offsets(ctx, offsets, L, false)) != SDL_OK) return st;
+  const int64_t n = offsets[L];
+  SDL_REQUIRE(aligned16(D) && (n == 0 || (aligned16(Y) && aligned16(idx) && aligned16(val))) &&
+                  (usage == nullptr || aligned16(usage)),
+              "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  if ((st = ws_reserve(ctx, mod_ws_bytes(L, K, m, n, s) + 1024)) != SDL_OK) return st;
+  ModArgs a{};
+  int32_t *d_max = nullptr;
+  if ((st = mod_prepare(ctx, a, offsets, L, K, m, s, usage, &d_max)) != SDL_OK) return st;
+  a.Y = Y; a.idx = idx; a.val = val; a.D = D;
+  SDL_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int32_t) * L, ctx->stream), "status clear");
+  cudaStream_t sm = ctx->stream;
+  const int nacc = a.total_tiles > 0 ? 4 : 2;
+  if (prec == SDL_PREC_F64)
+    SDL_CUDA(timed(ctx, "mod_accum", nacc, [&] { return launch_mod_accum<double>(a, sm); }), "mod accumulate");
+  else
+    SDL_CUDA(timed(ctx, "mod_accum", nacc, [&] { return launch_mod_accum<float>(a, sm); }), "mod accumulate");
+  SDL_CUDA(timed(ctx, "chol_fp64", 1, [&] { return launch_mod_chol(a, sm); }), "cholesky");
+  SDL_CUDA(timed(ctx, "solve_fp64", 1, [&] { return launch_mod_solve(a, ctx->num_sms, sm); }), "solve");
+  if (prec == SDL_PREC_F64)
+    SDL_CUDA(timed(ctx, "normalise", 1, [&] { return launch_mod_normalise<double>(a, sm); }), "normalise");
+  else
+    SDL_CUDA(timed(ctx, "normalise", 1, [&] { return launch_mod_normalise<float>(a, sm); }), "normalise");
+  return mod_status(ctx, a.status, L, d_max);
+}
+
+sdl_status sdl_mod_update(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t n,
+                          const int32_t *idx, const void *val, int s, void *D, int K, int32_t *usage) {
+  if (!ctx) return SDL_EINVAL;
+  if (n < 0) return set_error(ctx, SDL_EINVAL, "n must be >= 0");
+  const int64_t offsets[2] = {0, n};
+  return sdl_mod_update_batched(ctx, prec, Y, m, offsets, 1, idx, val, s, D, K, usage);
+}
+
+sdl_status sdl_split(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t N, const int64_t *perm,
+                     void *Yp) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  SDL_REQUIRE(m >= 1 && N >= 0, "m must be >= 1 and N >= 0");
+  if (N == 0) return SDL_OK;
+  SDL_REQUIRE(aligned16(Y) && aligned16(perm) && aligned16(Yp) && Y != Yp,
+              "device pointers must be non-NULL, 16-byte aligned, and Yp must not alias Y");
+  DeviceGuard g(ctx->device);
+  if (prec == SDL_PREC_F64)
+    SDL_CUDA(timed(ctx, "split", 1, [&] { return launch_split<double>(static_cast<const double *>(Y), m, N, perm, static_cast<double *>(Yp),
+                                  ctx->stream); }), "split");
+  else
+    SDL_CUDA(timed(ctx, "split", 1, [&] { return launch_split<float>(static_cast<const float *>(Y), m, N, perm, static_cast<float *>(Yp),
+                                 ctx->stream); }), "split");
+  return SDL_OK;
+}
+
+sdl_status sdl_init_dict(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t nY,
+                         const int64_t *pick, const void *fill, int64_t count, void *D) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  SDL_REQUIRE(m >= 1 && count >= 0 && nY >= 0, "bad sizes");
+  if (count == 0) return SDL_OK;
+  SDL_REQUIRE(aligned16(pick) && aligned16(D) && (nY == 0 || aligned16(Y)) &&
+                  (fill == nullptr || aligned16(fill)),
+              "device pointers must be non-NULL and 16-byte aligned");
+  (void)nY;
+  DeviceGuard g(ctx->device);
+  if (prec == SDL_PREC_F64)
+    SDL_CUDA(timed(ctx, "init_dict", 1, [&] { return launch_init_dict<double>(static_cast<const double *>(Y), m, pick,
+                                      static_cast<const double *>(fill), count, static_cast<double *>(D),
+                                      ctx->stream); }), "init");
+  else
+    SDL_CUDA(timed(ctx, "init_dict", 1, [&] { return launch_init_dict<float>(static_cast<const float *>(Y), m, pick, static_cast<const float *>(fill),
+                                     count, static_cast<float *>(D), ctx->stream); }), "init");
+  return SDL_OK;
+}
+
+sdl_status sdl_local_train(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, const int64_t *offsets,
+                           int L, int K1, int s1, double eps, int iters, void *D_local, double *xfro,
+                           double *rmse) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  if ((st = check_omp_shape(ctx, m, K1, s1, eps)) != SDL_OK) return st;
+  if ((st = check_offsets(ctx, offsets, L, true)) != SDL_OK) return st;
+  SDL_REQUIRE(iters >= 0, "iters must be >= 0");
+  SDL_REQUIRE(aligned16(Y) && aligned16(D_local) && aligned16(xfro) && (rmse == nullptr || aligned16(rmse)),
+              "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  const int64_t n = offsets[L];
+  if (prec == SDL_PREC_F64) {
+    if ((st = ws_reserve(ctx, train_ws_bytes<double>(L, K1, m, n, s1, iters))) != SDL_OK) return st;
+    return train_run<double>(ctx, static_cast<const double *>(Y), m, offsets, L, K1, s1, eps, iters,
+                             static_cast<double *>(D_local), xfro, rmse);
+  }
+  if ((st = ws_reserve(ctx, train_ws_bytes<float>(L, K1, m, n, s1, iters))) != SDL_OK) return st;
+  return train_run<float>(ctx, static_cast<const float *>(Y), m, offsets, L, K1, s1, eps, iters,
+                          static_cast<float *>(D_local), xfro, rmse);
+}
+
+sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, const double *xfro, int m,
+                     int K1, int L, const int32_t *pick, int K, int s2, double eps, int iters, void *D,
+                     double *rmse) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  if ((st = check_omp_shape(ctx, m, K, s2, eps)) != SDL_OK) return st;
+  SDL_REQUIRE(K1 >= 1 && L >= 1 && (int64_t)K1 * L < ((int64_t)1 << 31), "bad K1 or L");
+  SDL_REQUIRE(iters >= 0, "iters must be >= 0");
+  SDL_REQUIRE(aligned16(D_local) && aligned16(xfro) && aligned16(pick) && aligned16(D) &&
+                  (rmse == nullptr || aligned16(rmse)),
+              "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  const int64_t nt = (int64_t)K1 * L;
+  const int64_t offsets[2] = {0, nt};
+  const size_t es = elem_size(prec);
+  const size_t train_b = prec == SDL_PREC_F64 ? train_ws_bytes<double>(1, K, m, nt, s2, iters)
+                                              : train_ws_bytes<float>(1, K, m, nt, s2, iters);
+  if ((st = ws_reserve(ctx, round256(es * (size_t)nt * m) + round256(sizeof(double)) + train_b)) != SDL_OK)
+    return st;
+  void *Yt = ws_alloc(ctx, es * (size_t)nt * m);       // Ytilde, carved before the training scratch
+  double *xf_unused = static_cast<double *>(ws_alloc(ctx, sizeof(double)));
+  if (!Yt || !xf_unused) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  if (prec == SDL_PREC_F64) {
+    SDL_CUDA(timed(ctx, "stack", 1, [&] { return launch_stack<double>(static_cast<const double *>(D_local), xfro, m, K1, L,
+                                  static_cast<double *>(Yt), ctx->stream); }), "stack");
+    SDL_CUDA(timed(ctx, "pick_init", 1, [&] { return launch_pick_init<double>(static_cast<const double *>(Yt), m, pick, K, static_cast<double *>(D),
+                                      ctx->stream); }), "merge init");
+    return train_run<double>(ctx, static_cast<const double *>(Yt), m, offsets, 1, K, s2, eps, iters,
+                             static_cast<double *>(D), xf_unused, rmse);
+  }
+  SDL_CUDA(timed(ctx, "stack", 1, [&] { return launch_stack<float>(static_cast<const float *>(D_local), xfro, m, K1, L, static_cast<float *>(Yt),
+                               ctx->stream); }), "stack");
+  SDL_CUDA(timed(ctx, "pick_init", 1, [&] { return launch_pick_init<float>(static_cast<const float *>(Yt), m, pick, K, static_cast<float *>(D),
+                                   ctx->stream); }), "merge init");
+  return train_run<float>(ctx, static_cast<const float *>(Yt), m, offsets, 1, K, s2, eps, iters,
+                          static_cast<float *>(D), xf_unused, rmse);
+}
+
+sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t n, const void *D,
+                        int K, const int32_t *idx, const void *val, int s, double *out2) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  SDL_REQUIRE(m >= 1 && n >= 0 && K >= 1 && s >= 1, "bad sizes");
+  SDL_REQUIRE(aligned16(out2) && aligned16(D) && (n == 0 || (aligned16(Y) && aligned16(idx) && aligned16(val))),
+              "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  if (prec == SDL_PREC_F64)
+    SDL_CUDA(timed(ctx, "residual", 1, [&] { return launch_residual<double>(static_cast<const double *>(Y), m, n, static_cast<const double *>(D), idx,
+                                     static_cast<const double *>(val), s, out2, ctx->stream); }), "residual");
+  else
+    SDL_CUDA(timed(ctx, "residual", 1, [&] { return launch_residual<float>(static_cast<const float *>(Y), m, n, static_cast<const float *>(D), idx,
+                                    static_cast<const float *>(val), s, out2, ctx->stream); }), "residual");
+  return SDL_OK;
+}
+
+sdl_status sdl_recovery(sdl_ctx *ctx, sdl_precision prec, const void *D0, int K0, const void *D, int K, int m,
+                        double thresh, int32_t *count) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  SDL_REQUIRE(K0 >= 1 && K >= 1 && m >= 1, "bad sizes");
+  SDL_REQUIRE(aligned16(D0) && aligned16(D) && aligned16(count),
+              "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  if (prec == SDL_PREC_F64)
+    SDL_CUDA(timed(ctx, "recovery", 1, [&] { return launch_recovery<double>(static_cast<const double *>(D0), K0, static_cast<const double *>(D), K, m,
+                                     thresh, count, ctx->stream); }), "recovery");
+  else
+    SDL_CUDA(timed(ctx, "recovery", 1, [&] { return launch_recovery<float>(static_cast<const float *>(D0), K0, static_cast<const float *>(D), K, m,
+                                    thresh, count, ctx->stream); }), "recovery");
+  return SDL_OK;
+}
+
+sdl_status sdl_profile_enable(sdl_ctx *ctx, int on) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->prof.on = on != 0;
+  return SDL_OK;
+}
+
+sdl_status sdl_profile_reset(sdl_ctx *ctx) {
+  if (!ctx) return SDL_EINVAL;
+  DeviceGuard g(ctx->device);
+  prof_resolve(ctx);
+  ctx->prof.entries.clear();
+  return SDL_OK;
+}
+
+int sdl_profile_count(sdl_ctx *ctx) {
+  if (!ctx) return -1;
+  DeviceGuard g(ctx->device);
+  prof_resolve(ctx);
+  return (int)ctx->prof.entries.size();
+}
+
+sdl_status sdl_profile_entry(sdl_ctx *ctx, int i, const char **name, int64_t *launches, int64_t *calls,
+                             double *total_ms) {
+  if (!ctx || i < 0 || !name || !launches || !calls || !total_ms) return SDL_EINVAL;
+  DeviceGuard g(ctx->device);
+  prof_resolve(ctx);
+  if (i >= (int)ctx->prof.entries.size()) return SDL_EINVAL;
+  const ProfEntry &e = ctx->prof.entries[i];
+  *name = e.name.c_str();
+  *launches = e.launches;
+  *calls = e.calls;
+  *total_ms = e.ms;
+  return SDL_OK;
+}
+
+int64_t sdl_launch_count(const sdl_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sdl.h"
+
+namespace sdl {
+
+// Upper limits of the compiled kernels.
+constexpr int kMaxM = 256;      // signal length
+constexpr int kMaxK = 1024;     // atoms per dictionary
+constexpr int kMaxS = 32;       // sparsity (one lane per selected atom)
+
+// Pivot floors: an OMP atom whose squared distance to span(D_S) is below this
+// fraction of its squared norm is not added; a MOD normal-equation pivot below
+// this fraction of its diagonal counts as a breakdown.
+constexpr double kOmpPivotRelF64 = 1e-10;
+constexpr float kOmpPivotRelF32 = 1e-6f;
+constexpr double kModPivotRel = 1e-12;
+constexpr double kModRidge = 1e-10;
+
+// Device workspace: one cudaMalloc'd block, carved by a bump allocator that is
+// reset at the start of every public call.
+struct Workspace {
+  char *base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  size_t want = 0;     // bytes the current call asked for (to size a regrowth)
+};
+
+// Per-kernel instrumentation: CUDA-event pairs on the context stream around
+// each launcher, resolved lazily when read.
+struct ProfEntry {
+  std::string name;
+  int64_t launches = 0;
+  int64_t calls = 0;
+  double ms = 0.0;
+};
+struct ProfPending {
+  int entry;
+  cudaEvent_t e0, e1;
+};
+struct Prof {
+  bool on = false;
+  std::vector<ProfEntry> entries;
+  std::vector<ProfPending> pending;
+  std::vector<cudaEvent_t> pool;
+};
+
+}  // namespace sdl
+
+struct sdl_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  sdl::Workspace ws;
+  int num_sms = 0;
+  int32_t *h_status = nullptr;   // pinned host word for device status read-back
+  int64_t launches = 0;          // kernels launched by this context
+  sdl::Prof prof;
+};
+
+namespace sdl {
+
+// --- error plumbing ------------------------------------------------------------
+sdl_status set_error(sdl_ctx *ctx, sdl_status st, const std::string &msg);
+sdl_status check_cuda(sdl_ctx *ctx, cudaError_t e, const char *what);
+
+// Reserve `bytes` (256-byte aligned) from the workspace; grows it if needed.
+// Returns nullptr and sets ctx->err on failure.
+void *ws_alloc(sdl_ctx *ctx, size_t bytes);
+void ws_reset(sdl_ctx *ctx);
+
+// Tiles of a batched signal range: tile_start[t] = first tile of subset t.
+struct TilePlan {
+  std::vector<int32_t> tile_start;   // L+1 entries
+  int64_t total_tiles = 0;
+};
+TilePlan make_tiles(const int64_t *offsets, int L, int tile);
+
+// --- kernel launchers (templated on the data type T = float or double) ------
+template <typename T>
+cudaError_t launch_gram(const T *D, int m, int K, int L, T *G, cudaStream_t st);
+
+struct OmpArgs {
+  const void *D;          // [L][K][m]
+  const void *G;          // [L][K][K]
+  const void *Y;          // [n][m]
+  const int64_t *offsets; // device [L+1]
+  const int32_t *tile_start;  // device [L+1]
+  int64_t total_tiles;
+  int L, m, K, s;
+  double eps;
+  int32_t *idx;
+  void *val;
+  int32_t *nnz;
+  void *resid2;           // may be null
+};
+template <typename T>
+cudaError_t launch_omp(const OmpArgs &a, int num_sms, cudaStream_t st);
+int omp_tile_signals();
+
+struct ModArgs {
+  const void *Y;          // [n][m]
+  const int64_t *offsets; // device [L+1]
+  const int32_t *tile_start;  // device [L+1] (tiles of kModTile signals)
+  int64_t total_tiles;
+  int64_t n;
+  int L, m, K, s;
+  const int32_t *idx;
+  const void *val;
+  void *D;                // [L][K][m] in/out
+  int32_t *usage;         // [L][K] out (always provided internally)
+  // FP64 scratch
+  int32_t *cursor;        // [L][K]
+  int32_t *ptr;           // [L][K+1]
+  int32_t *lsig;          // [n*s]
+  int32_t *lslot;         // [n*s]
+  double *A;              // [L][K][K]
+  double *Lf;             // [L][K][K]
+  double *B;              // [L][K][m]
+  int32_t *status;        // [L] out: 0 ok, 1 ridge used, 2 breakdown
+};
+// MOD in four launchers: accumulation (usage count, scan, CSC fill, A/B
+// accumulation: 4 kernels), FP64 Cholesky, FP64 solve, renormalisation.
+template <typename T>
+cudaError_t launch_mod_accum(const ModArgs &a, cudaStream_t st);
+cudaError_t launch_mod_chol(const ModArgs &a, cudaStream_t st);
+cudaError_t launch_mod_solve(const ModArgs &a, int num_sms, cudaStream_t st);
+template <typename T>
+cudaError_t launch_mod_normalise(const ModArgs &a, cudaStream_t st);
+int mod_tile_signals();
+
+template <typename T>
+cudaError_t launch_split(const T *Y, int m, int64_t N, const int64_t *perm, T *Yp, cudaStream_t st);
+template <typename T>
+cudaError_t launch_init_dict(const T *Y, int m, const int64_t *pick, const T *fill, int64_t count,
+                             T *D, cudaStream_t st);
+template <typename T>
+cudaError_t launch_stack(const T *Dloc, const double *xfro, int m, int K1, int L, T *Yt,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t launch_pick_init(const T *Yt, int m, const int32_t *pick, int K, T *D, cudaStream_t st);
+// Per-subset sums: rmse[t] = sqrt(sum resid2 / (m n_t)); xfro[t] = sqrt(sum val^2).
+template <typename T>
+cudaError_t launch_subset_stats(const T *resid2, const T *val, const int64_t *offsets, int L, int m,
+                                int s, double *rmse_out, int64_t rmse_stride, double *xfro_out,
+                                cudaStream_t st);
+template <typename T>
+cudaError_t launch_residual(const T *Y, int m, int64_t n, const T *D, const int32_t *idx,
+                            const T *val, int s, double *out2, cudaStream_t st);
+template <typename T>
+cudaError_t launch_recovery(const T *D0, int K0, const T *D, int K, int m, double thresh,
+                            int32_t *count, cudaStream_t st);
+cudaError_t launch_status_max(const int32_t *status, int L, int32_t *out, cudaStream_t st);
+
+}  // namespace sdl

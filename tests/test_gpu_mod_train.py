@@ -1,0 +1,194 @@
+"""GPU MOD update, local training and merge through the C ABI against the oracle.
+
+Tolerances: MOD atoms within 2e-5 absolute (unit atoms; FP64 normal equations,
+FP32 output) on the FP32 path and 1e-10 on the FP64 path; the per-iteration
+training RMSE within 1e-3 relative of the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1403_4781_gb300 as sdl
+import sdl_inputs as si
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _codes(rng, n, K, s, unused_from=None):
+    hi = K if unused_from is None else unused_from
+    idx = np.stack([rng.choice(hi, s, replace=False) for _ in range(n)]).astype(np.int32)
+    val = rng.standard_normal((n, s))
+    return idx, val
+
+
+@pytest.mark.parametrize("dtype,atol", [(np.float32, 2e-5), (np.float64, 1e-10)])
+def test_mod_update_matches_oracle(dtype, atol):
+    rng = np.random.default_rng(200)
+    m, K, n, s = 64, 256, 4000, 6
+    Y = rng.standard_normal((n, m)).astype(dtype)
+    idx, val = _codes(rng, n, K, s, unused_from=250)      # atoms 250..255 unused
+    idx[::7, -1] = -1                                     # ragged nnz
+    val[::7, -1] = 0
+    val = val.astype(dtype)
+    D0 = si.unit_gaussian_atoms(rng, m, K).astype(dtype)
+    Dg = _t(D0.copy())
+    usage = sdl.mod_update(_t(Y), _t(idx), _t(val), Dg)
+    Do, uo, ridge, st = oracle.mod(Y.astype(np.float64), idx, val.astype(np.float64),
+                                   D0.astype(np.float64), True)
+    assert (usage.cpu().numpy() == uo).all()
+    Dgn = Dg.cpu().numpy()
+    np.testing.assert_array_equal(Dgn[250:], D0[250:])    # unused atoms: bit-exact
+    np.testing.assert_allclose(Dgn, Do, rtol=0, atol=atol)
+
+
+def test_mod_ridge_path_matches_oracle():
+    rng = np.random.default_rng(201)
+    m, K, n = 6, 5, 50
+    Y = rng.standard_normal((n, m))
+    third = rng.integers(2, K, size=n)
+    idx = np.stack([np.zeros(n), np.ones(n), third], axis=1).astype(np.int32)
+    c = rng.standard_normal(n)
+    val = np.stack([c, c, rng.standard_normal(n)], axis=1)
+    Dprev = si.unit_gaussian_atoms(rng, m, K)
+    Dg = _t(Dprev.copy())
+    sdl.mod_update(_t(Y), _t(idx), _t(val), Dg)
+    Do, _, ridge, st = oracle.mod(Y, idx, val, Dprev, True)
+    assert ridge and st == 0
+    np.testing.assert_allclose(Dg.cpu().numpy(), Do, atol=1e-5)
+
+
+def test_mod_batched_uneven():
+    rng = np.random.default_rng(202)
+    m, K, s = 32, 64, 3
+    sizes = [500, 64, 1200]
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = offsets[-1]
+    Y = rng.standard_normal((n, m)).astype(np.float32)
+    idx, val = _codes(rng, n, K, s)
+    val = val.astype(np.float32)
+    D0 = np.stack([si.unit_gaussian_atoms(rng, m, K) for _ in sizes]).astype(np.float32)
+    Dg = _t(D0.copy())
+    sdl.mod_update_batched(_t(Y), offsets, _t(idx), _t(val), Dg)
+    Dgn = Dg.cpu().numpy()
+    for t in range(len(sizes)):
+        a, b = offsets[t], offsets[t + 1]
+        Do, *_ = oracle.mod(Y[a:b].astype(np.float64), idx[a:b], val[a:b].astype(np.float64),
+                            D0[t].astype(np.float64), True)
+        np.testing.assert_allclose(Dgn[t], Do, atol=2e-5)
+
+
+def _local(p, iters, prec_dtype=np.float32):
+    Yp = p.Y[p.perm]
+    Dinit = np.stack([Yp[q] / np.linalg.norm(Yp[q], axis=1, keepdims=True) for q in p.picks])
+    Dg = _t(Dinit.astype(prec_dtype))
+    xfro, rmse = sdl.local_train(_t(Yp.astype(prec_dtype)), p.offsets, Dg, p.s1, iters)
+    torch.cuda.synchronize()
+    return Yp, Dinit.astype(prec_dtype), Dg, xfro, rmse
+
+
+def test_local_train_uneven_subsets_fp32():
+    p = si.split_merge_problem("t", 16, 32, 4, 2, 2, 32, [300, 900, 450, 33 * 2, 1000], 6, 6, 0.02,
+                               np.random.default_rng(203))
+    Yp, Dinit, Dg, xfro, rmse = _local(p, 6)
+    orc = oracle.local_train(Yp.astype(np.float64), p.offsets, Dinit.astype(np.float64), p.s1, 6)
+    rel = np.abs(rmse.cpu().numpy() - orc["rmse"]) / orc["rmse"]
+    assert rel.max() < 1e-3, rel
+    np.testing.assert_allclose(xfro.cpu().numpy(), orc["xfro"], rtol=1e-3)
+
+
+def test_standard_training_fp64_config0():
+    """Standard MOD/OMP in FP64 (m=64, K=128, s=5, N=10,000, 10 iterations)."""
+    c = si.config0()
+    Y, D0 = c["Y"], c["D0"]
+    Dinit = Y[c["pick"]] / np.linalg.norm(Y[c["pick"]], axis=1, keepdims=True)
+    Dg = _t(Dinit[None].copy())
+    xfro, rmse = sdl.local_train(_t(Y), [0, len(Y)], Dg, c["s"], c["iters"])
+    orc = oracle.train(Y, Dinit, c["s"], c["iters"])
+    rel = np.abs(rmse.cpu().numpy()[0] - orc["rmse"]) / orc["rmse"]
+    assert rel.max() < 1e-3, rel
+    rec_gpu = int(sdl.recovery(_t(D0), Dg[0]).cpu()[0])
+    assert rec_gpu == oracle.recovery(D0, orc["D"])
+
+
+def test_merge_matches_oracle():
+    rng = np.random.default_rng(204)
+    L, K1, m, K = 6, 40, 16, 32
+    Dloc = np.stack([si.unit_gaussian_atoms(rng, m, K1) for _ in range(L)]).astype(np.float32)
+    xfro = rng.uniform(5, 20, size=L)
+    pick = si.merge_pick(rng, L * K1, K)
+    D, rmse = sdl.merge(_t(Dloc), _t(xfro), _t(pick), K, 3, 8)
+    orc = oracle.merge(Dloc.astype(np.float64), xfro, pick, K, 3, 8)
+    rel = np.abs(rmse.cpu().numpy() - orc["rmse"]) / orc["rmse"]
+    assert rel.max() < 1e-3, rel
+
+
+def _full_local():
+    p = si.config1()
+    Y = _t(p.Y)
+    Yp = sdl.split(Y, _t(p.perm))
+    Dl = sdl.init_dict(Yp, _t(p.picks.reshape(-1))).reshape(p.L, p.K1, p.m)
+    Dinit = Dl.cpu().numpy().astype(np.float64)
+    xfro, rmse = sdl.local_train(Yp, p.offsets, Dl, p.s1, p.iters_local)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Yp.cpu().numpy(), p.Y[p.perm])
+    return p, Dinit, Dl, xfro, rmse
+
+
+def test_full_size_local_training_sampled_subsets():
+    """The full split-and-merge FP32 workload's local phase (N=200,000, m=64,
+    K1=256, L=100 x 2,000, s1=2, 20 iterations, one batched launch per kernel):
+    three sampled subsets' free-running RMSE traces against the oracle."""
+    p, Dinit, Dl, xfro, rmse = _full_local()
+    Ypn = p.Y[p.perm].astype(np.float64)
+    for t in (0, 37, 99):
+        a, b = p.offsets[t], p.offsets[t + 1]
+        o = oracle.train(Ypn[a:b], Dinit[t], p.s1, p.iters_local)
+        rel = np.abs(rmse.cpu().numpy()[t] - o["rmse"]) / o["rmse"]
+        assert rel.max() < 1e-3, (t, rel)
+        assert abs(xfro.cpu().numpy()[t] - o["xfro"]) < 1e-3 * o["xfro"]
+
+
+def test_full_size_merge_per_iteration():
+    """Merge of the 25,600 scaled local atoms (K=256, s2=3, 20 iterations).
+    Each iteration starts the GPU and the oracle from the same dictionary (the
+    GPU's current one) and compares the iteration's RMSE (1e-3 relative) and
+    updated atoms.  Free-running FP32 and FP64 trajectories separate at the rate
+    the alternating minimisation amplifies rounding differences, so they are
+    compared only at the end, loosely (the FP64 path is compared free-running in
+    test_full_size_merge_fp64_free_running)."""
+    p, Dinit, Dl, xfro, _ = _full_local()
+    Dln, xf = Dl.cpu().numpy().astype(np.float64), xfro.cpu().numpy()
+    Yt = (Dln * xf[:, None, None]).reshape(-1, p.m).astype(np.float32)
+    D = Yt[p.mpick].astype(np.float64)
+    D = (D / np.linalg.norm(D, axis=1, keepdims=True)).astype(np.float32)
+    Ytg = _t(Yt)
+    for it in range(p.iters_merge):
+        Dg = _t(D[None].copy())
+        _, rg = sdl.local_train(Ytg, [0, len(Yt)], Dg, p.s2, 1)
+        o = oracle.train(Yt.astype(np.float64), D.astype(np.float64), p.s2, 1)
+        rel = abs(rg.cpu().numpy()[0, 0] - o["rmse"][0]) / o["rmse"][0]
+        assert rel < 1e-3, (it, rel)
+        Dn = Dg.cpu().numpy()[0]
+        assert np.abs(Dn - o["D"]).max() < 5e-3, it
+        D = Dn
+    Dm, rm = sdl.merge(Dl, xfro, _t(p.mpick), p.K, p.s2, p.iters_merge)
+    orc = oracle.merge(Dln, xf, p.mpick, p.K, p.s2, p.iters_merge)
+    assert abs(rm.cpu().numpy()[-1] - orc["rmse"][-1]) < 0.05 * orc["rmse"][-1]
+
+
+def test_full_size_merge_fp64_free_running():
+    """The same merge run by the FP64 path follows the oracle's free-running
+    trajectory to rounding level at every iteration."""
+    p, Dinit, Dl, xfro, _ = _full_local()
+    Dln, xf = Dl.cpu().numpy().astype(np.float64), xfro.cpu().numpy()
+    D, rm = sdl.merge(_t(Dln), xfro, _t(p.mpick), p.K, p.s2, p.iters_merge)
+    orc = oracle.merge(Dln, xf, p.mpick, p.K, p.s2, p.iters_merge)
+    rel = np.abs(rm.cpu().numpy() - orc["rmse"]) / orc["rmse"]
+    assert rel.max() < 1e-9, rel
+    np.testing.assert_allclose(D.cpu().numpy(), orc["D"], atol=1e-9)
