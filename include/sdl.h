@@ -48,7 +48,8 @@ typedef enum {
   SDL_ENOTPD = 2,
   SDL_ETIMEOUT = 3,
   SDL_ECUDA = 4,
-  SDL_ENOMEM = 5
+  SDL_ENOMEM = 5,
+  SDL_ERANGE = 6   /* a size exceeds the fixed limit of sdl_omp_noalloc */
 } sdl_status;
 
 typedef enum {
@@ -164,6 +165,28 @@ sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, 
  * of D0 (K0 x m) for which some atom of D (K x m) has |d0_i^T d_j| >= thresh. */
 sdl_status sdl_recovery(sdl_ctx *ctx, sdl_precision prec, const void *D0, int K0, const void *D,
                         int K, int m, double thresh, int32_t *count);
+
+/* OMP without any allocation (the paper has no counterpart: this is a service
+ * entry point).  For callers that cannot call cudaMalloc where they code signals:
+ * processes whose device memory is entirely owned by another allocator, or loops
+ * that must not take the implicit synchronisation of an allocation.  It computes
+ * exactly what sdl_omp computes for SDL_PREC_F32 (same kernels), but keeps its
+ * scratch -- the K x K Gram matrix and a small launch plan -- in a fixed array
+ * of 1 MiB + 256 bytes inside the library, which every GPU that loads the
+ * library holds until the process exits.  The call allocates nothing: no
+ * cudaMalloc, no cudaFree, no context workspace.
+ *   stream  cudaStream_t on the calling thread's current device (NULL = legacy)
+ *   D, Y, idx, val, nnz, resid2: as sdl_omp with float data; resid2 may be NULL
+ * Limits: K <= 512 and m <= 256, else SDL_ERANGE (nothing launched); other bad
+ * arguments give SDL_EINVAL.  The first call on a device looks up the array's
+ * device address (once per device, with that device current); make that first
+ * call before any stream capture.  Every call on a device shares the one array
+ * and overwrites all of it that it reads, so calls that overlap on the GPU
+ * (concurrent streams, or several host threads) race and must be serialised by
+ * the caller. */
+sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const float *Y, int64_t n,
+                           int s, double eps, int32_t *idx, float *val, int32_t *nnz,
+                           float *resid2);
 
 /* Instrumentation (the paper has no counterpart; it serves the roofline
  * measurements): while enabled, every kernel launcher the context runs is

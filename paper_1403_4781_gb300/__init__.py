@@ -28,7 +28,7 @@ __all__ = [
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
 _STATUS = {0: "SDL_OK", 1: "SDL_EINVAL", 2: "SDL_ENOTPD", 3: "SDL_ETIMEOUT", 4: "SDL_ECUDA",
-           5: "SDL_ENOMEM"}
+           5: "SDL_ENOMEM", 6: "SDL_ERANGE"}
 
 _lock = threading.Lock()
 _lib = None
@@ -75,6 +75,7 @@ _SIGS = {
     "sdl_profile_entry": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_i64),
                                  ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "sdl_launch_count": (_i64, [_vp]),
+    "sdl_omp_noalloc": (_i32, [_vp, _vp, _i32, _i32, _vp, _i64, _i32, _dbl, _vp, _vp, _vp, _vp]),
 }
 
 
