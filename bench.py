@@ -122,6 +122,8 @@ def algorithmic_work(p):
     def omp_flops(K_, s_):          # 2mK (alpha0) + K s (s+1) (Batch-OMP updates)
         return 2 * m * K_ + K_ * s_ * (s_ + 1)
     return {
+        "mod_solve_fp64": ("alu", p.iters_local * L * (K1 ** 3 / 3 + 2 * K1 ** 2 * m)
+                           + p.iters_merge * (K ** 3 / 3 + 2 * K ** 2 * m)),
         "chol_fp64": ("alu", p.iters_local * L * K1 ** 3 / 3 + p.iters_merge * K ** 3 / 3),
         "solve_fp64": ("alu", p.iters_local * L * 2 * K1 ** 2 * m + p.iters_merge * 2 * K ** 2 * m),
         "omp": ("alu", p.iters_local * p.N * omp_flops(K1, p.s1) + p.iters_merge * nm * omp_flops(K, p.s2)

@@ -188,6 +188,15 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
                            int s, double eps, int32_t *idx, float *val, int32_t *nnz,
                            float *resid2);
 
+/* Execution options (the paper has no counterpart; they select between
+ * implementations that compute the same result):
+ *   SDL_OPT_MOD_SOLVE: 0 = automatic (default), 1 = one thread-block cluster per
+ *     subset (K <= 512), 2 = one thread block per subset.
+ *   SDL_OPT_CLUSTER: cluster size for option 1: 16 (default), 8 or 4.
+ * Returns SDL_EINVAL for an unknown option or value. */
+typedef enum { SDL_OPT_MOD_SOLVE = 1, SDL_OPT_CLUSTER = 2 } sdl_option;
+sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
+
 /* Instrumentation (the paper has no counterpart; it serves the roofline
  * measurements): while enabled, every kernel launcher the context runs is
  * bracketed by a pair of CUDA events recorded on the context's stream and

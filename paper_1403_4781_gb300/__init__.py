@@ -76,7 +76,9 @@ _SIGS = {
                                  ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "sdl_launch_count": (_i64, [_vp]),
     "sdl_omp_noalloc": (_i32, [_vp, _vp, _i32, _i32, _vp, _i64, _i32, _dbl, _vp, _vp, _vp, _vp]),
+    "sdl_set_option": (_i32, [_vp, _i32, _i64]),
 }
+OPT_MOD_SOLVE, OPT_CLUSTER = 1, 2
 
 
 def lib() -> ctypes.CDLL:
@@ -139,6 +141,9 @@ class Context:
                   ctypes.byref(nc), ctypes.byref(ms))
             out[name.value.decode()] = (int(nl.value), int(nc.value), float(ms.value))
         return out
+
+    def set_option(self, option: int, value: int):
+        _call("sdl_set_option", self.handle, option, value)
 
     def launch_count(self) -> int:
         return int(lib().sdl_launch_count(self.handle))

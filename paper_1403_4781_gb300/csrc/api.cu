@@ -111,6 +111,27 @@ void prof_resolve(sdl_ctx *ctx) {
   cudaGetLastError();
 }
 
+// FP64 Cholesky + solve + renormalisation: one cluster kernel when the shape
+// allows it, otherwise the three-kernel path (one block per subset).
+template <typename T>
+cudaError_t run_mod_solve(sdl_ctx *ctx, const ModArgs &ma) {
+  cudaStream_t sm = ctx->stream;
+  cudaError_t e = cudaErrorNotSupported;
+  // automatic choice: the cluster kernel spreads one subset over many SMs, which
+  // pays when there are too few subsets to fill the GPU with one block each
+  const bool want_cluster = ctx->opt_mod_solve == 1 ||
+                            (ctx->opt_mod_solve == 0 && (int64_t)ma.L * 2 < ctx->num_sms);
+  if (ma.K <= 512 && want_cluster)
+    e = timed(ctx, "mod_solve_fp64", 1, [&] { return launch_mod_solve_cluster<T>(ma, ctx->opt_cluster, sm); });
+  if (e != cudaErrorNotSupported) return e;
+  cudaGetLastError();
+  e = timed(ctx, "chol_fp64", 1, [&] { return launch_mod_chol(ma, sm); });
+  if (e != cudaSuccess) return e;
+  e = timed(ctx, "solve_fp64", 1, [&] { return launch_mod_solve(ma, ctx->num_sms, sm); });
+  if (e != cudaSuccess) return e;
+  return timed(ctx, "normalise", 1, [&] { return launch_mod_normalise<T>(ma, sm); });
+}
+
 struct DeviceGuard {
   int prev = -1;
   bool ok = true;
@@ -302,9 +323,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
              }), "subset stats");
     SDL_CUDA(timed(ctx, "mod_accum", ma.total_tiles > 0 ? 4 : 2,
                    [&] { return launch_mod_accum<T>(ma, sm); }), "mod accumulate");
-    SDL_CUDA(timed(ctx, "chol_fp64", 1, [&] { return launch_mod_chol(ma, sm); }), "cholesky");
-    SDL_CUDA(timed(ctx, "solve_fp64", 1, [&] { return launch_mod_solve(ma, ctx->num_sms, sm); }), "solve");
-    SDL_CUDA(timed(ctx, "normalise", 1, [&] { return launch_mod_normalise<T>(ma, sm); }), "normalise");
+    SDL_CUDA(run_mod_solve<T>(ctx, ma), "mod solve");
     SDL_CUDA(timed(ctx, "status", 1, [&] { return launch_status_max(ma.status, L, worst + it, sm); }),
              "status");
   }
@@ -448,12 +467,8 @@ sdl_status sdl_mod_update_batched(sdl_ctx *ctx, sdl_precision prec, const void *
     SDL_CUDA(timed(ctx, "mod_accum", nacc, [&] { return launch_mod_accum<double>(a, sm); }), "mod accumulate");
   else
     SDL_CUDA(timed(ctx, "mod_accum", nacc, [&] { return launch_mod_accum<float>(a, sm); }), "mod accumulate");
-  SDL_CUDA(timed(ctx, "chol_fp64", 1, [&] { return launch_mod_chol(a, sm); }), "cholesky");
-  SDL_CUDA(timed(ctx, "solve_fp64", 1, [&] { return launch_mod_solve(a, ctx->num_sms, sm); }), "solve");
-  if (prec == SDL_PREC_F64)
-    SDL_CUDA(timed(ctx, "normalise", 1, [&] { return launch_mod_normalise<double>(a, sm); }), "normalise");
-  else
-    SDL_CUDA(timed(ctx, "normalise", 1, [&] { return launch_mod_normalise<float>(a, sm); }), "normalise");
+  if (prec == SDL_PREC_F64) SDL_CUDA(run_mod_solve<double>(ctx, a), "mod solve");
+  else SDL_CUDA(run_mod_solve<float>(ctx, a), "mod solve");
   return mod_status(ctx, a.status, L, d_max);
 }
 
@@ -648,5 +663,22 @@ sdl_status sdl_profile_entry(sdl_ctx *ctx, int i, const char **name, int64_t *la
 }
 
 int64_t sdl_launch_count(const sdl_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
+  if (!ctx) return SDL_EINVAL;
+  switch (option) {
+    case SDL_OPT_MOD_SOLVE:
+      if (value < 0 || value > 2) return set_error(ctx, SDL_EINVAL, "SDL_OPT_MOD_SOLVE takes 0, 1 or 2");
+      ctx->opt_mod_solve = (int)value;
+      return SDL_OK;
+    case SDL_OPT_CLUSTER:
+      if (value != 4 && value != 8 && value != 16)
+        return set_error(ctx, SDL_EINVAL, "SDL_OPT_CLUSTER takes 4, 8 or 16");
+      ctx->opt_cluster = (int)value;
+      return SDL_OK;
+    default:
+      return set_error(ctx, SDL_EINVAL, "unknown option");
+  }
+}
 
 }  // extern "C"

@@ -13,6 +13,7 @@
 //  5. FP64 blocked forward/back substitution, the m right-hand sides split over
 //     blocks: B <- A^{-1} B (column j of B is atom j's m values).
 //  6. Used atoms scaled to unit norm; zero or non-finite columns keep the old atom.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "sdl_internal.cuh"
@@ -94,7 +95,9 @@ __global__ void mod_fill_kernel(ModArgs a) {
 }
 
 // ---- 3: A and B accumulation, one warp per (subset, atom) --------------------
-template <typename T>
+// The atom's list is walked in batches of 8 entries whose loads are all issued
+// before any is consumed; M32 = ceil(m / 32) signal entries per lane.
+template <typename T, int M32>
 __global__ void __launch_bounds__(256) mod_accum_kernel(ModArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *arow_all = reinterpret_cast<double *>(smem_raw);
@@ -118,37 +121,56 @@ __global__ void __launch_bounds__(256) mod_accum_kernel(ModArgs a) {
   }
   for (int q = lane; q < K; q += 32) arow[q] = 0.0;
   __syncwarp();
-  double b[kMaxM / 32];
+  double b[M32];
 #pragma unroll
-  for (int u = 0; u < kMaxM / 32; ++u) b[u] = 0.0;
+  for (int u = 0; u < M32; ++u) b[u] = 0.0;
   const int64_t base = a.offsets[t] * s + a.ptr[(size_t)t * (K + 1) + j];
+  constexpr int kB = 8;
   for (int e0 = 0; e0 < c; e0 += 32) {
     const int ne = (c - e0) < 32 ? (c - e0) : 32;
-    int my_i = 0, my_k = 0;
+    int my_i = 0;
+    double my_v = 0.0;
     if (lane < ne) {
       my_i = a.lsig[base + e0 + lane];
-      my_k = a.lslot[base + e0 + lane];
+      my_v = (double)val[(size_t)my_i * s + a.lslot[base + e0 + lane]];
     }
-    for (int e = 0; e < ne; ++e) {
-      const int i = __shfl_sync(0xffffffffu, my_i, e);
-      const int k = __shfl_sync(0xffffffffu, my_k, e);
-      const double v = (double)val[(size_t)i * s + k];
-      const T *yi = Y + (size_t)i * m;
+    for (int eb = 0; eb < ne; eb += kB) {
+      int ii[kB];
+      double vv[kB];
+      T yv[kB][M32];
+      int j2[kB];
+      double x2[kB];
 #pragma unroll
-      for (int u = 0; u < kMaxM / 32; ++u) {
-        const int r = lane + 32 * u;
-        if (r < m) b[u] = fma(v, (double)yi[r], b[u]);
+      for (int q = 0; q < kB; ++q) {
+        ii[q] = __shfl_sync(0xffffffffu, my_i, (eb + q) & 31);
+        vv[q] = __shfl_sync(0xffffffffu, my_v, (eb + q) & 31);
+        if (eb + q >= ne) vv[q] = 0.0;
       }
-      if (lane < s) {
-        const int j2 = idx[(size_t)i * s + lane];
-        if (j2 >= 0 && j2 < K) arow[j2] = fma(v, (double)val[(size_t)i * s + lane], arow[j2]);
+#pragma unroll
+      for (int q = 0; q < kB; ++q) {
+        const T *yi = Y + (size_t)ii[q] * m;
+#pragma unroll
+        for (int u = 0; u < M32; ++u) {
+          const int r = lane + 32 * u;
+          yv[q][u] = (r < m && eb + q < ne) ? yi[r] : T(0);
+        }
+        j2[q] = (lane < s && eb + q < ne) ? idx[(size_t)ii[q] * s + lane] : -1;
+        x2[q] = (lane < s && eb + q < ne) ? (double)val[(size_t)ii[q] * s + lane] : 0.0;
       }
-      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < kB; ++q)
+#pragma unroll
+        for (int u = 0; u < M32; ++u) b[u] = fma(vv[q], (double)yv[q][u], b[u]);
+#pragma unroll
+      for (int q = 0; q < kB; ++q) {
+        if (j2[q] >= 0 && j2[q] < K) arow[j2[q]] = fma(vv[q], x2[q], arow[j2[q]]);
+        __syncwarp();
+      }
     }
   }
   for (int q = lane; q < K; q += 32) Arow_g[q] = arow[q];
 #pragma unroll
-  for (int u = 0; u < kMaxM / 32; ++u) {
+  for (int u = 0; u < M32; ++u) {
     const int r = lane + 32 * u;
     if (r < m) Bcol[r] = b[u];
   }
@@ -397,6 +419,314 @@ __global__ void normalise_kernel(const double *__restrict__ B, const int32_t *__
   for (int r = lane; r < m; r += 32) d[r] = (T)(b[r] / nrm);
 }
 
+
+// ---- 4-6 fused: FP64 Cholesky, solve and renormalisation by one thread-block
+// cluster per subset.  A's lower triangle is cut into 16x16 tiles; tile (i, j)
+// lives in the shared memory of cluster rank (i + j) mod C.  Each right-looking
+// step k: the owner of (k, k) factors it; owners of the panel tiles (i, k)
+// solve them against L_kk (read through distributed shared memory); every rank
+// copies the finished panel column and updates the trailing tiles it owns.
+// The right-hand sides (rows of B = atoms) are split by columns: rank c solves
+// columns [c*mc, (c+1)*mc) of L L^T X = B alone, reading L tiles remotely.
+// Atom norms are summed across ranks, then each rank writes its columns of the
+// renormalised atoms.  A breakdown (squared pivot <= 1e-12 of its diagonal)
+// restarts the factorisation once from A + lambda I (A is re-read from global
+// memory, which the kernel never writes).
+constexpr int kT = 16;            // tile edge
+constexpr int kTP = kT + 1;       // padded row pitch (doubles)
+constexpr int kTile = kT * kTP;   // doubles per stored tile
+
+struct ClusterLayout {
+  int R, C, mc, nown;
+  size_t tiles, slot, own, panel, lkk, z, normp, dg, flag, total;
+};
+
+__host__ inline ClusterLayout cluster_layout(int K, int m, int C) {
+  ClusterLayout L{};
+  L.R = (K + kT - 1) / kT;
+  L.C = C;
+  L.mc = (m + C - 1) / C;
+  int cnt[32] = {0};
+  for (int i = 0; i < L.R; ++i)
+    for (int j = 0; j <= i; ++j) cnt[(i + j) % C]++;
+  L.nown = 0;
+  for (int c = 0; c < C; ++c) L.nown = cnt[c] > L.nown ? cnt[c] : L.nown;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 15) & ~size_t(15); return o; };
+  L.tiles = take(sizeof(double) * (size_t)L.nown * kTile);
+  L.slot = take(sizeof(int) * (size_t)L.R * L.R);
+  L.own = take(sizeof(int) * (size_t)L.nown);
+  L.panel = take(sizeof(double) * (size_t)2 * L.R * kTile);   // two panel buffers (steps k even / odd)
+  L.lkk = take(sizeof(double) * 2 * kTile);                    // two L_kk buffers
+  L.z = take(sizeof(double) * (size_t)L.R * kT * L.mc);
+  L.normp = take(sizeof(double) * (size_t)L.R * kT);
+  L.dg = take(sizeof(double) * (size_t)L.R * kT);
+  L.flag = take(sizeof(int) * 4);
+  L.total = off;
+  return L;
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(256) mod_solve_cluster_kernel(const double *__restrict__ A,
+                                                                const double *__restrict__ B,
+                                                                const int32_t *__restrict__ usage, int K,
+                                                                int m, T *D, int32_t *status,
+                                                                ClusterLayout lay) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = (int)cl.block_rank();
+  const int t = blockIdx.x / C;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int R = lay.R, mc = lay.mc;
+  const int col0 = c * mc;
+  const int ncol = m - col0 < mc ? (m - col0 > 0 ? m - col0 : 0) : mc;
+  double *tiles = reinterpret_cast<double *>(smem_raw + lay.tiles);
+  int *slot = reinterpret_cast<int *>(smem_raw + lay.slot);
+  int *own = reinterpret_cast<int *>(smem_raw + lay.own);
+  double *Pbuf = reinterpret_cast<double *>(smem_raw + lay.panel);   // [2][R][kTile]
+  double *Lbuf = reinterpret_cast<double *>(smem_raw + lay.lkk);     // [2][kTile]
+  double *Z = reinterpret_cast<double *>(smem_raw + lay.z);          // [R*kT][mc]
+  double *normp = reinterpret_cast<double *>(smem_raw + lay.normp);
+  double *dg = reinterpret_cast<double *>(smem_raw + lay.dg);        // original diagonal (+ ridge)
+  int *flag = reinterpret_cast<int *>(smem_raw + lay.flag);
+  const double *At = A + (size_t)t * K * K;
+  const double *Bt = B + (size_t)t * K * m;
+  const int32_t *ut = usage + (size_t)t * K;
+
+  if (tid == 0) {
+    int cnt[C];
+    for (int q = 0; q < C; ++q) cnt[q] = 0;
+    for (int i = 0; i < R; ++i)
+      for (int j = 0; j <= i; ++j) {
+        const int o = (i + j) % C;
+        if (o == c) own[cnt[o]] = i * R + j;
+        slot[i * R + j] = cnt[o]++;
+      }
+    flag[1] = cnt[c];
+  }
+  // ridge = 1e-10 tr(A_UU) / |U| (every rank computes the same value)
+  __shared__ double red[2][8];
+  double tr = 0.0, nu = 0.0;
+  for (int j = tid; j < K; j += 256)
+    if (ut[j] > 0) { tr += At[(size_t)j * K + j]; nu += 1.0; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    nu += __shfl_xor_sync(0xffffffffu, nu, o);
+  }
+  if (lane == 0) { red[0][warp] = tr; red[1][warp] = nu; }
+  __syncthreads();
+  double T0 = 0.0, N0 = 0.0;
+  for (int w = 0; w < 8; ++w) { T0 += red[0][w]; N0 += red[1][w]; }
+  const double lambda = N0 > 0.0 ? kModRidge * T0 / N0 : 0.0;
+  const int nown = flag[1];
+  auto owner = [&](int i, int j) { return (i + j) % C; };
+
+  int st = 0;
+  bool failed = false;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const double ridge = attempt == 0 ? 0.0 : lambda;
+    for (int g = tid; g < R * kT; g += 256)
+      dg[g] = g < K ? At[(size_t)g * K + g] + (ut[g] > 0 ? ridge : 0.0) : 1.0;
+    // load owned tiles (padding: identity on the diagonal) and own RHS columns
+    for (int q = tid; q < nown * kT * kT; q += 256) {
+      const int ot = q / (kT * kT), e = q % (kT * kT), r = e / kT, cc = e % kT;
+      const int i = own[ot] / R, j = own[ot] % R;
+      const int gi = i * kT + r, gj = j * kT + cc;
+      double v;
+      if (gi < K && gj < K) v = (gj <= gi) ? At[(size_t)gi * K + gj] + (gi == gj && ut[gi] > 0 ? ridge : 0.0) : 0.0;
+      else v = (gi == gj) ? 1.0 : 0.0;
+      tiles[(size_t)ot * kTile + r * kTP + cc] = v;
+    }
+    for (int q = tid; q < R * kT * mc; q += 256) {
+      const int row = q / mc, cc = q % mc;
+      Z[q] = (row < K && cc < ncol) ? Bt[(size_t)row * m + col0 + cc] : 0.0;
+    }
+    if (tid == 0) flag[0] = 0;
+    cl.sync();
+    failed = false;
+    for (int k = 0; k < R; ++k) {
+      const int okk = owner(k, k);
+      double *Lkk = Lbuf + (size_t)(k & 1) * kTile;
+      double *P = Pbuf + (size_t)(k & 1) * R * kTile;
+      // (a) owner of (k, k): factor it (warp 0), then push L_kk into every rank
+      if (c == okk) {
+        double *Tk = tiles + (size_t)slot[k * R + k] * kTile;
+        if (warp == 0) {
+          for (int col = 0; col < kT; ++col) {
+            const double d = Tk[col * kTP + col];
+            if (!(d > kModPivotRel * dg[k * kT + col]) || !(d > 0.0)) {
+              if (lane == 0) flag[0] = 1;
+              break;
+            }
+            const double lcc = sqrt(d);
+            __syncwarp();
+            if (lane == col) Tk[col * kTP + col] = lcc;
+            if (lane > col && lane < kT) Tk[lane * kTP + col] /= lcc;
+            __syncwarp();
+            if (lane > col && lane < kT) {
+              const double lr = Tk[lane * kTP + col];
+              for (int q = col + 1; q <= lane; ++q) Tk[lane * kTP + q] -= lr * Tk[q * kTP + col];
+            }
+            __syncwarp();
+          }
+        }
+        __syncthreads();
+        if (!flag[0]) {
+          for (int q = tid; q < C * (kTile / 2); q += 256) {
+            const int r2 = q / (kTile / 2), e = q % (kTile / 2);
+            reinterpret_cast<double2 *>(cl.map_shared_rank(Lkk, r2))[e] = reinterpret_cast<const double2 *>(Tk)[e];
+          }
+        }
+      }
+      cl.sync();
+      if (*cl.map_shared_rank(flag, okk)) failed = true;
+      if (failed) break;   // uniform: every rank read the same flag after the sync
+      // (b) panel tiles (i, k) owned here: X L_kk^T = T(i, k), one thread per tile row;
+      //     each finished tile is pushed into slot i-k-1 of every rank's panel buffer
+      for (int q = tid; q < (R - k - 1) * kT; q += 256) {
+        const int i = k + 1 + q / kT, r = q % kT;
+        if (owner(i, k) != c) continue;
+        double *row = tiles + (size_t)slot[i * R + k] * kTile + r * kTP;
+        double x[kT];
+#pragma unroll
+        for (int cc = 0; cc < kT; ++cc) x[cc] = row[cc];
+#pragma unroll
+        for (int cc = 0; cc < kT; ++cc) {
+          double v = x[cc];
+#pragma unroll
+          for (int p = 0; p < cc; ++p) v = fma(-x[p], Lkk[cc * kTP + p], v);
+          x[cc] = v / Lkk[cc * kTP + cc];
+        }
+#pragma unroll
+        for (int cc = 0; cc < kT; ++cc) row[cc] = x[cc];
+      }
+      __syncthreads();
+      for (int ot = 0; ot < nown; ++ot) {
+        const int i = own[ot] / R, j = own[ot] % R;
+        if (j != k || i <= k) continue;
+        const double2 *src = reinterpret_cast<const double2 *>(tiles + (size_t)ot * kTile);
+        for (int q = tid; q < C * (kTile / 2); q += 256) {
+          const int r2 = q / (kTile / 2), e = q % (kTile / 2);
+          reinterpret_cast<double2 *>(cl.map_shared_rank(P, r2) + (size_t)(i - k - 1) * kTile)[e] = src[e];
+        }
+      }
+      cl.sync();
+      // forward substitution on own columns, step k: Z_k <- L_kk^{-1} Z_k
+      if (tid < ncol) {
+        for (int r = 0; r < kT; ++r) {
+          double v = Z[(k * kT + r) * mc + tid];
+          for (int p = 0; p < r; ++p) v = fma(-Lkk[r * kTP + p], Z[(k * kT + p) * mc + tid], v);
+          Z[(k * kT + r) * mc + tid] = v / Lkk[r * kTP + r];
+        }
+      }
+      __syncthreads();
+      // (d) Z_i -= L_ik Z_k for i > k (own columns)
+      for (int q = tid; q < (R - k - 1) * kT * ncol; q += 256) {
+        const int ii = q / (kT * ncol), e = q % (kT * ncol), r = e / ncol, cc = e % ncol;
+        const double *Pi = P + (size_t)ii * kTile + r * kTP;
+        double acc = 0.0;
+#pragma unroll
+        for (int p = 0; p < kT; ++p) acc = fma(Pi[p], Z[(k * kT + p) * mc + cc], acc);
+        Z[((k + 1 + ii) * kT + r) * mc + cc] -= acc;
+      }
+      // (e) trailing update of owned tiles (i, j), k < j <= i: T(i,j) -= P_i P_j^T
+      for (int ot = 0; ot < nown; ++ot) {
+        const int i = own[ot] / R, j = own[ot] % R;
+        if (j <= k) continue;
+        const int r = tid >> 4, cc = tid & 15;
+        if (j == i && cc > r) continue;
+        const double *Pi = P + (size_t)(i - k - 1) * kTile + r * kTP;
+        const double *Pj = P + (size_t)(j - k - 1) * kTile + cc * kTP;
+        double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+        for (int p = 0; p < kT; p += 2) {
+          acc0 = fma(Pi[p], Pj[p], acc0);
+          acc1 = fma(Pi[p + 1], Pj[p + 1], acc1);
+        }
+        tiles[(size_t)ot * kTile + r * kTP + cc] -= acc0 + acc1;
+      }
+      __syncthreads();
+    }
+    if (!failed) { st = attempt; break; }
+    st = 2;
+    cl.sync();   // nobody still reads the flag before it is reset
+  }
+
+  if (!failed) {
+    // backward substitution on own columns: L^T X = Z (L tiles pulled, no cluster sync)
+    double *P = Pbuf;
+    for (int k = R - 1; k >= 0; --k) {
+      {   // pull row k of L (tiles (k, 0..k)), four remote loads in flight per thread
+        constexpr int h = kTile / 2;
+        const int n2 = (k + 1) * h;
+        double2 *dst = reinterpret_cast<double2 *>(P);
+        for (int q0 = tid; q0 < n2; q0 += 4 * 256) {
+          double2 v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * 256;
+            if (q < n2) {
+              const int j = q / h, e = q - j * h;
+              v[u] = reinterpret_cast<const double2 *>(cl.map_shared_rank(tiles, owner(k, j)) +
+                                                       (size_t)slot[k * R + j] * kTile)[e];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (q0 + u * 256 < n2) dst[q0 + u * 256] = v[u];
+        }
+      }
+      __syncthreads();
+      const double *Lk = P + (size_t)k * kTile;
+      if (tid < ncol) {
+        for (int r = kT - 1; r >= 0; --r) {
+          double v = Z[(k * kT + r) * mc + tid];
+          for (int p = r + 1; p < kT; ++p) v = fma(-Lk[p * kTP + r], Z[(k * kT + p) * mc + tid], v);
+          Z[(k * kT + r) * mc + tid] = v / Lk[r * kTP + r];
+        }
+      }
+      __syncthreads();
+      for (int q = tid; q < k * kT * ncol; q += 256) {
+        const int jj = q / (kT * ncol), e = q % (kT * ncol), r = e / ncol, cc = e % ncol;
+        const double *Lkj = P + (size_t)jj * kTile;
+        double acc = 0.0;
+#pragma unroll
+        for (int p = 0; p < kT; ++p) acc = fma(Lkj[p * kTP + r], Z[(k * kT + p) * mc + cc], acc);
+        Z[(jj * kT + r) * mc + cc] -= acc;
+      }
+      __syncthreads();
+    }
+    // partial squared norms of every atom over own columns
+    for (int row = tid; row < R * kT; row += 256) {
+      double acc = 0.0;
+      for (int cc = 0; cc < ncol; ++cc) acc = fma(Z[row * mc + cc], Z[row * mc + cc], acc);
+      normp[row] = acc;
+    }
+  }
+  cl.sync();
+  if (!failed) {
+    for (int row = tid; row < K; row += 256) {
+      double part[C];
+#pragma unroll
+      for (int r2 = 0; r2 < C; ++r2) part[r2] = cl.map_shared_rank(normp, r2)[row];
+      double n2 = 0.0;
+#pragma unroll
+      for (int r2 = 0; r2 < C; ++r2) n2 += part[r2];
+      dg[row] = sqrt(n2);
+    }
+    __syncthreads();
+    for (int q = tid; q < K * ncol; q += 256) {
+      const int row = q / ncol, cc = q % ncol;
+      const double nrm = dg[row];
+      if (ut[row] == 0 || !(nrm > 0.0) || !isfinite(nrm)) continue;   // keep the previous atom
+      D[((size_t)t * K + row) * m + col0 + cc] = (T)(Z[row * mc + cc] / nrm);
+    }
+  }
+  if (c == 0 && tid == 0) status[t] = st;
+  cl.sync();   // keep this block's shared memory alive until every rank is done reading it
+}
 }  // namespace
 
 int mod_tile_signals() { return kModTile; }
@@ -418,10 +748,13 @@ cudaError_t launch_mod_accum(const ModArgs &a, cudaStream_t st) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const size_t sm = sizeof(double) * 8 * (size_t)a.K;
-  e = cudaFuncSetAttribute(mod_accum_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   dim3 grid((a.K + 7) / 8, a.L);
-  mod_accum_kernel<T><<<grid, 256, sm, st>>>(a);
+  auto kern = a.m <= 32 ? mod_accum_kernel<T, 1>
+            : a.m <= 64 ? mod_accum_kernel<T, 2>
+            : a.m <= 128 ? mod_accum_kernel<T, 4> : mod_accum_kernel<T, 8>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 256, sm, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -458,6 +791,58 @@ cudaError_t launch_mod_solve(const ModArgs &a, int num_sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+
+template <typename T, int C>
+static cudaError_t launch_cluster_c(const ModArgs &a, const ClusterLayout &lay, cudaStream_t st) {
+  auto kern = mod_solve_cluster_kernel<T, C>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
+  if (e != cudaSuccess) return e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.L * C));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = lay.total;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+  if (e != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return cudaErrorNotSupported;
+  }
+  e = cudaLaunchKernelEx(&cfg, kern, (const double *)a.A, (const double *)a.B, (const int32_t *)a.usage,
+                         a.K, a.m, static_cast<T *>(a.D), a.status, lay);
+  return e;
+}
+
+template <typename T>
+cudaError_t launch_mod_solve_cluster(const ModArgs &a, int cluster, cudaStream_t st) {
+  if (a.L <= 0) return cudaSuccess;
+  if (a.K > 512) return cudaErrorNotSupported;
+  const size_t limit = 227 * 1024;
+  // requested size first, then the larger sizes (less shared memory per rank)
+  const int order[3] = {cluster, 16, 8};
+  for (int q = 0; q < 3; ++q) {
+    const int C = order[q];
+    if (C != 4 && C != 8 && C != 16) continue;
+    ClusterLayout lay = cluster_layout(a.K, a.m, C);
+    if (lay.total > limit) continue;
+    cudaError_t e = C == 16 ? launch_cluster_c<T, 16>(a, lay, st)
+                  : C == 8 ? launch_cluster_c<T, 8>(a, lay, st) : launch_cluster_c<T, 4>(a, lay, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  return cudaErrorNotSupported;
+}
+
 template <typename T>
 cudaError_t launch_mod_normalise(const ModArgs &a, cudaStream_t st) {
   if (a.L <= 0) return cudaSuccess;
@@ -470,5 +855,7 @@ template cudaError_t launch_mod_accum<float>(const ModArgs &, cudaStream_t);
 template cudaError_t launch_mod_accum<double>(const ModArgs &, cudaStream_t);
 template cudaError_t launch_mod_normalise<float>(const ModArgs &, cudaStream_t);
 template cudaError_t launch_mod_normalise<double>(const ModArgs &, cudaStream_t);
+template cudaError_t launch_mod_solve_cluster<float>(const ModArgs &, int, cudaStream_t);
+template cudaError_t launch_mod_solve_cluster<double>(const ModArgs &, int, cudaStream_t);
 
 }  // namespace sdl

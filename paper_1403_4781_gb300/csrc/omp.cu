@@ -94,57 +94,68 @@ __device__ __forceinline__ int find_subset(const int32_t *__restrict__ tile_star
   return lo;
 }
 
-// Shared-memory carve-up of one OMP block (sizes in elements of T unless noted).
+// Shared-memory carve-up of one OMP block.
 struct OmpLayout {
-  int TS, K, m, s;
+  int TS, K, m, s, lp;   // lp: odd row pitch of the per-warp Cholesky factor
   bool gcache;
-  size_t a0, yt, uni, ls, xs, a0s, gss, bs, ss, cp, total;
+  size_t a0, yt, uni, ls, total;
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+constexpr int kStagePitch = kJBlock + 1;   // conflict-free transposed staging
 
 template <typename T>
 __host__ __device__ inline OmpLayout omp_layout(int TS, int K, int m, int s, bool gcache) {
   OmpLayout L{};
   L.TS = TS; L.K = K; L.m = m; L.s = s; L.gcache = gcache;
+  L.lp = (s % 2 == 0) ? s + 1 : s + 2;
   size_t off = 0;
   L.a0 = off;  off += align16(sizeof(T) * (size_t)TS * K);
   L.yt = off;  off += align16(sizeof(T) * (size_t)TS * m);
-  const size_t stage = sizeof(T) * (size_t)kKChunk * kJBlock;
+  const size_t stage = sizeof(T) * (size_t)kKChunk * kStagePitch;
   const size_t gcol = gcache ? sizeof(T) * (size_t)kWarps * s * K : 0;
   L.uni = off; off += align16(stage > gcol ? stage : gcol);
-  L.ls = off;  off += align16(sizeof(T) * (size_t)kWarps * s * s);
-  L.xs = off;  off += align16(sizeof(T) * (size_t)kWarps * s);
-  L.a0s = off; off += align16(sizeof(T) * (size_t)kWarps * s);
-  L.gss = off; off += align16(sizeof(T) * (size_t)kWarps * s * s);
-  L.bs = off;  off += align16(sizeof(T) * (size_t)kWarps * s);
-  L.ss = off;  off += align16(sizeof(int) * (size_t)kWarps * s);
-  L.cp = off;  off += align16(sizeof(void *) * (size_t)kWarps * s);
+  L.ls = off;  off += align16(sizeof(T) * (size_t)kWarps * s * L.lp);
   L.total = off;
   return L;
 }
 
-// Solve L L^T x = b for the p x p lower factor L (row stride ld); one thread.
+// Lane-distributed triangular solves with the per-warp factor L (row pitch lp):
+// lane q holds entry q of the vector.  Column sweeps: one shuffle and one FMA
+// per step, every lane busy.
 template <typename T>
-__device__ void chol_solve_serial(const T *L, int ld, int p, const T *b, T *x) {
-  for (int q = 0; q < p; ++q) {
-    T v = b[q];
-    for (int r = 0; r < q; ++r) v -= L[q * ld + r] * x[r];
-    x[q] = v / L[q * ld + q];
+__device__ __forceinline__ T lower_solve(const T *L, int lp, int k, T b, int lane) {
+  T z = T(0);
+  for (int q = 0; q < k; ++q) {
+    const T zq = __shfl_sync(0xffffffffu, b / L[q * lp + q], q);
+    if (lane == q) z = zq;
+    if (lane > q && lane < k) b = fma(-L[lane * lp + q], zq, b);
   }
-  for (int q = p - 1; q >= 0; --q) {
-    T v = x[q];
-    for (int r = q + 1; r < p; ++r) v -= L[r * ld + q] * x[r];
-    x[q] = v / L[q * ld + q];
-  }
+  return z;
 }
 
-// One block codes a tile of TS signals of one subset.  SPW = signals per warp.
-template <typename T, int SPW>
+template <typename T>
+__device__ __forceinline__ T upper_solve(const T *L, int lp, int k, T z, int lane) {
+  T x = T(0);
+  for (int q = k - 1; q >= 0; --q) {
+    const T xq = __shfl_sync(0xffffffffu, z / L[q * lp + q], q);
+    if (lane == q) x = xq;
+    if (lane < q) z = fma(-L[q * lp + lane], xq, z);
+  }
+  return x;
+}
+
+// One block codes a tile of TS = 4 * 8 signals of one subset; each warp runs the
+// selection loop for its 4 signals.  KPL = atoms per lane (K <= 32 KPL): the
+// signal's alpha0 row lives in registers, atom j = lane + 32 c.  The support
+// (atom, alpha0, coefficient, factor row) is spread one entry per lane.
+template <typename T, int KPL>
 __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int SPW = 4;
   const int TS = SPW * kWarps;
-  const int K = a.K, m = a.m, s = a.s;
+  const int K = a.K, m = a.m, s = a.s, lp = lay.lp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   const int64_t g = blockIdx.x;
@@ -159,9 +170,8 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay)
 
   T *a0 = reinterpret_cast<T *>(smem + lay.a0);     // [TS][K]
   T *yt = reinterpret_cast<T *>(smem + lay.yt);     // [TS][m]
-  T *uni = reinterpret_cast<T *>(smem + lay.uni);   // GEMM stage [16][256] / G columns [warps][s][K]
+  T *uni = reinterpret_cast<T *>(smem + lay.uni);   // GEMM stage / G columns [warps][s][K]
 
-  // ---- load the signal tile (zero rows past the subset end)
   for (int q = threadIdx.x; q < TS * m; q += kThreads) {
     const int sig = q / m, r = q - sig * m;
     yt[q] = sig < nsig ? Y[(size_t)(row0 + sig) * m + r] : T(0);
@@ -179,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay)
       for (int q = threadIdx.x; q < kKChunk * kJBlock; q += kThreads) {
         const int jj = q / kKChunk, kk = q - jj * kKChunk;
         const int gj = jb + jj, gk = k0 + kk;
-        uni[kk * kJBlock + jj] = (gj < K && gk < m) ? Dt[(size_t)gj * m + gk] : T(0);
+        uni[kk * kStagePitch + jj] = (gj < K && gk < m) ? Dt[(size_t)gj * m + gk] : T(0);
       }
       __syncthreads();
       const int kmax = (m - k0) < kKChunk ? (m - k0) : kKChunk;
@@ -188,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay)
 #pragma unroll
         for (int r = 0; r < SPW; ++r) yv[r] = yt[(warp * SPW + r) * m + k0 + kk];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) dv[c] = uni[kk * kJBlock + lane + 32 * c];
+        for (int c = 0; c < 8; ++c) dv[c] = uni[kk * kStagePitch + lane + 32 * c];
 #pragma unroll
         for (int r = 0; r < SPW; ++r)
 #pragma unroll
@@ -203,19 +213,16 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay)
         if (j < K) a0[(warp * SPW + r) * K + j] = acc[r][c];
       }
   }
-  __syncthreads();   // GEMM staging is dead from here; the union becomes G columns
+  __syncthreads();   // staging is dead from here; the union holds G columns
 
-  T *Ls = reinterpret_cast<T *>(smem + lay.ls) + (size_t)warp * s * s;
-  T *xs = reinterpret_cast<T *>(smem + lay.xs) + (size_t)warp * s;
-  T *a0S = reinterpret_cast<T *>(smem + lay.a0s) + (size_t)warp * s;
-  T *Gss = reinterpret_cast<T *>(smem + lay.gss) + (size_t)warp * s * s;
-  T *bs = reinterpret_cast<T *>(smem + lay.bs) + (size_t)warp * s;
-  int *Ss = reinterpret_cast<int *>(smem + lay.ss) + (size_t)warp * s;
-  const T **cp = reinterpret_cast<const T **>(smem + lay.cp) + (size_t)warp * s;
-  T *gc = lay.gcache ? uni + (size_t)warp * s * K : nullptr;
-
-  const int KPL = (K + 31) >> 5;   // atoms per lane (<= 32)
+  T *Ls = reinterpret_cast<T *>(smem + lay.ls) + (size_t)warp * s * lp;
+  T *gc = uni + (size_t)warp * s * K;
+  const bool gcache = lay.gcache;
   const T eps = (T)a.eps;
+  uint32_t valid = 0;   // bit c: atom lane + 32 c exists
+#pragma unroll
+  for (int c = 0; c < KPL; ++c)
+    if (lane + 32 * c < K) valid |= 1u << c;
 
   for (int q = 0; q < SPW; ++q) {
     const int sig = warp * SPW + q;
@@ -223,26 +230,38 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay)
     const int64_t gi = row0 + sig;
     const T *ysig = yt + sig * m;
     const T *arow = a0 + sig * K;
+    T a0r[KPL];
+#pragma unroll
+    for (int c = 0; c < KPL; ++c) a0r[c] = (valid >> c) & 1u ? arow[lane + 32 * c] : T(0);
 
     T yn2 = T(0);
     for (int r = lane; r < m; r += 32) yn2 = fma(ysig[r], ysig[r], yn2);
     yn2 = warp_sum(yn2);
 
-    uint32_t selmask = 0;   // bit c: atom lane + 32 c selected
+    uint32_t avail = valid;   // unselected existing atoms of this lane
     int k = 0;
+    int Sl = -1;              // lane p: p-th selected atom
+    T a0Sl = T(0), xl = T(0); // lane p: its alpha0 and coefficient
     T rn2 = yn2;
     while (k < s) {
-      if (tsqrt(rn2) <= eps) break;   // rn2 is the explicit ||y - D_S x_S||^2
-      // alpha_j = alpha0_j - sum_q G[j, S_q] x_q ; masked argmax |alpha_j|
+      if (eps > T(0) && tsqrt(rn2) <= eps) break;
+      // alpha = alpha0 - G[:, S] x_S, masked argmax |alpha| (lowest index on ties)
+      T av[KPL];
+#pragma unroll
+      for (int c = 0; c < KPL; ++c) av[c] = a0r[c];
+      for (int p = 0; p < k; ++p) {
+        const T xp = __shfl_sync(0xffffffffu, xl, p);
+        const T *gp = gcache ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
+#pragma unroll
+        for (int c = 0; c < KPL; ++c)
+          if ((valid >> c) & 1u) av[c] = fma(-gp[lane + 32 * c], xp, av[c]);
+      }
       T bestv = T(-1);
       int best = -1;
+#pragma unroll
       for (int c = 0; c < KPL; ++c) {
-        const int j = lane + 32 * c;
-        if (j >= K || ((selmask >> c) & 1u)) continue;
-        T av = arow[j];
-        for (int p = 0; p < k; ++p) av = fma(-cp[p][j], xs[p], av);
-        const T v = fabs(av);
-        if (v > bestv) { bestv = v; best = j; }
+        const T v = fabs(av[c]);
+        if (((avail >> c) & 1u) && v > bestv) { bestv = v; best = lane + 32 * c; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -254,136 +273,97 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay)
         }
       }
       if (best < 0 || !(bestv > T(0))) break;
-      // column `best` of G (row `best`, G symmetric)
-      const T *gcol;
-      if (gc) {
+      T a0b = T(0);
+#pragma unroll
+      for (int c = 0; c < KPL; ++c)
+        if (c == (best >> 5)) a0b = a0r[c];
+      a0b = __shfl_sync(0xffffffffu, a0b, best & 31);
+      // column `best` of G (= row, G symmetric)
+      const T *gcol = Gt + (size_t)best * K;
+      if (gcache) {
         T *dst = gc + (size_t)k * K;
-        for (int j = lane; j < K; j += 32) dst[j] = Gt[(size_t)best * K + j];
+        for (int j = lane; j < K; j += 32) dst[j] = gcol[j];
+        __syncwarp();
         gcol = dst;
-      } else {
-        gcol = Gt + (size_t)best * K;
       }
-      __syncwarp();
-      // progressive Cholesky: new row [w^T, sqrt(g_bb - w^T w)], L w = G[S, best]
-      int ok = 0;
-      if (lane == 0) {
-        T ww = T(0);
-        for (int p = 0; p < k; ++p) {
-          T v = gcol[Ss[p]];
-          for (int r = 0; r < p; ++r) v -= Ls[p * s + r] * Ls[k * s + r];
-          v /= Ls[p * s + p];
-          Ls[k * s + p] = v;
-          ww = fma(v, v, ww);
-        }
-        const T gbb = gcol[best];
-        const T piv2 = gbb - ww;
-        if (piv2 > PivotRel<T>::v * gbb && piv2 > T(0)) {
-          ok = 1;
-          Ls[k * s + k] = tsqrt(piv2);
-          Ss[k] = best;
-          cp[k] = gcol;
-          a0S[k] = arow[best];
-          chol_solve_serial(Ls, s, k + 1, a0S, xs);
-        }
+      // progressive Cholesky: L w = G[S, best]; new row [w^T, sqrt(g_bb - w^T w)]
+      const T gS = lane < k ? gcol[Sl] : T(0);
+      const T w = lower_solve(Ls, lp, k, gS, lane);
+      const T gbb = gcol[best];
+      const T piv2 = gbb - warp_sum(lane < k ? w * w : T(0));
+      if (!(piv2 > PivotRel<T>::v * gbb) || !(piv2 > T(0))) break;
+      if (lane < k) Ls[k * lp + lane] = w;
+      if (lane == k) {
+        Ls[k * lp + k] = tsqrt(piv2);
+        Sl = best;
+        a0Sl = a0b;
       }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if ((best & 31) == lane) avail &= ~(1u << (best >> 5));
       __syncwarp();
-      if (!ok) break;
-      if ((best & 31) == lane) selmask |= 1u << (best >> 5);
       ++k;
-      if (k < s) {   // explicit residual for the stop test of the next step
-        T acc = T(0);
-        for (int r = lane; r < m; r += 32) {
-          T v = ysig[r];
-          for (int p = 0; p < k; ++p) v = fma(-Dt[(size_t)Ss[p] * m + r], xs[p], v);
-          acc = fma(v, v, acc);
+      xl = upper_solve(Ls, lp, k, lower_solve(Ls, lp, k, a0Sl, lane), lane);
+      if (eps > T(0) && k < s) {   // explicit residual for the error-constrained stop
+        constexpr int M32 = kMaxM / 32;
+        const int mu = (m + 31) >> 5;
+        T rl[M32];
+#pragma unroll
+        for (int u = 0; u < M32; ++u) rl[u] = (u < mu && lane + 32 * u < m) ? ysig[lane + 32 * u] : T(0);
+        for (int p = 0; p < k; ++p) {   // every lane runs the shuffles; rows are guarded inside
+          const T *dp = Dt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * m;
+          const T xp = __shfl_sync(0xffffffffu, xl, p);
+#pragma unroll
+          for (int u = 0; u < M32; ++u)
+            if (u < mu && lane + 32 * u < m) rl[u] = fma(-dp[lane + 32 * u], xp, rl[u]);
         }
+        T acc = T(0);
+#pragma unroll
+        for (int u = 0; u < M32; ++u) acc = fma(rl[u], rl[u], acc);
         rn2 = warp_sum(acc);
       }
     }
 
-    // ---- refinement on the support: exact Gram of D_S, solve, one correction step
+    // ---- one refinement step on the support: x += G_SS^{-1} D_S^T (y - D_S x)
     T res2 = yn2;
     if (k > 0) {
-      for (int p = 0; p < k; ++p) {
-        const T *dp = Dt + (size_t)Ss[p] * m;
-        for (int p2 = 0; p2 <= p; ++p2) {
-          const T *dq = Dt + (size_t)Ss[p2] * m;
-          T acc = T(0);
-          for (int r = lane; r < m; r += 32) acc = fma(dp[r], dq[r], acc);
-          acc = warp_sum(acc);
-          if (lane == 0) Gss[p * s + p2] = acc;
-        }
-        T acc = T(0);
-        for (int r = lane; r < m; r += 32) acc = fma(dp[r], ysig[r], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) bs[p] = acc;
-      }
-      __syncwarp();
-      int fact_ok = 1;
-      if (lane == 0) {
-        for (int p = 0; p < k && fact_ok; ++p) {
-          T d = Gss[p * s + p];
-          for (int r = 0; r < p; ++r) d -= Gss[p * s + r] * Gss[p * s + r];
-          if (!(d > T(0))) { fact_ok = 0; break; }
-          const T lpp = tsqrt(d);
-          Gss[p * s + p] = lpp;
-          for (int i = p + 1; i < k; ++i) {
-            T v = Gss[i * s + p];
-            for (int r = 0; r < p; ++r) v -= Gss[i * s + r] * Gss[p * s + r];
-            Gss[i * s + p] = v / lpp;
-          }
-        }
-        if (fact_ok) chol_solve_serial(Gss, s, k, bs, xs);
-      }
-      fact_ok = __shfl_sync(0xffffffffu, fact_ok, 0);
-      __syncwarp();
-      // (if the exact support Gram is not numerically positive, keep the Batch-OMP x)
+      constexpr int M32 = kMaxM / 32;
+      const int mu = (m + 31) >> 5;
       for (int pass = 0; pass < 2; ++pass) {
-        // r = y - D_S x; pass 0: correction right-hand side; pass 1: final residual
-        T racc = T(0);
-        T rloc[kMaxM / 32];
+        T rloc[M32];
 #pragma unroll
-        for (int u = 0; u < kMaxM / 32; ++u) {
-          const int r = lane + 32 * u;
-          T v = T(0);
-          if (r < m) {
-            v = ysig[r];
-            for (int p = 0; p < k; ++p) v = fma(-Dt[(size_t)Ss[p] * m + r], xs[p], v);
-          }
-          rloc[u] = v;
-          racc = fma(v, v, racc);
+        for (int u = 0; u < M32; ++u) rloc[u] = (u < mu && lane + 32 * u < m) ? ysig[lane + 32 * u] : T(0);
+        for (int p = 0; p < k; ++p) {
+          const T *dp = Dt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * m;
+          const T xp = __shfl_sync(0xffffffffu, xl, p);
+#pragma unroll
+          for (int u = 0; u < M32; ++u)
+            if (u < mu && lane + 32 * u < m) rloc[u] = fma(-dp[lane + 32 * u], xp, rloc[u]);
         }
-        if (pass == 1 || !fact_ok) {
+        if (pass == 1) {
+          T racc = T(0);
+#pragma unroll
+          for (int u = 0; u < M32; ++u) racc = fma(rloc[u], rloc[u], racc);
           res2 = warp_sum(racc);
           break;
         }
+        T cl = T(0);   // lane p: d_{S_p}^T r
         for (int p = 0; p < k; ++p) {
-          const T *dp = Dt + (size_t)Ss[p] * m;
+          const T *dp = Dt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * m;
           T acc = T(0);
 #pragma unroll
-          for (int u = 0; u < kMaxM / 32; ++u) {
-            const int r = lane + 32 * u;
-            if (r < m) acc = fma(dp[r], rloc[u], acc);
-          }
+          for (int u = 0; u < M32; ++u)
+            if (u < mu && lane + 32 * u < m) acc = fma(dp[lane + 32 * u], rloc[u], acc);
           acc = warp_sum(acc);
-          if (lane == 0) bs[p] = acc;
+          if (lane == p) cl = acc;
         }
-        __syncwarp();
-        if (lane == 0) {
-          T dx[kMaxS];
-          chol_solve_serial(Gss, s, k, bs, dx);
-          for (int p = 0; p < k; ++p) xs[p] += dx[p];
-        }
-        __syncwarp();
+        xl += upper_solve(Ls, lp, k, lower_solve(Ls, lp, k, cl, lane), lane);
       }
     }
 
-    // ---- write the ELL row
+    // ---- write the ELL row (lane p holds entry p)
     T *val = static_cast<T *>(a.val);
-    for (int p = lane; p < s; p += 32) {
-      a.idx[(size_t)gi * s + p] = p < k ? Ss[p] : -1;
-      val[(size_t)gi * s + p] = p < k ? xs[p] : T(0);
+    if (lane < s) {
+      a.idx[(size_t)gi * s + lane] = lane < k ? Sl : -1;
+      val[(size_t)gi * s + lane] = lane < k ? xl : T(0);
     }
     if (lane == 0) {
       a.nnz[gi] = k;
@@ -406,11 +386,10 @@ cudaError_t launch_gram(const T *D, int m, int K, int L, T *G, cudaStream_t st) 
 
 int omp_tile_signals() { return 32; }
 
-template <typename T, int SPW>
-static cudaError_t launch_omp_spw(const OmpArgs &a, const OmpLayout &lay, cudaStream_t st) {
-  auto kern = omp_kernel<T, SPW>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)lay.total);
+template <typename T, int KPL>
+static cudaError_t launch_omp_kpl(const OmpArgs &a, const OmpLayout &lay, cudaStream_t st) {
+  auto kern = omp_kernel<T, KPL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)a.total_tiles, kThreads, lay.total, st>>>(a, lay);
   return cudaGetLastError();
@@ -420,14 +399,18 @@ template <typename T>
 cudaError_t launch_omp(const OmpArgs &a, int num_sms, cudaStream_t st) {
   (void)num_sms;
   if (a.total_tiles <= 0) return cudaSuccess;
-  // Tile size is fixed at 32 signals (4 per warp); the G-column cache is used
-  // when it fits next to the correlation tile.
+  // Tile: 32 signals (4 per warp).  The selected G columns are cached per warp
+  // when they fit beside the correlation tile, else read from L2.
   const int TS = omp_tile_signals();
   const size_t limit = 227 * 1024;
   OmpLayout lay = omp_layout<T>(TS, a.K, a.m, a.s, true);
-  if (lay.total > limit) lay = omp_layout<T>(TS, a.K, a.m, a.s, false);
+  if (lay.total > 112 * 1024) lay = omp_layout<T>(TS, a.K, a.m, a.s, false);
   if (lay.total > limit) return cudaErrorInvalidConfiguration;
-  return launch_omp_spw<T, 4>(a, lay, st);
+  const int kpl = (a.K + 31) / 32;
+  if (kpl <= 4) return launch_omp_kpl<T, 4>(a, lay, st);
+  if (kpl <= 8) return launch_omp_kpl<T, 8>(a, lay, st);
+  if (kpl <= 16) return launch_omp_kpl<T, 16>(a, lay, st);
+  return launch_omp_kpl<T, 32>(a, lay, st);
 }
 
 template cudaError_t launch_gram<float>(const float *, int, int, int, float *, cudaStream_t);

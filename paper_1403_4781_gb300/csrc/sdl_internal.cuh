@@ -63,6 +63,8 @@ struct sdl_ctx {
   int32_t *h_status = nullptr;   // pinned host word for device status read-back
   int64_t launches = 0;          // kernels launched by this context
   sdl::Prof prof;
+  int opt_mod_solve = 0;         // 0 auto, 1 cluster, 2 block per subset
+  int opt_cluster = 16;
 };
 
 namespace sdl {
@@ -134,6 +136,11 @@ cudaError_t launch_mod_chol(const ModArgs &a, cudaStream_t st);
 cudaError_t launch_mod_solve(const ModArgs &a, int num_sms, cudaStream_t st);
 template <typename T>
 cudaError_t launch_mod_normalise(const ModArgs &a, cudaStream_t st);
+// Cholesky + solve + renormalisation in one launch, one thread-block cluster
+// of `cluster` (16 or 8) CTAs per subset; K <= 512.  Returns
+// cudaErrorNotSupported when the shape or the device does not allow it.
+template <typename T>
+cudaError_t launch_mod_solve_cluster(const ModArgs &a, int cluster, cudaStream_t st);
 int mod_tile_signals();
 
 template <typename T>

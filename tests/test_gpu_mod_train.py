@@ -47,6 +47,20 @@ def test_mod_update_matches_oracle(dtype, atol):
     np.testing.assert_allclose(Dgn, Do, rtol=0, atol=atol)
 
 
+def test_mod_update_large_K_three_kernel_path():
+    """K > 512 takes the one-block-per-subset Cholesky / solve / normalise path."""
+    rng = np.random.default_rng(205)
+    m, K, n, s = 32, 600, 6000, 4
+    Y = rng.standard_normal((n, m)).astype(np.float32)
+    idx, val = _codes(rng, n, K, s)
+    val = val.astype(np.float32)
+    D0 = si.unit_gaussian_atoms(rng, m, K).astype(np.float32)
+    Dg = _t(D0.copy())
+    sdl.mod_update(_t(Y), _t(idx), _t(val), Dg)
+    Do, *_ = oracle.mod(Y.astype(np.float64), idx, val.astype(np.float64), D0.astype(np.float64), True)
+    np.testing.assert_allclose(Dg.cpu().numpy(), Do, atol=5e-5)
+
+
 def test_mod_ridge_path_matches_oracle():
     rng = np.random.default_rng(201)
     m, K, n = 6, 5, 50
