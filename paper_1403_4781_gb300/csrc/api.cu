@@ -159,10 +159,45 @@ bool aligned16(const void *p) { return p && ((uintptr_t)p & 15u) == 0; }
   } while (0)
 
 sdl_status check_prec(sdl_ctx *ctx, sdl_precision prec) {
-  if (prec == SDL_PREC_F64 || prec == SDL_PREC_F32) return SDL_OK;
-  if (prec == SDL_PREC_BF16)
-    return set_error(ctx, SDL_EINVAL, "SDL_PREC_BF16 is not available in this build");
+  if (prec == SDL_PREC_F64 || prec == SDL_PREC_F32 || prec == SDL_PREC_BF16) return SDL_OK;
   return set_error(ctx, SDL_EINVAL, "unknown precision");
+}
+
+// Workspace of the BF16 tensor-core coding pass: BF16 image of D, error word.
+size_t tc_ws_bytes(int L, int K, int m) {
+  return round256((size_t)L * round16(K) * round16(m) * 2) + round256(sizeof(int32_t) * 4) +
+         round256(sizeof(float) * (size_t)L * K * K);
+}
+
+// One BF16 coding pass: BF16 image of D, Gram and correlations on the tensor
+// cores, selection loop, FP32 refit on the support.
+cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, float *Gex, int32_t *err) {
+  cudaStream_t sm = ctx->stream;
+  oa.Dimg = img;
+  oa.Gexact = Gex;
+  oa.Kp = round16(oa.K);
+  oa.mp = round16(oa.m);
+  oa.err = err;
+  oa.G = G;
+  cudaError_t e = timed(ctx, "bf16_image", 1, [&] {
+    return launch_bf16_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, img, sm);
+  });
+  if (e != cudaSuccess) return e;
+  e = timed(ctx, "gram_tc", 1, [&] { return launch_gram_tc(img, oa.K, oa.m, oa.L, G, err, sm); });
+  if (e != cudaSuccess) return e;
+  e = timed(ctx, "gram", 1, [&] {
+    return launch_gram<float>(static_cast<const float *>(oa.D), oa.m, oa.K, oa.L, Gex, sm);
+  });
+  if (e != cudaSuccess) return e;
+  return timed(ctx, "omp_tc", 1, [&] { return launch_omp_tc(oa, sm); });
+}
+
+// Read back the error word of the tensor-core kernels (synchronises).
+sdl_status tc_status(sdl_ctx *ctx, const int32_t *err) {
+  SDL_CUDA(cudaMemcpyAsync(ctx->h_status, err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "err read");
+  SDL_CUDA(cudaStreamSynchronize(ctx->stream), "err sync");
+  if (*ctx->h_status != 0) return set_error(ctx, SDL_ETIMEOUT, "a bounded wait of a tensor-core kernel gave up");
+  return SDL_OK;
 }
 
 sdl_status check_offsets(sdl_ctx *ctx, const int64_t *offsets, int L, bool nonempty) {
@@ -273,6 +308,7 @@ sdl_status check_omp_shape(sdl_ctx *ctx, int m, int K, int s, double eps) {
 template <typename T>
 size_t train_ws_bytes(int L, int K, int m, int64_t n, int s, int iters) {
   return omp_ws_bytes(sizeof(T) == 8 ? SDL_PREC_F64 : SDL_PREC_F32, L, K) + mod_ws_bytes(L, K, m, n, s) +
+         tc_ws_bytes(L, K, m) +
          round256(sizeof(int32_t) * (size_t)n * s) + round256(sizeof(T) * (size_t)n * s) +
          round256(sizeof(int32_t) * (size_t)n) + round256(sizeof(T) * (size_t)n) +
          round256(sizeof(int32_t) * (size_t)(iters + 1)) + 4096;
@@ -283,15 +319,22 @@ size_t train_ws_bytes(int L, int K, int m, int64_t n, int s, int iters) {
 // last round), MOD.  Synchronises once at the end to report a breakdown.
 template <typename T>
 sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, int L, int K, int s,
-                     double eps, int iters, T *D, double *xfro, double *rmse) {
+                     double eps, int iters, T *D, double *xfro, double *rmse, bool bf16 = false) {
   const int64_t n = offsets[L];
   sdl_status st;
   OmpArgs oa{};
   int64_t *d_off = nullptr;
   int32_t *d_tiles = nullptr;
   int64_t tiles = 0;
-  if ((st = upload_plan(ctx, offsets, L, omp_tile_signals(), &d_off, &d_tiles, &tiles)) != SDL_OK)
+  const int tile = bf16 ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
+  if (tile <= 0) return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
+  if ((st = upload_plan(ctx, offsets, L, tile, &d_off, &d_tiles, &tiles)) != SDL_OK)
     return st;
+  void *img = bf16 ? ws_alloc(ctx, (size_t)L * round16(K) * round16(m) * 2) : nullptr;
+  int32_t *tc_err = bf16 ? static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4)) : nullptr;
+  float *Gex = bf16 ? static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)L * K * K)) : nullptr;
+  if (bf16 && (!img || !tc_err || !Gex)) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  if (bf16) SDL_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int32_t), ctx->stream), "err clear");
   T *G = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)L * K * K));
   int32_t *idx = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * s));
   T *val = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)n * s));
@@ -312,8 +355,13 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   if (xfro) SDL_CUDA(cudaMemsetAsync(xfro, 0, sizeof(double) * L, ctx->stream), "xfro clear");
   cudaStream_t sm = ctx->stream;
   for (int it = 0; it < iters; ++it) {
-    SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
-    cudaError_t e = timed(ctx, "omp", 1, [&] { return launch_omp<T>(oa, ctx->num_sms, sm); });
+    cudaError_t e;
+    if (bf16) {
+      e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), Gex, tc_err);
+    } else {
+      SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
+      e = timed(ctx, "omp", 1, [&] { return launch_omp<T>(oa, ctx->num_sms, sm); });
+    }
     if (e == cudaErrorInvalidConfiguration)
       return set_error(ctx, SDL_EINVAL, "shape too large for the OMP kernel's shared memory");
     SDL_CUDA(e, "omp");
@@ -327,7 +375,10 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
     SDL_CUDA(timed(ctx, "status", 1, [&] { return launch_status_max(ma.status, L, worst + it, sm); }),
              "status");
   }
-  if (iters > 0) return mod_status(ctx, worst, iters, d_max);
+  if (iters > 0) {
+    if ((st = mod_status(ctx, worst, iters, d_max)) != SDL_OK) return st;
+    if (bf16) return tc_status(ctx, tc_err);
+  }
   return SDL_OK;
 }
 
@@ -400,18 +451,33 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
               "device pointers must be non-NULL and 16-byte aligned");
   DeviceGuard g(ctx->device);
   SDL_REQUIRE(g.ok, "cannot select the context device");
-  if ((st = ws_reserve(ctx, omp_ws_bytes(prec, L, K) + 1024)) != SDL_OK) return st;
+  if ((st = ws_reserve(ctx, omp_ws_bytes(prec, L, K) + tc_ws_bytes(L, K, m) + 1024)) != SDL_OK) return st;
   OmpArgs a{};
   int64_t *d_off = nullptr;
   int32_t *d_tiles = nullptr;
   int64_t tiles = 0;
-  if ((st = upload_plan(ctx, offsets, L, omp_tile_signals(), &d_off, &d_tiles, &tiles)) != SDL_OK)
+  const bool bf16 = prec == SDL_PREC_BF16;
+  const int tile = bf16 ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
+  if (tile <= 0) return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
+  if ((st = upload_plan(ctx, offsets, L, tile, &d_off, &d_tiles, &tiles)) != SDL_OK)
     return st;
   void *G = ws_alloc(ctx, elem_size(prec) * (size_t)L * K * K);
   if (!G) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
   a.D = D; a.G = G; a.Y = Y; a.offsets = d_off; a.tile_start = d_tiles; a.total_tiles = tiles;
   a.L = L; a.m = m; a.K = K; a.s = s; a.eps = eps;
   a.idx = idx; a.val = val; a.nnz = nnz; a.resid2 = resid2;
+  if (bf16) {
+    void *img = ws_alloc(ctx, (size_t)L * round16(K) * round16(m) * 2);
+    int32_t *err = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
+    float *Gex = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)L * K * K));
+    if (!img || !err || !Gex) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+    SDL_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream), "err clear");
+    cudaError_t e = run_omp_bf16(ctx, a, img, static_cast<float *>(G), Gex, err);
+    if (e == cudaErrorInvalidConfiguration)
+      return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
+    SDL_CUDA(e, "omp bf16");
+    return tc_status(ctx, err);
+  }
   if (prec == SDL_PREC_F64) {
     SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<double>(static_cast<const double *>(D), m, K, L, static_cast<double *>(G),
                                  ctx->stream); }), "gram");
@@ -545,7 +611,7 @@ sdl_status sdl_local_train(sdl_ctx *ctx, sdl_precision prec, const void *Y, int 
   }
   if ((st = ws_reserve(ctx, train_ws_bytes<float>(L, K1, m, n, s1, iters))) != SDL_OK) return st;
   return train_run<float>(ctx, static_cast<const float *>(Y), m, offsets, L, K1, s1, eps, iters,
-                          static_cast<float *>(D_local), xfro, rmse);
+                          static_cast<float *>(D_local), xfro, rmse, prec == SDL_PREC_BF16);
 }
 
 sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, const double *xfro, int m,
@@ -586,7 +652,7 @@ sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, cons
   SDL_CUDA(timed(ctx, "pick_init", 1, [&] { return launch_pick_init<float>(static_cast<const float *>(Yt), m, pick, K, static_cast<float *>(D),
                                    ctx->stream); }), "merge init");
   return train_run<float>(ctx, static_cast<const float *>(Yt), m, offsets, 1, K, s2, eps, iters,
-                          static_cast<float *>(D), xf_unused, rmse);
+                          static_cast<float *>(D), xf_unused, rmse, prec == SDL_PREC_BF16);
 }
 
 sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t n, const void *D,

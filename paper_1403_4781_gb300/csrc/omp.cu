@@ -11,30 +11,18 @@
 #include <float.h>
 #include <math.h>
 
-#include "sdl_internal.cuh"
+#include "omp_common.cuh"
 
 namespace sdl {
 namespace {
+
+using namespace omp_detail;
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kJBlock = 256;   // atoms per GEMM pass (8 per lane)
 constexpr int kKChunk = 16;    // signal entries per GEMM stage
-
-template <typename T> __device__ __forceinline__ T tsqrt(T v);
-template <> __device__ __forceinline__ float tsqrt<float>(float v) { return sqrtf(v); }
-template <> __device__ __forceinline__ double tsqrt<double>(double v) { return sqrt(v); }
-
-template <typename T> struct PivotRel;
-template <> struct PivotRel<float> { static constexpr float v = kOmpPivotRelF32; };
-template <> struct PivotRel<double> { static constexpr double v = kOmpPivotRelF64; };
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+constexpr int kStagePitch = kJBlock + 1;   // conflict-free transposed staging
 
 // ---------------------------------------------------------------- Gram ------
 // G_t = D_t D_t^T for D_t stored [K][m]; one 64x64 tile of G per block.
@@ -85,31 +73,18 @@ __global__ void __launch_bounds__(256) gram_kernel(const T *__restrict__ D, int 
 }
 
 // ------------------------------------------------------------------ OMP -----
-__device__ __forceinline__ int find_subset(const int32_t *__restrict__ tile_start, int L, int64_t g) {
-  int lo = 0, hi = L;   // tile_start[lo] <= g < tile_start[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (tile_start[mid] <= g) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-// Shared-memory carve-up of one OMP block.
+// Shared-memory carve-up of one CUDA-core OMP block.
 struct OmpLayout {
   int TS, K, m, s, lp;   // lp: odd row pitch of the per-warp Cholesky factor
   bool gcache;
   size_t a0, yt, uni, ls, total;
 };
 
-__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-
-constexpr int kStagePitch = kJBlock + 1;   // conflict-free transposed staging
-
 template <typename T>
 __host__ __device__ inline OmpLayout omp_layout(int TS, int K, int m, int s, bool gcache) {
   OmpLayout L{};
   L.TS = TS; L.K = K; L.m = m; L.s = s; L.gcache = gcache;
-  L.lp = (s % 2 == 0) ? s + 1 : s + 2;
+  L.lp = odd_pitch(s);
   size_t off = 0;
   L.a0 = off;  off += align16(sizeof(T) * (size_t)TS * K);
   L.yt = off;  off += align16(sizeof(T) * (size_t)TS * m);
@@ -121,41 +96,15 @@ __host__ __device__ inline OmpLayout omp_layout(int TS, int K, int m, int s, boo
   return L;
 }
 
-// Lane-distributed triangular solves with the per-warp factor L (row pitch lp):
-// lane q holds entry q of the vector.  Column sweeps: one shuffle and one FMA
-// per step, every lane busy.
-template <typename T>
-__device__ __forceinline__ T lower_solve(const T *L, int lp, int k, T b, int lane) {
-  T z = T(0);
-  for (int q = 0; q < k; ++q) {
-    const T zq = __shfl_sync(0xffffffffu, b / L[q * lp + q], q);
-    if (lane == q) z = zq;
-    if (lane > q && lane < k) b = fma(-L[lane * lp + q], zq, b);
-  }
-  return z;
-}
-
-template <typename T>
-__device__ __forceinline__ T upper_solve(const T *L, int lp, int k, T z, int lane) {
-  T x = T(0);
-  for (int q = k - 1; q >= 0; --q) {
-    const T xq = __shfl_sync(0xffffffffu, z / L[q * lp + q], q);
-    if (lane == q) x = xq;
-    if (lane < q) z = fma(-L[q * lp + lane], xq, z);
-  }
-  return x;
-}
-
-// One block codes a tile of TS = 4 * 8 signals of one subset; each warp runs the
-// selection loop for its 4 signals.  KPL = atoms per lane (K <= 32 KPL): the
-// signal's alpha0 row lives in registers, atom j = lane + 32 c.  The support
-// (atom, alpha0, coefficient, factor row) is spread one entry per lane.
+// One block codes a tile of TS = 4 * 8 signals of one subset: the correlation
+// tile alpha0 = Y_tile D^T is a register-tiled FFMA GEMM staged through shared
+// memory, then each warp runs the selection loop for its 4 signals.
 template <typename T, int KPL>
 __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int SPW = 4;
   const int TS = SPW * kWarps;
-  const int K = a.K, m = a.m, s = a.s, lp = lay.lp;
+  const int K = a.K, m = a.m, s = a.s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   const int64_t g = blockIdx.x;
@@ -215,162 +164,9 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay)
   }
   __syncthreads();   // staging is dead from here; the union holds G columns
 
-  T *Ls = reinterpret_cast<T *>(smem + lay.ls) + (size_t)warp * s * lp;
-  T *gc = uni + (size_t)warp * s * K;
-  const bool gcache = lay.gcache;
-  const T eps = (T)a.eps;
-  uint32_t valid = 0;   // bit c: atom lane + 32 c exists
-#pragma unroll
-  for (int c = 0; c < KPL; ++c)
-    if (lane + 32 * c < K) valid |= 1u << c;
-
-  for (int q = 0; q < SPW; ++q) {
-    const int sig = warp * SPW + q;
-    if (sig >= nsig) break;
-    const int64_t gi = row0 + sig;
-    const T *ysig = yt + sig * m;
-    const T *arow = a0 + sig * K;
-    T a0r[KPL];
-#pragma unroll
-    for (int c = 0; c < KPL; ++c) a0r[c] = (valid >> c) & 1u ? arow[lane + 32 * c] : T(0);
-
-    T yn2 = T(0);
-    for (int r = lane; r < m; r += 32) yn2 = fma(ysig[r], ysig[r], yn2);
-    yn2 = warp_sum(yn2);
-
-    uint32_t avail = valid;   // unselected existing atoms of this lane
-    int k = 0;
-    int Sl = -1;              // lane p: p-th selected atom
-    T a0Sl = T(0), xl = T(0); // lane p: its alpha0 and coefficient
-    T rn2 = yn2;
-    while (k < s) {
-      if (eps > T(0) && tsqrt(rn2) <= eps) break;
-      // alpha = alpha0 - G[:, S] x_S, masked argmax |alpha| (lowest index on ties)
-      T av[KPL];
-#pragma unroll
-      for (int c = 0; c < KPL; ++c) av[c] = a0r[c];
-      for (int p = 0; p < k; ++p) {
-        const T xp = __shfl_sync(0xffffffffu, xl, p);
-        const T *gp = gcache ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
-#pragma unroll
-        for (int c = 0; c < KPL; ++c)
-          if ((valid >> c) & 1u) av[c] = fma(-gp[lane + 32 * c], xp, av[c]);
-      }
-      T bestv = T(-1);
-      int best = -1;
-#pragma unroll
-      for (int c = 0; c < KPL; ++c) {
-        const T v = fabs(av[c]);
-        if (((avail >> c) & 1u) && v > bestv) { bestv = v; best = lane + 32 * c; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, bestv, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, best, o);
-        if (ov > bestv || (ov == bestv && oj >= 0 && (best < 0 || oj < best))) {
-          bestv = ov;
-          best = oj;
-        }
-      }
-      if (best < 0 || !(bestv > T(0))) break;
-      T a0b = T(0);
-#pragma unroll
-      for (int c = 0; c < KPL; ++c)
-        if (c == (best >> 5)) a0b = a0r[c];
-      a0b = __shfl_sync(0xffffffffu, a0b, best & 31);
-      // column `best` of G (= row, G symmetric)
-      const T *gcol = Gt + (size_t)best * K;
-      if (gcache) {
-        T *dst = gc + (size_t)k * K;
-        for (int j = lane; j < K; j += 32) dst[j] = gcol[j];
-        __syncwarp();
-        gcol = dst;
-      }
-      // progressive Cholesky: L w = G[S, best]; new row [w^T, sqrt(g_bb - w^T w)]
-      const T gS = lane < k ? gcol[Sl] : T(0);
-      const T w = lower_solve(Ls, lp, k, gS, lane);
-      const T gbb = gcol[best];
-      const T piv2 = gbb - warp_sum(lane < k ? w * w : T(0));
-      if (!(piv2 > PivotRel<T>::v * gbb) || !(piv2 > T(0))) break;
-      if (lane < k) Ls[k * lp + lane] = w;
-      if (lane == k) {
-        Ls[k * lp + k] = tsqrt(piv2);
-        Sl = best;
-        a0Sl = a0b;
-      }
-      if ((best & 31) == lane) avail &= ~(1u << (best >> 5));
-      __syncwarp();
-      ++k;
-      xl = upper_solve(Ls, lp, k, lower_solve(Ls, lp, k, a0Sl, lane), lane);
-      if (eps > T(0) && k < s) {   // explicit residual for the error-constrained stop
-        constexpr int M32 = kMaxM / 32;
-        const int mu = (m + 31) >> 5;
-        T rl[M32];
-#pragma unroll
-        for (int u = 0; u < M32; ++u) rl[u] = (u < mu && lane + 32 * u < m) ? ysig[lane + 32 * u] : T(0);
-        for (int p = 0; p < k; ++p) {   // every lane runs the shuffles; rows are guarded inside
-          const T *dp = Dt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * m;
-          const T xp = __shfl_sync(0xffffffffu, xl, p);
-#pragma unroll
-          for (int u = 0; u < M32; ++u)
-            if (u < mu && lane + 32 * u < m) rl[u] = fma(-dp[lane + 32 * u], xp, rl[u]);
-        }
-        T acc = T(0);
-#pragma unroll
-        for (int u = 0; u < M32; ++u) acc = fma(rl[u], rl[u], acc);
-        rn2 = warp_sum(acc);
-      }
-    }
-
-    // ---- one refinement step on the support: x += G_SS^{-1} D_S^T (y - D_S x)
-    T res2 = yn2;
-    if (k > 0) {
-      constexpr int M32 = kMaxM / 32;
-      const int mu = (m + 31) >> 5;
-      for (int pass = 0; pass < 2; ++pass) {
-        T rloc[M32];
-#pragma unroll
-        for (int u = 0; u < M32; ++u) rloc[u] = (u < mu && lane + 32 * u < m) ? ysig[lane + 32 * u] : T(0);
-        for (int p = 0; p < k; ++p) {
-          const T *dp = Dt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * m;
-          const T xp = __shfl_sync(0xffffffffu, xl, p);
-#pragma unroll
-          for (int u = 0; u < M32; ++u)
-            if (u < mu && lane + 32 * u < m) rloc[u] = fma(-dp[lane + 32 * u], xp, rloc[u]);
-        }
-        if (pass == 1) {
-          T racc = T(0);
-#pragma unroll
-          for (int u = 0; u < M32; ++u) racc = fma(rloc[u], rloc[u], racc);
-          res2 = warp_sum(racc);
-          break;
-        }
-        T cl = T(0);   // lane p: d_{S_p}^T r
-        for (int p = 0; p < k; ++p) {
-          const T *dp = Dt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * m;
-          T acc = T(0);
-#pragma unroll
-          for (int u = 0; u < M32; ++u)
-            if (u < mu && lane + 32 * u < m) acc = fma(dp[lane + 32 * u], rloc[u], acc);
-          acc = warp_sum(acc);
-          if (lane == p) cl = acc;
-        }
-        xl += upper_solve(Ls, lp, k, lower_solve(Ls, lp, k, cl, lane), lane);
-      }
-    }
-
-    // ---- write the ELL row (lane p holds entry p)
-    T *val = static_cast<T *>(a.val);
-    if (lane < s) {
-      a.idx[(size_t)gi * s + lane] = lane < k ? Sl : -1;
-      val[(size_t)gi * s + lane] = lane < k ? xl : T(0);
-    }
-    if (lane == 0) {
-      a.nnz[gi] = k;
-      if (a.resid2) static_cast<T *>(a.resid2)[gi] = res2;
-    }
-    __syncwarp();
-  }
+  T *Ls = reinterpret_cast<T *>(smem + lay.ls) + (size_t)warp * s * lay.lp;
+  code_warp_signals<T, KPL, false>(a, a0, yt, warp * SPW, SPW, nsig, row0, Dt, Gt, Ls, Ls,
+                                   uni + (size_t)warp * s * K, lay.lp, lay.gcache);
 }
 
 }  // namespace

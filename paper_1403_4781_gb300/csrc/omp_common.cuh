@@ -1,0 +1,274 @@
+// Device code shared by the OMP kernels (CUDA-core and tensor-core correlation
+// front ends): tile-to-subset lookup, lane-distributed small triangular solves,
+// and the per-warp Batch-OMP selection loop with its refinement on the support.
+#pragma once
+
+#include <math.h>
+
+#include "sdl_internal.cuh"
+
+namespace sdl {
+namespace omp_detail {
+
+template <typename T> __device__ __forceinline__ T tsqrt(T v);
+template <> __device__ __forceinline__ float tsqrt<float>(float v) { return sqrtf(v); }
+template <> __device__ __forceinline__ double tsqrt<double>(double v) { return sqrt(v); }
+
+template <typename T> struct PivotRel;
+template <> struct PivotRel<float> { static constexpr float v = kOmpPivotRelF32; };
+template <> struct PivotRel<double> { static constexpr double v = kOmpPivotRelF64; };
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int find_subset(const int32_t *__restrict__ tile_start, int L, int64_t g) {
+  int lo = 0, hi = L;   // tile_start[lo] <= g < tile_start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tile_start[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+__host__ __device__ inline int odd_pitch(int s) { return (s % 2 == 0) ? s + 1 : s + 2; }
+
+// Lane-distributed triangular solves with a per-warp lower factor L (row pitch
+// lp): lane q holds entry q of the vector.  Column sweeps: one shuffle and one
+// FMA per step, every lane busy.
+template <typename T>
+__device__ __forceinline__ T lower_solve(const T *L, int lp, int k, T b, int lane) {
+  T z = T(0);
+  for (int q = 0; q < k; ++q) {
+    const T zq = __shfl_sync(0xffffffffu, b / L[q * lp + q], q);
+    if (lane == q) z = zq;
+    if (lane > q && lane < k) b = fma(-L[lane * lp + q], zq, b);
+  }
+  return z;
+}
+
+template <typename T>
+__device__ __forceinline__ T upper_solve(const T *L, int lp, int k, T z, int lane) {
+  T x = T(0);
+  for (int q = k - 1; q >= 0; --q) {
+    const T xq = __shfl_sync(0xffffffffu, z / L[q * lp + q], q);
+    if (lane == q) x = xq;
+    if (lane < q) z = fma(-L[q * lp + lane], xq, z);
+  }
+  return x;
+}
+
+// Lane-distributed dot products of the support atoms with a vector held as
+// rloc[u] = v[lane + 32 u]: returns d_{S_p}^T v in lane p.
+template <typename T, int M32>
+__device__ __forceinline__ T support_dots(const T *Dt, int m, int mu, int k, int Sl, const T (&rloc)[M32], int lane) {
+  T out = T(0);
+  for (int p = 0; p < k; ++p) {
+    const T *dp = Dt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * m;
+    T acc = T(0);
+#pragma unroll
+    for (int u = 0; u < M32; ++u)
+      if (u < mu && lane + 32 * u < m) acc = fma(dp[lane + 32 * u], rloc[u], acc);
+    acc = warp_sum(acc);
+    if (lane == p) out = acc;
+  }
+  return out;
+}
+
+// r = y - D_S x as rloc[u] = r[lane + 32 u].
+template <typename T, int M32>
+__device__ __forceinline__ void support_residual(const T *Dt, const T *ysig, int m, int mu, int k, int Sl, T xl,
+                                                 T (&rloc)[M32], int lane) {
+#pragma unroll
+  for (int u = 0; u < M32; ++u) rloc[u] = (u < mu && lane + 32 * u < m) ? ysig[lane + 32 * u] : T(0);
+  for (int p = 0; p < k; ++p) {
+    const T *dp = Dt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * m;
+    const T xp = __shfl_sync(0xffffffffu, xl, p);
+#pragma unroll
+    for (int u = 0; u < M32; ++u)
+      if (u < mu && lane + 32 * u < m) rloc[u] = fma(-dp[lane + 32 * u], xp, rloc[u]);
+  }
+}
+
+// The selection loop (Sec. 1 greedy choice, Batch-OMP form), refinement on the
+// support and the ELL write-out for signals sig_begin .. sig_begin+sig_count-1
+// of a tile, run by one warp.
+//   a0     correlation tile alpha0 [tile signals][K] (shared memory)
+//   ybase  signal 0 of the tile, row stride m (shared or global memory)
+//   Ls, Gx per-warp [s][lp] factor scratch;  gc per-warp [s][K] G-column cache
+//   EXACT  refit the coefficients from the exact Gram entries (a.Gexact, the Gram
+//          of D in T) and D_S^T y before the correction step (used when G and
+//          alpha0 came from reduced-precision products)
+template <typename T, int KPL, bool EXACT>
+__device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase, int sig_begin, int sig_count,
+                                  int nsig, int64_t row0, const T *__restrict__ Dt, const T *__restrict__ Gt, T *Ls,
+                                  T *Gx, T *gc, int lp, bool gcache) {
+  constexpr int M32 = kMaxM / 32;
+  const int K = a.K, m = a.m, s = a.s;
+  const int lane = threadIdx.x & 31;
+  const int mu = (m + 31) >> 5;
+  const T eps = (T)a.eps;
+  uint32_t valid = 0;   // bit c: atom lane + 32 c exists
+#pragma unroll
+  for (int c = 0; c < KPL; ++c)
+    if (lane + 32 * c < K) valid |= 1u << c;
+
+  for (int q = 0; q < sig_count; ++q) {
+    const int sig = sig_begin + q;
+    if (sig >= nsig) break;
+    const int64_t gi = row0 + sig;
+    const T *ysig = ybase + (size_t)sig * m;
+    const T *arow = a0 + (size_t)sig * K;
+    T a0r[KPL];
+#pragma unroll
+    for (int c = 0; c < KPL; ++c) a0r[c] = (valid >> c) & 1u ? arow[lane + 32 * c] : T(0);
+
+    T yn2 = T(0);
+#pragma unroll
+    for (int u = 0; u < M32; ++u)
+      if (u < mu && lane + 32 * u < m) yn2 = fma(ysig[lane + 32 * u], ysig[lane + 32 * u], yn2);
+    yn2 = warp_sum(yn2);
+
+    uint32_t avail = valid;   // unselected existing atoms of this lane
+    int k = 0;
+    int Sl = -1;              // lane p: p-th selected atom
+    T a0Sl = T(0), xl = T(0); // lane p: its alpha0 and coefficient
+    T rn2 = yn2;
+    while (k < s) {
+      if (eps > T(0) && tsqrt(rn2) <= eps) break;
+      // alpha = alpha0 - G[:, S] x_S, masked argmax |alpha| (lowest index on ties)
+      T av[KPL];
+#pragma unroll
+      for (int c = 0; c < KPL; ++c) av[c] = a0r[c];
+      for (int p = 0; p < k; ++p) {
+        const T xp = __shfl_sync(0xffffffffu, xl, p);
+        const T *gp = gcache ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
+#pragma unroll
+        for (int c = 0; c < KPL; ++c)
+          if ((valid >> c) & 1u) av[c] = fma(-gp[lane + 32 * c], xp, av[c]);
+      }
+      T bestv = T(-1);
+      int best = -1;
+#pragma unroll
+      for (int c = 0; c < KPL; ++c) {
+        const T v = fabs(av[c]);
+        if (((avail >> c) & 1u) && v > bestv) { bestv = v; best = lane + 32 * c; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, bestv, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, best, o);
+        if (ov > bestv || (ov == bestv && oj >= 0 && (best < 0 || oj < best))) {
+          bestv = ov;
+          best = oj;
+        }
+      }
+      if (best < 0 || !(bestv > T(0))) break;
+      T a0b = T(0);
+#pragma unroll
+      for (int c = 0; c < KPL; ++c)
+        if (c == (best >> 5)) a0b = a0r[c];
+      a0b = __shfl_sync(0xffffffffu, a0b, best & 31);
+      // column `best` of G (= row, G symmetric)
+      const T *gcol = Gt + (size_t)best * K;
+      if (gcache) {
+        T *dst = gc + (size_t)k * K;
+        for (int j = lane; j < K; j += 32) dst[j] = gcol[j];
+        __syncwarp();
+        gcol = dst;
+      }
+      // progressive Cholesky: L w = G[S, best]; new row [w^T, sqrt(g_bb - w^T w)]
+      const T gS = lane < k ? gcol[Sl] : T(0);
+      const T w = lower_solve(Ls, lp, k, gS, lane);
+      const T gbb = gcol[best];
+      const T piv2 = gbb - warp_sum(lane < k ? w * w : T(0));
+      if (!(piv2 > PivotRel<T>::v * gbb) || !(piv2 > T(0))) break;
+      if (lane < k) Ls[k * lp + lane] = w;
+      if (lane == k) {
+        Ls[k * lp + k] = tsqrt(piv2);
+        Sl = best;
+        a0Sl = a0b;
+      }
+      if ((best & 31) == lane) avail &= ~(1u << (best >> 5));
+      __syncwarp();
+      ++k;
+      xl = upper_solve(Ls, lp, k, lower_solve(Ls, lp, k, a0Sl, lane), lane);
+      if (eps > T(0) && k < s) {   // explicit residual for the error-constrained stop
+        T rl[M32];
+        support_residual(Dt, ysig, m, mu, k, Sl, xl, rl, lane);
+        T acc = T(0);
+#pragma unroll
+        for (int u = 0; u < M32; ++u) acc = fma(rl[u], rl[u], acc);
+        rn2 = warp_sum(acc);
+      }
+    }
+
+    // ---- refinement on the support
+    T res2 = yn2;
+    if (k > 0) {
+      const T *F = Ls;   // factor used for the correction step
+      if (EXACT) {
+        // exact Gram entries of the support (FP32 Gram of D) and D_S^T y, fresh factor
+        const T *Gex = static_cast<const T *>(a.Gexact) + (size_t)(Dt - static_cast<const T *>(a.D)) / m * K;
+        for (int p = 0; p < k; ++p) {
+          const int Sp = __shfl_sync(0xffffffffu, Sl, p);
+          if (lane <= p) Gx[p * lp + lane] = Gex[(size_t)Sp * K + Sl];
+        }
+        T yl[M32];
+#pragma unroll
+        for (int u = 0; u < M32; ++u) yl[u] = (u < mu && lane + 32 * u < m) ? ysig[lane + 32 * u] : T(0);
+        const T bl = support_dots(Dt, m, mu, k, Sl, yl, lane);
+        __syncwarp();
+        // column-sweep Cholesky of Gx (lane r owns row r)
+        bool ok = true;
+        for (int c = 0; c < k; ++c) {
+          const T d = Gx[c * lp + c];
+          if (!(d > T(0))) { ok = false; break; }
+          const T lcc = tsqrt(d);
+          __syncwarp();
+          if (lane == c) Gx[c * lp + c] = lcc;
+          if (lane > c && lane < k) Gx[lane * lp + c] /= lcc;
+          __syncwarp();
+          if (lane > c && lane < k) {
+            const T lr = Gx[lane * lp + c];
+            for (int q2 = c + 1; q2 <= lane; ++q2) Gx[lane * lp + q2] = fma(-lr, Gx[q2 * lp + c], Gx[lane * lp + q2]);
+          }
+          __syncwarp();
+        }
+        if (ok) {
+          F = Gx;
+          xl = upper_solve(Gx, lp, k, lower_solve(Gx, lp, k, bl, lane), lane);
+        }
+      }
+      // one correction step x += F^{-T} F^{-1} D_S^T (y - D_S x), then ||y - D_S x||^2
+      T rloc[M32];
+      support_residual(Dt, ysig, m, mu, k, Sl, xl, rloc, lane);
+      const T cl = support_dots(Dt, m, mu, k, Sl, rloc, lane);
+      xl += upper_solve(F, lp, k, lower_solve(F, lp, k, cl, lane), lane);
+      support_residual(Dt, ysig, m, mu, k, Sl, xl, rloc, lane);
+      T racc = T(0);
+#pragma unroll
+      for (int u = 0; u < M32; ++u) racc = fma(rloc[u], rloc[u], racc);
+      res2 = warp_sum(racc);
+    }
+
+    // ---- write the ELL row (lane p holds entry p)
+    T *val = static_cast<T *>(a.val);
+    if (lane < s) {
+      a.idx[(size_t)gi * s + lane] = lane < k ? Sl : -1;
+      val[(size_t)gi * s + lane] = lane < k ? xl : T(0);
+    }
+    if (lane == 0) {
+      a.nnz[gi] = k;
+      if (a.resid2) static_cast<T *>(a.resid2)[gi] = res2;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace omp_detail
+}  // namespace sdl

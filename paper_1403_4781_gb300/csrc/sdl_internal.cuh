@@ -102,10 +102,22 @@ struct OmpArgs {
   void *val;
   int32_t *nnz;
   void *resid2;           // may be null
+  // tensor-core (BF16) path only
+  const void *Dimg;       // [L][Kp][mp] BF16 canonical K-major image of D
+  const void *Gexact;     // [L][K][K] Gram of D in FP32 (refit on the support)
+  int Kp, mp;             // K and m rounded up to multiples of 16
+  int32_t *err;           // device word: bit 0 set when a bounded wait gave up
 };
 template <typename T>
 cudaError_t launch_omp(const OmpArgs &a, int num_sms, cudaStream_t st);
 int omp_tile_signals();
+
+// BF16 tensor-core path (tcgen05 + TMEM, operands fed by bulk TMA copies).
+inline int round16(int x) { return (x + 15) & ~15; }
+cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, cudaStream_t st);
+cudaError_t launch_gram_tc(const void *img, int K, int m, int L, float *G, int32_t *err, cudaStream_t st);
+cudaError_t launch_omp_tc(const OmpArgs &a, cudaStream_t st);
+int omp_tc_tile_signals(int K, int m, int s);   // 0 when no layout fits
 
 struct ModArgs {
   const void *Y;          // [n][m]
