@@ -68,8 +68,11 @@ def _load():
                                       _dp, i32]
             lib.orc_residual.argtypes = [_dp, i32, i64, _dp, i32, _ip, _dp, i32, _dp, _dp]
             lib.orc_recovery.argtypes = [_dp, i32, _dp, i32, i32, dbl, ctypes.POINTER(ctypes.c_int)]
+            lib.orc_mlp_forward.argtypes = [_dp, i32, i32, i32, i32, _dp, i64, _dp]
+            lib.orc_mlp_loss_grad.argtypes = [_dp, i32, i32, i32, i32, _dp, _ip, i32, i64, _dp, _dp]
             for f in ("orc_omp", "orc_mod", "orc_train", "orc_split", "orc_local_train",
-                      "orc_merge", "orc_residual", "orc_recovery"):
+                      "orc_merge", "orc_residual", "orc_recovery", "orc_mlp_forward",
+                      "orc_mlp_loss_grad"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -226,3 +229,31 @@ def recovery(D0, D, thresh=0.98):
     _check(lib.orc_recovery(_d(D0), D0.shape[0], _d(D), D.shape[0], D.shape[1], float(thresh),
                             ctypes.byref(c)), "orc_recovery")
     return c.value
+
+
+def mlp_sizes(m, h1, h2, K):
+    """Offsets of W1, b1, W2, b2, W3, b3 in the packed proposer parameters."""
+    sizes = [h1 * m, h1, h2 * h1, h2, K * h2, K]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    return offs
+
+
+def mlp_forward(params, m, h1, h2, K, Y):
+    """Logits z (B, K) of the proposer MLP."""
+    lib = _load()
+    params, Y = _f64(params), _f64(Y).reshape(-1, m)
+    Z = np.empty((Y.shape[0], K))
+    _check(lib.orc_mlp_forward(_d(params), m, h1, h2, K, _d(Y), Y.shape[0], _d(Z)), "orc_mlp_forward")
+    return Z
+
+
+def mlp_loss_grad(params, m, h1, h2, K, Y, idx, with_grad=True):
+    """(loss, grad) of the proposer's binary cross-entropy on support labels."""
+    lib = _load()
+    params, Y = _f64(params), _f64(Y).reshape(-1, m)
+    idx = np.ascontiguousarray(idx, np.int32)
+    loss = ctypes.c_double(0.0)
+    grad = np.empty_like(params) if with_grad else None
+    _check(lib.orc_mlp_loss_grad(_d(params), m, h1, h2, K, _d(Y), _i(idx), idx.shape[1], Y.shape[0],
+                                 ctypes.cast(ctypes.byref(loss), _dp), _d(grad)), "orc_mlp_loss_grad")
+    return loss.value, grad

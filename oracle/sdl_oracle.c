@@ -363,3 +363,84 @@ int orc_recovery(const double *D0, int K0, const double *D, int K, int m,
   *count = c;
   return 0;
 }
+
+/* ------------------------------------------------------- MLP proposer --- */
+
+static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+static double gelu_prime(double x) {
+  return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) * 0.39894228040143267794; /* 1/sqrt(2 pi) */
+}
+
+int orc_mlp_forward(const double *params, int m, int h1, int h2, int K, const double *Y, int64_t B,
+                    double *Z) {
+  if (m <= 0 || h1 <= 0 || h2 <= 0 || K <= 0 || B < 0 || !params || !Z) return 1;
+  const double *W1 = params, *b1 = W1 + (size_t)h1 * m, *W2 = b1 + h1, *b2 = W2 + (size_t)h2 * h1;
+  const double *W3 = b2 + h2, *b3 = W3 + (size_t)K * h2;
+  double *x1 = (double *)malloc(sizeof(double) * (size_t)h1);
+  double *x2 = (double *)malloc(sizeof(double) * (size_t)h2);
+  for (int64_t b = 0; b < B; ++b) {
+    const double *y = Y + (size_t)b * m;
+    for (int i = 0; i < h1; ++i) x1[i] = gelu(dot(W1 + (size_t)i * m, y, m) + b1[i]);
+    for (int i = 0; i < h2; ++i) x2[i] = gelu(dot(W2 + (size_t)i * h1, x1, h1) + b2[i]);
+    for (int j = 0; j < K; ++j) Z[(size_t)b * K + j] = dot(W3 + (size_t)j * h2, x2, h2) + b3[j];
+  }
+  free(x1);
+  free(x2);
+  return 0;
+}
+
+int orc_mlp_loss_grad(const double *params, int m, int h1, int h2, int K, const double *Y,
+                      const int32_t *idx, int s, int64_t B, double *loss, double *grad) {
+  if (m <= 0 || h1 <= 0 || h2 <= 0 || K <= 0 || B <= 0 || s <= 0 || !params || !loss) return 1;
+  const size_t nW1 = (size_t)h1 * m, nW2 = (size_t)h2 * h1, nW3 = (size_t)K * h2;
+  const size_t np = nW1 + h1 + nW2 + h2 + nW3 + K;
+  const double *W1 = params, *b1 = W1 + nW1, *W2 = b1 + h1, *b2 = W2 + nW2, *W3 = b2 + h2, *b3 = W3 + nW3;
+  double *gW1 = NULL, *gb1 = NULL, *gW2 = NULL, *gb2 = NULL, *gW3 = NULL, *gb3 = NULL;
+  if (grad) {
+    memset(grad, 0, sizeof(double) * np);
+    gW1 = grad; gb1 = gW1 + nW1; gW2 = gb1 + h1; gb2 = gW2 + nW2; gW3 = gb2 + h2; gb3 = gW3 + nW3;
+  }
+  double *a1 = (double *)malloc(sizeof(double) * (size_t)h1), *x1 = (double *)malloc(sizeof(double) * (size_t)h1);
+  double *a2 = (double *)malloc(sizeof(double) * (size_t)h2), *x2 = (double *)malloc(sizeof(double) * (size_t)h2);
+  double *z = (double *)malloc(sizeof(double) * (size_t)K), *dz = (double *)malloc(sizeof(double) * (size_t)K);
+  double *d2 = (double *)malloc(sizeof(double) * (size_t)h2), *d1 = (double *)malloc(sizeof(double) * (size_t)h1);
+  char *t = (char *)malloc((size_t)K);
+  double total = 0.0;
+  for (int64_t b = 0; b < B; ++b) {
+    const double *y = Y + (size_t)b * m;
+    for (int i = 0; i < h1; ++i) { a1[i] = dot(W1 + (size_t)i * m, y, m) + b1[i]; x1[i] = gelu(a1[i]); }
+    for (int i = 0; i < h2; ++i) { a2[i] = dot(W2 + (size_t)i * h1, x1, h1) + b2[i]; x2[i] = gelu(a2[i]); }
+    memset(t, 0, (size_t)K);
+    for (int k = 0; k < s; ++k) {
+      int j = idx[(size_t)b * s + k];
+      if (j >= 0 && j < K) t[j] = 1;
+    }
+    for (int j = 0; j < K; ++j) {
+      z[j] = dot(W3 + (size_t)j * h2, x2, h2) + b3[j];
+      total += (z[j] > 0 ? z[j] : 0.0) - z[j] * t[j] + log1p(exp(-fabs(z[j])));
+      dz[j] = (1.0 / (1.0 + exp(-z[j])) - t[j]) / (double)B;
+    }
+    if (!grad) continue;
+    for (int j = 0; j < K; ++j) {
+      gb3[j] += dz[j];
+      for (int i = 0; i < h2; ++i) gW3[(size_t)j * h2 + i] += dz[j] * x2[i];
+    }
+    for (int i = 0; i < h2; ++i) {
+      double v = 0.0;
+      for (int j = 0; j < K; ++j) v += W3[(size_t)j * h2 + i] * dz[j];
+      d2[i] = v * gelu_prime(a2[i]);
+      gb2[i] += d2[i];
+      for (int q = 0; q < h1; ++q) gW2[(size_t)i * h1 + q] += d2[i] * x1[q];
+    }
+    for (int q = 0; q < h1; ++q) {
+      double v = 0.0;
+      for (int i = 0; i < h2; ++i) v += W2[(size_t)i * h1 + q] * d2[i];
+      d1[q] = v * gelu_prime(a1[q]);
+      gb1[q] += d1[q];
+      for (int r = 0; r < m; ++r) gW1[(size_t)q * m + r] += d1[q] * y[r];
+    }
+  }
+  *loss = total / (double)B;
+  free(a1); free(x1); free(a2); free(x2); free(z); free(dz); free(d2); free(d1); free(t);
+  return 0;
+}

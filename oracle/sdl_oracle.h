@@ -94,3 +94,25 @@ int orc_recovery(const double *D0, int K0, const double *D, int K, int m,
 }
 #endif
 #endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+/* Learned support proposer (an extension beyond the paper: a small MLP that
+ * scores atoms for a signal).  Parameters are packed in one array:
+ *   W1 [h1][m], b1 [h1], W2 [h2][h1], b2 [h2], W3 [K][h2], b3 [K].
+ * Forward: a1 = W1 y + b1, h1 = gelu(a1), a2 = W2 h1 + b2, h2 = gelu(a2),
+ * z = W3 h2 + b3 with gelu(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2.
+ * Loss over a batch of B signals with supports idx [B][s] (-1 pads):
+ *   (1/B) sum_b sum_j [ max(z,0) - z t + log(1 + exp(-|z|)) ], t_bj = 1 iff j in
+ *   the support of signal b (binary cross-entropy on the logits).
+ * orc_mlp_loss_grad returns the loss and (grad != NULL) its gradient with
+ * respect to every packed parameter, by backpropagation; orc_mlp_forward
+ * returns the logits z [B][K]. */
+int orc_mlp_forward(const double *params, int m, int h1, int h2, int K, const double *Y, int64_t B,
+                    double *Z);
+int orc_mlp_loss_grad(const double *params, int m, int h1, int h2, int K, const double *Y,
+                      const int32_t *idx, int s, int64_t B, double *loss, double *grad);
+#ifdef __cplusplus
+}
+#endif
