@@ -166,6 +166,45 @@ sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, 
 sdl_status sdl_recovery(sdl_ctx *ctx, sdl_precision prec, const void *D0, int K0, const void *D,
                         int K, int m, double thresh, int32_t *count);
 
+/* ---- Learned support proposer (an extension beyond the paper: it accelerates
+ * the OMP stage of Sec. 1 by proposing candidate atoms).  An MLP
+ * m -> h1 -> h2 -> K with GELU hidden layers scores every atom for a signal;
+ * its products run on the tensor cores in BF16 with FP32 accumulation; master
+ * weights, Adam moments and the loss are FP32.  Parameters are one packed FP32
+ * array: W1 [h1][m], b1 [h1], W2 [h2][h1], b2 [h2], W3 [K][h2], b3 [K].
+ * The proposer owns its device memory (allocated at creation and grown to the
+ * largest batch seen); it is tied to the context's device. */
+typedef struct sdl_proposer sdl_proposer;
+
+/* Create a proposer with initial parameters `params` (device, packed as above).
+ * h1, h2, K multiples of 8; 1 <= m <= 256; K <= 1024.  Synchronises. */
+sdl_status sdl_proposer_create(sdl_ctx *ctx, int m, int h1, int h2, int K, const float *params,
+                               sdl_proposer **out);
+sdl_status sdl_proposer_destroy(sdl_proposer *p);
+/* Copy the FP32 master parameters into `params` (device, packed). */
+sdl_status sdl_proposer_get_params(sdl_ctx *ctx, const sdl_proposer *p, float *params);
+/* Binary cross-entropy of the logits against support labels, averaged over the
+ * batch: (1/B) sum_b sum_j [max(z,0) - z t + log(1 + exp(-|z|))], t_bj = 1 iff atom
+ * j is in idx[b] (device int32 [B][s], -1 pads).  loss: device float [1] or NULL;
+ * grad: device float [nparams] packed like the parameters, or NULL.  B must be a
+ * positive multiple of 8. */
+sdl_status sdl_proposer_loss_grad(sdl_ctx *ctx, sdl_proposer *p, const float *Y, const int32_t *idx, int s,
+                                  int64_t B, float *loss, float *grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the batch. */
+sdl_status sdl_proposer_train_step(sdl_ctx *ctx, sdl_proposer *p, const float *Y, const int32_t *idx, int s,
+                                   int64_t B, float lr, float *loss);
+/* Logits Z (device float [n][K]) of n signals. */
+sdl_status sdl_proposer_scores(sdl_ctx *ctx, sdl_proposer *p, const float *Y, int64_t n, float *Z);
+/* Proposer-assisted OMP (FP32 data): for each signal, the top `ncand` atoms by
+ * score (s <= ncand <= 32) are the candidates; OMP (Sec. 1 greedy rule, lowest
+ * atom index on ties) runs over them, the coefficients are refitted on the
+ * support; every signal whose residual norm exceeds eps_fb is recoded by the
+ * full OMP of sdl_omp (the fallback).  Outputs as sdl_omp; *n_fallback (host)
+ * receives the number of recoded signals.  Synchronises once. */
+sdl_status sdl_omp_proposed(sdl_ctx *ctx, sdl_proposer *p, const float *D, int m, int K, const float *Y,
+                            int64_t n, int s, int ncand, double eps_fb, int32_t *idx, float *val,
+                            int32_t *nnz, float *resid2, int64_t *n_fallback);
+
 /* OMP without any allocation (the paper has no counterpart: this is a service
  * entry point).  For callers that cannot call cudaMalloc where they code signals:
  * processes whose device memory is entirely owned by another allocator, or loops

@@ -23,7 +23,7 @@ from . import _build
 __all__ = [
     "PREC_F64", "PREC_F32", "PREC_BF16", "SdlError", "lib", "library_path", "declared_symbols",
     "Context", "context", "omp", "omp_batched", "mod_update", "mod_update_batched", "split",
-    "init_dict", "local_train", "merge", "residual", "recovery",
+    "init_dict", "local_train", "merge", "residual", "recovery", "Proposer",
 ]
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
@@ -77,6 +77,14 @@ _SIGS = {
     "sdl_launch_count": (_i64, [_vp]),
     "sdl_omp_noalloc": (_i32, [_vp, _vp, _i32, _i32, _vp, _i64, _i32, _dbl, _vp, _vp, _vp, _vp]),
     "sdl_set_option": (_i32, [_vp, _i32, _i64]),
+    "sdl_proposer_create": (_i32, [_vp, _i32, _i32, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+    "sdl_proposer_destroy": (_i32, [_vp]),
+    "sdl_proposer_get_params": (_i32, [_vp, _vp, _vp]),
+    "sdl_proposer_loss_grad": (_i32, [_vp, _vp, _vp, _vp, _i32, _i64, _vp, _vp]),
+    "sdl_proposer_train_step": (_i32, [_vp, _vp, _vp, _vp, _i32, _i64, ctypes.c_float, _vp]),
+    "sdl_proposer_scores": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+    "sdl_omp_proposed": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp,
+                                ctypes.POINTER(_i64)]),
 }
 OPT_MOD_SOLVE, OPT_CLUSTER = 1, 2
 
@@ -341,3 +349,70 @@ def recovery(D0, D, thresh=0.98, prec=None):
     ctx = context(D.device.index)
     _call("sdl_recovery", ctx.bind_stream(), prec, _ptr(D0), K0, _ptr(D), K, m, float(thresh), _ptr(out))
     return out
+
+
+class Proposer:
+    """The learned support proposer (MLP m -> h1 -> h2 -> K) living on one device."""
+
+    def __init__(self, params, m, h1, h2, K, ctx=None):
+        import torch
+        self.ctx = ctx or context(params.device.index)
+        self.m, self.h1, self.h2, self.K = m, h1, h2, K
+        self.nparams = params.numel()
+        h = _vp()
+        _call("sdl_proposer_create", self.ctx.bind_stream(), m, h1, h2, K, _ptr(params.contiguous()),
+              ctypes.byref(h))
+        self.handle = h
+        self.device = params.device
+
+    def params(self):
+        import torch
+        out = torch.empty((self.nparams,), dtype=torch.float32, device=self.device)
+        _call("sdl_proposer_get_params", self.ctx.bind_stream(), self.handle, _ptr(out))
+        return out
+
+    def loss_grad(self, Y, idx):
+        import torch
+        B, s = idx.shape
+        loss = torch.empty((4,), dtype=torch.float32, device=self.device)
+        grad = torch.empty((self.nparams,), dtype=torch.float32, device=self.device)
+        _call("sdl_proposer_loss_grad", self.ctx.bind_stream(), self.handle, _ptr(Y), _ptr(idx), s, B,
+              _ptr(loss), _ptr(grad))
+        return loss[0], grad
+
+    def train_step(self, Y, idx, lr, loss=None):
+        B, s = idx.shape
+        _call("sdl_proposer_train_step", self.ctx.bind_stream(), self.handle, _ptr(Y), _ptr(idx), s, B,
+              float(lr), _ptr(loss))
+
+    def scores(self, Y):
+        import torch
+        n = Y.shape[0]
+        Z = torch.empty((n, self.K), dtype=torch.float32, device=self.device)
+        _call("sdl_proposer_scores", self.ctx.bind_stream(), self.handle, _ptr(Y), n, _ptr(Z))
+        return Z
+
+    def omp(self, D, Y, s, ncand, eps_fb, with_resid=True):
+        """Proposer-assisted OMP; returns (idx, val, nnz, resid2, n_fallback)."""
+        import torch
+        K, m = D.shape
+        n = Y.shape[0]
+        idx = torch.empty((n, s), dtype=torch.int32, device=self.device)
+        val = torch.empty((n, s), dtype=torch.float32, device=self.device)
+        nnz = torch.empty((n,), dtype=torch.int32, device=self.device)
+        r2 = torch.empty((n,), dtype=torch.float32, device=self.device) if with_resid else None
+        nf = ctypes.c_int64(0)
+        _call("sdl_omp_proposed", self.ctx.bind_stream(), self.handle, _ptr(D), m, K, _ptr(Y), n, s, ncand,
+              float(eps_fb), _ptr(idx), _ptr(val), _ptr(nnz), _ptr(r2), ctypes.byref(nf))
+        return idx, val, nnz, r2, int(nf.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sdl_proposer_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -257,9 +257,10 @@ __global__ void __launch_bounds__(kTcThreads) omp_tc_kernel(OmpArgs a, TcLayout 
 template <int KPL>
 cudaError_t launch_omp_tc_kpl(const OmpArgs &a, const TcLayout &lay, cudaStream_t st) {
   auto kern = omp_tc_kernel<KPL>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
+  const size_t smem = tc::smem_for_tmem(lay.total, lay.NT);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)a.total_tiles, kTcThreads, lay.total, st>>>(a, lay);
+  kern<<<(unsigned)a.total_tiles, kTcThreads, smem, st>>>(a, lay);
   return cudaGetLastError();
 }
 
@@ -278,7 +279,7 @@ cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, cu
 cudaError_t launch_gram_tc(const void *img, int K, int m, int L, float *G, int32_t *err, cudaStream_t st) {
   const int Kp = round16(K), mp = round16(m);
   const int NG = Kp > 128 ? 256 : 128;
-  const size_t smem = (size_t)(128 + NG) * mp * 2 + 64;
+  const size_t smem = tc::smem_for_tmem((size_t)(128 + NG) * mp * 2 + 64, NG <= 128 ? 128 : 256);
   cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((Kp + 127) / 128, (Kp + NG - 1) / NG, L);

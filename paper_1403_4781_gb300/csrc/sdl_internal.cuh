@@ -178,4 +178,20 @@ cudaError_t launch_recovery(const T *D0, int K0, const T *D, int K, int m, doubl
                             int32_t *count, cudaStream_t st);
 cudaError_t launch_status_max(const int32_t *status, int L, int32_t *out, cudaStream_t st);
 
+// Learned support proposer (proposer.cu).
+int proposer_m(const sdl_proposer *p);
+int proposer_K(const sdl_proposer *p);
+// Scores of n signals (chunked forward passes) and their top-c atoms cand [n][c].
+cudaError_t proposer_topk(sdl_proposer *p, const float *Y, int64_t n, int c, int32_t *cand, cudaStream_t st);
+// OMP restricted to the candidates; flag[i] = 1 where ||r|| > eps_fb.
+cudaError_t launch_romp(const float *D, const float *G, int m, int K, const float *Y, int64_t n, int s, int c,
+                        const int32_t *cand, float eps_fb, int32_t *idx, float *val, int32_t *nnz, float *resid2,
+                        int32_t *flag, cudaStream_t st);
+cudaError_t launch_compact(const int32_t *flag, int64_t n, int32_t *list, int32_t *count, cudaStream_t st);
+cudaError_t launch_gather_rows(const float *Y, int m, const int32_t *list, const int32_t *count, int64_t nmax,
+                               float *Yf, cudaStream_t st);
+cudaError_t launch_scatter_codes(const int32_t *list, const int32_t *count, int64_t nmax, int s, const int32_t *fi,
+                                 const float *fv, const int32_t *fn, const float *fr, int32_t *idx, float *val,
+                                 int32_t *nnz, float *resid2, cudaStream_t st);
+
 }  // namespace sdl

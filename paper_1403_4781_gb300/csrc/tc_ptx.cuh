@@ -91,5 +91,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// Dynamic shared memory to request so that the blocks resident on one SM never
+// ask for more than the 512 tensor-memory columns an SM has: at most 512/ncols
+// blocks may share an SM, so each asks for more than 1/(512/ncols + 1) of the
+// SM's 228 KB of shared memory.
+inline size_t smem_for_tmem(size_t smem, int ncols) {
+  const size_t sm_total = 228 * 1024;
+  const size_t max_blocks = 512 / (size_t)ncols;
+  const size_t floor_bytes = sm_total / (max_blocks + 1) + 1024;
+  return smem > floor_bytes ? smem : floor_bytes;
+}
+
 }  // namespace tc
 }  // namespace sdl

@@ -166,3 +166,23 @@ def e1_problem(trial: int = 0):
     picks = init_picks(rng, offsets, 50)
     mpick = merge_pick(rng, 50 * 40, 60)
     return dict(D0=D0, Y=Y, perm=perm, offsets=offsets, picks=picks, mpick=mpick)
+
+
+def mlp_init(rng: np.random.Generator, m: int, h1: int, h2: int, K: int, s: int) -> np.ndarray:
+    """Packed initial proposer parameters (W1, b1, W2, b2, W3, b3): He-scaled
+    Gaussian weights, zero hidden biases, output bias at the label prior log(s/(K-s))."""
+    parts = [rng.standard_normal(h1 * m) * np.sqrt(2.0 / m), np.zeros(h1),
+             rng.standard_normal(h2 * h1) * np.sqrt(2.0 / h1), np.zeros(h2),
+             rng.standard_normal(K * h2) * np.sqrt(1.0 / h2), np.full(K, np.log(s / (K - s)))]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def config3(n_train: int = 1_000_000, n_eval: int = 1_000_000):
+    """Learned-proposer workload: D0 64x256 unit atoms, s=6, noise 0.01; training
+    and evaluation signals drawn independently from the same model."""
+    rng = rng_for(3)
+    D0 = unit_gaussian_atoms(rng, 64, 256).astype(np.float32)
+    Ytr, _, _ = sparse_signals(rng, D0.astype(np.float64), n_train, 6, 0.01, dtype=np.float32)
+    Yev, _, _ = sparse_signals(rng, D0.astype(np.float64), n_eval, 6, 0.01, dtype=np.float32)
+    params = mlp_init(rng, 64, 512, 512, 256, 6)
+    return dict(D0=D0, Ytr=Ytr, Yev=Yev, params=params, m=64, h1=512, h2=512, K=256, s=6)
