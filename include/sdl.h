@@ -228,12 +228,24 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
                            float *resid2);
 
 /* Execution options (the paper has no counterpart; they select between
- * implementations that compute the same result):
- *   SDL_OPT_MOD_SOLVE: 0 = automatic (default), 1 = one thread-block cluster per
- *     subset (K <= 512), 2 = one thread block per subset.
- *   SDL_OPT_CLUSTER: cluster size for option 1: 16 (default), 8 or 4.
+ * implementations of the FP64 MOD solve that compute the same result):
+ *   SDL_OPT_MOD_SOLVE: 0 = automatic (default: the tiled solve with an
+ *     automatic tile and cluster size), 1 = one thread-block cluster per subset
+ *     holding the factor in distributed shared memory (K <= 512), 2 = one
+ *     thread block per subset for the factorisation, then a separate solve,
+ *     3 = the tiled solve with the tile and cluster size set below.
+ *   SDL_OPT_CLUSTER: cluster size, 0 = automatic (default); 4, 8 or 16 for
+ *     option 1, 1 to 16 for option 3.
+ *   SDL_OPT_MOD_TILE: tile edge of the tiled solve: 0 = automatic (default),
+ *     16 or 32.
+ *   SDL_OPT_AUTOTUNE: 1 (default) = where tile and cluster size are automatic,
+ *     the first call for a shape (element type, number of subsets, K, m) times
+ *     every candidate on the call's own inputs with CUDA events (this
+ *     synchronises the stream once) and keeps the fastest for the context;
+ *     calls made while the stream is being captured use a rule on the shape
+ *     instead.  0 = always use that rule (and forget tuned shapes).
  * Returns SDL_EINVAL for an unknown option or value. */
-typedef enum { SDL_OPT_MOD_SOLVE = 1, SDL_OPT_CLUSTER = 2 } sdl_option;
+typedef enum { SDL_OPT_MOD_SOLVE = 1, SDL_OPT_CLUSTER = 2, SDL_OPT_MOD_TILE = 3, SDL_OPT_AUTOTUNE = 4 } sdl_option;
 sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
 
 /* Instrumentation (the paper has no counterpart; it serves the roofline

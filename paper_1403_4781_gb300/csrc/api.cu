@@ -111,18 +111,116 @@ void prof_resolve(sdl_ctx *ctx) {
   cudaGetLastError();
 }
 
-// FP64 Cholesky + solve + renormalisation: one cluster kernel when the shape
-// allows it, otherwise the three-kernel path (one block per subset).
+// Cached number of clusters of the tiled solve that fit on the device at once.
+template <typename T>
+int tiled_occupancy(sdl_ctx *ctx, int ts, int C) {
+  const int64_t key = ((int64_t)(sizeof(T)) << 32) | ((int64_t)ts << 8) | C;
+  auto it = ctx->occ.find(key);
+  if (it != ctx->occ.end()) return it->second;
+  const int n = mod_tiled_max_clusters<T>(ts, C, 0, 0);
+  ctx->occ[key] = n;
+  return n;
+}
+
+// Tile edge and cluster size of the tiled FP64 solve from the shape alone.
+// Few subsets: the factorisation's dependency chain dominates, so small tiles
+// spread each subset over the largest cluster.  Many subsets: the largest
+// cluster for which every subset's cluster is resident at once.
+template <typename T>
+void pick_tiled(sdl_ctx *ctx, int L, int *ts, int *C) {
+  int t = ctx->opt_tile;
+  int c = ctx->opt_cluster;
+  if (t == 0) t = (int64_t)L * 8 <= ctx->num_sms ? 16 : 32;
+  if (c == 0) {
+    c = 1;
+    const int cand[6] = {16, 8, 6, 4, 2, 1};
+    for (int q = 0; q < 6; ++q) {
+      const int n = tiled_occupancy<T>(ctx, t, cand[q]);
+      if (n >= L) { c = cand[q]; break; }
+    }
+  }
+  *ts = t;
+  *C = c;
+}
+
+// Autotuner of the tiled solve: on the first call for a shape (element type,
+// subsets, K, m) that leaves the tile and cluster size automatic, every
+// candidate is run on the caller's own inputs (the solve reads A, B and the
+// usage counts and rewrites only scratch, D and the status, so repeated runs
+// give the same result) and timed with CUDA events; the fastest is cached in
+// the context and run last.  Skipped while the stream is being captured (the
+// shape rule above is used then) or when the option turns it off.
+template <typename T>
+cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
+  cudaStream_t sm = ctx->stream;
+  int ts = 32, C = 1;
+  const bool manual = ctx->opt_tile != 0 || ctx->opt_cluster != 0;
+  const std::string key = std::to_string(sizeof(T)) + ":" + std::to_string(ma.L) + ":" + std::to_string(ma.K) +
+                          ":" + std::to_string(ma.m);
+  auto it = ctx->tuned.find(key);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(sm, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;
+  }
+  if (!manual && it != ctx->tuned.end()) {
+    ts = it->second.first;
+    C = it->second.second;
+  } else if (manual || !ctx->opt_autotune || cap != cudaStreamCaptureStatusNone) {
+    pick_tiled<T>(ctx, ma.L, &ts, &C);
+  } else {
+    int best_ts = 0, best_c = 0;
+    float best = 3.4e38f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int tiles[2] = {16, 32};
+    const int cls[7] = {1, 2, 3, 4, 6, 8, 16};
+    for (int a = 0; a < 2 && e == cudaSuccess; ++a)
+      for (int b = 0; b < 7 && e == cudaSuccess; ++b) {
+        const int t = tiles[a], c = cls[b];
+        // a subset's cluster must fit on the device; small clusters for few
+        // subsets leave most SMs idle and are not worth timing
+        if (tiled_occupancy<T>(ctx, t, c) < 1) continue;
+        if ((int64_t)ma.L * c * 4 < ctx->num_sms && c < 16) continue;
+        float ms_best = 3.4e38f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+          e = cudaEventRecord(e0, sm);
+          if (e == cudaSuccess) e = launch_mod_tiled<T>(ma, t, c, sm);
+          if (e == cudaSuccess) ctx->launches += 1;
+          if (e == cudaSuccess) e = cudaEventRecord(e1, sm);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e == cudaSuccess && ms < ms_best) ms_best = ms;
+        }
+        if (e == cudaSuccess && ms_best < best) { best = ms_best; best_ts = t; best_c = c; }
+      }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    if (best_ts == 0) {
+      pick_tiled<T>(ctx, ma.L, &ts, &C);
+    } else {
+      ts = best_ts;
+      C = best_c;
+    }
+    ctx->tuned[key] = std::make_pair(ts, C);
+  }
+  return timed(ctx, "mod_solve_fp64", 1, [&] { return launch_mod_tiled<T>(ma, ts, C, sm); });
+}
+
+// FP64 Cholesky + solve + renormalisation: the tiled cluster kernel unless an
+// option selects one of the other implementations.
 template <typename T>
 cudaError_t run_mod_solve(sdl_ctx *ctx, const ModArgs &ma) {
   cudaStream_t sm = ctx->stream;
   cudaError_t e = cudaErrorNotSupported;
-  // automatic choice: the cluster kernel spreads one subset over many SMs, which
-  // pays when there are too few subsets to fill the GPU with one block each
-  const bool want_cluster = ctx->opt_mod_solve == 1 ||
-                            (ctx->opt_mod_solve == 0 && (int64_t)ma.L * 2 < ctx->num_sms);
-  if (ma.K <= 512 && want_cluster)
-    e = timed(ctx, "mod_solve_fp64", 1, [&] { return launch_mod_solve_cluster<T>(ma, ctx->opt_cluster, sm); });
+  if (ctx->opt_mod_solve == 0 || ctx->opt_mod_solve == 3) return run_tiled_tuned<T>(ctx, ma);
+  if (ma.K <= 512 && ctx->opt_mod_solve == 1)
+    e = timed(ctx, "mod_solve_fp64", 1, [&] {
+      return launch_mod_solve_cluster<T>(ma, ctx->opt_cluster ? ctx->opt_cluster : 16, sm);
+    });
   if (e != cudaErrorNotSupported) return e;
   cudaGetLastError();
   e = timed(ctx, "chol_fp64", 1, [&] { return launch_mod_chol(ma, sm); });
@@ -244,7 +342,8 @@ size_t mod_ws_bytes(int L, int K, int m, int64_t n, int s) {
   b += round256(sizeof(int32_t) * (size_t)L * K);          // cursor
   b += round256(sizeof(int32_t) * (size_t)L * (K + 1));    // ptr
   b += 2 * round256(sizeof(int32_t) * (size_t)(n * s + 1));  // lsig, lslot
-  b += 2 * round256(sizeof(double) * (size_t)L * K * K);   // A, Lf
+  b += round256(sizeof(double) * (size_t)L * K * K);       // A
+  b += round256(sizeof(double) * mod_tiled_scratch_doubles(L, K, m));   // factor scratch
   b += round256(sizeof(double) * (size_t)L * K * m);       // B
   b += round256(sizeof(int32_t) * (size_t)L);              // status
   b += round256(sizeof(int32_t) * (size_t)L * K);          // usage scratch
@@ -271,7 +370,7 @@ sdl_status mod_prepare(sdl_ctx *ctx, ModArgs &a, const int64_t *offsets_h, int L
   a.lsig = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)(n * s + 1)));
   a.lslot = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)(n * s + 1)));
   a.A = static_cast<double *>(ws_alloc(ctx, sizeof(double) * (size_t)L * K * K));
-  a.Lf = static_cast<double *>(ws_alloc(ctx, sizeof(double) * (size_t)L * K * K));
+  a.Lf = static_cast<double *>(ws_alloc(ctx, sizeof(double) * mod_tiled_scratch_doubles(L, K, m)));
   a.B = static_cast<double *>(ws_alloc(ctx, sizeof(double) * (size_t)L * K * m));
   a.status = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)L));
   int32_t *us = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)L * K));
@@ -803,13 +902,22 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
   if (!ctx) return SDL_EINVAL;
   switch (option) {
     case SDL_OPT_MOD_SOLVE:
-      if (value < 0 || value > 2) return set_error(ctx, SDL_EINVAL, "SDL_OPT_MOD_SOLVE takes 0, 1 or 2");
+      if (value < 0 || value > 3) return set_error(ctx, SDL_EINVAL, "SDL_OPT_MOD_SOLVE takes 0, 1, 2 or 3");
       ctx->opt_mod_solve = (int)value;
       return SDL_OK;
     case SDL_OPT_CLUSTER:
-      if (value != 4 && value != 8 && value != 16)
-        return set_error(ctx, SDL_EINVAL, "SDL_OPT_CLUSTER takes 4, 8 or 16");
+      if (value < 0 || value > 16) return set_error(ctx, SDL_EINVAL, "SDL_OPT_CLUSTER takes 0 to 16");
       ctx->opt_cluster = (int)value;
+      return SDL_OK;
+    case SDL_OPT_MOD_TILE:
+      if (value != 0 && value != 16 && value != 32)
+        return set_error(ctx, SDL_EINVAL, "SDL_OPT_MOD_TILE takes 0, 16 or 32");
+      ctx->opt_tile = (int)value;
+      return SDL_OK;
+    case SDL_OPT_AUTOTUNE:
+      if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_AUTOTUNE takes 0 or 1");
+      ctx->opt_autotune = (int)value;
+      if (!value) ctx->tuned.clear();
       return SDL_OK;
     default:
       return set_error(ctx, SDL_EINVAL, "unknown option");

@@ -1,0 +1,474 @@
+// MOD solve (Sec. 1): D_U^T = (X X^T)_UU^{-1} (Y X^T)_U^T in FP64, with the
+// renormalisation of Sec. 3.1, for a batch of independent subsets.
+//
+// One thread-block cluster of C blocks per subset; the subset's matrices live in
+// an L2-resident scratch M of (K + m) rows x K columns:
+//   rows 0..K-1   the lower triangle of A = X X^T (overwritten by its factor L),
+//   rows K..K+m-1 the right-hand sides B^T (row r holds coordinate r of every
+//                 atom's B column), which the right-looking factorisation carries
+//                 along as extra rows: they end up as W = B^T L^{-T}.
+// The matrix is cut into TS x TS tiles.  Step k of the factorisation: every
+// tile below the diagonal tile (k, k) is multiplied by the inverse of its
+// factor (the panel); every trailing tile (i, j), j > k, subtracts
+// panel_i panel_j^T.  The block that updates tile (k+1, k+1) does so first,
+// factors and inverts it at once in its shared memory and pushes the inverse
+// (and the breakdown verdict) into every block of the cluster through
+// distributed shared memory, while the other blocks go on with their trailing
+// tiles; so the latency-bound diagonal factorisation runs once per step and
+// off the critical path of the other blocks.  The backward sweep then forms
+// X^T = W L^{-1} tile column by tile column from the kept inverses.  Each
+// step's tile tasks are dealt round-robin to the cluster's blocks, which load
+// the next task's tiles while multiplying the current one, and meet at a
+// cluster barrier between dependent steps.  Several clusters share each SM, so
+// one subset's barrier waits overlap another subset's tile products on the
+// FP64 pipe.
+//
+// Breakdown (a squared pivot <= 1e-12 of its original diagonal, or not
+// positive) restarts the factorisation once from A + lambda I on the used
+// atoms, lambda = 1e-10 tr(A_UU) / |U|.  Unused atoms carry the identity row in
+// A and their previous value in B, so they come back unchanged and are not
+// renormalised.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "sdl_internal.cuh"
+
+namespace sdl {
+namespace {
+
+constexpr int kTThreads = 256;
+
+template <int TS>
+struct TiledSmem {
+  double a[TS][TS + 1];      // A operand; the diagonal factor during factor_diag
+  double b[TS][TS + 1];      // B operand; the inverse during factor_diag
+  double v[2][TS + 0][TS + 1];   // inverses of diagonal factors k (v[k & 1]), pushed by their owner
+  double invd[TS];
+  double dg[TS];
+  int fail;
+  int verdict[2];            // breakdown verdict of diagonal tile k (verdict[k & 1]), pushed by its owner
+};
+
+struct TGeom {
+  int K, m, R, RT, TS;
+  __device__ int64_t row(int i, int r) const {
+    return i < R ? (int64_t)i * TS + r : (int64_t)K + (int64_t)(i - R) * TS + r;
+  }
+  __device__ int rows_in(int i) const {
+    const int v = i < R ? K - i * TS : m - (i - R) * TS;
+    return v < TS ? v : TS;
+  }
+  __device__ int cols_in(int j) const {
+    const int v = K - j * TS;
+    return v < TS ? v : TS;
+  }
+};
+
+// A TS x TS operand in global memory: p[r * ld + c] for r < nr, c < nc, zero
+// elsewhere.
+struct Opnd {
+  const double *p;
+  int ld, nr, nc;
+};
+
+template <int TS>
+__device__ __forceinline__ Opnd tile_of(const double *Mt, const TGeom &g, int i, int j) {
+  return Opnd{Mt + g.row(i, 0) * g.K + (int64_t)j * TS, g.K, g.rows_in(i), g.cols_in(j)};
+}
+
+// One tile task: out (=|-=) A B^T with B staged as given (bt: from the
+// transpose of its source; bsm: B is the inverse held in shared memory).
+struct TileTask {
+  Opnd a, b, o;
+  bool bt, bsm, sub, lower;
+};
+
+// Thread-to-element map shared by the loads, the products and the stores:
+// element u of this thread is (tid / TS + (256 / TS) u, tid mod TS).
+template <int TS>
+__device__ __forceinline__ void fetch(const Opnd &o, double (&r)[TS * TS / kTThreads]) {
+  constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
+  const int cc = threadIdx.x % TS, r0 = threadIdx.x / TS;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int rr = r0 + RS * u;
+    r[u] = (rr < o.nr && cc < o.nc) ? __ldcg(o.p + (int64_t)rr * o.ld + cc) : 0.0;
+  }
+}
+template <int TS>
+__device__ __forceinline__ void commit(double (*S)[TS + 1], const double (&r)[TS * TS / kTThreads], bool t) {
+  constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
+  const int cc = threadIdx.x % TS, r0 = threadIdx.x / TS;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (t) S[cc][r0 + RS * u] = r[u];
+    else S[r0 + RS * u][cc] = r[u];
+  }
+}
+
+// For this thread's outputs (r_u, c): acc[u] = sum_q As[r_u][q] Bs[c][q], or,
+// with sub, acc[u] = old[u] - sum_q As[r_u][q] Bs[c][q] (the subtraction folded
+// into the fused multiply-adds).
+template <int TS>
+__device__ __forceinline__ void tile_product(const double (*As)[TS + 1], const double (*Bs)[TS + 1], bool sub,
+                                             const double (&old)[TS * TS / kTThreads],
+                                             double (&acc)[TS * TS / kTThreads]) {
+  constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
+  const int c = threadIdx.x % TS, r0 = threadIdx.x / TS;
+#pragma unroll
+  for (int u = 0; u < U; ++u) acc[u] = sub ? old[u] : 0.0;
+  if (sub) {
+#pragma unroll 8
+    for (int q = 0; q < TS; ++q) {
+      const double bv = Bs[c][q];
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u] = fma(-As[r0 + RS * u][q], bv, acc[u]);
+    }
+  } else {
+#pragma unroll 8
+    for (int q = 0; q < TS; ++q) {
+      const double bv = Bs[c][q];
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u] = fma(As[r0 + RS * u][q], bv, acc[u]);
+    }
+  }
+}
+
+template <int TS>
+__device__ __forceinline__ void put(const TileTask &t, const double (&acc)[TS * TS / kTThreads]) {
+  constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
+  const int c = threadIdx.x % TS, r0 = threadIdx.x / TS;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int r = r0 + RS * u;
+    if (r < t.o.nr && c < t.o.nc && (!t.lower || c <= r))
+      const_cast<double *>(t.o.p)[(int64_t)r * t.o.ld + c] = acc[u];
+  }
+}
+
+// Run tasks first, first + C, ... < n of one step; the operands (and the old
+// output) of the next task are loaded into registers while the current one is
+// multiplied.  Tasks of one step never read a tile another task of the step
+// writes.  vs: the inverse used by tasks whose B operand is in shared memory.
+template <int TS, class Desc>
+__device__ __forceinline__ void run_step(TiledSmem<TS> &sm, const double (*vs)[TS + 1], int n, int first, int C,
+                                         Desc desc) {
+  constexpr int U = TS * TS / kTThreads;
+  if (first >= n) return;
+  TileTask cur = desc(first);
+  double ra[U], rb[U], ro[U];
+  fetch<TS>(cur.a, ra);
+  if (!cur.bsm) fetch<TS>(cur.b, rb);
+  if (cur.sub) fetch<TS>(cur.o, ro);
+  for (int q = first; q < n; q += C) {
+    __syncthreads();
+    commit<TS>(sm.a, ra, false);
+    if (!cur.bsm) commit<TS>(sm.b, rb, cur.bt);
+    __syncthreads();
+    const bool more = q + C < n;
+    TileTask nxt = cur;
+    double rn[U];
+    if (more) {
+      nxt = desc(q + C);
+      fetch<TS>(nxt.a, ra);
+      if (!nxt.bsm) fetch<TS>(nxt.b, rb);
+      if (nxt.sub) fetch<TS>(nxt.o, rn);
+    }
+    double acc[U];
+    tile_product<TS>(sm.a, cur.bsm ? vs : sm.b, cur.sub, ro, acc);
+    put<TS>(cur, acc);
+    if (more) {
+      cur = nxt;
+#pragma unroll
+      for (int u = 0; u < U; ++u) ro[u] = rn[u];
+    }
+  }
+}
+
+template <int TS>
+__device__ __forceinline__ void pivot(TiledSmem<TS> &sm, int c, double d) {
+  if (!(d > kModPivotRel * sm.dg[c]) || !(d > 0.0)) {
+    sm.fail = 1;
+    return;
+  }
+  const double inv = rsqrt(d);
+  sm.a[c][c] = d * inv;
+  sm.invd[c] = inv;
+}
+
+// Factor the diagonal tile (k, k) into sm.a and invert the factor into sm.b
+// (zero above the diagonal, identity on padding).  Returns false on breakdown.
+template <int TS>
+__device__ bool factor_diag(TiledSmem<TS> &sm, const double *Mt, const TGeom &g, int k, const double *At,
+                            const int32_t *ut, double ridge) {
+  const int tid = threadIdx.x;
+  const int nb = g.cols_in(k);
+  const int64_t base = (int64_t)k * TS;
+  __syncthreads();
+  for (int e = tid; e < TS * TS; e += kTThreads) {
+    const int r = e / TS, c = e % TS;
+    double v;
+    if (r < nb && c < nb) v = c <= r ? __ldcg(Mt + (base + r) * g.K + base + c) : 0.0;
+    else v = r == c ? 1.0 : 0.0;
+    sm.a[r][c] = v;
+    sm.b[r][c] = r == c ? 1.0 : 0.0;
+  }
+  if (tid < TS)
+    sm.dg[tid] = tid < nb ? At[(base + tid) * g.K + base + tid] + (ut[base + tid] > 0 ? ridge : 0.0) : 1.0;
+  if (tid == 0) sm.fail = 0;
+  __syncthreads();
+  if (tid == 0) pivot(sm, 0, sm.a[0][0]);
+  __syncthreads();
+  for (int c = 0; c < TS; ++c) {
+    if (sm.fail) break;   // uniform: read after a barrier
+    if (tid > c && tid < TS) sm.a[tid][c] *= sm.invd[c];
+    __syncthreads();
+    // rank-1 update of the trailing triangle; the thread that updates the next
+    // diagonal entry takes its pivot
+    for (int e = tid; e < TS * TS; e += kTThreads) {
+      const int r = e / TS, q = e % TS;
+      if (q > c && q <= r) {
+        const double v = fma(-sm.a[r][c], sm.a[q][c], sm.a[r][q]);
+        if (r == c + 1 && q == c + 1) pivot(sm, c + 1, v);
+        else sm.a[r][q] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (sm.fail) return false;
+  // inverse: column-oriented forward substitution of L V = I
+  for (int q = 0; q < TS; ++q) {
+    if (tid <= q) sm.b[q][tid] *= sm.invd[q];
+    __syncthreads();
+    for (int e = tid; e < TS * TS; e += kTThreads) {
+      const int r = e / TS, j = e % TS;
+      if (r > q && j <= q) sm.b[r][j] = fma(-sm.a[r][q], sm.b[q][j], sm.b[r][j]);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+template <typename T, int TS>
+__global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *__restrict__ A,
+                                                                 const double *__restrict__ B,
+                                                                 const int32_t *__restrict__ usage, int K, int m,
+                                                                 int C, double *M, double *V, T *D,
+                                                                 int32_t *status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ TiledSmem<TS> sm;
+  __shared__ double red[2][kTThreads / 32];
+  const int rank = (int)cl.block_rank();
+  const int t = blockIdx.x / C;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  TGeom g;
+  g.K = K; g.m = m; g.TS = TS;
+  g.R = (K + TS - 1) / TS;
+  g.RT = g.R + (m + TS - 1) / TS;
+  const int R = g.R, RT = g.RT, Rm = RT - R;
+  const double *At = A + (size_t)t * K * K;
+  const double *Bt = B + (size_t)t * K * m;
+  const int32_t *ut = usage + (size_t)t * K;
+  double *Mt = M + (size_t)t * (K + m) * K;
+  double *Vt = V + (size_t)t * R * TS * TS;
+
+  double tr = 0.0, nu = 0.0;
+  for (int j = tid; j < K; j += kTThreads)
+    if (ut[j] > 0) { tr += At[(size_t)j * K + j]; nu += 1.0; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    nu += __shfl_xor_sync(0xffffffffu, nu, o);
+  }
+  if (lane == 0) { red[0][warp] = tr; red[1][warp] = nu; }
+  __syncthreads();
+  double T0 = 0.0, N0 = 0.0;
+  for (int w = 0; w < kTThreads / 32; ++w) { T0 += red[0][w]; N0 += red[1][w]; }
+  const double lambda = N0 > 0.0 ? kModRidge * T0 / N0 : 0.0;
+
+  // Factor diagonal tile kk, keep its inverse for the backward sweep and push
+  // inverse and verdict into every block of the cluster.
+  double ridge = 0.0;
+  auto own_diag = [&](int kk) {
+    const bool ok = factor_diag<TS>(sm, Mt, g, kk, At, ut, ridge);
+    const int par = kk & 1;
+    for (int r2 = 0; r2 < C; ++r2) {
+      double *dst = &cl.map_shared_rank(&sm.v[0][0][0], r2)[(size_t)par * TS * (TS + 1)];
+      for (int e = tid; e < TS * TS; e += kTThreads) dst[(e / TS) * (TS + 1) + e % TS] = sm.b[e / TS][e % TS];
+      if (tid == 0) cl.map_shared_rank(&sm.verdict[0], r2)[par] = ok ? 0 : 1;
+    }
+    for (int e = tid; e < TS * TS; e += kTThreads) Vt[(size_t)kk * TS * TS + e] = sm.b[e / TS][e % TS];
+  };
+
+  int st = 2;
+  bool failed = true;
+  for (int attempt = 0; attempt < 2 && failed; ++attempt) {
+    ridge = attempt == 0 ? 0.0 : lambda;
+    // M <- [lower(A) + ridge on used diagonal entries; B^T]
+    const int64_t total = (int64_t)(K + m) * K;
+    for (int64_t q = (int64_t)rank * kTThreads + tid; q < total; q += (int64_t)C * kTThreads) {
+      const int r = (int)(q / K), c = (int)(q % K);
+      if (r < K) {
+        if (c <= r) Mt[q] = At[(size_t)r * K + c] + ((r == c && ut[r] > 0) ? ridge : 0.0);
+      } else {
+        Mt[q] = Bt[(size_t)c * m + (r - K)];
+      }
+    }
+    cl.sync();
+    // diagonal tile 0: factored by block 0, its inverse and verdict pushed to every block
+    if (rank == 0) own_diag(0);
+    cl.sync();
+    failed = false;
+    for (int k = 0; k < R; ++k) {
+      if (sm.verdict[k & 1]) { failed = true; break; }   // uniform: every block holds the pushed verdict
+      const double (*vk)[TS + 1] = sm.v[k & 1];
+      // panel: tile (i, k) <- tile (i, k) V_k^T for every tile row below k
+      run_step<TS>(sm, vk, RT - k - 1, rank, C, [&](int q) {
+        const Opnd p = tile_of<TS>(Mt, g, k + 1 + q, k);
+        return TileTask{p, p, p, false, true, false, false};
+      });
+      cl.sync();
+      // trailing: tile (i, j) -= panel_i panel_j^T, k < j <= i, j a column of A.
+      // Task q enumerates (i, j) row by row (row i holds min(i, R - 1) - k
+      // tasks), so task 0 is the next diagonal tile; its owner takes it first,
+      // factors it at once and pushes the inverse while the other blocks go on
+      // with their trailing tiles.
+      const int ntr = (R - k - 1) * (R - k) / 2 + Rm * (R - k - 1);
+      auto trail = [&](int q) {
+        int i = k + 1, w = 1;
+        while (q >= w) {
+          q -= w;
+          ++i;
+          w = (i < R ? i : R - 1) - k;
+        }
+        const int j = k + 1 + q;
+        return TileTask{tile_of<TS>(Mt, g, i, k), tile_of<TS>(Mt, g, j, k), tile_of<TS>(Mt, g, i, j), false, false,
+                        true, i == j};
+      };
+      if (ntr > 0) {
+        const int owner = (k + 1) % C;
+        const int first = (rank - owner + C) % C;
+        if (rank == owner) {
+          run_step<TS>(sm, vk, 1, 0, C, trail);
+          __syncthreads();   // the updated diagonal tile is in global memory
+          own_diag(k + 1);
+          run_step<TS>(sm, vk, ntr, C, C, trail);
+        } else {
+          run_step<TS>(sm, vk, ntr, first, C, trail);
+        }
+      }
+      cl.sync();
+    }
+    if (!failed) st = attempt;
+    cl.sync();
+  }
+
+  if (!failed) {
+    // backward sweep on the right-hand-side rows: X^T = W L^{-1}
+    for (int k = R - 1; k >= 0; --k) {
+      run_step<TS>(sm, sm.v[0], Rm, rank, C, [&](int q) {
+        const Opnd w = tile_of<TS>(Mt, g, R + q, k);
+        return TileTask{w, Opnd{Vt + (size_t)k * TS * TS, TS, TS, TS}, w, true, false, false, false};
+      });
+      cl.sync();
+      if (k > 0)
+        run_step<TS>(sm, sm.v[0], Rm * k, rank, C, [&](int q) {
+          const int rb = q / k, i = q % k;
+          return TileTask{tile_of<TS>(Mt, g, R + rb, k), tile_of<TS>(Mt, g, k, i), tile_of<TS>(Mt, g, R + rb, i),
+                          true, false, true, false};
+        });
+      cl.sync();
+    }
+    // renormalise the used atoms (atom j = column j of the right-hand-side rows)
+    for (int j = rank * kTThreads + tid; j < K; j += C * kTThreads) {
+      if (ut[j] == 0) continue;   // unused: keeps the previous atom
+      const double *xj = Mt + (size_t)K * K + j;
+      double n2 = 0.0;
+      for (int r = 0; r < m; ++r) {
+        const double v = __ldcg(xj + (size_t)r * K);
+        n2 = fma(v, v, n2);
+      }
+      const double nrm = sqrt(n2);
+      if (!(nrm > 0.0) || !isfinite(nrm)) continue;
+      const double inv = 1.0 / nrm;
+      T *dj = D + ((size_t)t * K + j) * m;
+      for (int r = 0; r < m; ++r) dj[r] = (T)(__ldcg(xj + (size_t)r * K) * inv);
+    }
+  }
+  if (rank == 0 && tid == 0) status[t] = st;
+}
+
+}  // namespace
+
+size_t mod_tiled_scratch_doubles(int L, int K, int m) {
+  const int R = (K + 15) / 16;   // the smaller tile needs the most inverse blocks
+  return (size_t)L * ((size_t)(K + m) * K + (size_t)R * 16 * 16 + (size_t)((K + 31) / 32) * 32 * 32);
+}
+
+template <typename T, int TS>
+static cudaError_t launch_tiled_ts(const ModArgs &a, int C, cudaStream_t st) {
+  auto kern = mod_tiled_kernel<T, TS>;
+  cudaError_t e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((int64_t)a.L * C));
+  cfg.blockDim = dim3(kTThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  double *M = a.Lf;
+  double *V = a.Lf + (size_t)a.L * (a.K + a.m) * a.K;
+  return cudaLaunchKernelEx(&cfg, kern, (const double *)a.A, (const double *)a.B, (const int32_t *)a.usage, a.K,
+                            a.m, C, M, V, static_cast<T *>(a.D), a.status);
+}
+
+template <typename T>
+int mod_tiled_max_clusters(int ts, int C, int K, int m) {
+  auto kern = ts == 16 ? mod_tiled_kernel<T, 16> : mod_tiled_kernel<T, 32>;
+  if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)C);
+  cfg.blockDim = dim3(kTThreads);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  (void)K;
+  (void)m;
+  return n;
+}
+
+template <typename T>
+cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, cudaStream_t st) {
+  if (a.L <= 0) return cudaSuccess;
+  if (C < 1 || C > 16 || (ts != 16 && ts != 32)) return cudaErrorInvalidValue;
+  return ts == 16 ? launch_tiled_ts<T, 16>(a, C, st) : launch_tiled_ts<T, 32>(a, C, st);
+}
+
+template cudaError_t launch_mod_tiled<float>(const ModArgs &, int, int, cudaStream_t);
+template cudaError_t launch_mod_tiled<double>(const ModArgs &, int, int, cudaStream_t);
+template int mod_tiled_max_clusters<float>(int, int, int, int);
+template int mod_tiled_max_clusters<double>(int, int, int, int);
+
+}  // namespace sdl

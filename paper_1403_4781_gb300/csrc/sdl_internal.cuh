@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -63,8 +64,12 @@ struct sdl_ctx {
   int32_t *h_status = nullptr;   // pinned host word for device status read-back
   int64_t launches = 0;          // kernels launched by this context
   sdl::Prof prof;
-  int opt_mod_solve = 0;         // 0 auto, 1 cluster, 2 block per subset
-  int opt_cluster = 16;
+  int opt_mod_solve = 0;         // 0 auto, 1 DSMEM cluster, 2 block per subset, 3 tiled
+  int opt_cluster = 0;           // 0 = automatic
+  int opt_tile = 0;              // tiled solve: 16, 32 or 0 = automatic
+  std::map<int64_t, int> occ;    // cached max active clusters of the tiled solve
+  int opt_autotune = 1;          // time candidate launch shapes on first use
+  std::map<std::string, std::pair<int, int>> tuned;   // shape key -> chosen (tile, cluster)
 };
 
 namespace sdl {
@@ -154,6 +159,14 @@ cudaError_t launch_mod_normalise(const ModArgs &a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_mod_solve_cluster(const ModArgs &a, int cluster, cudaStream_t st);
 int mod_tile_signals();
+// Tiled FP64 factorisation + solve + renormalisation, one cluster of C (1..16)
+// blocks per subset, TS x TS tiles (16 or 32); scratch in a.Lf of
+// mod_tiled_scratch_doubles(L, K, m) doubles.
+template <typename T>
+cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, cudaStream_t st);
+template <typename T>
+int mod_tiled_max_clusters(int ts, int C, int K, int m);
+size_t mod_tiled_scratch_doubles(int L, int K, int m);
 
 template <typename T>
 cudaError_t launch_split(const T *Y, int m, int64_t N, const int64_t *perm, T *Yp, cudaStream_t st);

@@ -1,0 +1,130 @@
+"""The FP64 MOD solve implementations against the oracle's MOD (Sec. 1:
+D = Y X^T (X X^T)^{-1} over the used atoms, then unit columns, Sec. 3.1).
+
+Every implementation the context can select is forced in turn: the tiled
+cluster solve with each tile edge and cluster size (ragged shapes whose K and m
+are not multiples of the tile), the distributed-shared-memory cluster solve and
+the one-block factorisation + separate solve; the autotuned default is checked
+for a cached, repeatable choice.  FP64 path: atoms within 1e-10 absolute (unit
+atoms, condition numbers of these normal equations below 1e3); FP32 path:
+2e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1403_4781_gb300 as sdl
+import sdl_inputs as si
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.fixture
+def ctx():
+    c = sdl.context(0)
+    yield c
+    c.set_option(sdl.OPT_MOD_SOLVE, 0)
+    c.set_option(sdl.OPT_CLUSTER, 0)
+    c.set_option(sdl.OPT_MOD_TILE, 0)
+    c.set_option(sdl.OPT_AUTOTUNE, 1)
+
+
+def _problem(seed, sizes, m, K, s, dtype, unused=3):
+    rng = np.random.default_rng(seed)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offsets[-1])
+    Y = rng.standard_normal((n, m)).astype(dtype)
+    hi = K - unused                                # the last `unused` atoms stay unused
+    idx = np.stack([rng.choice(hi, s, replace=False) for _ in range(n)]).astype(np.int32)
+    val = rng.standard_normal((n, s)).astype(dtype)
+    idx[::5, -1] = -1                              # ragged nnz
+    val[::5, -1] = 0
+    D0 = np.stack([si.unit_gaussian_atoms(rng, m, K) for _ in sizes]).astype(dtype)
+    return offsets, Y, idx, val, D0
+
+
+def _oracle_batched(offsets, Y, idx, val, D0):
+    out = []
+    for t in range(len(offsets) - 1):
+        a, b = offsets[t], offsets[t + 1]
+        Do, _, _, st = oracle.mod(Y[a:b].astype(np.float64), idx[a:b], val[a:b].astype(np.float64),
+                                  D0[t].astype(np.float64), True)
+        assert st == 0
+        out.append(Do)
+    return np.stack(out)
+
+
+def _run(ctx, path, ts, C, offsets, Y, idx, val, D0):
+    ctx.set_option(sdl.OPT_MOD_SOLVE, path)
+    ctx.set_option(sdl.OPT_MOD_TILE, ts)
+    ctx.set_option(sdl.OPT_CLUSTER, C)
+    Dg = _t(D0.copy())
+    sdl.mod_update_batched(_t(Y), offsets, _t(idx), _t(val), Dg)
+    return Dg.cpu().numpy()
+
+
+@pytest.mark.parametrize("K,m,s", [(60, 30, 4), (97, 33, 5), (256, 64, 6)])
+@pytest.mark.parametrize("ts,C", [(16, 1), (16, 3), (16, 16), (32, 1), (32, 2), (32, 8), (32, 16)])
+def test_tiled_solve_fp64_matches_oracle(ctx, ts, C, K, m, s):
+    offsets, Y, idx, val, D0 = _problem(300 + K, [3 * K, 5 * K, 4 * K], m, K, s, np.float64)
+    want = _oracle_batched(offsets, Y, idx, val, D0)
+    got = _run(ctx, 3, ts, C, offsets, Y, idx, val, D0)
+    np.testing.assert_array_equal(got[:, K - 3:], D0[:, K - 3:])   # unused atoms: bit-exact
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("ts,C", [(16, 1), (16, 4), (32, 2)])
+def test_tiled_solve_ridge_retry(ctx, ts, C):
+    """Atoms 0 and 1 always appear together with equal coefficients, so
+    X X^T is singular and the factorisation breaks down; the retry with
+    A + lambda I on the used atoms matches the oracle, which takes the same
+    retry."""
+    rng = np.random.default_rng(301)
+    m, K, n = 6, 5, 50
+    Y = rng.standard_normal((n, m))
+    third = rng.integers(2, K, size=n)
+    idx = np.stack([np.zeros(n), np.ones(n), third], axis=1).astype(np.int32)
+    c = rng.standard_normal(n)
+    val = np.stack([c, c, rng.standard_normal(n)], axis=1)
+    Dprev = si.unit_gaussian_atoms(rng, m, K)
+    Do, _, ridge, st = oracle.mod(Y, idx, val, Dprev, True)
+    assert ridge and st == 0
+    got = _run(ctx, 3, ts, C, np.array([0, n], np.int64), Y, idx, val, Dprev[None])
+    np.testing.assert_allclose(got[0], Do, atol=1e-5)
+
+
+def test_tiled_solve_merge_shape_K1024(ctx):
+    """One subset with K=1024, m=256 (the large image-patch merge shape), 32 x 32
+    tiles over a cluster of 16 blocks, FP32 atoms."""
+    offsets, Y, idx, val, D0 = _problem(302, [6000], 256, 1024, 4, np.float32, unused=0)
+    want = _oracle_batched(offsets, Y, idx, val, D0)
+    got = _run(ctx, 3, 32, 16, offsets, Y, idx, val, D0)
+    np.testing.assert_allclose(got, want, rtol=0, atol=2e-5)
+
+
+def test_all_paths_agree_fp32(ctx):
+    offsets, Y, idx, val, D0 = _problem(303, [700, 512, 1100, 900], 64, 256, 3, np.float32)
+    want = _oracle_batched(offsets, Y, idx, val, D0)
+    for path in (1, 2, 3):
+        got = _run(ctx, path, 0, 0, offsets, Y, idx, val, D0)
+        np.testing.assert_allclose(got, want, rtol=0, atol=2e-5, err_msg=f"path {path}")
+
+
+def test_autotuned_choice_matches_oracle(ctx):
+    """The first call tunes (every candidate runs on the call's inputs), later
+    calls reuse the cached choice; all agree with the oracle.  Repeated calls
+    agree to rounding level, not bit for bit: the accumulation of A and B
+    visits each atom's signals in an order set by atomics."""
+    offsets, Y, idx, val, D0 = _problem(304, [800, 900, 1000, 700, 600], 64, 128, 4, np.float64)
+    ctx.set_option(sdl.OPT_AUTOTUNE, 0)
+    ctx.set_option(sdl.OPT_AUTOTUNE, 1)
+    want = _oracle_batched(offsets, Y, idx, val, D0)
+    for _ in range(3):
+        got = _run(ctx, 0, 0, 0, offsets, Y, idx, val, D0)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-10)

@@ -47,8 +47,8 @@ def test_mod_update_matches_oracle(dtype, atol):
     np.testing.assert_allclose(Dgn, Do, rtol=0, atol=atol)
 
 
-def test_mod_update_large_K_three_kernel_path():
-    """K > 512 takes the one-block-per-subset Cholesky / solve / normalise path."""
+def test_mod_update_large_K():
+    """K = 600, beyond the distributed-shared-memory cluster solve's limit."""
     rng = np.random.default_rng(205)
     m, K, n, s = 32, 600, 6000, 4
     Y = rng.standard_normal((n, m)).astype(np.float32)
