@@ -20,9 +20,10 @@ using namespace omp_detail;
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kJBlock = 256;   // atoms per GEMM pass (8 per lane)
+constexpr int kJBlock = 256;   // atoms per GEMM pass (8 per lane: lane + 32 c)
 constexpr int kKChunk = 16;    // signal entries per GEMM stage
-constexpr int kStagePitch = kJBlock + 1;   // conflict-free transposed staging
+constexpr int kDPitch = 20;    // staged atom row pitch (floats): 5 x 16 bytes, so the
+                               // 16-byte loads of lanes 0..7 hit distinct bank groups
 
 // ---------------------------------------------------------------- Gram ------
 // G_t = D_t D_t^T for D_t stored [K][m]; one 64x64 tile of G per block.
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const T *__restrict__ D, int 
 // Shared-memory carve-up of one CUDA-core OMP block.
 struct OmpLayout {
   int TS, K, m, s, lp;   // lp: odd row pitch of the per-warp Cholesky factor
+  int yp;                // signal row pitch in shared memory (m rounded up to 16, zero padded)
   bool gcache;
   size_t a0, yt, uni, ls, total;
 };
@@ -85,10 +87,11 @@ __host__ __device__ inline OmpLayout omp_layout(int TS, int K, int m, int s, boo
   OmpLayout L{};
   L.TS = TS; L.K = K; L.m = m; L.s = s; L.gcache = gcache;
   L.lp = odd_pitch(s);
+  L.yp = (m + kKChunk - 1) / kKChunk * kKChunk;
   size_t off = 0;
   L.a0 = off;  off += align16(sizeof(T) * (size_t)TS * K);
-  L.yt = off;  off += align16(sizeof(T) * (size_t)TS * m);
-  const size_t stage = sizeof(T) * (size_t)kKChunk * kStagePitch;
+  L.yt = off;  off += align16(sizeof(T) * (size_t)TS * L.yp);
+  const size_t stage = sizeof(T) * (size_t)kJBlock * kDPitch;
   const size_t gcol = gcache ? sizeof(T) * (size_t)kWarps * s * K : 0;
   L.uni = off; off += align16(stage > gcol ? stage : gcol);
   L.ls = off;  off += align16(sizeof(T) * (size_t)kWarps * s * L.lp);
@@ -96,15 +99,23 @@ __host__ __device__ inline OmpLayout omp_layout(int TS, int K, int m, int s, boo
   return L;
 }
 
+// 16-byte shared/global vector of four T.
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+
 // One block codes a tile of TS = 4 * 8 signals of one subset: the correlation
-// tile alpha0 = Y_tile D^T is a register-tiled FFMA GEMM staged through shared
-// memory, then each warp runs the selection loop for its 4 signals.
-template <typename T, int KPL>
-__global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay) {
+// tile alpha0 = Y_tile D^T is a register-tiled FFMA GEMM (4 signals x 8 atoms
+// per thread) over D staged in chunks of 16 signal entries, read back as
+// 4-entry vectors; then each warp runs the selection loop for its 4 signals.
+template <typename T, int KPL, int MU>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (KPL <= 16 ? 3 : 2) : 1) omp_kernel(OmpArgs a, OmpLayout lay) {
   extern __shared__ __align__(16) unsigned char smem[];
+  using V4 = typename Vec4<T>::type;
   constexpr int SPW = 4;
   const int TS = SPW * kWarps;
-  const int K = a.K, m = a.m, s = a.s;
+  const int K = a.K, m = a.m;
+  const int yp = lay.yp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   const int64_t g = blockIdx.x;
@@ -118,15 +129,18 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay)
   const T *__restrict__ Y = static_cast<const T *>(a.Y);
 
   T *a0 = reinterpret_cast<T *>(smem + lay.a0);     // [TS][K]
-  T *yt = reinterpret_cast<T *>(smem + lay.yt);     // [TS][m]
-  T *uni = reinterpret_cast<T *>(smem + lay.uni);   // GEMM stage / G columns [warps][s][K]
+  T *yt = reinterpret_cast<T *>(smem + lay.yt);     // [TS][yp], zero beyond m
+  T *uni = reinterpret_cast<T *>(smem + lay.uni);   // GEMM stage [256][kDPitch] / G columns [warps][s][K]
 
-  for (int q = threadIdx.x; q < TS * m; q += kThreads) {
-    const int sig = q / m, r = q - sig * m;
-    yt[q] = sig < nsig ? Y[(size_t)(row0 + sig) * m + r] : T(0);
+  for (int q = threadIdx.x; q < TS * yp; q += kThreads) {
+    const int sig = q / yp, r = q - sig * yp;
+    yt[q] = (sig < nsig && r < m) ? Y[(size_t)(row0 + sig) * m + r] : T(0);
   }
+  // 16-byte global loads of D rows need m a multiple of 4 (D itself is
+  // 16-byte aligned)
+  const bool vec = (m & 3) == 0;
 
-  // ---- alpha0[sig][j] = <y_sig, d_j>: register tile SPW signals x 8 atoms per thread
+  // ---- alpha0[sig][j] = <y_sig, d_j>
   for (int jb = 0; jb < K; jb += kJBlock) {
     T acc[SPW][8];
 #pragma unroll
@@ -135,23 +149,40 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay)
       for (int c = 0; c < 8; ++c) acc[r][c] = T(0);
     for (int k0 = 0; k0 < m; k0 += kKChunk) {
       __syncthreads();
-      for (int q = threadIdx.x; q < kKChunk * kJBlock; q += kThreads) {
-        const int jj = q / kKChunk, kk = q - jj * kKChunk;
-        const int gj = jb + jj, gk = k0 + kk;
-        uni[kk * kStagePitch + jj] = (gj < K && gk < m) ? Dt[(size_t)gj * m + gk] : T(0);
+      {   // thread jj stages entries k0 .. k0+15 of atom jb + jj (zero outside D)
+        const int jj = threadIdx.x, gj = jb + jj;
+        T *dst = uni + jj * kDPitch;
+        const T *src = Dt + (size_t)gj * m + k0;
+        if (vec) {
+#pragma unroll
+          for (int e = 0; e < kKChunk; e += 4) {
+            V4 v;
+            if (gj < K && k0 + e < m) v = *reinterpret_cast<const V4 *>(src + e);
+            else v.x = v.y = v.z = v.w = T(0);
+            *reinterpret_cast<V4 *>(dst + e) = v;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < kKChunk; ++e) dst[e] = (gj < K && k0 + e < m) ? src[e] : T(0);
+        }
       }
       __syncthreads();
-      const int kmax = (m - k0) < kKChunk ? (m - k0) : kKChunk;
-      for (int kk = 0; kk < kmax; ++kk) {
-        T yv[SPW], dv[8];
+#pragma unroll 1
+      for (int kq = 0; kq < kKChunk; kq += 4) {
+        V4 yv[SPW];
 #pragma unroll
-        for (int r = 0; r < SPW; ++r) yv[r] = yt[(warp * SPW + r) * m + k0 + kk];
+        for (int r = 0; r < SPW; ++r) yv[r] = *reinterpret_cast<const V4 *>(yt + (warp * SPW + r) * yp + k0 + kq);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) dv[c] = uni[kk * kStagePitch + lane + 32 * c];
+        for (int c = 0; c < 8; ++c) {
+          const V4 dv = *reinterpret_cast<const V4 *>(uni + (lane + 32 * c) * kDPitch + kq);
 #pragma unroll
-        for (int r = 0; r < SPW; ++r)
-#pragma unroll
-          for (int c = 0; c < 8; ++c) acc[r][c] = fma(yv[r], dv[c], acc[r][c]);
+          for (int r = 0; r < SPW; ++r) {
+            acc[r][c] = fma(yv[r].x, dv.x, acc[r][c]);
+            acc[r][c] = fma(yv[r].y, dv.y, acc[r][c]);
+            acc[r][c] = fma(yv[r].z, dv.z, acc[r][c]);
+            acc[r][c] = fma(yv[r].w, dv.w, acc[r][c]);
+          }
+        }
       }
     }
 #pragma unroll
@@ -164,9 +195,9 @@ __global__ void __launch_bounds__(kThreads) omp_kernel(OmpArgs a, OmpLayout lay)
   }
   __syncthreads();   // staging is dead from here; the union holds G columns
 
-  T *Ls = reinterpret_cast<T *>(smem + lay.ls) + (size_t)warp * s * lay.lp;
-  code_warp_signals<T, KPL, false>(a, a0, yt, warp * SPW, SPW, nsig, row0, Dt, Gt, Ls, Ls,
-                                   uni + (size_t)warp * s * K, lay.lp, lay.gcache);
+  T *Ls = reinterpret_cast<T *>(smem + lay.ls) + (size_t)warp * a.s * lay.lp;
+  code_warp_signals<T, KPL, MU, false>(a, a0, yt, yp, warp * SPW, SPW, nsig, row0, Dt, Gt, Ls, Ls,
+                                       uni + (size_t)warp * a.s * K, lay.lp, lay.gcache);
 }
 
 }  // namespace
@@ -182,9 +213,9 @@ cudaError_t launch_gram(const T *D, int m, int K, int L, T *G, cudaStream_t st) 
 
 int omp_tile_signals() { return 32; }
 
-template <typename T, int KPL>
+template <typename T, int KPL, int MU>
 static cudaError_t launch_omp_kpl(const OmpArgs &a, const OmpLayout &lay, cudaStream_t st) {
-  auto kern = omp_kernel<T, KPL>;
+  auto kern = omp_kernel<T, KPL, MU>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)a.total_tiles, kThreads, lay.total, st>>>(a, lay);
@@ -203,10 +234,16 @@ cudaError_t launch_omp(const OmpArgs &a, int num_sms, cudaStream_t st) {
   if (lay.total > 112 * 1024) lay = omp_layout<T>(TS, a.K, a.m, a.s, false);
   if (lay.total > limit) return cudaErrorInvalidConfiguration;
   const int kpl = (a.K + 31) / 32;
-  if (kpl <= 4) return launch_omp_kpl<T, 4>(a, lay, st);
-  if (kpl <= 8) return launch_omp_kpl<T, 8>(a, lay, st);
-  if (kpl <= 16) return launch_omp_kpl<T, 16>(a, lay, st);
-  return launch_omp_kpl<T, 32>(a, lay, st);
+  if (a.m <= 64) {
+    if (kpl <= 4) return launch_omp_kpl<T, 4, 2>(a, lay, st);
+    if (kpl <= 8) return launch_omp_kpl<T, 8, 2>(a, lay, st);
+    if (kpl <= 16) return launch_omp_kpl<T, 16, 2>(a, lay, st);
+    return launch_omp_kpl<T, 32, 2>(a, lay, st);
+  }
+  if (kpl <= 4) return launch_omp_kpl<T, 4, 8>(a, lay, st);
+  if (kpl <= 8) return launch_omp_kpl<T, 8, 8>(a, lay, st);
+  if (kpl <= 16) return launch_omp_kpl<T, 16, 8>(a, lay, st);
+  return launch_omp_kpl<T, 32, 8>(a, lay, st);
 }
 
 template cudaError_t launch_gram<float>(const float *, int, int, int, float *, cudaStream_t);

@@ -38,13 +38,14 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(
 __host__ __device__ inline int odd_pitch(int s) { return (s % 2 == 0) ? s + 1 : s + 2; }
 
 // Lane-distributed triangular solves with a per-warp lower factor L (row pitch
-// lp): lane q holds entry q of the vector.  Column sweeps: one shuffle and one
-// FMA per step, every lane busy.
+// lp) whose diagonal slots hold the reciprocals 1 / L_qq: lane q holds entry q
+// of the vector.  Column sweeps: one shuffle and one FMA per step, every lane
+// busy.
 template <typename T>
 __device__ __forceinline__ T lower_solve(const T *L, int lp, int k, T b, int lane) {
   T z = T(0);
   for (int q = 0; q < k; ++q) {
-    const T zq = __shfl_sync(0xffffffffu, b / L[q * lp + q], q);
+    const T zq = __shfl_sync(0xffffffffu, b * L[q * lp + q], q);
     if (lane == q) z = zq;
     if (lane > q && lane < k) b = fma(-L[lane * lp + q], zq, b);
   }
@@ -55,7 +56,7 @@ template <typename T>
 __device__ __forceinline__ T upper_solve(const T *L, int lp, int k, T z, int lane) {
   T x = T(0);
   for (int q = k - 1; q >= 0; --q) {
-    const T xq = __shfl_sync(0xffffffffu, z / L[q * lp + q], q);
+    const T xq = __shfl_sync(0xffffffffu, z * L[q * lp + q], q);
     if (lane == q) x = xq;
     if (lane < q) z = fma(-L[q * lp + lane], xq, z);
   }
@@ -98,19 +99,20 @@ __device__ __forceinline__ void support_residual(const T *Dt, const T *ysig, int
 // support and the ELL write-out for signals sig_begin .. sig_begin+sig_count-1
 // of a tile, run by one warp.
 //   a0     correlation tile alpha0 [tile signals][K] (shared memory)
-//   ybase  signal 0 of the tile, row stride m (shared or global memory)
+//   ybase  signal 0 of the tile, row stride ypitch (shared or global memory)
+//   MU     ceil(m / 32): signal entries per lane
 //   Ls, Gx per-warp [s][lp] factor scratch;  gc per-warp [s][K] G-column cache
 //   EXACT  refit the coefficients from the exact Gram entries (a.Gexact, the Gram
 //          of D in T) and D_S^T y before the correction step (used when G and
 //          alpha0 came from reduced-precision products)
-template <typename T, int KPL, bool EXACT>
-__device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase, int sig_begin, int sig_count,
-                                  int nsig, int64_t row0, const T *__restrict__ Dt, const T *__restrict__ Gt, T *Ls,
-                                  T *Gx, T *gc, int lp, bool gcache) {
-  constexpr int M32 = kMaxM / 32;
+template <typename T, int KPL, int MU, bool EXACT>
+__device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase, int ypitch, int sig_begin,
+                                  int sig_count, int nsig, int64_t row0, const T *__restrict__ Dt,
+                                  const T *__restrict__ Gt, T *Ls, T *Gx, T *gc, int lp, bool gcache) {
+  constexpr int M32 = MU;
   const int K = a.K, m = a.m, s = a.s;
   const int lane = threadIdx.x & 31;
-  const int mu = (m + 31) >> 5;
+  constexpr int mu = MU;
   const T eps = (T)a.eps;
   uint32_t valid = 0;   // bit c: atom lane + 32 c exists
 #pragma unroll
@@ -121,7 +123,7 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
     const int sig = sig_begin + q;
     if (sig >= nsig) break;
     const int64_t gi = row0 + sig;
-    const T *ysig = ybase + (size_t)sig * m;
+    const T *ysig = ybase + (size_t)sig * ypitch;
     const T *arow = a0 + (size_t)sig * K;
     T a0r[KPL];
 #pragma unroll
@@ -189,7 +191,7 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
       if (!(piv2 > PivotRel<T>::v * gbb) || !(piv2 > T(0))) break;
       if (lane < k) Ls[k * lp + lane] = w;
       if (lane == k) {
-        Ls[k * lp + k] = tsqrt(piv2);
+        Ls[k * lp + k] = T(1) / tsqrt(piv2);
         Sl = best;
         a0Sl = a0b;
       }
@@ -228,10 +230,10 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
         for (int c = 0; c < k; ++c) {
           const T d = Gx[c * lp + c];
           if (!(d > T(0))) { ok = false; break; }
-          const T lcc = tsqrt(d);
+          const T inv = T(1) / tsqrt(d);
           __syncwarp();
-          if (lane == c) Gx[c * lp + c] = lcc;
-          if (lane > c && lane < k) Gx[lane * lp + c] /= lcc;
+          if (lane == c) Gx[c * lp + c] = inv;
+          if (lane > c && lane < k) Gx[lane * lp + c] *= inv;
           __syncwarp();
           if (lane > c && lane < k) {
             const T lr = Gx[lane * lp + c];

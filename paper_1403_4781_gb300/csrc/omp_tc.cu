@@ -148,7 +148,7 @@ bool pick_tc_layout(int K, int mp, int s, TcLayout *out) {
 
 // One block codes TS signals of one subset: alpha0 tile on the tensor cores
 // (one M=128 MMA row block, N-tiles of NT atoms), then the selection loop.
-template <int KPL>
+template <int KPL, int MU>
 __global__ void __launch_bounds__(kTcThreads) omp_tc_kernel(OmpArgs a, TcLayout lay) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int K = a.K, m = a.m, s = a.s, mp = a.mp, Kp = a.Kp, TS = lay.TS, NT = lay.NT;
@@ -250,13 +250,13 @@ __global__ void __launch_bounds__(kTcThreads) omp_tc_kernel(OmpArgs a, TcLayout 
   float *Gx = reinterpret_cast<float *>(smem + lay.gx) + (size_t)warp * s * lay.lp;
   float *gc = reinterpret_cast<float *>(smem + lay.uni) + (size_t)warp * s * K;
   const int spw = TS / 8;
-  code_warp_signals<float, KPL, true>(a, a0, Y + (size_t)row0 * m, warp * spw, spw, nsig, row0, Dt, Gt, Ls, Gx, gc,
+  code_warp_signals<float, KPL, MU, true>(a, a0, Y + (size_t)row0 * m, m, warp * spw, spw, nsig, row0, Dt, Gt, Ls, Gx, gc,
                                       lay.lp, lay.gcache);
 }
 
-template <int KPL>
+template <int KPL, int MU>
 cudaError_t launch_omp_tc_kpl(const OmpArgs &a, const TcLayout &lay, cudaStream_t st) {
-  auto kern = omp_tc_kernel<KPL>;
+  auto kern = omp_tc_kernel<KPL, MU>;
   const size_t smem = tc::smem_for_tmem(lay.total, lay.NT);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -297,10 +297,16 @@ cudaError_t launch_omp_tc(const OmpArgs &a, cudaStream_t st) {
   TcLayout lay;
   if (!pick_tc_layout(a.K, a.mp, a.s, &lay)) return cudaErrorInvalidConfiguration;
   const int kpl = (a.K + 31) / 32;
-  if (kpl <= 4) return launch_omp_tc_kpl<4>(a, lay, st);
-  if (kpl <= 8) return launch_omp_tc_kpl<8>(a, lay, st);
-  if (kpl <= 16) return launch_omp_tc_kpl<16>(a, lay, st);
-  return launch_omp_tc_kpl<32>(a, lay, st);
+  if (a.m <= 64) {
+    if (kpl <= 4) return launch_omp_tc_kpl<4, 2>(a, lay, st);
+    if (kpl <= 8) return launch_omp_tc_kpl<8, 2>(a, lay, st);
+    if (kpl <= 16) return launch_omp_tc_kpl<16, 2>(a, lay, st);
+    return launch_omp_tc_kpl<32, 2>(a, lay, st);
+  }
+  if (kpl <= 4) return launch_omp_tc_kpl<4, 8>(a, lay, st);
+  if (kpl <= 8) return launch_omp_tc_kpl<8, 8>(a, lay, st);
+  if (kpl <= 16) return launch_omp_tc_kpl<16, 8>(a, lay, st);
+  return launch_omp_tc_kpl<32, 8>(a, lay, st);
 }
 
 }  // namespace sdl

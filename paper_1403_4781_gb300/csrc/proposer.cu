@@ -327,7 +327,7 @@ __global__ void romp_kernel(const float *__restrict__ D, const float *__restrict
     if (!(piv2 > kOmpPivotRelF32 * gbb) || !(piv2 > 0.f)) break;
     if (lane < k) Ls[k * lp + lane] = w;
     if (lane == k) {
-      Ls[k * lp + k] = sqrtf(piv2);
+      Ls[k * lp + k] = 1.f / sqrtf(piv2);
       Sl = best;
       a0Sl = a0b;
     }
