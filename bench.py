@@ -41,6 +41,9 @@ WORKLOAD = "splitmerge_fp32_m64_K256_s6_N200000_L100x2000_iters20+20"
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # FP32 CUDA-core rate: 152 SMs x 128 FFMA/clock x 2 flops x 2.07 GHz.
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
+# DRAM bytes (read + write) per launch of a kernel family, from one ncu capture
+# of this workload with the current kernels (see profiles/); absent = none.
+TRAFFIC = {"mod_solve_fp64": 52.7e6}
 
 
 def load_peaks():
@@ -122,14 +125,32 @@ def algorithmic_work(p):
     def omp_flops(K_, s_):          # 2mK (alpha0) + K s (s+1) (Batch-OMP updates)
         return 2 * m * K_ + K_ * s_ * (s_ + 1)
     return {
-        "mod_solve_fp64": ("alu", p.iters_local * L * (K1 ** 3 / 3 + 2 * K1 ** 2 * m)
-                           + p.iters_merge * (K ** 3 / 3 + 2 * K ** 2 * m)),
+        # FP64 MOD solve per system: Cholesky K^3/3 + forward and back substitution
+        # of m right-hand sides 2 K^2 m
+        "mod_solve_fp64": ("alu", p.iters_local * L * (K1 ** 3 / 3 + 2 * K1 ** 2 * m)),
+        "mod_solve_fp64_single": ("alu", p.iters_merge * (K ** 3 / 3 + 2 * K ** 2 * m)),
         "chol_fp64": ("alu", p.iters_local * L * K1 ** 3 / 3 + p.iters_merge * K ** 3 / 3),
         "solve_fp64": ("alu", p.iters_local * L * 2 * K1 ** 2 * m + p.iters_merge * 2 * K ** 2 * m),
         "omp": ("alu", p.iters_local * p.N * omp_flops(K1, p.s1) + p.iters_merge * nm * omp_flops(K, p.s2)
                 + p.N * omp_flops(K, p.s)),
         "gram": ("alu", p.iters_local * L * 2 * K1 * K1 * m + p.iters_merge * 2 * K * K * m),
     }
+
+
+def _timed_steps(step, inputs, steps, flush, stream, clk=None):
+    """Run `steps` steps with the L2 flushed before each; CUDA events on `stream`
+    around each step.  Returns (per-step ms list, last outputs)."""
+    import torch
+    ms, out = [], None
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = step(*inputs)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms, out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -153,9 +174,25 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     def step(Y, perm, picks, mpick):
+        """Chosen form: every subset of a phase in one batched launch per kernel,
+        launch shapes chosen by the library's autotuner."""
         Yp = sdl.split(Y, perm)
         Dl = sdl.init_dict(Yp, picks).view(p.L, p.K1, p.m)
         xfro, _ = sdl.local_train(Yp, p.offsets, Dl, p.s1, p.iters_local, with_rmse=False)
+        D, _ = sdl.merge(Dl, xfro, mpick, p.K, p.s2, p.iters_merge, with_rmse=False)
+        idx, val, nnz, _ = sdl.omp(D, Y, p.s, with_resid=False)
+        out2 = sdl.residual(Y, D, idx, val)
+        return D, out2
+
+    def step_plain(Y, perm, picks, mpick):
+        """Plain form: the same algorithm with one launch sequence per subset."""
+        Yp = sdl.split(Y, perm)
+        Dl = sdl.init_dict(Yp, picks).view(p.L, p.K1, p.m)
+        xfro = torch.empty((p.L,), dtype=torch.float64, device=dev)
+        for t in range(p.L):
+            a, b = int(p.offsets[t]), int(p.offsets[t + 1])
+            xf, _ = sdl.local_train(Yp[a:b], [0, b - a], Dl[t:t + 1], p.s1, p.iters_local, with_rmse=False)
+            xfro[t:t + 1] = xf
         D, _ = sdl.merge(Dl, xfro, mpick, p.K, p.s2, p.iters_merge, with_rmse=False)
         idx, val, nnz, _ = sdl.omp(D, Y, p.s, with_resid=False)
         out2 = sdl.residual(Y, D, idx, val)
@@ -168,65 +205,68 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(v):
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([v], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return v
+
+    inputs = (Y, perm, picks, mpick)
     for _ in range(args.warmup):
-        step(Y, perm, picks, mpick)
+        step(*inputs)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
-    # ---- device-resident timed region (per-step events; L2 flushed between steps)
+    # ---- chosen form, device-resident timed region
     ctx.profile(True)
     ctx.profile_reset()
     launches0 = ctx.launch_count()
-    ms = []
     barrier()
     with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            D, out2 = step(Y, perm, picks, mpick)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
+        ms, (D, out2) = _timed_steps(step, inputs, args.steps, flush, stream)
     barrier()
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_read()
     ctx.profile(False)
     clocks = clk.summary()
-    total_ms = float(sum(ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(ms)))
     r2, y2 = out2.cpu().tolist()
     n_sig = counts(p)
     value = world * n_sig * args.steps / (total_ms / 1e3)
+    rmse = float(np.sqrt(r2 / (p.m * p.N)))
+
+    # ---- plain form (per-subset launch sequences), fewer steps: it is slow by design
+    plain = None
+    if args.plain_steps > 0:
+        step_plain(*inputs)
+        barrier()
+        pms, (_, pout2) = _timed_steps(step_plain, inputs, args.plain_steps, flush, stream)
+        ptot = max_over_ranks(float(sum(pms)))
+        pr2, _ = pout2.cpu().tolist()
+        prmse = float(np.sqrt(pr2 / (p.m * p.N)))
+        plain = {"value": world * n_sig * args.plain_steps / (ptot / 1e3), "unit": UNIT,
+                 "ms_per_step": ptot / args.plain_steps, "steps": args.plain_steps,
+                 "train_to_rmse_s": ptot / args.plain_steps / 1e3, "rmse_final": prmse,
+                 "form": "one launch sequence per subset (100 local trainings in turn), FP32 CUDA-core OMP, "
+                         "FP64 MOD solve, no proposer, no graph capture",
+                 "chosen_speedup": (ptot / args.plain_steps) / (total_ms / args.steps),
+                 "chosen_reaches_rmse": bool(rmse <= prmse * (1 + 1e-3))}
 
     # ---- end to end: pinned host inputs -> device, step, result -> host, every step
     D_host = torch.empty((p.K, p.m), dtype=torch.float32).pin_memory()
     out_host = torch.empty((2,), dtype=torch.float64).pin_memory()
-    e2e_ms = []
-    barrier()
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        Yd = Y_h.to(dev, non_blocking=True)
-        permd = perm_h.to(dev, non_blocking=True)
-        picksd = picks_h.to(dev, non_blocking=True)
-        mpickd = mpick_h.to(dev, non_blocking=True)
-        Dd, o2 = step(Yd, permd, picksd, mpickd)
+
+    def step_e2e(Y_h, perm_h, picks_h, mpick_h):
+        Dd, o2 = step(Y_h.to(dev, non_blocking=True), perm_h.to(dev, non_blocking=True),
+                      picks_h.to(dev, non_blocking=True), mpick_h.to(dev, non_blocking=True))
         D_host.copy_(Dd, non_blocking=True)
         out_host.copy_(o2, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = float(sum(e2e_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+        return Dd, o2
+
+    barrier()
+    e2e_ms, _ = _timed_steps(step_e2e, (Y_h, perm_h, picks_h, mpick_h), args.steps, flush, stream)
+    e2e_total = max_over_ranks(float(sum(e2e_ms)))
     h2d = sum(t.numel() * t.element_size() for t in (Y_h, perm_h, picks_h, mpick_h))
     d2h = D_host.numel() * 4 + 16
 
@@ -240,9 +280,11 @@ def run_ours(args, rank, world, local_rank):
         peak = FP64_PEAK_FLOPS if "fp64" in name else FP32_PEAK_FLOPS
         achieved = flops_step * args.steps / (kms / 1e3)
         roof = {"kernel": name, "bound": kind, "achieved": achieved / 1e12,
-                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": ("nominal FP64 1.25 TFLOP/s = 152 SMs x 2 DFMA/clk x 2.07 GHz"
-                                if "fp64" in name else "152 SMs x 128 FFMA/clk x 2.07 GHz"),
+                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TRAFFIC.get(name), "traffic_unit": "bytes per launch",
+                "peak_source": ("FP64 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived from unit counts and "
+                                "the maximum clock; a DFMA probe measured 1.254 TFLOP/s)"
+                                if "fp64" in name else "FP32 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"),
                 "share_of_step": kms / total_ms, "launches": nl}
     kernels = {k: {"ms_per_step": v[2] / args.steps, "launches_per_step": v[0] / args.steps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}
@@ -254,13 +296,16 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded; Sec. 3.1 data model, sizes of the split-and-merge FP32 config)",
         "config": {"workload": WORKLOAD, "m": p.m, "K": p.K, "N": p.N, "L": p.L, "n": int(p.N // p.L),
                    "K1": p.K1, "s": p.s, "s1": p.s1, "s2": p.s2, "iters_local": p.iters_local,
-                   "iters_merge": p.iters_merge, "form": "plain (FP32 CUDA-core OMP, FP64 MOD)",
+                   "iters_merge": p.iters_merge,
+                   "form": "chosen: batched (all subsets of a phase per launch), autotuned FP64 MOD solve, "
+                           "FP32 CUDA-core OMP",
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "signals_per_step": n_sig,
         "train_to_rmse_s": total_ms / args.steps / 1e3,
-        "rmse_final": float(np.sqrt(r2 / (p.m * p.N))),
+        "rmse_final": rmse,
         "mse_train_db": float(10 * np.log10(r2 / y2)),
+        "plain": plain,
         "e2e": {"value": world * n_sig * args.steps / (e2e_total / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -268,6 +313,8 @@ def run_ours(args, rank, world, local_rank):
         "kernels": kernels,
         "clocks": clocks,
     }
+    if rank == 0 and world == 1 and not args.no_proposer:
+        res["proposer"] = proposer_bench(sdl, dev, flush, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(p, Y_h.numpy())
     if rank == 0:
@@ -275,6 +322,65 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def proposer_bench(sdl, dev, flush, stream):
+    """Learned support proposer on its own workload (64 -> 512 -> 512 -> 256 MLP,
+    D0 64 x 256, s = 6, noise 0.01): labels from plain OMP on the training
+    signals, Adam training (timed), then proposer-assisted OMP (top-2s
+    candidates, restricted OMP, plain OMP where ||r|| > 8.5 sigma) against plain
+    OMP on fresh signals.  Sizes are reduced from the 1M / 1M pairs of the
+    workload to keep the run short; they are stated in the output."""
+    import torch
+    n_train, n_eval, epochs, B = 1 << 19, 1 << 19, 4, 4096
+    c = si.config3(n_train=n_train, n_eval=n_eval)
+    D = torch.from_numpy(c["D0"]).to(dev)
+    Ytr = torch.from_numpy(c["Ytr"]).to(dev)
+    Yev = torch.from_numpy(c["Yev"]).to(dev)
+    s, ncand, eps_fb = c["s"], 2 * c["s"], 8.5 * 0.01
+    labels, *_ = sdl.omp(D, Ytr, s, with_resid=False)
+    prop = sdl.Proposer(torch.from_numpy(c["params"]).to(dev), c["m"], c["h1"], c["h2"], c["K"])
+    loss = torch.zeros(4, dtype=torch.float32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(3)
+    first = None
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for epoch in range(epochs):
+        lr = 2e-3 * 0.5 * (1 + np.cos(np.pi * epoch / epochs))
+        order = torch.randperm(n_train, device=dev, generator=g)
+        Ys, Is = Ytr[order], labels[order]
+        for a in range(0, n_train, B):
+            prop.train_step(Ys[a:a + B], Is[a:a + B], lr, loss)
+            if first is None:
+                first = float(loss[0])
+    e1.record(stream)
+    e1.synchronize()
+    train_s = e0.elapsed_time(e1) / 1e3
+    last = float(loss[0])
+
+    def timed(fn):
+        fn()
+        flush.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        out = fn()
+        a1.record(stream)
+        a1.synchronize()
+        return a0.elapsed_time(a1) / 1e3, out
+
+    t_plain, (pi, pv, pn, pr) = timed(lambda: sdl.omp(D, Yev, s))
+    t_prop, (qi, qv, qn, qr, nf) = timed(lambda: prop.omp(D, Yev, s, ncand, eps_fb))
+    same = (torch.sort(pi, dim=1).values == torch.sort(qi, dim=1).values).all(dim=1).float().mean().item()
+    met = (torch.sqrt(qr) <= eps_fb).float().mean().item()
+    prop.close()
+    return {"train_pairs": n_train, "epochs": epochs, "batch": B, "train_s": train_s,
+            "train_samples_per_s": epochs * n_train / train_s, "loss_first": first, "loss_last": last,
+            "eval_signals": n_eval, "plain_omp_signals_per_s": n_eval / t_plain,
+            "proposed_omp_signals_per_s": n_eval / t_prop, "fallback_rate": nf / n_eval,
+            "support_agreement_with_plain": same, "residual_within_eps_fb": met,
+            "candidates": ncand, "eps_fb": eps_fb}
 
 
 # ------------------------------------------------------------ CPU oracle ------
@@ -298,10 +404,11 @@ def _oracle_sample(p, Y, n_sub, final_n, merge_iters):
 
 
 def cpu_baseline(p, Y):
-    coded, dt, th = _oracle_sample(p, Y, n_sub=24, final_n=20_000, merge_iters=2)
+    n_sub, final_n, merge_iters = 100, 100_000, 8
+    coded, dt, th = _oracle_sample(p, Y, n_sub=n_sub, final_n=final_n, merge_iters=merge_iters)
     return {"value": coded / dt, "unit": UNIT, "cores": th, "kind": "oracle",
-            "sample": f"24 of 100 subsets x {p.iters_local} local iterations, merge of their "
-                      f"{24 * p.K1} atoms x 2 iterations, final coding of 20,000 signals "
+            "sample": f"{n_sub} of {p.L} subsets x {p.iters_local} local iterations, merge of their "
+                      f"{n_sub * p.K1} atoms x {merge_iters} iterations, final coding of {final_n:,} signals "
                       f"({coded} coded signals in {dt:.1f} s)"}
 
 
@@ -339,6 +446,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-proposer", action="store_true", help="skip the proposer sub-benchmark")
+    ap.add_argument("--plain-steps", type=int, default=1,
+                    help="timed steps of the per-subset plain form (0 skips it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
