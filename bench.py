@@ -137,6 +137,23 @@ def algorithmic_work(p):
     }
 
 
+def max_over_ranks(v: float, world: int, device) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, world: int, steps: int, max_total_ms: float) -> float:
+    """Units all ranks processed over `steps` steps per second of the slowest
+    rank's timed total."""
+    return world * units_per_rank_step * steps / (max_total_ms / 1e3)
+
+
 def _timed_steps(step, inputs, steps, flush, stream, clk=None):
     """Run `steps` steps with the L2 flushed before each; CUDA events on `stream`
     around each step.  Returns (per-step ms list, last outputs)."""
@@ -205,14 +222,6 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v):
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([v], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return v
-
     inputs = (Y, perm, picks, mpick)
     for _ in range(args.warmup):
         step(*inputs)
@@ -230,10 +239,10 @@ def run_ours(args, rank, world, local_rank):
     prof = ctx.profile_read()
     ctx.profile(False)
     clocks = clk.summary()
-    total_ms = max_over_ranks(float(sum(ms)))
+    total_ms = max_over_ranks(float(sum(ms)), world, dev)
     r2, y2 = out2.cpu().tolist()
     n_sig = counts(p)
-    value = world * n_sig * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(n_sig, world, args.steps, total_ms)
     rmse = float(np.sqrt(r2 / (p.m * p.N)))
 
     # ---- plain form (per-subset launch sequences), fewer steps: it is slow by design
@@ -242,10 +251,10 @@ def run_ours(args, rank, world, local_rank):
         step_plain(*inputs)
         barrier()
         pms, (_, pout2) = _timed_steps(step_plain, inputs, args.plain_steps, flush, stream)
-        ptot = max_over_ranks(float(sum(pms)))
+        ptot = max_over_ranks(float(sum(pms)), world, dev)
         pr2, _ = pout2.cpu().tolist()
         prmse = float(np.sqrt(pr2 / (p.m * p.N)))
-        plain = {"value": world * n_sig * args.plain_steps / (ptot / 1e3), "unit": UNIT,
+        plain = {"value": whole_job_rate(n_sig, world, args.plain_steps, ptot), "unit": UNIT,
                  "ms_per_step": ptot / args.plain_steps, "steps": args.plain_steps,
                  "train_to_rmse_s": ptot / args.plain_steps / 1e3, "rmse_final": prmse,
                  "form": "one launch sequence per subset (100 local trainings in turn), FP32 CUDA-core OMP, "
@@ -266,7 +275,7 @@ def run_ours(args, rank, world, local_rank):
 
     barrier()
     e2e_ms, _ = _timed_steps(step_e2e, (Y_h, perm_h, picks_h, mpick_h), args.steps, flush, stream)
-    e2e_total = max_over_ranks(float(sum(e2e_ms)))
+    e2e_total = max_over_ranks(float(sum(e2e_ms)), world, dev)
     h2d = sum(t.numel() * t.element_size() for t in (Y_h, perm_h, picks_h, mpick_h))
     d2h = D_host.numel() * 4 + 16
 
@@ -306,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
         "rmse_final": rmse,
         "mse_train_db": float(10 * np.log10(r2 / y2)),
         "plain": plain,
-        "e2e": {"value": world * n_sig * args.steps / (e2e_total / 1e3), "unit": UNIT,
+        "e2e": {"value": whole_job_rate(n_sig, world, args.steps, e2e_total), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": roof,
