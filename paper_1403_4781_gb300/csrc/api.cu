@@ -343,7 +343,7 @@ size_t mod_ws_bytes(int L, int K, int m, int64_t n, int s) {
   b += round256(sizeof(int64_t) * (L + 1)) + round256(sizeof(int32_t) * (L + 1));
   b += round256(sizeof(int32_t) * (size_t)L * K);          // cursor
   b += round256(sizeof(int32_t) * (size_t)L * (K + 1));    // ptr
-  b += 2 * round256(sizeof(int32_t) * (size_t)(n * s + 1));  // lsig, lslot
+  b += 3 * round256(sizeof(int32_t) * (size_t)(n * s + 1));  // lsig, lslot, latom
   b += round256(sizeof(double) * (size_t)L * K * K);       // A
   b += round256(sizeof(double) * mod_tiled_scratch_doubles(L, K, m));   // factor scratch
   b += round256(sizeof(double) * (size_t)L * K * m);       // B
@@ -371,6 +371,7 @@ sdl_status mod_prepare(sdl_ctx *ctx, ModArgs &a, const int64_t *offsets_h, int L
   a.ptr = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)L * (K + 1)));
   a.lsig = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)(n * s + 1)));
   a.lslot = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)(n * s + 1)));
+  a.latom = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)(n * s + 1)));
   a.A = static_cast<double *>(ws_alloc(ctx, sizeof(double) * (size_t)L * K * K));
   a.Lf = static_cast<double *>(ws_alloc(ctx, sizeof(double) * mod_tiled_scratch_doubles(L, K, m)));
   a.B = static_cast<double *>(ws_alloc(ctx, sizeof(double) * (size_t)L * K * m));
@@ -378,11 +379,16 @@ sdl_status mod_prepare(sdl_ctx *ctx, ModArgs &a, const int64_t *offsets_h, int L
   int32_t *us = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)L * K));
   a.usage = usage ? usage : us;
   *status_max = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
-  if (!a.cursor || !a.ptr || !a.lsig || !a.lslot || !a.A || !a.Lf || !a.B || !a.status || !us ||
+  if (!a.cursor || !a.ptr || !a.lsig || !a.lslot || !a.latom || !a.A || !a.Lf || !a.B || !a.status || !us ||
       !*status_max)
     return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
   return SDL_OK;
 }
+
+// Kernels one MOD accumulation launches: usage count, scan, CSC fill, the
+// accumulation and, on the FP32 path, the unused-atom pass.  Without signals
+// only the scan and the pass that sets the unused atoms run.
+int mod_accum_kernels(bool f32, int64_t tiles) { return tiles > 0 ? (f32 ? 5 : 4) : 2; }
 
 // Read back the worst MOD status of the last launch (synchronises).
 sdl_status mod_status(sdl_ctx *ctx, const int32_t *status, int L, int32_t *d_max) {
@@ -470,7 +476,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
                return launch_subset_stats<T>(res2, val, d_off, L, m, s, rmse ? rmse + it : nullptr, iters,
                                              it == iters - 1 ? xfro : nullptr, sm);
              }), "subset stats");
-    SDL_CUDA(timed(ctx, "mod_accum", ma.total_tiles > 0 ? 4 : 2,
+    SDL_CUDA(timed(ctx, "mod_accum", mod_accum_kernels(sizeof(T) == 4, ma.total_tiles),
                    [&] { return launch_mod_accum<T>(ma, sm); }), "mod accumulate");
     SDL_CUDA(run_mod_solve<T>(ctx, ma), "mod solve");
     SDL_CUDA(timed(ctx, "status", 1, [&] { return launch_status_max(ma.status, L, worst + it, sm); }),
@@ -629,7 +635,7 @@ sdl_status sdl_mod_update_batched(sdl_ctx *ctx, sdl_precision prec, const void *
   a.Y = Y; a.idx = idx; a.val = val; a.D = D;
   SDL_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int32_t) * L, ctx->stream), "status clear");
   cudaStream_t sm = ctx->stream;
-  const int nacc = a.total_tiles > 0 ? 4 : 2;
+  const int nacc = mod_accum_kernels(prec != SDL_PREC_F64, a.total_tiles);
   if (prec == SDL_PREC_F64)
     SDL_CUDA(timed(ctx, "mod_accum", nacc, [&] { return launch_mod_accum<double>(a, sm); }), "mod accumulate");
   else

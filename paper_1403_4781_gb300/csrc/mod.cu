@@ -91,6 +91,7 @@ __global__ void mod_fill_kernel(ModArgs a) {
     const int pos = atomicAdd(&a.cursor[(size_t)t * a.K + j], 1);
     a.lsig[base + pos] = (int32_t)(i - a.offsets[t]);
     a.lslot[base + pos] = k;
+    a.latom[base + pos] = j;
   }
 }
 
@@ -174,6 +175,107 @@ __global__ void __launch_bounds__(256) mod_accum_kernel(ModArgs a) {
     const int r = lane + 32 * u;
     if (r < m) Bcol[r] = b[u];
   }
+}
+
+// ---- 3 (FP32 signals): A and B from the CSC entries, warps over entry ranges --
+// Each warp takes 32 s consecutive CSC entries of a subset (atom-major, so a
+// range spans few atoms).  B[:, j] = sum x_ij y_i is accumulated per run of
+// equal atoms in double-single precision on the FP32 pipe -- each product x y of
+// two floats is split exactly into p + e by an FMA, then added with TwoSum, so
+// about 48 significant bits are kept -- and added to B in FP64 when the atom
+// changes.  Every entry (i, j) adds x_ij x_ij2 (exact in FP64) to A[j][j2] for
+// the atoms j2 <= j of its signal, so A's lower triangle is complete.  A and B
+// start at zero; unused atoms get their identity row and previous value after.
+struct DSum {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void ds_add_product(DSum &a, float x, float y) {
+  const float p = x * y;
+  const float e = fmaf(x, y, -p);          // x y = p + e exactly
+  const float s = a.hi + p;                // TwoSum(a.hi, p) = s + err
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (p - bb);
+  const float lo = a.lo + (e + err);
+  const float hi = s + lo;                  // renormalise
+  a.lo = lo - (hi - s);
+  a.hi = hi;
+}
+
+template <int MU>
+__global__ void __launch_bounds__(256) mod_accum_ds_kernel(ModArgs a) {
+  const int K = a.K, m = a.m, s = a.s;
+  const int64_t g = blockIdx.x;
+  const int t = find_subset_tiles(a.tile_start, a.L, g);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t E = a.ptr[(size_t)t * (K + 1) + K];
+  const int64_t span = 32 * (int64_t)s;
+  const int64_t e_lo = (g - a.tile_start[t]) * (int64_t)kModTile * s + warp * span;
+  if (e_lo >= E) return;
+  const int64_t e_hi = e_lo + span < E ? e_lo + span : E;
+  const int64_t base = a.offsets[t] * s;
+  const float *__restrict__ Yt = static_cast<const float *>(a.Y) + (size_t)a.offsets[t] * m;
+  const float *__restrict__ vt = static_cast<const float *>(a.val) + (size_t)a.offsets[t] * s;
+  const int32_t *__restrict__ it = a.idx + (size_t)a.offsets[t] * s;
+  double *At = a.A + (size_t)t * K * K;
+  double *Bt = a.B + (size_t)t * K * m;
+  DSum acc[MU];
+#pragma unroll
+  for (int u = 0; u < MU; ++u) acc[u] = DSum{0.f, 0.f};
+  int cur = -1;
+  for (int64_t e0 = e_lo; e0 < e_hi; e0 += 32) {
+    const int64_t e = e0 + lane;
+    const bool ok = e < e_hi;
+    const int i = ok ? a.lsig[base + e] : 0;
+    const int j = ok ? a.latom[base + e] : -1;
+    const float x = ok ? vt[(size_t)i * s + a.lslot[base + e]] : 0.f;
+    if (ok)
+      for (int k = 0; k < s; ++k) {
+        const int j2 = it[(size_t)i * s + k];
+        if (j2 >= 0 && j2 <= j) atomicAdd(&At[(size_t)j * K + j2], (double)x * (double)vt[(size_t)i * s + k]);
+      }
+    const int nq = e_hi - e0 < 32 ? (int)(e_hi - e0) : 32;
+    for (int q = 0; q < nq; ++q) {
+      const int jq = __shfl_sync(0xffffffffu, j, q);
+      const int iq = __shfl_sync(0xffffffffu, i, q);
+      const float xq = __shfl_sync(0xffffffffu, x, q);
+      if (jq != cur) {   // warp-uniform
+        if (cur >= 0)
+#pragma unroll
+          for (int u = 0; u < MU; ++u) {
+            const int r = lane + 32 * u;
+            if (r < m) atomicAdd(&Bt[(size_t)cur * m + r], (double)acc[u].hi + (double)acc[u].lo);
+            acc[u] = DSum{0.f, 0.f};
+          }
+        cur = jq;
+      }
+      const float *yr = Yt + (size_t)iq * m;
+#pragma unroll
+      for (int u = 0; u < MU; ++u) {
+        const int r = lane + 32 * u;
+        if (r < m) ds_add_product(acc[u], xq, yr[r]);
+      }
+    }
+  }
+  if (cur >= 0)
+#pragma unroll
+    for (int u = 0; u < MU; ++u) {
+      const int r = lane + 32 * u;
+      if (r < m) atomicAdd(&Bt[(size_t)cur * m + r], (double)acc[u].hi + (double)acc[u].lo);
+    }
+}
+
+// Unused atoms: identity row of A (its off-diagonal entries stayed zero) and
+// B = the previous atom, which decouples them in the solve.
+template <typename T>
+__global__ void mod_unused_kernel(ModArgs a) {
+  const int t = blockIdx.y;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= a.K || a.usage[(size_t)t * a.K + j] != 0) return;
+  if (lane == 0) a.A[((size_t)t * a.K + j) * a.K + j] = 1.0;
+  const T *Dj = static_cast<const T *>(a.D) + ((size_t)t * a.K + j) * a.m;
+  for (int r = lane; r < a.m; r += 32) a.B[((size_t)t * a.K + j) * a.m + r] = (double)Dj[r];
 }
 
 // ---- 4: FP64 blocked Cholesky, one block (256 threads) per subset -----------
@@ -746,6 +848,19 @@ cudaError_t launch_mod_accum(const ModArgs &a, cudaStream_t st) {
   if (a.total_tiles > 0) {
     mod_fill_kernel<<<(unsigned)a.total_tiles, kModTile, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (sizeof(T) == 4) {
+    // FP32 signals: zeroed A and B, entry-range warps, then the unused atoms
+    e = cudaMemsetAsync(a.A, 0, sizeof(double) * (size_t)a.L * a.K * a.K, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.B, 0, sizeof(double) * (size_t)a.L * a.K * a.m, st);
+    if (e != cudaSuccess) return e;
+    if (a.total_tiles > 0) {
+      auto kern = a.m <= 64 ? mod_accum_ds_kernel<2> : mod_accum_ds_kernel<8>;
+      kern<<<(unsigned)a.total_tiles, kModTile, 0, st>>>(a);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    mod_unused_kernel<T><<<dim3((a.K + 7) / 8, a.L), 256, 0, st>>>(a);
+    return cudaGetLastError();
   }
   const size_t sm = sizeof(double) * 8 * (size_t)a.K;
   dim3 grid((a.K + 7) / 8, a.L);

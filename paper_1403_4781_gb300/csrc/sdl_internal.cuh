@@ -140,6 +140,7 @@ struct ModArgs {
   int32_t *ptr;           // [L][K+1]
   int32_t *lsig;          // [n*s]
   int32_t *lslot;         // [n*s]
+  int32_t *latom;         // [n*s] atom of each CSC entry
   double *A;              // [L][K][K]
   double *Lf;             // [L][K][K]
   double *B;              // [L][K][m]
