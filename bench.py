@@ -392,6 +392,54 @@ def proposer_bench(sdl, dev, flush, stream):
             "candidates": ncand, "eps_fb": eps_fb}
 
 
+def run_uneven(args, shape):
+    """The uneven batched local-training workload (512 subsets, sizes on
+    [500, 8000]; shape A m=64/K=256/s=6 or B m=144/K=512/s=10): all subsets
+    trained for 20 iterations in one batched launch per kernel, BF16 tensor-core
+    correlations and Gram (the workload's precision) and the FP32 CUDA-core path
+    beside it.  A measurement of a parity workload, printed as its own line."""
+    import torch
+
+    import paper_1403_4781_gb300 as sdl
+
+    dev = torch.device("cuda", 0)
+    p = si.config2(shape)
+    Yg = sdl.split(torch.from_numpy(p.Y).to(dev), torch.from_numpy(p.perm).to(dev))
+    D0 = sdl.init_dict(Yg, torch.from_numpy(p.picks.reshape(-1)).to(dev),
+                       torch.from_numpy(p.fill.reshape(-1, p.m)).to(dev)).reshape(p.L, p.K1, p.m)
+    ctx = sdl.context(0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, prec in (("bf16", sdl.PREC_BF16), ("fp32", sdl.PREC_F32)):
+        D = D0.clone()
+        sdl.local_train(Yg, p.offsets, D, p.s1, 1, prec=prec, with_rmse=False)   # warm-up, autotune
+        D = D0.clone()
+        flush.zero_()
+        ctx.profile(True)
+        ctx.profile_reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            _, rmse = sdl.local_train(Yg, p.offsets, D, p.s1, p.iters_local, prec=prec)
+            e1.record(stream)
+            e1.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        ms = e0.elapsed_time(e1)
+        r = rmse.cpu().numpy()
+        w = (np.diff(p.offsets) * p.m).astype(np.float64)
+        out[name] = {"value": p.iters_local * p.N / (ms / 1e3), "unit": UNIT, "ms": ms,
+                     "ms_per_iteration": ms / p.iters_local,
+                     "rmse_last": float(np.sqrt((r[:, -1] ** 2 * w).sum() / w.sum())),
+                     "kernels": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])},
+                     "clocks": clk.summary()}
+    res = {"metric": METRIC, "workload": p.name, "L": p.L, "N": p.N, "m": p.m, "K": p.K, "s": p.s1,
+           "iters": p.iters_local, "sizes": [int(np.diff(p.offsets).min()), int(np.diff(p.offsets).max())],
+           "data": "synthetic (seeded; uneven batched workload)", **out}
+    print(json.dumps(res), flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle ------
 def _oracle_sample(p, Y, n_sub, final_n, merge_iters):
     """Run the oracle on a bounded sample of the workload: local training of the
@@ -456,6 +504,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposer sub-benchmark")
+    ap.add_argument("--workload", choices=["splitmerge", "uneven-A", "uneven-B"], default="splitmerge",
+                    help="the bench workload (default) or one of the parity workloads, measured alone")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed steps of the per-subset plain form (0 skips it)")
     args = ap.parse_args()
@@ -464,6 +514,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload != "splitmerge":
+        if rank == 0:
+            run_uneven(args, args.workload[-1])
     else:
         run_ours(args, rank, world, local_rank)
 

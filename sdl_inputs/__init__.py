@@ -186,3 +186,17 @@ def config3(n_train: int = 1_000_000, n_eval: int = 1_000_000):
     Yev, _, _ = sparse_signals(rng, D0.astype(np.float64), n_eval, 6, 0.01, dtype=np.float32)
     params = mlp_init(rng, 64, 512, 512, 256, 6)
     return dict(D0=D0, Ytr=Ytr, Yev=Yev, params=params, m=64, h1=512, h2=512, K=256, s=6)
+
+
+def config2(shape: str = "A", L: int = 512, iters: int = 20) -> SplitMergeProblem:
+    """Uneven batched local-training workload: L subsets with sizes uniform on
+    the integers [500, 8000], one ground-truth dictionary per shape, noise 0.02.
+    Shape A: m=64, K=256, s=6; shape B: m=144, K=512, s=10.  Each subset is
+    trained with K atoms and sparsity s; its initial atoms are K distinct
+    signals of the subset, Gaussian fill columns where it has fewer."""
+    if shape not in ("A", "B"):
+        raise ValueError("shape is 'A' or 'B'")
+    rng = rng_for(2, trial=0 if shape == "A" else 1)
+    m, K, s = (64, 256, 6) if shape == "A" else (144, 512, 10)
+    sizes = uneven_sizes(rng, L, 500, 8000)
+    return split_merge_problem(f"uneven_{shape}_m{m}_K{K}", m, K, s, s, 1, K, sizes, iters, 0, 0.02, rng)

@@ -18,6 +18,7 @@ import torch
 import oracle
 import paper_1403_4781_gb300 as sdl
 import sdl_inputs as si
+from _parity import check_bf16_codes
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -32,30 +33,6 @@ def _problem(seed, m, K, n, s, sigma):
     D0 = si.unit_gaussian_atoms(rng, m, K).astype(np.float32)
     Y, _, _ = si.sparse_signals(rng, D0.astype(np.float64), n, s, sigma, dtype=np.float32)
     return D0, Y
-
-
-def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2):
-    D64, Y64 = D.astype(np.float64), Y.astype(np.float64)
-    n, s = idx.shape
-    tol = 2 * 2.0 ** -8 * (np.linalg.norm(Y64, axis=1) + 2 * np.abs(orc["val"]).sum(axis=1))
-    excused = 0
-    for i in range(n):
-        k = int(nnz[i])
-        S = idx[i, :k]
-        assert len(set(S.tolist())) == k and (idx[i, k:] == -1).all()
-        if k:
-            x, *_ = np.linalg.lstsq(D64[S].T, Y64[i], rcond=None)
-            scale = max(np.abs(x).max(), 1e-12)
-            assert np.abs(val[i, :k] - x).max() <= coef_rtol * scale, (i, val[i, :k], x)
-            res = Y64[i] - D64[S].T @ x
-            assert abs(r2[i] - res @ res) <= 1e-3 * (Y64[i] @ Y64[i]) + 1e-6
-        if not ((idx[i] == orc["idx"][i]).all() and nnz[i] == orc["nnz"][i]):
-            diff = np.nonzero(idx[i] != orc["idx"][i])[0]
-            step = int(diff[0]) if len(diff) else min(int(nnz[i]), int(orc["nnz"][i]))
-            g = orc["gap"][i][step] if step < s else np.inf
-            assert g < tol[i], (i, step, g, tol[i], idx[i], orc["idx"][i])
-            excused += 1
-    return excused
 
 
 @pytest.mark.parametrize("m,K,n,s", [(64, 256, 4133, 6), (64, 128, 700, 5), (144, 512, 1500, 10),
