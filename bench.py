@@ -440,6 +440,63 @@ def run_uneven(args, shape):
     print(json.dumps(res), flush=True)
 
 
+def run_patches(args):
+    """The large image-patch workload (4,194,304 16x16 patches of synthetic
+    images, m=256; 256 subsets of 16,384; local K1=512, s1=4; merge to K=1024,
+    s2=4; final sparsity 16; overcomplete DCT initial dictionaries; 20 + 20
+    iterations), run whole with the FP32 CUDA-core OMP and with BF16 tensor-core
+    correlations.  A measurement of a parity workload, printed as its own line."""
+    import torch
+
+    import paper_1403_4781_gb300 as sdl
+
+    dev = torch.device("cuda", 0)
+    p = si.config4()
+    Y = torch.from_numpy(p.Y).to(dev)
+    perm = torch.from_numpy(p.perm).to(dev)
+    picks = torch.from_numpy(p.picks.reshape(-1)).to(dev)
+    fill = torch.from_numpy(p.fill.reshape(-1, p.m)).to(dev)
+    Dm0 = torch.from_numpy(p.extra["D_merge0"]).to(dev)
+    sF = p.extra["s_final"]
+    ctx = sdl.context(0)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec):
+        Yp = sdl.split(Y, perm)
+        Dl = sdl.init_dict(Yp, picks, fill).view(p.L, p.K1, p.m)
+        xfro, _ = sdl.local_train(Yp, p.offsets, Dl, p.s1, p.iters_local, prec=prec, with_rmse=False)
+        D, _ = sdl.merge(Dl, xfro, None, p.K, p.s2, p.iters_merge, prec=prec, with_rmse=False, D_init=Dm0)
+        idx, val, nnz, _ = sdl.omp(D, Y, sF, prec=prec, with_resid=False)
+        return sdl.residual(Y, D, idx, val)
+
+    out = {}
+    coded = p.iters_local * p.N + p.iters_merge * p.K1 * p.L + p.N
+    for name, prec in (("fp32", sdl.PREC_F32), ("bf16", sdl.PREC_BF16)):
+        step(prec)   # warm-up: autotuner, workspace
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            o2 = step(prec)
+            e1.record(stream)
+            e1.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        ms = e0.elapsed_time(e1)
+        r2, y2 = o2.cpu().tolist()
+        out[name] = {"value": coded / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "rmse_final": float(np.sqrt(r2 / (p.m * p.N))), "mse_train_db": float(10 * np.log10(r2 / y2)),
+                     "kernels": {k: round(v[2], 2) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])},
+                     "clocks": clk.summary()}
+    res = {"metric": METRIC, "workload": p.name, "N": p.N, "m": p.m, "L": p.L, "K1": p.K1, "K": p.K,
+           "s1": p.s1, "s2": p.s2, "s_final": sF, "iters": [p.iters_local, p.iters_merge],
+           "signals_per_step": coded, "data": "synthetic images (seeded piecewise-smooth fields + noise 0.1)",
+           **out}
+    print(json.dumps(res), flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle ------
 def _oracle_sample(p, Y, n_sub, final_n, merge_iters):
     """Run the oracle on a bounded sample of the workload: local training of the
@@ -504,7 +561,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposer sub-benchmark")
-    ap.add_argument("--workload", choices=["splitmerge", "uneven-A", "uneven-B"], default="splitmerge",
+    ap.add_argument("--workload", choices=["splitmerge", "uneven-A", "uneven-B", "patches"], default="splitmerge",
                     help="the bench workload (default) or one of the parity workloads, measured alone")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed steps of the per-subset plain form (0 skips it)")
@@ -514,6 +571,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "patches":
+        if rank == 0:
+            run_patches(args)
     elif args.workload != "splitmerge":
         if rank == 0:
             run_uneven(args, args.workload[-1])

@@ -149,8 +149,12 @@ sdl_status sdl_local_train(sdl_ctx *ctx, sdl_precision prec, const void *Y, int 
 /* Algorithm 1 step 3: Ytilde = [ xfro[0] D^(0) ... xfro[L-1] D^(L-1) ] (m x K1 L);
  * D starts from the unit-normalised columns Ytilde[:, pick[j]] and is trained on
  * Ytilde for `iters` rounds with sparsity s2.
- *   D_local device [L][K1][m];  xfro device double [L];  pick device int32 [K]
- *   D device [K][m] out;  rmse device double [iters] out or NULL. */
+ *   D_local device [L][K1][m];  xfro device double [L]
+ *   pick device int32 [K], or NULL: then D's contents on entry are the initial
+ *        atoms (any fixed initial dictionary, e.g. the overcomplete DCT the
+ *        paper's image experiments start from, Sec. 3.2.1)
+ *   D device [K][m] out (in as well when pick is NULL);  rmse device double
+ *   [iters] out or NULL. */
 sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, const double *xfro,
                      int m, int K1, int L, const int32_t *pick, int K, int s2, double eps,
                      int iters, void *D, double *rmse);

@@ -312,12 +312,19 @@ def local_train(Y, offsets, D_local, s1, iters, eps=0.0, prec=None, with_rmse=Tr
     return xfro, rmse
 
 
-def merge(D_local, xfro, pick, K, s2, iters, eps=0.0, prec=None, with_rmse=True):
-    """Algorithm 1 step 3.  Returns (D (K, m), rmse (iters,) f64 or None)."""
+def merge(D_local, xfro, pick, K, s2, iters, eps=0.0, prec=None, with_rmse=True, D_init=None):
+    """Algorithm 1 step 3.  pick (K,) int32 selects the initial stacked columns;
+    pick=None starts from D_init (K, m) instead.  Returns (D (K, m), rmse
+    (iters,) f64 or None)."""
     import torch
     prec = _prec_of(D_local, prec)
     L, K1, m = D_local.shape
-    D = torch.empty((K, m), dtype=D_local.dtype, device=D_local.device)
+    if pick is None:
+        if D_init is None or tuple(D_init.shape) != (K, m):
+            raise ValueError("pick=None needs D_init of shape (K, m)")
+        D = D_init.to(dtype=D_local.dtype).contiguous().clone()
+    else:
+        D = torch.empty((K, m), dtype=D_local.dtype, device=D_local.device)
     rmse = torch.empty((iters,), dtype=torch.float64, device=D_local.device) if with_rmse else None
     ctx = context(D_local.device.index)
     _call("sdl_merge", ctx.bind_stream(), prec, _ptr(D_local), _ptr(xfro), m, K1, L, _ptr(pick), K, s2,

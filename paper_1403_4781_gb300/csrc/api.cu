@@ -263,15 +263,21 @@ sdl_status check_prec(sdl_ctx *ctx, sdl_precision prec) {
   return set_error(ctx, SDL_EINVAL, "unknown precision");
 }
 
-// Workspace of the BF16 tensor-core coding pass: BF16 image of D, error word.
-size_t tc_ws_bytes(int L, int K, int m) {
+// Workspace of the BF16 tensor-core coding pass over n signals in L subsets:
+// BF16 image of D, error word, FP32 Gram, and the correlation scratch (one
+// chunk of 128-signal tiles).
+size_t tc_a0_bytes(int L, int K, int64_t n) {
+  const int64_t tiles = (n + 127) / 128 + L;
+  return sizeof(float) * (size_t)omp_tc_chunk_tiles(K, tiles) * 128 * K;
+}
+size_t tc_ws_bytes(int L, int K, int m, int64_t n) {
   return round256((size_t)L * round16(K) * round16(m) * 2) + round256(sizeof(int32_t) * 4) +
-         round256(sizeof(float) * (size_t)L * K * K);
+         round256(sizeof(float) * (size_t)L * K * K) + round256(tc_a0_bytes(L, K, n));
 }
 
 // One BF16 coding pass: BF16 image of D, Gram and correlations on the tensor
 // cores, selection loop, FP32 refit on the support.
-cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, float *Gex, int32_t *err) {
+cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, float *Gex, int32_t *err, float *a0c) {
   cudaStream_t sm = ctx->stream;
   oa.Dimg = img;
   oa.Gexact = Gex;
@@ -289,7 +295,9 @@ cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, float *
     return launch_gram<float>(static_cast<const float *>(oa.D), oa.m, oa.K, oa.L, Gex, sm);
   });
   if (e != cudaSuccess) return e;
-  return timed(ctx, "omp_tc", 1, [&] { return launch_omp_tc(oa, sm); });
+  const int64_t chunk = omp_tc_chunk_tiles(oa.K, oa.total_tiles);
+  const int nk = oa.total_tiles > 0 ? 2 * (int)((oa.total_tiles + chunk - 1) / chunk) : 0;
+  return timed(ctx, "omp_tc", nk, [&] { return launch_omp_tc(oa, a0c, sm); });
 }
 
 // Read back the error word of the tensor-core kernels (synchronises).
@@ -415,7 +423,7 @@ sdl_status check_omp_shape(sdl_ctx *ctx, int m, int K, int s, double eps) {
 template <typename T>
 size_t train_ws_bytes(int L, int K, int m, int64_t n, int s, int iters) {
   return omp_ws_bytes(sizeof(T) == 8 ? SDL_PREC_F64 : SDL_PREC_F32, L, K) + mod_ws_bytes(L, K, m, n, s) +
-         tc_ws_bytes(L, K, m) +
+         tc_ws_bytes(L, K, m, n) +
          round256(sizeof(int32_t) * (size_t)n * s) + round256(sizeof(T) * (size_t)n * s) +
          round256(sizeof(int32_t) * (size_t)n) + round256(sizeof(T) * (size_t)n) +
          round256(sizeof(int32_t) * (size_t)(iters + 1)) + 4096;
@@ -440,7 +448,8 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   void *img = bf16 ? ws_alloc(ctx, (size_t)L * round16(K) * round16(m) * 2) : nullptr;
   int32_t *tc_err = bf16 ? static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4)) : nullptr;
   float *Gex = bf16 ? static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)L * K * K)) : nullptr;
-  if (bf16 && (!img || !tc_err || !Gex)) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  float *a0c = bf16 ? static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n))) : nullptr;
+  if (bf16 && (!img || !tc_err || !Gex || !a0c)) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
   if (bf16) SDL_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int32_t), ctx->stream), "err clear");
   T *G = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)L * K * K));
   int32_t *idx = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * s));
@@ -464,7 +473,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   for (int it = 0; it < iters; ++it) {
     cudaError_t e;
     if (bf16) {
-      e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), Gex, tc_err);
+      e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), Gex, tc_err, a0c);
     } else {
       SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
       e = timed(ctx, "omp", 1, [&] { return launch_omp<T>(oa, ctx->num_sms, sm); });
@@ -558,7 +567,7 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
               "device pointers must be non-NULL and 16-byte aligned");
   DeviceGuard g(ctx->device);
   SDL_REQUIRE(g.ok, "cannot select the context device");
-  if ((st = ws_reserve(ctx, omp_ws_bytes(prec, L, K) + tc_ws_bytes(L, K, m) + 1024)) != SDL_OK) return st;
+  if ((st = ws_reserve(ctx, omp_ws_bytes(prec, L, K) + tc_ws_bytes(L, K, m, n) + 1024)) != SDL_OK) return st;
   OmpArgs a{};
   int64_t *d_off = nullptr;
   int32_t *d_tiles = nullptr;
@@ -577,9 +586,10 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
     void *img = ws_alloc(ctx, (size_t)L * round16(K) * round16(m) * 2);
     int32_t *err = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
     float *Gex = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)L * K * K));
-    if (!img || !err || !Gex) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+    float *a0c = static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n)));
+    if (!img || !err || !Gex || !a0c) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
     SDL_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream), "err clear");
-    cudaError_t e = run_omp_bf16(ctx, a, img, static_cast<float *>(G), Gex, err);
+    cudaError_t e = run_omp_bf16(ctx, a, img, static_cast<float *>(G), Gex, err, a0c);
     if (e == cudaErrorInvalidConfiguration)
       return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
     SDL_CUDA(e, "omp bf16");
@@ -731,7 +741,7 @@ sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, cons
   if ((st = check_omp_shape(ctx, m, K, s2, eps)) != SDL_OK) return st;
   SDL_REQUIRE(K1 >= 1 && L >= 1 && (int64_t)K1 * L < ((int64_t)1 << 31), "bad K1 or L");
   SDL_REQUIRE(iters >= 0, "iters must be >= 0");
-  SDL_REQUIRE(aligned16(D_local) && aligned16(xfro) && aligned16(pick) && aligned16(D) &&
+  SDL_REQUIRE(aligned16(D_local) && aligned16(xfro) && (pick == nullptr || aligned16(pick)) && aligned16(D) &&
                   (rmse == nullptr || aligned16(rmse)),
               "device pointers must be non-NULL and 16-byte aligned");
   DeviceGuard g(ctx->device);
@@ -749,15 +759,17 @@ sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, cons
   if (prec == SDL_PREC_F64) {
     SDL_CUDA(timed(ctx, "stack", 1, [&] { return launch_stack<double>(static_cast<const double *>(D_local), xfro, m, K1, L,
                                   static_cast<double *>(Yt), ctx->stream); }), "stack");
-    SDL_CUDA(timed(ctx, "pick_init", 1, [&] { return launch_pick_init<double>(static_cast<const double *>(Yt), m, pick, K, static_cast<double *>(D),
-                                      ctx->stream); }), "merge init");
+    if (pick)
+      SDL_CUDA(timed(ctx, "pick_init", 1, [&] { return launch_pick_init<double>(static_cast<const double *>(Yt), m, pick, K, static_cast<double *>(D),
+                                        ctx->stream); }), "merge init");
     return train_run<double>(ctx, static_cast<const double *>(Yt), m, offsets, 1, K, s2, eps, iters,
                              static_cast<double *>(D), xf_unused, rmse);
   }
   SDL_CUDA(timed(ctx, "stack", 1, [&] { return launch_stack<float>(static_cast<const float *>(D_local), xfro, m, K1, L, static_cast<float *>(Yt),
                                ctx->stream); }), "stack");
-  SDL_CUDA(timed(ctx, "pick_init", 1, [&] { return launch_pick_init<float>(static_cast<const float *>(Yt), m, pick, K, static_cast<float *>(D),
-                                   ctx->stream); }), "merge init");
+  if (pick)
+    SDL_CUDA(timed(ctx, "pick_init", 1, [&] { return launch_pick_init<float>(static_cast<const float *>(Yt), m, pick, K, static_cast<float *>(D),
+                                     ctx->stream); }), "merge init");
   return train_run<float>(ctx, static_cast<const float *>(Yt), m, offsets, 1, K, s2, eps, iters,
                           static_cast<float *>(D), xf_unused, rmse, prec == SDL_PREC_BF16);
 }

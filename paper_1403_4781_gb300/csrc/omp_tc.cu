@@ -5,10 +5,12 @@
 // (kind::f16, BF16 operands, FP32 accumulation) with the accumulator tile in
 // tensor memory, operands in shared memory in the canonical K-major layout.
 // Dictionary tiles are streamed in by bulk TMA copies of a pre-laid-out BF16
-// image of D; the signal tile is converted from FP32 in the kernel.  After the
-// readout of alpha0 into shared memory each warp runs the shared selection loop
-// and then refits the coefficients on the support exactly in FP32 from D (one
-// refinement step), so the BF16 rounding affects only which atoms are chosen.
+// image of D; the signal tile is converted from FP32 in the kernel.  The
+// correlation kernel writes alpha0 of 128-signal tiles to a global scratch (in
+// chunks of at most 1 GiB); the selection kernel then runs the shared selection
+// loop from there with little shared memory per block, and refits the
+// coefficients on the support exactly in FP32 from D (one refinement step), so
+// the BF16 rounding affects only which atoms are chosen.
 #include "omp_common.cuh"
 #include "tc_ptx.cuh"
 
@@ -19,7 +21,6 @@ namespace {
 
 using namespace omp_detail;
 
-constexpr int kTcThreads = 256;
 constexpr int kWaitLimit = 1 << 22;   // polls of a bounded mbarrier wait
 
 // D [L][K][m] FP32 -> BF16 image [L][Kp][mp]; zero padding rows / columns.
@@ -108,84 +109,68 @@ __global__ void __launch_bounds__(128) gram_tc_kernel(const unsigned char *__res
   if (warp == 0) tc::tmem_dealloc(tbase, ncols);
 }
 
-struct TcLayout {
-  int TS, NT, lp;
-  bool gcache;
-  size_t a0, uni, ls, gx, bar, total;
+// ---- correlations: alpha0 = Y D^T of 128-signal tiles into global memory ----
+// One block per tile of 128 signals (the MMA's M), 4 warps.  The signal tile is
+// converted to a BF16 K-major image once; dictionary tiles of 128 atoms stream
+// in by bulk copies into two buffers, and their products go to two TMEM
+// accumulators, so the MMA of tile nt+1 runs while tile nt is read out.  Row r
+// of the tile's alpha0 block (atoms in order) is written to a0 + r * K.
+constexpr int kCorrThreads = 128;
+constexpr int kCorrNT = 128;
+
+struct CorrLayout {
+  size_t aim, bim, bar, total;
 };
 
-TcLayout tc_layout(int TS, int NT, int K, int mp, int s, bool gcache) {
-  TcLayout L{};
-  L.TS = TS; L.NT = NT; L.gcache = gcache;
-  L.lp = odd_pitch(s);
+inline CorrLayout corr_layout(int mp) {
+  CorrLayout L{};
   size_t off = 0;
-  L.uni = off;   // first: 1024-aligned operand images / G-column cache
-  const size_t imgs = (size_t)(128 + NT) * mp * 2;
-  const size_t gcol = gcache ? sizeof(float) * (size_t)8 * s * K : 0;
-  off += align16(imgs > gcol ? imgs : gcol);
-  L.a0 = off;  off += align16(sizeof(float) * (size_t)TS * K);
-  L.ls = off;  off += align16(sizeof(float) * (size_t)8 * s * L.lp);
-  L.gx = off;  off += align16(sizeof(float) * (size_t)8 * s * L.lp);
+  L.aim = off; off += (size_t)128 * mp * 2;
+  L.bim = off; off += (size_t)2 * kCorrNT * mp * 2;
   L.bar = off; off += 64;
   L.total = off;
   return L;
 }
 
-// Prefer layouts that let two blocks share an SM (the selection loop is latency
-// bound and wants warps), then the largest signal tile.
-bool pick_tc_layout(int K, int mp, int s, TcLayout *out) {
-  const size_t limits[2] = {113 * 1024, 227 * 1024};
-  const int tss[4] = {128, 64, 32, 16}, nts[3] = {256, 128, 64};
-  for (int li = 0; li < 2; ++li)
-    for (int ti = 0; ti < 4; ++ti)
-      for (int ni = 0; ni < 3; ++ni)
-        for (int gcv = 1; gcv >= 0; --gcv) {
-          TcLayout L = tc_layout(tss[ti], nts[ni], K, mp, s, gcv == 1);
-          if (L.total <= limits[li]) { *out = L; return true; }
-        }
-  return false;
-}
-
-// One block codes TS signals of one subset: alpha0 tile on the tensor cores
-// (one M=128 MMA row block, N-tiles of NT atoms), then the selection loop.
-template <int KPL, int MU>
-__global__ void __launch_bounds__(kTcThreads) omp_tc_kernel(OmpArgs a, TcLayout lay) {
+__global__ void __launch_bounds__(kCorrThreads) corr_tc_kernel(OmpArgs a, CorrLayout lay, float *a0c, int64_t tile0) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int K = a.K, m = a.m, s = a.s, mp = a.mp, Kp = a.Kp, TS = lay.TS, NT = lay.NT;
+  const int K = a.K, m = a.m, mp = a.mp, Kp = a.Kp;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t g = blockIdx.x;
+  const int64_t g = tile0 + blockIdx.x;
   const int t = find_subset(a.tile_start, a.L, g);
-  const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)TS;
+  const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)128;
   const int64_t rows_left = a.offsets[t + 1] - row0;
-  const int nsig = rows_left < TS ? (int)rows_left : TS;
-  const float *__restrict__ Dt = static_cast<const float *>(a.D) + (size_t)t * K * m;
-  const float *__restrict__ Gt = static_cast<const float *>(a.G) + (size_t)t * K * K;
+  const int nsig = rows_left < 128 ? (int)rows_left : 128;
   const float *__restrict__ Y = static_cast<const float *>(a.Y);
   const unsigned char *sub = static_cast<const unsigned char *>(a.Dimg) + (size_t)t * Kp * mp * 2;
-  float *a0 = reinterpret_cast<float *>(smem + lay.a0);
-  unsigned char *Aim = smem + lay.uni;
-  unsigned char *Bim = Aim + (size_t)128 * mp * 2;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + lay.bar);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
-  int *fail = reinterpret_cast<int *>(mbar + 3);
-  const uint32_t ncols = (uint32_t)NT;
+  unsigned char *Aim = smem + lay.aim;
+  unsigned char *Bim = smem + lay.bim;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + lay.bar);   // [0,1] loads, [2,3] MMA commits
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 4);
+  int *fail = reinterpret_cast<int *>(bar + 5);
+  const size_t btile = (size_t)kCorrNT * mp * 2;
+  const int ntiles = (K + kCorrNT - 1) / kCorrNT;
+  auto tile_bytes = [&](int nt) { return (uint32_t)min(kCorrNT, Kp - nt * kCorrNT) * (uint32_t)mp * 2u; };
 
-  if (warp == 0) tc::tmem_alloc(tslot, ncols);
+  if (warp == 0) tc::tmem_alloc(tslot, 2 * kCorrNT);
   if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
+    for (int q = 0; q < 4; ++q) tc::mbar_init(&bar[q], 1);
     tc::mbar_fence_init();
     *fail = 0;
+    for (int nt = 0; nt < 2 && nt < ntiles; ++nt) {
+      tc::mbar_expect_tx(&bar[nt], tile_bytes(nt));
+      tc::bulk_g2s(Bim + nt * btile, sub + (size_t)nt * kCorrNT * mp * 2, tile_bytes(nt), &bar[nt]);
+    }
   }
   // signal tile -> BF16 A image (rows beyond the tile are zero)
   const int kc8 = mp >> 3;
-  for (int q = tid; q < 128 * kc8; q += kTcThreads) {
+  for (int q = tid; q < 128 * kc8; q += kCorrThreads) {
     const int r = q / kc8, kc = q - r * kc8;
+    const float *yr = Y + (size_t)(row0 + r) * m;
     uint32_t packed[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int k0 = kc * 8 + 2 * e;
-      const float *yr = Y + (size_t)(row0 + r) * m;
       const float lo = (r < nsig && k0 < m) ? yr[k0] : 0.f;
       const float hi = (r < nsig && k0 + 1 < m) ? yr[k0 + 1] : 0.f;
       __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
@@ -199,68 +184,121 @@ __global__ void __launch_bounds__(kTcThreads) omp_tc_kernel(OmpArgs a, TcLayout 
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = *tslot;
-  const uint32_t idesc = tc::idesc_bf16(128, NT);
+  const uint32_t idesc = tc::idesc_bf16(128, kCorrNT);
   const uint32_t sbo = (uint32_t)kc8 * 128;
-  const int ntiles = (K + NT - 1) / NT;
-  for (int nt = 0; nt < ntiles; ++nt) {
-    const int rows = min(NT, Kp - nt * NT);
-    if (tid == 0) {
-      tc::mbar_expect_tx(&mbar[0], (uint32_t)rows * mp * 2);
-      tc::bulk_g2s(Bim, sub + (size_t)nt * NT * mp * 2, (uint32_t)rows * mp * 2, &mbar[0]);
-    }
-    if (!tc::mbar_wait(&mbar[0], nt & 1, kWaitLimit)) *fail = 1;
-    __syncthreads();
-    if (*fail) break;
-    if (tid == 0) {
-      tc::fence_after();
-      for (int ks = 0; ks < (mp >> 4); ++ks)
-        tc::mma_bf16(tbase, tc::smem_desc(tc::smem_u32(Aim) + ks * 256, 128, sbo),
-                     tc::smem_desc(tc::smem_u32(Bim) + ks * 256, 128, sbo), idesc, ks > 0);
-      tc::mma_commit(&mbar[1]);
-    }
-    if (!tc::mbar_wait(&mbar[1], nt & 1, kWaitLimit)) *fail = 1;
+  // tile nt's product into TMEM columns (nt & 1) * 128 (thread 0)
+  auto issue = [&](int nt) {
+    const int b = nt & 1;
+    if (!tc::mbar_wait(&bar[b], (nt >> 1) & 1, kWaitLimit)) { *fail = 1; return; }
+    tc::fence_after();
+    const uint32_t bsm = tc::smem_u32(Bim + b * btile);
+    for (int ks = 0; ks < (mp >> 4); ++ks)
+      tc::mma_bf16(tbase + (uint32_t)(b * kCorrNT), tc::smem_desc(tc::smem_u32(Aim) + ks * 256, 128, sbo),
+                   tc::smem_desc(bsm + ks * 256, 128, sbo), idesc, ks > 0);
+    tc::mma_commit(&bar[2 + b]);
+  };
+  if (tid == 0) issue(0);
+  const int row = 32 * warp + lane;
+  float *arow = a0c + ((size_t)(g - tile0) * 128 + row) * K;
+  int nt = 0;
+  for (; nt < ntiles; ++nt) {
+    const int b = nt & 1;
+    if (tid == 0 && nt + 1 < ntiles && !*fail) issue(nt + 1);
+    if (!tc::mbar_wait(&bar[2 + b], (nt >> 1) & 1, kWaitLimit)) *fail = 1;
     __syncthreads();
     if (*fail) break;
     tc::fence_after();
-    {   // warp w: TMEM lanes 32 (w % 4) .., columns of half w / 4
-      const int rq = (warp & 3) * 32, cb = (warp >> 2) * (NT >> 1);
-      const int row = rq + lane;
-      for (int c0 = cb; c0 < cb + (NT >> 1); c0 += 32) {
-        float v[32];
-        tc::tmem_ld32(tbase + ((uint32_t)rq << 16) + c0, v);
-        if (row < TS) {
+    for (int c0 = 0; c0 < kCorrNT; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * kCorrNT + c0), v);
+      const int col0 = nt * kCorrNT + c0;
+      if (row < nsig) {
+        if (col0 + 32 <= K && (K & 3) == 0) {
 #pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int col = nt * NT + c0 + e;
-            if (col < K) a0[(size_t)row * K + col] = v[e];
-          }
+          for (int e = 0; e < 32; e += 4)
+            *reinterpret_cast<float4 *>(arow + col0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            if (col0 + e < K) arow[col0 + e] = v[e];
         }
       }
     }
     tc::fence_before();
-    __syncthreads();   // TMEM and the B image are free for the next tile
+    __syncthreads();   // buffer b (TMEM columns and B image) is free again
+    if (tid == 0 && nt + 2 < ntiles) {
+      tc::mbar_expect_tx(&bar[b], tile_bytes(nt + 2));
+      tc::bulk_g2s(Bim + b * btile, sub + (size_t)(nt + 2) * kCorrNT * mp * 2, tile_bytes(nt + 2), &bar[b]);
+    }
   }
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, ncols);
   if (*fail) {
-    if (tid == 0 && a.err) atomicOr(a.err, 1);
-    return;
+    // wait (bounded) for the bulk copies still in flight before the shared
+    // memory is given back: loads of tiles nt .. nt + 1 may be outstanding
+    if (tid == 0) {
+      for (int q = nt; q < nt + 2 && q < ntiles; ++q) tc::mbar_wait(&bar[q & 1], (q >> 1) & 1, kWaitLimit);
+      if (a.err) atomicOr(a.err, 1);
+    }
   }
-  float *Ls = reinterpret_cast<float *>(smem + lay.ls) + (size_t)warp * s * lay.lp;
-  float *Gx = reinterpret_cast<float *>(smem + lay.gx) + (size_t)warp * s * lay.lp;
-  float *gc = reinterpret_cast<float *>(smem + lay.uni) + (size_t)warp * s * K;
-  const int spw = TS / 8;
-  code_warp_signals<float, KPL, MU, true>(a, a0, Y + (size_t)row0 * m, m, warp * spw, spw, nsig, row0, Dt, Gt, Ls, Gx, gc,
-                                      lay.lp, lay.gcache);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 2 * kCorrNT);
+}
+
+// ---- selection: the Batch-OMP loop and exact refit from alpha0 in global memory
+// A block covers a quarter (32 signals, 4 per warp) of a 128-signal tile; shared
+// memory holds only the per-warp factors and, when it fits, the G-column cache,
+// so many blocks share an SM to hide the loop's latency.
+constexpr int kSelThreads = 256;
+
+struct SelLayout {
+  int lp;
+  bool gcache;
+  size_t ls, gx, gc, total;
+};
+
+inline SelLayout sel_layout(int K, int s) {
+  SelLayout L{};
+  L.lp = odd_pitch(s);
+  const size_t gcol = sizeof(float) * (size_t)8 * s * K;
+  L.gcache = gcol <= 48 * 1024;
+  size_t off = 0;
+  L.ls = off; off += align16(sizeof(float) * (size_t)8 * s * L.lp);
+  L.gx = off; off += align16(sizeof(float) * (size_t)8 * s * L.lp);
+  L.gc = off; off += L.gcache ? align16(gcol) : 0;
+  L.total = off;
+  return L;
 }
 
 template <int KPL, int MU>
-cudaError_t launch_omp_tc_kpl(const OmpArgs &a, const TcLayout &lay, cudaStream_t st) {
-  auto kern = omp_tc_kernel<KPL, MU>;
-  const size_t smem = tc::smem_for_tmem(lay.total, lay.NT);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+__global__ void __launch_bounds__(kSelThreads) omp_select_kernel(OmpArgs a, SelLayout lay, const float *a0c,
+                                                                 int64_t tile0) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int K = a.K, m = a.m, s = a.s;
+  const int warp = threadIdx.x >> 5;
+  const int64_t g = tile0 + blockIdx.x / 4;
+  const int quarter = blockIdx.x & 3;
+  const int t = find_subset(a.tile_start, a.L, g);
+  const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)128 + quarter * 32;
+  const int64_t rows_left = a.offsets[t + 1] - row0;
+  if (rows_left <= 0) return;   // whole block: nothing below is a block-wide barrier
+  const int nsig = rows_left < 32 ? (int)rows_left : 32;
+  const float *__restrict__ Dt = static_cast<const float *>(a.D) + (size_t)t * K * m;
+  const float *__restrict__ Gt = static_cast<const float *>(a.G) + (size_t)t * K * K;
+  const float *a0 = a0c + ((size_t)(g - tile0) * 128 + quarter * 32) * K;
+  float *Ls = reinterpret_cast<float *>(smem + lay.ls) + (size_t)warp * s * lay.lp;
+  float *Gx = reinterpret_cast<float *>(smem + lay.gx) + (size_t)warp * s * lay.lp;
+  float *gc = lay.gcache ? reinterpret_cast<float *>(smem + lay.gc) + (size_t)warp * s * K : nullptr;
+  code_warp_signals<float, KPL, MU, true>(a, a0, static_cast<const float *>(a.Y) + (size_t)row0 * m, m, warp * 4, 4,
+                                          nsig, row0, Dt, Gt, Ls, Gx, gc, lay.lp, lay.gcache);
+}
+
+template <int KPL, int MU>
+cudaError_t launch_select(const OmpArgs &a, const SelLayout &lay, const float *a0c, int64_t tile0, int64_t ntile,
+                          cudaStream_t st) {
+  auto kern = omp_select_kernel<KPL, MU>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)a.total_tiles, kTcThreads, smem, st>>>(a, lay);
+  kern<<<(unsigned)(ntile * 4), kSelThreads, lay.total, st>>>(a, lay, a0c, tile0);
   return cudaGetLastError();
 }
 
@@ -288,25 +326,46 @@ cudaError_t launch_gram_tc(const void *img, int K, int m, int L, float *G, int32
 }
 
 int omp_tc_tile_signals(int K, int m, int s) {
-  TcLayout lay;
-  return pick_tc_layout(K, round16(m), s, &lay) ? lay.TS : 0;
+  (void)K;
+  (void)m;
+  (void)s;
+  return 128;
 }
 
-cudaError_t launch_omp_tc(const OmpArgs &a, cudaStream_t st) {
+// Tiles per chunk of the alpha0 scratch (at most 1 GiB, at least one tile).
+int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles) {
+  const int64_t per = (int64_t)128 * K * (int64_t)sizeof(float);
+  int64_t c = ((int64_t)1 << 30) / per;
+  if (c < 1) c = 1;
+  return c < total_tiles ? c : (total_tiles > 0 ? total_tiles : 1);
+}
+
+cudaError_t launch_omp_tc(const OmpArgs &a, float *a0c, cudaStream_t st) {
   if (a.total_tiles <= 0) return cudaSuccess;
-  TcLayout lay;
-  if (!pick_tc_layout(a.K, a.mp, a.s, &lay)) return cudaErrorInvalidConfiguration;
+  const CorrLayout cl = corr_layout(a.mp);
+  const size_t csm = tc::smem_for_tmem(cl.total, 2 * kCorrNT);
+  if (csm > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+  if (e != cudaSuccess) return e;
+  const SelLayout sl = sel_layout(a.K, a.s);
   const int kpl = (a.K + 31) / 32;
-  if (a.m <= 64) {
-    if (kpl <= 4) return launch_omp_tc_kpl<4, 2>(a, lay, st);
-    if (kpl <= 8) return launch_omp_tc_kpl<8, 2>(a, lay, st);
-    if (kpl <= 16) return launch_omp_tc_kpl<16, 2>(a, lay, st);
-    return launch_omp_tc_kpl<32, 2>(a, lay, st);
+  const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles);
+  for (int64_t g0 = 0; g0 < a.total_tiles; g0 += chunk) {
+    const int64_t nt = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
+    corr_tc_kernel<<<(unsigned)nt, kCorrThreads, csm, st>>>(a, cl, a0c, g0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.m <= 64) {
+      e = kpl <= 4 ? launch_select<4, 2>(a, sl, a0c, g0, nt, st)
+        : kpl <= 8 ? launch_select<8, 2>(a, sl, a0c, g0, nt, st)
+        : kpl <= 16 ? launch_select<16, 2>(a, sl, a0c, g0, nt, st) : launch_select<32, 2>(a, sl, a0c, g0, nt, st);
+    } else {
+      e = kpl <= 4 ? launch_select<4, 8>(a, sl, a0c, g0, nt, st)
+        : kpl <= 8 ? launch_select<8, 8>(a, sl, a0c, g0, nt, st)
+        : kpl <= 16 ? launch_select<16, 8>(a, sl, a0c, g0, nt, st) : launch_select<32, 8>(a, sl, a0c, g0, nt, st);
+    }
+    if (e != cudaSuccess) return e;
   }
-  if (kpl <= 4) return launch_omp_tc_kpl<4, 8>(a, lay, st);
-  if (kpl <= 8) return launch_omp_tc_kpl<8, 8>(a, lay, st);
-  if (kpl <= 16) return launch_omp_tc_kpl<16, 8>(a, lay, st);
-  return launch_omp_tc_kpl<32, 8>(a, lay, st);
+  return cudaSuccess;
 }
 
 }  // namespace sdl

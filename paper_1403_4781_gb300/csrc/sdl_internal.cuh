@@ -121,8 +121,12 @@ int omp_tile_signals();
 inline int round16(int x) { return (x + 15) & ~15; }
 cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, cudaStream_t st);
 cudaError_t launch_gram_tc(const void *img, int K, int m, int L, float *G, int32_t *err, cudaStream_t st);
-cudaError_t launch_omp_tc(const OmpArgs &a, cudaStream_t st);
-int omp_tc_tile_signals(int K, int m, int s);   // 0 when no layout fits
+// Correlations of 128-signal tiles on the tensor cores into the scratch a0c
+// (omp_tc_chunk_tiles tiles of 128 x K floats at a time), then the selection
+// loop from there.
+cudaError_t launch_omp_tc(const OmpArgs &a, float *a0c, cudaStream_t st);
+int omp_tc_tile_signals(int K, int m, int s);
+int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles);
 
 struct ModArgs {
   const void *Y;          // [n][m]

@@ -200,3 +200,81 @@ def config2(shape: str = "A", L: int = 512, iters: int = 20) -> SplitMergeProble
     m, K, s = (64, 256, 6) if shape == "A" else (144, 512, 10)
     sizes = uneven_sizes(rng, L, 500, 8000)
     return split_merge_problem(f"uneven_{shape}_m{m}_K{K}", m, K, s, s, 1, K, sizes, iters, 0, 0.02, rng)
+
+
+def synthetic_image(rng: np.random.Generator, size: int = 512, bumps: int = 32, edges: int = 8,
+                    sigma: float = 0.1) -> np.ndarray:
+    """A piecewise-smooth random field: the sum of `bumps` 2-D Gaussian bumps
+    (centres uniform over the image, widths uniform on [8, 64] pixels,
+    amplitudes uniform on [-1, 1]) and `edges` straight edges (a step uniform on
+    [-0.5, 0.5] on one side of a line through a uniform point at a uniform
+    angle), min-max scaled to [0, 1], plus N(0, sigma^2) noise (not clipped)."""
+    g = np.arange(size, dtype=np.float64)
+    img = np.zeros((size, size))
+    for _ in range(bumps):
+        cy, cx = rng.uniform(0, size, 2)
+        w = rng.uniform(8, 64)
+        a = rng.uniform(-1, 1)
+        img += a * np.outer(np.exp(-0.5 * ((g - cy) / w) ** 2), np.exp(-0.5 * ((g - cx) / w) ** 2))
+    for _ in range(edges):
+        py, px = rng.uniform(0, size, 2)
+        th = rng.uniform(0, np.pi)
+        step = rng.uniform(-0.5, 0.5)
+        side = (np.cos(th) * (g[:, None] - py) + np.sin(th) * (g[None, :] - px)) > 0
+        img += step * side
+    lo, hi = img.min(), img.max()
+    img = (img - lo) / (hi - lo) if hi > lo else np.zeros_like(img)
+    return img + sigma * rng.standard_normal(img.shape)
+
+
+def random_patches(rng: np.random.Generator, img: np.ndarray, count: int, p: int = 16) -> np.ndarray:
+    """`count` p x p patches at uniform positions, each flattened row-major."""
+    H, W = img.shape
+    ys = rng.integers(0, H - p + 1, size=count)
+    xs = rng.integers(0, W - p + 1, size=count)
+    win = np.lib.stride_tricks.sliding_window_view(img, (p, p))
+    return win[ys, xs].reshape(count, p * p)
+
+
+def overcomplete_dct(p: int, qa: int, qb: int) -> np.ndarray:
+    """Separable overcomplete DCT dictionary for p x p patches with qa x qb
+    atoms, returned [qa qb][p p]: atom (a, b) is the outer product of 1-D
+    cosines cos(pi i a / qa) and cos(pi j b / qb) (i, j = 0..p-1), each 1-D
+    frame with its non-constant columns made zero-mean, every atom scaled to
+    unit norm."""
+    def frame(q):
+        i = np.arange(p)[:, None]
+        F = np.cos(np.pi * i * np.arange(q)[None, :] / q)
+        F[:, 1:] -= F[:, 1:].mean(axis=0, keepdims=True)
+        return F / np.linalg.norm(F, axis=0, keepdims=True)
+    Fa, Fb = frame(qa), frame(qb)
+    D = np.einsum("ia,jb->abij", Fa, Fb).reshape(qa * qb, p * p)
+    return D / np.linalg.norm(D, axis=1, keepdims=True)
+
+
+def config4(n_images: int = 256, per_image: int = 16384, L: int = 256, iters_local: int = 20,
+            iters_merge: int = 20) -> SplitMergeProblem:
+    """Large image-patch split-and-merge workload: 16 x 16 patches (m = 256,
+    FP32) of synthetic images, split at random into L equal subsets; local
+    K1 = 512 atoms with s1 = 4, merge to K = 1024 atoms with s2 = 4, final
+    sparsity 16.  Both the local and the merge dictionaries start from an
+    overcomplete DCT (256 x 512 and 256 x 1024), as the paper's image experiment
+    does; `extra` holds those initial dictionaries and the final sparsity.
+    Smaller n_images / per_image / L give the same recipe at a smaller size."""
+    rng = rng_for(4)
+    N = n_images * per_image
+    Y = np.empty((N, 256), dtype=np.float32)
+    for q in range(n_images):
+        img = synthetic_image(rng)
+        Y[q * per_image:(q + 1) * per_image] = random_patches(rng, img, per_image)
+    sizes = np.full(L, N // L, dtype=np.int64)
+    sizes[: N % L] += 1
+    perm, offsets = random_partition(rng, sizes)
+    K1, K = 512, 1024
+    D_loc0 = overcomplete_dct(16, 16, 32).astype(np.float32)
+    D_mer0 = overcomplete_dct(16, 32, 32).astype(np.float32)
+    prob = SplitMergeProblem("patches_m256_K1024", 256, K, 16, 4, 4, K1, iters_local, iters_merge, 0.1,
+                             D_mer0, Y, perm, offsets, np.full((L, K1), -1, np.int64),
+                             np.broadcast_to(D_loc0, (L, K1, 256)).copy(), np.zeros(K, np.int32),
+                             extra={"D_local0": D_loc0, "D_merge0": D_mer0, "s_final": 16})
+    return prob
