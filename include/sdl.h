@@ -248,8 +248,22 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     synchronises the stream once) and keeps the fastest for the context;
  *     calls made while the stream is being captured use a rule on the shape
  *     instead.  0 = always use that rule (and forget tuned shapes).
+ *   SDL_OPT_GRAPH: 1 = the training loops of sdl_local_train and sdl_merge run
+ *     as CUDA graphs: the first call with a given set of buffers, sizes and
+ *     options runs eagerly, the second captures the iterations and launches
+ *     the graph, later ones relaunch it (the per-call plans and the status
+ *     read-back stay outside the graph).  While instrumentation is on, calls
+ *     run eagerly.  Graphs refer to the caller's buffers: do not free a buffer
+ *     that a cached graph uses while the option is on (turning it off, or a
+ *     workspace reallocation, drops the cache).  0 (default) = always eager.
  * Returns SDL_EINVAL for an unknown option or value. */
-typedef enum { SDL_OPT_MOD_SOLVE = 1, SDL_OPT_CLUSTER = 2, SDL_OPT_MOD_TILE = 3, SDL_OPT_AUTOTUNE = 4 } sdl_option;
+typedef enum {
+  SDL_OPT_MOD_SOLVE = 1,
+  SDL_OPT_CLUSTER = 2,
+  SDL_OPT_MOD_TILE = 3,
+  SDL_OPT_AUTOTUNE = 4,
+  SDL_OPT_GRAPH = 5
+} sdl_option;
 sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
 
 /* Instrumentation (the paper has no counterpart; it serves the roofline

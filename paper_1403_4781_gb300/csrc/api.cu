@@ -27,11 +27,20 @@ void ws_reset(sdl_ctx *ctx) { ctx->ws.used = 0; }
 static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Make sure the workspace holds `bytes`; regrowth synchronises the stream.
+// Captured training loops refer to workspace addresses: drop them all.
+static void clear_graphs(sdl_ctx *ctx) {
+  for (auto &kv : ctx->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  ctx->graphs.clear();
+  ctx->graph_seen.clear();
+}
+
 static sdl_status ws_reserve(sdl_ctx *ctx, size_t bytes) {
   ws_reset(ctx);
   if (bytes <= ctx->ws.cap) return SDL_OK;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return check_cuda(ctx, e, "workspace sync");
+  clear_graphs(ctx);
   if (ctx->ws.base) cudaFree(ctx->ws.base);
   ctx->ws.base = nullptr;
   ctx->ws.cap = 0;
@@ -470,26 +479,80 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   SDL_CUDA(cudaMemsetAsync(worst, 0, sizeof(int32_t) * (iters + 1), ctx->stream), "status clear");
   if (xfro) SDL_CUDA(cudaMemsetAsync(xfro, 0, sizeof(double) * L, ctx->stream), "xfro clear");
   cudaStream_t sm = ctx->stream;
-  for (int it = 0; it < iters; ++it) {
-    cudaError_t e;
-    if (bf16) {
-      e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), Gex, tc_err, a0c);
-    } else {
-      SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
-      e = timed(ctx, "omp", 1, [&] { return launch_omp<T>(oa, ctx->num_sms, sm); });
+  auto run_loop = [&]() -> sdl_status {
+    for (int it = 0; it < iters; ++it) {
+      cudaError_t e;
+      if (bf16) {
+        e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), Gex, tc_err, a0c);
+      } else {
+        SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
+        e = timed(ctx, "omp", 1, [&] { return launch_omp<T>(oa, ctx->num_sms, sm); });
+      }
+      if (e == cudaErrorInvalidConfiguration)
+        return set_error(ctx, SDL_EINVAL, "shape too large for the OMP kernel's shared memory");
+      SDL_CUDA(e, "omp");
+      SDL_CUDA(timed(ctx, "subset_stats", 1, [&] {
+                 return launch_subset_stats<T>(res2, val, d_off, L, m, s, rmse ? rmse + it : nullptr, iters,
+                                               it == iters - 1 ? xfro : nullptr, sm);
+               }), "subset stats");
+      SDL_CUDA(timed(ctx, "mod_accum", mod_accum_kernels(sizeof(T) == 4, ma.total_tiles),
+                     [&] { return launch_mod_accum<T>(ma, sm); }), "mod accumulate");
+      SDL_CUDA(run_mod_solve<T>(ctx, ma), "mod solve");
+      SDL_CUDA(timed(ctx, "status", 1, [&] { return launch_status_max(ma.status, L, worst + it, sm); }),
+               "status");
     }
-    if (e == cudaErrorInvalidConfiguration)
-      return set_error(ctx, SDL_EINVAL, "shape too large for the OMP kernel's shared memory");
-    SDL_CUDA(e, "omp");
-    SDL_CUDA(timed(ctx, "subset_stats", 1, [&] {
-               return launch_subset_stats<T>(res2, val, d_off, L, m, s, rmse ? rmse + it : nullptr, iters,
-                                             it == iters - 1 ? xfro : nullptr, sm);
-             }), "subset stats");
-    SDL_CUDA(timed(ctx, "mod_accum", mod_accum_kernels(sizeof(T) == 4, ma.total_tiles),
-                   [&] { return launch_mod_accum<T>(ma, sm); }), "mod accumulate");
-    SDL_CUDA(run_mod_solve<T>(ctx, ma), "mod solve");
-    SDL_CUDA(timed(ctx, "status", 1, [&] { return launch_status_max(ma.status, L, worst + it, sm); }),
-             "status");
+    return SDL_OK;
+  };
+  // Graph replay: the loop's launches depend only on the pointers and sizes in
+  // the key (the per-call plans are re-uploaded into the same workspace
+  // addresses before it), so a key seen once eagerly is captured on its second
+  // call and replayed from then on.
+  const bool use_graph = ctx->opt_graph && !ctx->prof.on && iters > 0;
+  if (!use_graph) {
+    if ((st = run_loop()) != SDL_OK) return st;
+  } else {
+    char kb[512];
+    snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d",
+             sizeof(T), (int)bf16, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
+             (void *)d_off, m, K, s, L, (long long)n, (long long)tiles, (long long)ma.total_tiles, eps, iters,
+             ctx->opt_mod_solve, ctx->opt_tile, ctx->opt_cluster, ctx->opt_autotune, (int)ctx->tuned.size());
+    const std::string key(kb);
+    auto hit = ctx->graphs.find(key);
+    if (hit != ctx->graphs.end()) {
+      SDL_CUDA(cudaGraphLaunch(hit->second.exec, sm), "graph launch");
+      ctx->launches += hit->second.kernels;
+    } else if (!ctx->graph_seen.count(key)) {
+      ctx->graph_seen[key] = 1;
+      if ((st = run_loop()) != SDL_OK) return st;
+    } else {
+      if (ctx->graphs.size() >= 16) clear_graphs(ctx);
+      if (!ctx->capture_stream)
+        SDL_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "capture stream");
+      const int64_t before = ctx->launches;
+      const cudaStream_t user = ctx->stream;
+      SDL_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed), "graph capture");
+      ctx->stream = sm = ctx->capture_stream;   // every launcher of the loop records into the capture
+      st = run_loop();
+      ctx->stream = sm = user;
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
+      if (st != SDL_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return st;
+      }
+      SDL_CUDA(ce, "graph capture end");
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      SDL_CUDA(ie, "graph instantiate");
+      sdl_ctx::GraphEntry ent;
+      ent.exec = exec;
+      ent.kernels = ctx->launches - before;
+      ctx->graphs[key] = ent;
+      ctx->graph_seen[key] = 1;
+      SDL_CUDA(cudaGraphLaunch(exec, sm), "graph launch");
+    }
   }
   if (iters > 0) {
     if ((st = mod_status(ctx, worst, iters, d_max)) != SDL_OK) return st;
@@ -534,6 +597,8 @@ sdl_status sdl_destroy(sdl_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     prof_resolve(ctx);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    clear_graphs(ctx);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->ws.base) cudaFree(ctx->ws.base);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
   }
@@ -938,6 +1003,11 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
       if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_AUTOTUNE takes 0 or 1");
       ctx->opt_autotune = (int)value;
       if (!value) ctx->tuned.clear();
+      return SDL_OK;
+    case SDL_OPT_GRAPH:
+      if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_GRAPH takes 0 or 1");
+      ctx->opt_graph = (int)value;
+      if (!value) clear_graphs(ctx);
       return SDL_OK;
     default:
       return set_error(ctx, SDL_EINVAL, "unknown option");

@@ -70,6 +70,14 @@ struct sdl_ctx {
   std::map<int64_t, int> occ;    // cached max active clusters of the tiled solve
   int opt_autotune = 1;          // time candidate launch shapes on first use
   std::map<std::string, std::pair<int, int>> tuned;   // shape key -> chosen (tile, cluster)
+  int opt_graph = 0;             // replay training loops as captured CUDA graphs
+  struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+  };
+  std::map<std::string, GraphEntry> graphs;   // call key -> instantiated training loop
+  cudaStream_t capture_stream = nullptr;       // graphs are captured here (never the legacy stream)
+  std::map<std::string, int> graph_seen;      // call keys run once eagerly
 };
 
 namespace sdl {
