@@ -522,6 +522,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
       SDL_CUDA(cudaGraphLaunch(hit->second.exec, sm), "graph launch");
       ctx->launches += hit->second.kernels;
     } else if (!ctx->graph_seen.count(key)) {
+      if (ctx->graph_seen.size() >= 256) ctx->graph_seen.clear();
       ctx->graph_seen[key] = 1;
       if ((st = run_loop()) != SDL_OK) return st;
     } else {
