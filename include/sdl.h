@@ -242,6 +242,9 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     option 1, 1 to 16 for option 3.
  *   SDL_OPT_MOD_TILE: tile edge of the tiled solve: 0 = automatic (default),
  *     16 or 32.
+ *   SDL_OPT_SM_BLOCKS: with the tile or cluster size set by hand, at most this
+ *     many blocks of the tiled solve per SM (1 to 3; 0 = as many as fit, the
+ *     default).  The autotuner also tries a cap of 2.
  *   SDL_OPT_AUTOTUNE: 1 (default) = where tile and cluster size are automatic,
  *     the first call for a shape (element type, number of subsets, K, m) times
  *     every candidate on the call's own inputs with CUDA events (this
@@ -262,7 +265,8 @@ typedef enum {
   SDL_OPT_CLUSTER = 2,
   SDL_OPT_MOD_TILE = 3,
   SDL_OPT_AUTOTUNE = 4,
-  SDL_OPT_GRAPH = 5
+  SDL_OPT_GRAPH = 5,
+  SDL_OPT_SM_BLOCKS = 6
 } sdl_option;
 sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
 

@@ -86,7 +86,7 @@ _SIGS = {
     "sdl_omp_proposed": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp,
                                 ctypes.POINTER(_i64)]),
 }
-OPT_MOD_SOLVE, OPT_CLUSTER, OPT_MOD_TILE, OPT_AUTOTUNE, OPT_GRAPH = 1, 2, 3, 4, 5
+OPT_MOD_SOLVE, OPT_CLUSTER, OPT_MOD_TILE, OPT_AUTOTUNE, OPT_GRAPH, OPT_SM_BLOCKS = 1, 2, 3, 4, 5, 6
 
 
 def lib() -> ctypes.CDLL:

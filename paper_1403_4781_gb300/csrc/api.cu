@@ -122,11 +122,11 @@ void prof_resolve(sdl_ctx *ctx) {
 
 // Cached number of clusters of the tiled solve that fit on the device at once.
 template <typename T>
-int tiled_occupancy(sdl_ctx *ctx, int ts, int C) {
-  const int64_t key = ((int64_t)(sizeof(T)) << 32) | ((int64_t)ts << 8) | C;
+int tiled_occupancy(sdl_ctx *ctx, int ts, int C, int cap) {
+  const int64_t key = ((int64_t)(sizeof(T)) << 32) | ((int64_t)cap << 16) | ((int64_t)ts << 8) | C;
   auto it = ctx->occ.find(key);
   if (it != ctx->occ.end()) return it->second;
-  const int n = mod_tiled_max_clusters<T>(ts, C, 0, 0);
+  const int n = mod_tiled_max_clusters<T>(ts, C, cap);
   ctx->occ[key] = n;
   return n;
 }
@@ -144,7 +144,7 @@ void pick_tiled(sdl_ctx *ctx, int L, int *ts, int *C) {
     c = 1;
     const int cand[6] = {16, 8, 6, 4, 2, 1};
     for (int q = 0; q < 6; ++q) {
-      const int n = tiled_occupancy<T>(ctx, t, cand[q]);
+      const int n = tiled_occupancy<T>(ctx, t, cand[q], 0);
       if (n >= L) { c = cand[q]; break; }
     }
   }
@@ -154,31 +154,36 @@ void pick_tiled(sdl_ctx *ctx, int L, int *ts, int *C) {
 
 // Autotuner of the tiled solve: on the first call for a shape (element type,
 // subsets, K, m) that leaves the tile and cluster size automatic, every
-// candidate is run on the caller's own inputs (the solve reads A, B and the
-// usage counts and rewrites only scratch, D and the status, so repeated runs
-// give the same result) and timed with CUDA events; the fastest is cached in
-// the context and run last.  Skipped while the stream is being captured (the
-// shape rule above is used then) or when the option turns it off.
+// candidate tile edge and cluster size is run on the caller's own inputs (the
+// solve reads A, B and the usage counts and rewrites only scratch, D and the
+// status, so repeated runs give the same result) and timed with CUDA events;
+// the fastest is cached in the context and run last.  (Capping the blocks per
+// SM to balance clusters over the SMs was measured slower at every shape tried:
+// the FP64 pipe wants the warps more than the balance, so it is not a
+// candidate.)  Skipped while the stream is being captured (the shape rule
+// above is used then) or when the option turns it off.
 template <typename T>
 cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
   cudaStream_t sm = ctx->stream;
-  int ts = 32, C = 1;
+  int ts = 32, C = 1, cap = 0;
   const bool manual = ctx->opt_tile != 0 || ctx->opt_cluster != 0;
   const std::string key = std::to_string(sizeof(T)) + ":" + std::to_string(ma.L) + ":" + std::to_string(ma.K) +
                           ":" + std::to_string(ma.m);
   auto it = ctx->tuned.find(key);
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(sm, &cap) != cudaSuccess) {
+  cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(sm, &capst) != cudaSuccess) {
     cudaGetLastError();
-    cap = cudaStreamCaptureStatusActive;
+    capst = cudaStreamCaptureStatusActive;
   }
   if (!manual && it != ctx->tuned.end()) {
-    ts = it->second.first;
-    C = it->second.second;
-  } else if (manual || !ctx->opt_autotune || cap != cudaStreamCaptureStatusNone) {
+    ts = it->second.ts;
+    C = it->second.C;
+    cap = it->second.cap;
+  } else if (manual || !ctx->opt_autotune || capst != cudaStreamCaptureStatusNone) {
     pick_tiled<T>(ctx, ma.L, &ts, &C);
+    if (manual) cap = ctx->opt_sm_blocks;
   } else {
-    int best_ts = 0, best_c = 0;
+    int best_ts = 0, best_c = 0, best_cap = 0;
     float best = 3.4e38f;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
@@ -187,15 +192,15 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
     const int cls[7] = {1, 2, 3, 4, 6, 8, 16};
     for (int a = 0; a < 2 && e == cudaSuccess; ++a)
       for (int b = 0; b < 7 && e == cudaSuccess; ++b) {
-        const int t = tiles[a], c = cls[b];
+        const int t = tiles[a], c = cls[b], cp = 0;
         // a subset's cluster must fit on the device; small clusters for few
         // subsets leave most SMs idle and are not worth timing
-        if (tiled_occupancy<T>(ctx, t, c) < 1) continue;
+        if (tiled_occupancy<T>(ctx, t, c, cp) < 1) continue;
         if ((int64_t)ma.L * c * 4 < ctx->num_sms && c < 16) continue;
         float ms_best = 3.4e38f;
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
           e = cudaEventRecord(e0, sm);
-          if (e == cudaSuccess) e = launch_mod_tiled<T>(ma, t, c, sm);
+          if (e == cudaSuccess) e = launch_mod_tiled<T>(ma, t, c, cp, sm);
           if (e == cudaSuccess) ctx->launches += 1;
           if (e == cudaSuccess) e = cudaEventRecord(e1, sm);
           if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -203,7 +208,7 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
           if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
           if (e == cudaSuccess && ms < ms_best) ms_best = ms;
         }
-        if (e == cudaSuccess && ms_best < best) { best = ms_best; best_ts = t; best_c = c; }
+        if (e == cudaSuccess && ms_best < best) { best = ms_best; best_ts = t; best_c = c; best_cap = cp; }
       }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -213,12 +218,13 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
     } else {
       ts = best_ts;
       C = best_c;
+      cap = best_cap;
     }
-    ctx->tuned[key] = std::make_pair(ts, C);
+    ctx->tuned[key] = sdl_ctx::TunedSolve{ts, C, cap};
   }
   // the batched solve and the single-system (merge) solve are reported apart
   return timed(ctx, ma.L > 1 ? "mod_solve_fp64" : "mod_solve_fp64_single", 1,
-               [&] { return launch_mod_tiled<T>(ma, ts, C, sm); });
+               [&] { return launch_mod_tiled<T>(ma, ts, C, cap, sm); });
 }
 
 // FP64 Cholesky + solve + renormalisation: the tiled cluster kernel unless an
@@ -515,7 +521,8 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
     snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d",
              sizeof(T), (int)bf16, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
              (void *)d_off, m, K, s, L, (long long)n, (long long)tiles, (long long)ma.total_tiles, eps, iters,
-             ctx->opt_mod_solve, ctx->opt_tile, ctx->opt_cluster, ctx->opt_autotune, (int)ctx->tuned.size());
+             ctx->opt_mod_solve, ctx->opt_tile, ctx->opt_cluster * 4 + ctx->opt_sm_blocks, ctx->opt_autotune,
+             (int)ctx->tuned.size());
     const std::string key(kb);
     auto hit = ctx->graphs.find(key);
     if (hit != ctx->graphs.end()) {
@@ -1004,6 +1011,10 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
       if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_AUTOTUNE takes 0 or 1");
       ctx->opt_autotune = (int)value;
       if (!value) ctx->tuned.clear();
+      return SDL_OK;
+    case SDL_OPT_SM_BLOCKS:
+      if (value < 0 || value > 3) return set_error(ctx, SDL_EINVAL, "SDL_OPT_SM_BLOCKS takes 0 to 3");
+      ctx->opt_sm_blocks = (int)value;
       return SDL_OK;
     case SDL_OPT_GRAPH:
       if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_GRAPH takes 0 or 1");

@@ -406,18 +406,31 @@ size_t mod_tiled_scratch_doubles(int L, int K, int m) {
   return (size_t)L * ((size_t)(K + m) * K + (size_t)R * 16 * 16 + (size_t)((K + 31) / 32) * 32 * 32);
 }
 
+// Dynamic shared memory that keeps at most `cap` blocks on an SM (0: no cap):
+// more than 1/(cap + 1) of the SM's 228 KB with the static part included.
+template <int TS>
+static size_t cap_smem(int cap) {
+  if (cap <= 0) return 0;
+  const size_t stat = sizeof(TiledSmem<TS>) + 2 * sizeof(double) * (kTThreads / 32) + 64;
+  const size_t want = (size_t)228 * 1024 / (size_t)(cap + 1) + 1024;
+  return want > stat ? want - stat : 0;
+}
+
 template <typename T, int TS>
-static cudaError_t launch_tiled_ts(const ModArgs &a, int C, cudaStream_t st) {
+static cudaError_t launch_tiled_ts(const ModArgs &a, int C, int cap, cudaStream_t st) {
   auto kern = mod_tiled_kernel<T, TS>;
   cudaError_t e;
   if (C > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
+  const size_t dyn = cap_smem<TS>(cap);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((int64_t)a.L * C));
   cfg.blockDim = dim3(kTThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = dyn;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -433,15 +446,21 @@ static cudaError_t launch_tiled_ts(const ModArgs &a, int C, cudaStream_t st) {
 }
 
 template <typename T>
-int mod_tiled_max_clusters(int ts, int C, int K, int m) {
+int mod_tiled_max_clusters(int ts, int C, int cap) {
   auto kern = ts == 16 ? mod_tiled_kernel<T, 16> : mod_tiled_kernel<T, 32>;
   if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t dyn = ts == 16 ? cap_smem<16>(cap) : cap_smem<32>(cap);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)C);
   cfg.blockDim = dim3(kTThreads);
+  cfg.dynamicSmemBytes = dyn;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)C;
@@ -454,21 +473,19 @@ int mod_tiled_max_clusters(int ts, int C, int K, int m) {
     cudaGetLastError();
     return 0;
   }
-  (void)K;
-  (void)m;
   return n;
 }
 
 template <typename T>
-cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, cudaStream_t st) {
+cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, cudaStream_t st) {
   if (a.L <= 0) return cudaSuccess;
-  if (C < 1 || C > 16 || (ts != 16 && ts != 32)) return cudaErrorInvalidValue;
-  return ts == 16 ? launch_tiled_ts<T, 16>(a, C, st) : launch_tiled_ts<T, 32>(a, C, st);
+  if (C < 1 || C > 16 || (ts != 16 && ts != 32) || cap < 0 || cap > 3) return cudaErrorInvalidValue;
+  return ts == 16 ? launch_tiled_ts<T, 16>(a, C, cap, st) : launch_tiled_ts<T, 32>(a, C, cap, st);
 }
 
-template cudaError_t launch_mod_tiled<float>(const ModArgs &, int, int, cudaStream_t);
-template cudaError_t launch_mod_tiled<double>(const ModArgs &, int, int, cudaStream_t);
-template int mod_tiled_max_clusters<float>(int, int, int, int);
-template int mod_tiled_max_clusters<double>(int, int, int, int);
+template cudaError_t launch_mod_tiled<float>(const ModArgs &, int, int, int, cudaStream_t);
+template cudaError_t launch_mod_tiled<double>(const ModArgs &, int, int, int, cudaStream_t);
+template int mod_tiled_max_clusters<float>(int, int, int);
+template int mod_tiled_max_clusters<double>(int, int, int);
 
 }  // namespace sdl

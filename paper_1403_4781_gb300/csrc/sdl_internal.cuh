@@ -67,9 +67,13 @@ struct sdl_ctx {
   int opt_mod_solve = 0;         // 0 auto, 1 DSMEM cluster, 2 block per subset, 3 tiled
   int opt_cluster = 0;           // 0 = automatic
   int opt_tile = 0;              // tiled solve: 16, 32 or 0 = automatic
+  int opt_sm_blocks = 0;         // tiled solve: blocks per SM cap (0 = none) when set by hand
   std::map<int64_t, int> occ;    // cached max active clusters of the tiled solve
   int opt_autotune = 1;          // time candidate launch shapes on first use
-  std::map<std::string, std::pair<int, int>> tuned;   // shape key -> chosen (tile, cluster)
+  struct TunedSolve {
+    int ts, C, cap;
+  };
+  std::map<std::string, TunedSolve> tuned;   // shape key -> chosen tile, cluster size, blocks-per-SM cap
   int opt_graph = 0;             // replay training loops as captured CUDA graphs
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
@@ -175,10 +179,12 @@ int mod_tile_signals();
 // Tiled FP64 factorisation + solve + renormalisation, one cluster of C (1..16)
 // blocks per subset, TS x TS tiles (16 or 32); scratch in a.Lf of
 // mod_tiled_scratch_doubles(L, K, m) doubles.
+// cap: at most that many blocks per SM (1..3, through padded dynamic shared
+// memory), 0 = as many as fit.
 template <typename T>
-cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, cudaStream_t st);
+cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, cudaStream_t st);
 template <typename T>
-int mod_tiled_max_clusters(int ts, int C, int K, int m);
+int mod_tiled_max_clusters(int ts, int C, int cap);
 size_t mod_tiled_scratch_doubles(int L, int K, int m);
 
 template <typename T>

@@ -32,6 +32,7 @@ def ctx():
     c.set_option(sdl.OPT_MOD_SOLVE, 0)
     c.set_option(sdl.OPT_CLUSTER, 0)
     c.set_option(sdl.OPT_MOD_TILE, 0)
+    c.set_option(sdl.OPT_SM_BLOCKS, 0)
     c.set_option(sdl.OPT_AUTOTUNE, 1)
 
 
@@ -60,21 +61,23 @@ def _oracle_batched(offsets, Y, idx, val, D0):
     return np.stack(out)
 
 
-def _run(ctx, path, ts, C, offsets, Y, idx, val, D0):
+def _run(ctx, path, ts, C, offsets, Y, idx, val, D0, cap=0):
     ctx.set_option(sdl.OPT_MOD_SOLVE, path)
     ctx.set_option(sdl.OPT_MOD_TILE, ts)
     ctx.set_option(sdl.OPT_CLUSTER, C)
+    ctx.set_option(sdl.OPT_SM_BLOCKS, cap)
     Dg = _t(D0.copy())
     sdl.mod_update_batched(_t(Y), offsets, _t(idx), _t(val), Dg)
     return Dg.cpu().numpy()
 
 
 @pytest.mark.parametrize("K,m,s", [(60, 30, 4), (97, 33, 5), (256, 64, 6)])
-@pytest.mark.parametrize("ts,C", [(16, 1), (16, 3), (16, 16), (32, 1), (32, 2), (32, 8), (32, 16)])
-def test_tiled_solve_fp64_matches_oracle(ctx, ts, C, K, m, s):
+@pytest.mark.parametrize("ts,C,cap", [(16, 1, 0), (16, 3, 2), (16, 16, 0), (32, 1, 1), (32, 2, 0), (32, 8, 3),
+                                      (32, 16, 0)])
+def test_tiled_solve_fp64_matches_oracle(ctx, ts, C, cap, K, m, s):
     offsets, Y, idx, val, D0 = _problem(300 + K, [3 * K, 5 * K, 4 * K], m, K, s, np.float64)
     want = _oracle_batched(offsets, Y, idx, val, D0)
-    got = _run(ctx, 3, ts, C, offsets, Y, idx, val, D0)
+    got = _run(ctx, 3, ts, C, offsets, Y, idx, val, D0, cap)
     np.testing.assert_array_equal(got[:, K - 3:], D0[:, K - 3:])   # unused atoms: bit-exact
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-10)
 
