@@ -274,37 +274,40 @@ def mod_update_batched(Y, offsets, idx, val, D, prec=None):
     return usage
 
 
-def split(Y, perm, prec=None):
-    """Algorithm 1 step 1: returns Y[perm] computed by the gather kernel."""
+def split(Y, perm, prec=None, out=None):
+    """Algorithm 1 step 1: returns Y[perm] computed by the gather kernel (into
+    `out` when given)."""
     import torch
     prec = _prec_of(Y, prec)
     N, m = Y.shape
-    out = torch.empty_like(Y)
+    out = torch.empty_like(Y) if out is None else out
     ctx = context(Y.device.index)
     _call("sdl_split", ctx.bind_stream(), prec, _ptr(Y), m, N, _ptr(perm), _ptr(out))
     return out
 
 
-def init_dict(Y, pick, fill=None, prec=None):
-    """Unit-normalised Y[pick] (fill[c] where pick[c] < 0); pick int64 (count,)."""
+def init_dict(Y, pick, fill=None, prec=None, out=None):
+    """Unit-normalised Y[pick] (fill[c] where pick[c] < 0); pick int64 (count,);
+    written into `out` (count, m) when given."""
     import torch
     prec = _prec_of(Y, prec)
     nY, m = Y.shape
     count = pick.numel()
-    out = torch.empty((count, m), dtype=Y.dtype, device=Y.device)
+    out = torch.empty((count, m), dtype=Y.dtype, device=Y.device) if out is None else out
     ctx = context(Y.device.index)
     _call("sdl_init_dict", ctx.bind_stream(), prec, _ptr(Y), m, nY, _ptr(pick), _ptr(fill), count, _ptr(out))
     return out
 
 
-def local_train(Y, offsets, D_local, s1, iters, eps=0.0, prec=None, with_rmse=True):
+def local_train(Y, offsets, D_local, s1, iters, eps=0.0, prec=None, with_rmse=True, xfro=None):
     """Algorithm 1 step 2 in place on D_local (L, K1, m).
-    Returns (xfro (L,) f64, rmse (L, iters) f64 or None)."""
+    Returns (xfro (L,) f64 -- the buffer given, if any -- , rmse (L, iters) f64 or None)."""
     import torch
     prec = _prec_of(D_local, prec)
     L, K1, m = D_local.shape
     oh, op = _offsets_host(offsets)
-    xfro = torch.empty((L,), dtype=torch.float64, device=D_local.device)
+    if xfro is None:
+        xfro = torch.empty((L,), dtype=torch.float64, device=D_local.device)
     rmse = torch.empty((L, iters), dtype=torch.float64, device=D_local.device) if with_rmse else None
     ctx = context(D_local.device.index)
     _call("sdl_local_train", ctx.bind_stream(), prec, _ptr(Y), m, op, L, K1, s1, float(eps), iters,
@@ -312,19 +315,18 @@ def local_train(Y, offsets, D_local, s1, iters, eps=0.0, prec=None, with_rmse=Tr
     return xfro, rmse
 
 
-def merge(D_local, xfro, pick, K, s2, iters, eps=0.0, prec=None, with_rmse=True, D_init=None):
+def merge(D_local, xfro, pick, K, s2, iters, eps=0.0, prec=None, with_rmse=True, D_init=None, out=None):
     """Algorithm 1 step 3.  pick (K,) int32 selects the initial stacked columns;
-    pick=None starts from D_init (K, m) instead.  Returns (D (K, m), rmse
-    (iters,) f64 or None)."""
+    pick=None starts from D_init (K, m) instead.  The merged dictionary goes to
+    `out` (K, m) when given.  Returns (D (K, m), rmse (iters,) f64 or None)."""
     import torch
     prec = _prec_of(D_local, prec)
     L, K1, m = D_local.shape
+    D = torch.empty((K, m), dtype=D_local.dtype, device=D_local.device) if out is None else out
     if pick is None:
         if D_init is None or tuple(D_init.shape) != (K, m):
             raise ValueError("pick=None needs D_init of shape (K, m)")
-        D = D_init.to(dtype=D_local.dtype).contiguous().clone()
-    else:
-        D = torch.empty((K, m), dtype=D_local.dtype, device=D_local.device)
+        D.copy_(D_init)
     rmse = torch.empty((iters,), dtype=torch.float64, device=D_local.device) if with_rmse else None
     ctx = context(D_local.device.index)
     _call("sdl_merge", ctx.bind_stream(), prec, _ptr(D_local), _ptr(xfro), m, K1, L, _ptr(pick), K, s2,

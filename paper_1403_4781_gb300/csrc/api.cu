@@ -200,7 +200,7 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
         float ms_best = 3.4e38f;
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
           e = cudaEventRecord(e0, sm);
-          if (e == cudaSuccess) e = launch_mod_tiled<T>(ma, t, c, cp, sm);
+          if (e == cudaSuccess) e = launch_mod_tiled<T>(ma, t, c, cp, ctx->num_sms, sm);
           if (e == cudaSuccess) ctx->launches += 1;
           if (e == cudaSuccess) e = cudaEventRecord(e1, sm);
           if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -224,7 +224,7 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
   }
   // the batched solve and the single-system (merge) solve are reported apart
   return timed(ctx, ma.L > 1 ? "mod_solve_fp64" : "mod_solve_fp64_single", 1,
-               [&] { return launch_mod_tiled<T>(ma, ts, C, cap, sm); });
+               [&] { return launch_mod_tiled<T>(ma, ts, C, cap, ctx->num_sms, sm); });
 }
 
 // FP64 Cholesky + solve + renormalisation: the tiled cluster kernel unless an

@@ -219,12 +219,17 @@ __device__ bool factor_diag(TiledSmem<TS> &sm, const double *Mt, const TGeom &g,
   __syncthreads();
   if (tid == 0) pivot(sm, 0, sm.a[0][0]);
   __syncthreads();
+  // One sweep over the columns factors the tile and inverts the factor: once
+  // column c of L is final, row c of V = L^{-1} is (the unit row minus the
+  // earlier rows' contributions) / L_cc, and its contributions to the rows
+  // below are subtracted in the same phase as the trailing update.
   for (int c = 0; c < TS; ++c) {
     if (sm.fail) break;   // uniform: read after a barrier
     if (tid > c && tid < TS) sm.a[tid][c] *= sm.invd[c];
+    if (tid >= TS && tid - TS <= c) sm.b[c][tid - TS] *= sm.invd[c];
     __syncthreads();
-    // rank-1 update of the trailing triangle; the thread that updates the next
-    // diagonal entry takes its pivot
+    // rank-1 update of the trailing triangle (the thread that updates the next
+    // diagonal entry takes its pivot) and elimination of V's column block
     for (int e = tid; e < TS * TS; e += kTThreads) {
       const int r = e / TS, q = e % TS;
       if (q > c && q <= r) {
@@ -232,20 +237,11 @@ __device__ bool factor_diag(TiledSmem<TS> &sm, const double *Mt, const TGeom &g,
         if (r == c + 1 && q == c + 1) pivot(sm, c + 1, v);
         else sm.a[r][q] = v;
       }
+      if (r > c && q <= c) sm.b[r][q] = fma(-sm.a[r][c], sm.b[c][q], sm.b[r][q]);
     }
     __syncthreads();
   }
   if (sm.fail) return false;
-  // inverse: column-oriented forward substitution of L V = I
-  for (int q = 0; q < TS; ++q) {
-    if (tid <= q) sm.b[q][tid] *= sm.invd[q];
-    __syncthreads();
-    for (int e = tid; e < TS * TS; e += kTThreads) {
-      const int r = e / TS, j = e % TS;
-      if (r > q && j <= q) sm.b[r][j] = fma(-sm.a[r][q], sm.b[q][j], sm.b[r][j]);
-    }
-    __syncthreads();
-  }
   return true;
 }
 
@@ -253,7 +249,7 @@ template <typename T, int TS>
 __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *__restrict__ A,
                                                                  const double *__restrict__ B,
                                                                  const int32_t *__restrict__ usage, int K, int m,
-                                                                 int C, double *M, double *V, T *D,
+                                                                 int C, int light, double *M, double *V, T *D,
                                                                  int32_t *status) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
@@ -348,14 +344,23 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
       };
       if (ntr > 0) {
         const int owner = (k + 1) % C;
-        const int first = (rank - owner + C) % C;
-        if (rank == owner) {
+        if (light && C > 1) {
+          // every block has an SM to itself: the owner's latency-bound diagonal
+          // factorisation would lengthen the step, so it takes no other tile
+          if (rank == owner) {
+            run_step<TS>(sm, vk, 1, 0, C, trail);
+            __syncthreads();   // the updated diagonal tile is in global memory
+            own_diag(k + 1);
+          } else {
+            run_step<TS>(sm, vk, ntr, 1 + (rank - owner - 1 + C) % C, C - 1, trail);
+          }
+        } else if (rank == owner) {
           run_step<TS>(sm, vk, 1, 0, C, trail);
           __syncthreads();   // the updated diagonal tile is in global memory
           own_diag(k + 1);
           run_step<TS>(sm, vk, ntr, C, C, trail);
         } else {
-          run_step<TS>(sm, vk, ntr, first, C, trail);
+          run_step<TS>(sm, vk, ntr, (rank - owner + C) % C, C, trail);
         }
       }
       cl.sync();
@@ -417,7 +422,7 @@ static size_t cap_smem(int cap) {
 }
 
 template <typename T, int TS>
-static cudaError_t launch_tiled_ts(const ModArgs &a, int C, int cap, cudaStream_t st) {
+static cudaError_t launch_tiled_ts(const ModArgs &a, int C, int cap, int num_sms, cudaStream_t st) {
   auto kern = mod_tiled_kernel<T, TS>;
   cudaError_t e;
   if (C > 8) {
@@ -441,8 +446,9 @@ static cudaError_t launch_tiled_ts(const ModArgs &a, int C, int cap, cudaStream_
   cfg.numAttrs = 1;
   double *M = a.Lf;
   double *V = a.Lf + (size_t)a.L * (a.K + a.m) * a.K;
+  const int light = (int64_t)a.L * C <= num_sms ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, (const double *)a.A, (const double *)a.B, (const int32_t *)a.usage, a.K,
-                            a.m, C, M, V, static_cast<T *>(a.D), a.status);
+                            a.m, C, light, M, V, static_cast<T *>(a.D), a.status);
 }
 
 template <typename T>
@@ -477,14 +483,14 @@ int mod_tiled_max_clusters(int ts, int C, int cap) {
 }
 
 template <typename T>
-cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, cudaStream_t st) {
+cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, int num_sms, cudaStream_t st) {
   if (a.L <= 0) return cudaSuccess;
   if (C < 1 || C > 16 || (ts != 16 && ts != 32) || cap < 0 || cap > 3) return cudaErrorInvalidValue;
-  return ts == 16 ? launch_tiled_ts<T, 16>(a, C, cap, st) : launch_tiled_ts<T, 32>(a, C, cap, st);
+  return ts == 16 ? launch_tiled_ts<T, 16>(a, C, cap, num_sms, st) : launch_tiled_ts<T, 32>(a, C, cap, num_sms, st);
 }
 
-template cudaError_t launch_mod_tiled<float>(const ModArgs &, int, int, int, cudaStream_t);
-template cudaError_t launch_mod_tiled<double>(const ModArgs &, int, int, int, cudaStream_t);
+template cudaError_t launch_mod_tiled<float>(const ModArgs &, int, int, int, int, cudaStream_t);
+template cudaError_t launch_mod_tiled<double>(const ModArgs &, int, int, int, int, cudaStream_t);
 template int mod_tiled_max_clusters<float>(int, int, int);
 template int mod_tiled_max_clusters<double>(int, int, int);
 

@@ -180,9 +180,10 @@ int mod_tile_signals();
 // blocks per subset, TS x TS tiles (16 or 32); scratch in a.Lf of
 // mod_tiled_scratch_doubles(L, K, m) doubles.
 // cap: at most that many blocks per SM (1..3, through padded dynamic shared
-// memory), 0 = as many as fit.
+// memory), 0 = as many as fit.  num_sms decides whether every block has an SM
+// to itself (then the block factoring a diagonal tile takes no trailing tile).
 template <typename T>
-cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, cudaStream_t st);
+cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, int num_sms, cudaStream_t st);
 template <typename T>
 int mod_tiled_max_clusters(int ts, int C, int cap);
 size_t mod_tiled_scratch_doubles(int L, int K, int m);
