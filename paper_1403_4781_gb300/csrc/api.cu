@@ -481,6 +481,9 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   int32_t *d_max = nullptr;
   if ((st = mod_prepare(ctx, ma, offsets, L, K, m, s, nullptr, &d_max)) != SDL_OK) return st;
   ma.Y = Y; ma.idx = idx; ma.val = val; ma.D = D;
+  // the tiled solve folds every iteration's worst status into worst[0]
+  const bool tiled_folds_status = ctx->opt_mod_solve == 0 || ctx->opt_mod_solve == 3;
+  ma.status_max = tiled_folds_status ? worst : nullptr;
   SDL_CUDA(cudaMemsetAsync(ma.status, 0, sizeof(int32_t) * L, ctx->stream), "status clear");
   SDL_CUDA(cudaMemsetAsync(worst, 0, sizeof(int32_t) * (iters + 1), ctx->stream), "status clear");
   if (xfro) SDL_CUDA(cudaMemsetAsync(xfro, 0, sizeof(double) * L, ctx->stream), "xfro clear");
@@ -504,8 +507,9 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
       SDL_CUDA(timed(ctx, "mod_accum", mod_accum_kernels(sizeof(T) == 4, ma.total_tiles),
                      [&] { return launch_mod_accum<T>(ma, sm); }), "mod accumulate");
       SDL_CUDA(run_mod_solve<T>(ctx, ma), "mod solve");
-      SDL_CUDA(timed(ctx, "status", 1, [&] { return launch_status_max(ma.status, L, worst + it, sm); }),
-               "status");
+      if (!tiled_folds_status)   // the other solve implementations only write status[]
+        SDL_CUDA(timed(ctx, "status", 1, [&] { return launch_status_max(ma.status, L, worst + it, sm); }),
+                 "status");
     }
     return SDL_OK;
   };

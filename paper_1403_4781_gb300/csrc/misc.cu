@@ -73,18 +73,18 @@ __global__ void pick_init_kernel(const T *__restrict__ Yt, int m, const int32_t 
 
 // Per-subset RMSE of a coding pass and Frobenius norm of its codes, FP64 sums.
 template <typename T>
-__global__ void __launch_bounds__(256) subset_stats_kernel(const T *__restrict__ resid2,
+__global__ void __launch_bounds__(1024) subset_stats_kernel(const T *__restrict__ resid2,
                                                            const T *__restrict__ val,
                                                            const int64_t *__restrict__ offsets, int m,
                                                            int s, double *rmse_out, int64_t rmse_stride,
                                                            double *xfro_out) {
-  __shared__ double red[2][8];
+  __shared__ double red[2][32];
   const int t = blockIdx.x;
   const int64_t a = offsets[t], b = offsets[t + 1];
   double r2 = 0.0, v2 = 0.0;
-  for (int64_t i = a + threadIdx.x; i < b; i += 256) r2 += (double)resid2[i];
+  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) r2 += (double)resid2[i];
   if (xfro_out)
-    for (int64_t e = a * s + threadIdx.x; e < b * s; e += 256) {
+    for (int64_t e = a * s + threadIdx.x; e < b * s; e += blockDim.x) {
       const double v = (double)val[e];
       v2 = fma(v, v, v2);
     }
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) subset_stats_kernel(const T *__restrict__
   __syncthreads();
   if (threadIdx.x == 0) {
     double R = 0.0, V = 0.0;
-    for (int q = 0; q < 8; ++q) { R += red[0][q]; V += red[1][q]; }
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { R += red[0][q]; V += red[1][q]; }
     const double n = (double)(b - a);
     if (rmse_out) rmse_out[(size_t)t * rmse_stride] = n > 0 ? sqrt(R / ((double)m * n)) : 0.0;
     if (xfro_out) xfro_out[t] = sqrt(V);
@@ -208,7 +208,10 @@ template <typename T>
 cudaError_t launch_subset_stats(const T *resid2, const T *val, const int64_t *offsets, int L, int m, int s,
                                 double *rmse_out, int64_t rmse_stride, double *xfro_out, cudaStream_t st) {
   if (L <= 0) return cudaSuccess;
-  subset_stats_kernel<T><<<L, 256, 0, st>>>(resid2, val, offsets, m, s, rmse_out, rmse_stride, xfro_out);
+  // one block per subset: wide blocks where few subsets (the merge's one) must
+  // each sum many codes, narrow ones where many subsets fill the GPU
+  const int threads = L < 16 ? 1024 : 256;
+  subset_stats_kernel<T><<<L, threads, 0, st>>>(resid2, val, offsets, m, s, rmse_out, rmse_stride, xfro_out);
   return cudaGetLastError();
 }
 

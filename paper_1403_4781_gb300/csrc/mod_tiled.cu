@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
                                                                  const double *__restrict__ B,
                                                                  const int32_t *__restrict__ usage, int K, int m,
                                                                  int C, int light, double *M, double *V, T *D,
-                                                                 int32_t *status) {
+                                                                 int32_t *status, int32_t *status_max) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   __shared__ TiledSmem<TS> sm;
@@ -401,7 +401,10 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
       for (int r = 0; r < m; ++r) dj[r] = (T)(__ldcg(xj + (size_t)r * K) * inv);
     }
   }
-  if (rank == 0 && tid == 0) status[t] = st;
+  if (rank == 0 && tid == 0) {
+    status[t] = st;
+    if (status_max) atomicMax(status_max, st);
+  }
 }
 
 }  // namespace
@@ -448,7 +451,7 @@ static cudaError_t launch_tiled_ts(const ModArgs &a, int C, int cap, int num_sms
   double *V = a.Lf + (size_t)a.L * (a.K + a.m) * a.K;
   const int light = (int64_t)a.L * C <= num_sms ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, (const double *)a.A, (const double *)a.B, (const int32_t *)a.usage, a.K,
-                            a.m, C, light, M, V, static_cast<T *>(a.D), a.status);
+                            a.m, C, light, M, V, static_cast<T *>(a.D), a.status, a.status_max);
 }
 
 template <typename T>

@@ -161,6 +161,7 @@ struct ModArgs {
   double *Lf;             // [L][K][K]
   double *B;              // [L][K][m]
   int32_t *status;        // [L] out: 0 ok, 1 ridge used, 2 breakdown
+  int32_t *status_max;    // may be null: the tiled solve folds max(status) into it
 };
 // MOD in four launchers: accumulation (usage count, scan, CSC fill, A/B
 // accumulation: 4 kernels), FP64 Cholesky, FP64 solve, renormalisation.
