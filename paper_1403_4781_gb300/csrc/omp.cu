@@ -102,7 +102,7 @@ __host__ __device__ inline OmpLayout omp_layout(int TS, int K, int m, int s, boo
 // 16-byte shared/global vector of four T.
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
-template <> struct Vec4<double> { using type = double4; };
+template <> struct Vec4<double> { using type = double4_16a; };
 
 // One block codes a tile of TS = 4 * 8 signals of one subset: the correlation
 // tile alpha0 = Y_tile D^T is a register-tiled FFMA GEMM (4 signals x 8 atoms
