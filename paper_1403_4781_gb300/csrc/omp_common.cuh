@@ -63,6 +63,32 @@ __device__ __forceinline__ T upper_solve(const T *L, int lp, int k, T z, int lan
   return x;
 }
 
+// Warp argmax of per-lane candidates (bestv, best): the largest value, the
+// lowest atom index among equal values; best < 0 marks a lane without one.
+// FP32: non-negative floats order like their bit patterns read as unsigned
+// integers, so two warp reductions do it; other types take shuffle rounds.
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T &bestv, int &best) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T ov = __shfl_xor_sync(0xffffffffu, bestv, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, best, o);
+    if (ov > bestv || (ov == bestv && oj >= 0 && (best < 0 || oj < best))) {
+      bestv = ov;
+      best = oj;
+    }
+  }
+}
+template <>
+__device__ __forceinline__ void warp_argmax<float>(float &bestv, int &best) {
+  const unsigned key = (best >= 0 && bestv > 0.f) ? __float_as_uint(bestv) : 0u;
+  const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+  const unsigned cand = (key == kmax && best >= 0) ? (unsigned)best : 0xffffffffu;
+  const unsigned bmin = __reduce_min_sync(0xffffffffu, cand);
+  bestv = __uint_as_float(kmax);
+  best = kmax == 0u ? -1 : (int)bmin;
+}
+
 // Lane-distributed dot products of the support atoms with a vector held as
 // rloc[u] = v[lane + 32 u]: returns d_{S_p}^T v in lane p.
 template <typename T, int M32>
@@ -118,6 +144,7 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
 #pragma unroll
   for (int c = 0; c < KPL; ++c)
     if (lane + 32 * c < K) valid |= 1u << c;
+  const bool full = K == 32 * KPL;   // every lane holds KPL atoms (warp-uniform)
 
   for (int q = 0; q < sig_count; ++q) {
     const int sig = sig_begin + q;
@@ -149,9 +176,14 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
       for (int p = 0; p < k; ++p) {
         const T xp = __shfl_sync(0xffffffffu, xl, p);
         const T *gp = gcache ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
+        if (full) {
 #pragma unroll
-        for (int c = 0; c < KPL; ++c)
-          if ((valid >> c) & 1u) av[c] = fma(-gp[lane + 32 * c], xp, av[c]);
+          for (int c = 0; c < KPL; ++c) av[c] = fma(-gp[lane + 32 * c], xp, av[c]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < KPL; ++c)
+            if ((valid >> c) & 1u) av[c] = fma(-gp[lane + 32 * c], xp, av[c]);
+        }
       }
       T bestv = T(-1);
       int best = -1;
@@ -160,24 +192,17 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
         const T v = fabs(av[c]);
         if (((avail >> c) & 1u) && v > bestv) { bestv = v; best = lane + 32 * c; }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, bestv, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, best, o);
-        if (ov > bestv || (ov == bestv && oj >= 0 && (best < 0 || oj < best))) {
-          bestv = ov;
-          best = oj;
-        }
-      }
+      warp_argmax<T>(bestv, best);
       if (best < 0 || !(bestv > T(0))) break;
       T a0b = T(0);
 #pragma unroll
       for (int c = 0; c < KPL; ++c)
         if (c == (best >> 5)) a0b = a0r[c];
       a0b = __shfl_sync(0xffffffffu, a0b, best & 31);
-      // column `best` of G (= row, G symmetric)
+      // column `best` of G (= row, G symmetric); the cached copy serves the
+      // updates of later steps only, so the last step reads it from L2
       const T *gcol = Gt + (size_t)best * K;
-      if (gcache) {
+      if (gcache && k + 1 < s) {
         T *dst = gc + (size_t)k * K;
         for (int j = lane; j < K; j += 32) dst[j] = gcol[j];
         __syncwarp();
