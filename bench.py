@@ -43,7 +43,7 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
 # DRAM bytes (read + write) per launch of a kernel family, from one ncu capture
 # of this workload with the current kernels (see profiles/); absent = none.
-TRAFFIC = {"mod_solve_fp64": 52.7e6}
+TRAFFIC = {"mod_solve_fp64": 53.3e6}
 
 
 def load_peaks():
