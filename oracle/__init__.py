@@ -70,9 +70,11 @@ def _load():
             lib.orc_recovery.argtypes = [_dp, i32, _dp, i32, i32, dbl, ctypes.POINTER(ctypes.c_int)]
             lib.orc_mlp_forward.argtypes = [_dp, i32, i32, i32, i32, _dp, i64, _dp]
             lib.orc_mlp_loss_grad.argtypes = [_dp, i32, i32, i32, i32, _dp, _ip, i32, i64, _dp, _dp]
+            lib.orc_extract_patches.argtypes = [_dp, i32, i32, i32, _dp]
+            lib.orc_patch_average.argtypes = [_dp, i32, _ip, _dp, i32, i32, i32, i32, _dp]
             for f in ("orc_omp", "orc_mod", "orc_train", "orc_split", "orc_local_train",
                       "orc_merge", "orc_residual", "orc_recovery", "orc_mlp_forward",
-                      "orc_mlp_loss_grad"):
+                      "orc_mlp_loss_grad", "orc_extract_patches", "orc_patch_average"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -257,3 +259,25 @@ def mlp_loss_grad(params, m, h1, h2, K, Y, idx, with_grad=True):
     _check(lib.orc_mlp_loss_grad(_d(params), m, h1, h2, K, _d(Y), _i(idx), idx.shape[1], Y.shape[0],
                                  ctypes.cast(ctypes.byref(loss), _dp), _d(grad)), "orc_mlp_loss_grad")
     return loss.value, grad
+
+
+def extract_patches(img, p):
+    """Every p x p patch of img (H, W), row-major: shape ((H-p+1)(W-p+1), p*p)."""
+    lib = _load()
+    img = _f64(img)
+    H, W = img.shape
+    out = np.empty(((H - p + 1) * (W - p + 1), p * p))
+    _check(lib.orc_extract_patches(_d(img), H, W, p, _d(out)), "orc_extract_patches")
+    return out
+
+
+def patch_average(D, idx, val, H, W, p):
+    """Denoised image (H, W): per pixel, the mean of D x over the patches covering it."""
+    lib = _load()
+    D = _f64(D)
+    idx = np.ascontiguousarray(idx, np.int32)
+    val = _f64(val)
+    out = np.empty((H, W))
+    _check(lib.orc_patch_average(_d(D), D.shape[0], _i(idx), _d(val), idx.shape[1], H, W, p, _d(out)),
+           "orc_patch_average")
+    return out

@@ -444,3 +444,46 @@ int orc_mlp_loss_grad(const double *params, int m, int h1, int h2, int K, const 
   free(a1); free(x1); free(a2); free(x2); free(z); free(dz); free(d2); free(d1); free(t);
   return 0;
 }
+
+/* ------------------------------------------------- image denoising --- */
+
+int orc_extract_patches(const double *img, int H, int W, int p, double *out) {
+  if (!img || !out || p <= 0 || H < p || W < p) return 1;
+  const int nr = H - p + 1, nc = W - p + 1;
+  for (int r = 0; r < nr; ++r)
+    for (int c = 0; c < nc; ++c) {
+      double *dst = out + ((size_t)r * nc + c) * (size_t)p * p;
+      for (int u = 0; u < p; ++u)
+        for (int v = 0; v < p; ++v) dst[u * p + v] = img[(size_t)(r + u) * W + (c + v)];
+    }
+  return 0;
+}
+
+int orc_patch_average(const double *D, int K, const int32_t *idx, const double *val, int s, int H, int W,
+                      int p, double *out) {
+  if (!D || !idx || !val || !out || p <= 0 || H < p || W < p || s <= 0 || K <= 0) return 1;
+  const int nr = H - p + 1, nc = W - p + 1, m = p * p;
+  double *acc = (double *)calloc((size_t)H * W, sizeof(double));
+  int *cnt = (int *)calloc((size_t)H * W, sizeof(int));
+  double *rec = (double *)malloc(sizeof(double) * (size_t)m);
+  for (int r = 0; r < nr; ++r)
+    for (int c = 0; c < nc; ++c) {
+      const size_t i = (size_t)r * nc + c;
+      for (int e = 0; e < m; ++e) rec[e] = 0.0;
+      for (int k = 0; k < s; ++k) {
+        const int j = idx[i * s + k];
+        if (j < 0 || j >= K) continue;
+        for (int e = 0; e < m; ++e) rec[e] += val[i * s + k] * D[(size_t)j * m + e];
+      }
+      for (int u = 0; u < p; ++u)
+        for (int v = 0; v < p; ++v) {
+          acc[(size_t)(r + u) * W + (c + v)] += rec[u * p + v];
+          cnt[(size_t)(r + u) * W + (c + v)] += 1;
+        }
+    }
+  for (size_t q = 0; q < (size_t)H * W; ++q) out[q] = acc[q] / (double)cnt[q];
+  free(acc);
+  free(cnt);
+  free(rec);
+  return 0;
+}

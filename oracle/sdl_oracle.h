@@ -116,3 +116,21 @@ int orc_mlp_loss_grad(const double *params, int m, int h1, int h2, int K, const 
 #ifdef __cplusplus
 }
 #endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+/* Image denoising with the learned dictionary (Sec. 3.2.2): every p x p patch
+ * of an H x W image (row-major, one patch per position (r, c), r < H-p+1,
+ * c < W-p+1, patch index r (W-p+1) + c, entry (u, v) at u p + v) is coded
+ * with the error-constrained OMP, its estimate is D x, and the denoised image
+ * is, at every pixel, the mean of the estimates of the patches covering it.
+ *   orc_extract_patches: out [(H-p+1)(W-p+1)][p p].
+ *   orc_patch_average:   D [K][p p]; codes idx/val [(H-p+1)(W-p+1)][s]
+ *                        (-1 pads); out [H][W]. */
+int orc_extract_patches(const double *img, int H, int W, int p, double *out);
+int orc_patch_average(const double *D, int K, const int32_t *idx, const double *val, int s, int H, int W,
+                      int p, double *out);
+#ifdef __cplusplus
+}
+#endif
