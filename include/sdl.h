@@ -170,6 +170,27 @@ sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, 
 sdl_status sdl_recovery(sdl_ctx *ctx, sdl_precision prec, const void *D0, int K0, const void *D,
                         int K, int m, double thresh, int32_t *count);
 
+/* ---- Image denoising with the learned dictionary (Sec. 3.2.2).  Every p x p
+ * patch of an H x W image (row-major pixels, one patch per position (r, c) with
+ * r < H-p+1, c < W-p+1; patch index r (W-p+1) + c; entry (u, v) at u p + v) is
+ * coded with the error-constrained sdl_omp (eps = 8.5 sigma in the paper), its
+ * estimate is D x, and the denoised image holds at every pixel the mean of the
+ * estimates of the patches covering it.  prec F64 or F32 (BF16: FP32 data).
+ *
+ * sdl_extract_patches: img device [H][W]; patches device [(H-p+1)(W-p+1)][p p]
+ *   out.  1 <= p <= 16, p <= H, p <= W.
+ * sdl_patch_average: D device [K][p p]; idx/val device ELL codes
+ *   [(H-p+1)(W-p+1)][s] (-1 pads at the end of a row); out device [H][W].
+ * sdl_sq_error: out2 device double [2] receives sum (a - b)^2 and sum b^2 over
+ *   n entries (PSNR = 10 log10(peak^2 n / out2[0])).
+ * All return SDL_EINVAL on a bad size or a NULL / unaligned pointer. */
+sdl_status sdl_extract_patches(sdl_ctx *ctx, sdl_precision prec, const void *img, int H, int W, int p,
+                               void *patches);
+sdl_status sdl_patch_average(sdl_ctx *ctx, sdl_precision prec, const void *D, int K, const int32_t *idx,
+                             const void *val, int s, int H, int W, int p, void *out);
+sdl_status sdl_sq_error(sdl_ctx *ctx, sdl_precision prec, const void *a, const void *b, int64_t n,
+                        double *out2);
+
 /* ---- Learned support proposer (an extension beyond the paper: it accelerates
  * the OMP stage of Sec. 1 by proposing candidate atoms).  An MLP
  * m -> h1 -> h2 -> K with GELU hidden layers scores every atom for a signal;

@@ -76,6 +76,9 @@ _SIGS = {
                                  ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "sdl_launch_count": (_i64, [_vp]),
     "sdl_omp_noalloc": (_i32, [_vp, _vp, _i32, _i32, _vp, _i64, _i32, _dbl, _vp, _vp, _vp, _vp]),
+    "sdl_extract_patches": (_i32, [_vp, _i32, _vp, _i32, _i32, _i32, _vp]),
+    "sdl_patch_average": (_i32, [_vp, _i32, _vp, _i32, _vp, _vp, _i32, _i32, _i32, _i32, _vp]),
+    "sdl_sq_error": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp]),
     "sdl_set_option": (_i32, [_vp, _i32, _i64]),
     "sdl_proposer_create": (_i32, [_vp, _i32, _i32, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
     "sdl_proposer_destroy": (_i32, [_vp]),
@@ -346,6 +349,48 @@ def residual(Y, D, idx, val, prec=None):
     _call("sdl_residual", ctx.bind_stream(), prec, _ptr(Y), m, n, _ptr(D), K, _ptr(idx), _ptr(val), s,
           _ptr(out))
     return out
+
+
+def extract_patches(img, p, prec=None):
+    """Every p x p patch of img (H, W), row-major: ((H-p+1)(W-p+1), p*p)."""
+    import torch
+    prec = _prec_of(img, prec)
+    H, W = img.shape
+    out = torch.empty(((H - p + 1) * (W - p + 1), p * p), dtype=img.dtype, device=img.device)
+    ctx = context(img.device.index)
+    _call("sdl_extract_patches", ctx.bind_stream(), prec, _ptr(img), H, W, p, _ptr(out))
+    return out
+
+
+def patch_average(D, idx, val, H, W, p, prec=None):
+    """Per pixel, the mean of the estimates D x of the patches covering it: (H, W)."""
+    import torch
+    prec = _prec_of(D, prec)
+    out = torch.empty((H, W), dtype=D.dtype, device=D.device)
+    ctx = context(D.device.index)
+    _call("sdl_patch_average", ctx.bind_stream(), prec, _ptr(D), D.shape[0], _ptr(idx), _ptr(val), idx.shape[1], H,
+          W, p, _ptr(out))
+    return out
+
+
+def sq_error(a, b, prec=None):
+    """(sum (a - b)^2, sum b^2) as a device float64 tensor of 2 entries."""
+    import torch
+    prec = _prec_of(a, prec)
+    out = torch.empty((2,), dtype=torch.float64, device=a.device)
+    ctx = context(a.device.index)
+    _call("sdl_sq_error", ctx.bind_stream(), prec, _ptr(a), _ptr(b), a.numel(), _ptr(out))
+    return out
+
+
+def denoise(noisy, D, p, eps, s_max=32, prec=None):
+    """Sec. 3.2.2 denoising of noisy (H, W) with dictionary D (K, p*p): every
+    overlapping patch coded by OMP until ||r|| <= eps (at most s_max atoms),
+    estimates averaged per pixel.  Returns (denoised (H, W), codes (idx, val, nnz))."""
+    H, W = noisy.shape
+    P = extract_patches(noisy, p, prec=prec)
+    idx, val, nnz, _ = omp(D, P, s_max, eps=eps, prec=prec, with_resid=False)
+    return patch_average(D, idx, val, H, W, p, prec=None if prec == PREC_BF16 else prec), (idx, val, nnz)
 
 
 def recovery(D0, D, thresh=0.98, prec=None):

@@ -889,6 +889,78 @@ sdl_status sdl_recovery(sdl_ctx *ctx, sdl_precision prec, const void *D0, int K0
   return SDL_OK;
 }
 
+sdl_status sdl_extract_patches(sdl_ctx *ctx, sdl_precision prec, const void *img, int H, int W, int p,
+                               void *patches) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  SDL_REQUIRE(p >= 1 && p <= 16 && H >= p && W >= p, "need 1 <= p <= 16, p <= H, p <= W");
+  SDL_REQUIRE(aligned16(img) && aligned16(patches), "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  if (prec == SDL_PREC_F64)
+    SDL_CUDA(timed(ctx, "extract_patches", 1, [&] {
+               return launch_extract_patches<double>(static_cast<const double *>(img), H, W, p,
+                                                     static_cast<double *>(patches), ctx->stream);
+             }), "extract patches");
+  else
+    SDL_CUDA(timed(ctx, "extract_patches", 1, [&] {
+               return launch_extract_patches<float>(static_cast<const float *>(img), H, W, p,
+                                                    static_cast<float *>(patches), ctx->stream);
+             }), "extract patches");
+  return SDL_OK;
+}
+
+sdl_status sdl_patch_average(sdl_ctx *ctx, sdl_precision prec, const void *D, int K, const int32_t *idx,
+                             const void *val, int s, int H, int W, int p, void *out) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  SDL_REQUIRE(p >= 1 && p <= 16 && H >= p && W >= p && K >= 1 && s >= 1, "bad sizes");
+  SDL_REQUIRE(aligned16(D) && aligned16(idx) && aligned16(val) && aligned16(out),
+              "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  if (prec == SDL_PREC_F64)
+    SDL_CUDA(timed(ctx, "patch_average", 1, [&] {
+               return launch_patch_average<double>(static_cast<const double *>(D), K, idx,
+                                                   static_cast<const double *>(val), s, H, W, p,
+                                                   static_cast<double *>(out), ctx->stream);
+             }), "patch average");
+  else
+    SDL_CUDA(timed(ctx, "patch_average", 1, [&] {
+               return launch_patch_average<float>(static_cast<const float *>(D), K, idx,
+                                                  static_cast<const float *>(val), s, H, W, p,
+                                                  static_cast<float *>(out), ctx->stream);
+             }), "patch average");
+  return SDL_OK;
+}
+
+sdl_status sdl_sq_error(sdl_ctx *ctx, sdl_precision prec, const void *a, const void *b, int64_t n, double *out2) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  SDL_REQUIRE(n >= 0, "bad size");
+  SDL_REQUIRE(aligned16(out2) && (n == 0 || (aligned16(a) && aligned16(b))),
+              "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  if (prec == SDL_PREC_F64)
+    SDL_CUDA(timed(ctx, "sq_error", 1, [&] {
+               return launch_sq_error<double>(static_cast<const double *>(a), static_cast<const double *>(b), n, out2,
+                                              ctx->stream);
+             }), "squared error");
+  else
+    SDL_CUDA(timed(ctx, "sq_error", 1, [&] {
+               return launch_sq_error<float>(static_cast<const float *>(a), static_cast<const float *>(b), n, out2,
+                                             ctx->stream);
+             }), "squared error");
+  return SDL_OK;
+}
+
 sdl_status sdl_omp_proposed(sdl_ctx *ctx, sdl_proposer *p, const float *D, int m, int K, const float *Y, int64_t n,
                             int s, int ncand, double eps_fb, int32_t *idx, float *val, int32_t *nnz, float *resid2,
                             int64_t *n_fallback) {

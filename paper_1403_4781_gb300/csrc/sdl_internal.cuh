@@ -211,6 +211,14 @@ template <typename T>
 cudaError_t launch_recovery(const T *D0, int K0, const T *D, int K, int m, double thresh,
                             int32_t *count, cudaStream_t st);
 cudaError_t launch_status_max(const int32_t *status, int L, int32_t *out, cudaStream_t st);
+// Denoising (denoise.cu).
+template <typename T>
+cudaError_t launch_extract_patches(const T *img, int H, int W, int p, T *out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_patch_average(const T *D, int K, const int32_t *idx, const T *val, int s, int H, int W, int p,
+                                 T *out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_sq_error(const T *a, const T *b, int64_t n, double *out2, cudaStream_t st);
 
 // Learned support proposer (proposer.cu).
 int proposer_m(const sdl_proposer *p);
