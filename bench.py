@@ -528,6 +528,75 @@ def run_patches(args):
     print(json.dumps(res), flush=True)
 
 
+def run_denoise(args):
+    """Image denoising as in the paper's image experiment (Sec. 3.2), on
+    synthetic images: dictionaries trained on 10^5 clean 8x8 patches, by
+    split-and-merge (20 subsets of 5,000, K1=128, s1=4, merged to K=256 with
+    s2=2) and by the standard approach (K=256, s=8), both from overcomplete DCT
+    dictionaries with 20 (+20) iterations; a new noisy image (sigma = 20/255)
+    denoised with each and with the DCT itself (every overlapping patch coded
+    to ||r|| <= 8.5 sigma, at most 32 atoms, estimates averaged per pixel).
+    A measurement of a widening workload, printed as its own line."""
+    import torch
+
+    import paper_1403_4781_gb300 as sdl
+
+    dev = torch.device("cuda", 0)
+    rng = si.rng_for(5)
+    train = np.concatenate([si.random_patches(rng, si.synthetic_image(rng, sigma=0.0), 12_500, 8)
+                            for _ in range(8)]).astype(np.float32)
+    clean = si.synthetic_image(rng, sigma=0.0)
+    sigma = 20 / 255
+    noisy = (clean + sigma * rng.standard_normal(clean.shape)).astype(np.float32)
+    L, n = 20, 5000
+    perm, offsets = si.random_partition(rng, [n] * L)
+    D_loc0 = si.overcomplete_dct(8, 8, 16).astype(np.float32)
+    D_mer0 = si.overcomplete_dct(8, 16, 16).astype(np.float32)
+    Y = torch.from_numpy(train).to(dev)
+    Yp = sdl.split(Y, torch.from_numpy(perm).to(dev))
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3, out
+
+    def split_merge():
+        Dl = torch.from_numpy(np.broadcast_to(D_loc0, (L, 128, 64)).copy()).to(dev)
+        xf, _ = sdl.local_train(Yp, offsets, Dl, 4, 20, with_rmse=False)
+        D, _ = sdl.merge(Dl, xf, None, 256, 2, 20, with_rmse=False, D_init=torch.from_numpy(D_mer0).to(dev))
+        return D
+
+    def standard():
+        D = torch.from_numpy(D_mer0.copy()).to(dev)[None]
+        sdl.local_train(Y, [0, len(train)], D, 8, 20, with_rmse=False)
+        return D[0]
+
+    split_merge(), standard()   # warm-up: autotuner, workspace
+    t_sm, D_sm = timed(split_merge)
+    t_std, D_std = timed(standard)
+    ng = torch.from_numpy(noisy).to(dev)
+    cg = torch.from_numpy(clean.astype(np.float32)).to(dev)
+
+    def psnr(img):
+        e2 = sdl.sq_error(img, cg).cpu().numpy()[0]
+        return float(10 * np.log10(img.numel() / e2))
+
+    out = {"train_s": {"split_merge": t_sm, "standard": t_std}, "psnr_noisy": psnr(ng)}
+    for name, D in (("split_merge", D_sm), ("standard", D_std), ("dct", torch.from_numpy(D_mer0).to(dev))):
+        sdl.denoise(ng, D, 8, 8.5 * sigma)
+        t, (den, (idx, val, nnz)) = timed(lambda: sdl.denoise(ng, D, 8, 8.5 * sigma))
+        out[name] = {"psnr": psnr(den), "denoise_s": t, "patches_per_s": idx.shape[0] / t,
+                     "mean_atoms": float(nnz.float().mean())}
+    res = {"metric": METRIC, "workload": "denoise_synthetic_512x512_sigma20", "train_patches": len(train),
+           "data": "synthetic piecewise-smooth images (seeded), pixel values in [0, 1]", **out}
+    print(json.dumps(res), flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle ------
 def _oracle_sample(p, Y, n_sub, final_n, merge_iters):
     """Run the oracle on a bounded sample of the workload: local training of the
@@ -592,7 +661,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposer sub-benchmark")
-    ap.add_argument("--workload", choices=["splitmerge", "uneven-A", "uneven-B", "patches"], default="splitmerge",
+    ap.add_argument("--workload", choices=["splitmerge", "uneven-A", "uneven-B", "patches", "denoise"],
+                    default="splitmerge",
                     help="the bench workload (default) or one of the parity workloads, measured alone")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed steps of the per-subset plain form (0 skips it)")
@@ -605,6 +675,9 @@ def main():
     elif args.workload == "patches":
         if rank == 0:
             run_patches(args)
+    elif args.workload == "denoise":
+        if rank == 0:
+            run_denoise(args)
     elif args.workload != "splitmerge":
         if rank == 0:
             run_uneven(args, args.workload[-1])
