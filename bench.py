@@ -597,6 +597,45 @@ def run_denoise(args):
     print(json.dumps(res), flush=True)
 
 
+def run_coding(args):
+    """One OMP coding pass of 2^19 signals (m=256, K=512, s=8, noise 0.02, one
+    dictionary) with FP32 CUDA-core correlations and with BF16 tensor-core ones:
+    the shape where the correlation GEMM is most of the arithmetic.  Printed as
+    its own line; also the small case the tensor-core kernels are profiled on."""
+    import torch
+
+    import paper_1403_4781_gb300 as sdl
+
+    dev = torch.device("cuda", 0)
+    rng = si.rng_for(6)
+    m, K, s, n = 256, 512, 8, 1 << 19
+    D0 = si.unit_gaussian_atoms(rng, m, K)
+    Y, _, _ = si.sparse_signals(rng, D0, n, s, 0.02, dtype=np.float32)
+    D = torch.from_numpy(D0.astype(np.float32)).to(dev)
+    Yg = torch.from_numpy(Y).to(dev)
+    ctx = sdl.context(0)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, prec in (("fp32", sdl.PREC_F32), ("bf16", sdl.PREC_BF16)):
+        sdl.omp(D, Yg, s, prec=prec)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sdl.omp(D, Yg, s, prec=prec)
+        e1.record(stream)
+        e1.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        ms = e0.elapsed_time(e1)
+        out[name] = {"signals_per_s": n / (ms / 1e3), "ms": ms,
+                     "kernels": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}
+    res = {"metric": METRIC, "workload": "coding_m256_K512_s8_n524288", "correlation_tflop": 2 * m * K * n / 1e12,
+           "data": "synthetic (seeded; Sec. 3.1 data model)", **out}
+    print(json.dumps(res), flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle ------
 def _oracle_sample(p, Y, n_sub, final_n, merge_iters):
     """Run the oracle on a bounded sample of the workload: local training of the
@@ -661,7 +700,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposer sub-benchmark")
-    ap.add_argument("--workload", choices=["splitmerge", "uneven-A", "uneven-B", "patches", "denoise"],
+    ap.add_argument("--workload", choices=["splitmerge", "uneven-A", "uneven-B", "patches", "denoise", "coding"],
                     default="splitmerge",
                     help="the bench workload (default) or one of the parity workloads, measured alone")
     ap.add_argument("--plain-steps", type=int, default=1,
@@ -678,6 +717,9 @@ def main():
     elif args.workload == "denoise":
         if rank == 0:
             run_denoise(args)
+    elif args.workload == "coding":
+        if rank == 0:
+            run_coding(args)
     elif args.workload != "splitmerge":
         if rank == 0:
             run_uneven(args, args.workload[-1])
