@@ -279,23 +279,22 @@ sdl_status check_prec(sdl_ctx *ctx, sdl_precision prec) {
 }
 
 // Workspace of the BF16 tensor-core coding pass over n signals in L subsets:
-// BF16 image of D, error word, FP32 Gram, and the correlation scratch (one
-// chunk of 128-signal tiles).
+// BF16 image of D, error word, and the correlation scratch (one chunk of
+// 128-signal tiles).  The FP32 Gram lives in the caller's G.
 size_t tc_a0_bytes(int L, int K, int64_t n) {
   const int64_t tiles = (n + 127) / 128 + L;
   return sizeof(float) * (size_t)omp_tc_chunk_tiles(K, tiles) * 128 * K;
 }
 size_t tc_ws_bytes(int L, int K, int m, int64_t n) {
   return round256((size_t)L * round16(K) * round16(m) * 2) + round256(sizeof(int32_t) * 4) +
-         round256(sizeof(float) * (size_t)L * K * K) + round256(tc_a0_bytes(L, K, n));
+         round256(tc_a0_bytes(L, K, n));
 }
 
-// One BF16 coding pass: BF16 image of D, Gram and correlations on the tensor
+// One BF16 coding pass: BF16 image of D, FP32 Gram, correlations on the tensor
 // cores, selection loop, FP32 refit on the support.
-cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, float *Gex, int32_t *err, float *a0c) {
+cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *err, float *a0c) {
   cudaStream_t sm = ctx->stream;
   oa.Dimg = img;
-  oa.Gexact = Gex;
   oa.Kp = round16(oa.K);
   oa.mp = round16(oa.m);
   oa.err = err;
@@ -304,10 +303,8 @@ cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, float *
     return launch_bf16_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, img, sm);
   });
   if (e != cudaSuccess) return e;
-  e = timed(ctx, "gram_tc", 1, [&] { return launch_gram_tc(img, oa.K, oa.m, oa.L, G, err, sm); });
-  if (e != cudaSuccess) return e;
   e = timed(ctx, "gram", 1, [&] {
-    return launch_gram<float>(static_cast<const float *>(oa.D), oa.m, oa.K, oa.L, Gex, sm);
+    return launch_gram<float>(static_cast<const float *>(oa.D), oa.m, oa.K, oa.L, G, sm);
   });
   if (e != cudaSuccess) return e;
   const int64_t chunk = omp_tc_chunk_tiles(oa.K, oa.total_tiles);
@@ -462,9 +459,8 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
     return st;
   void *img = bf16 ? ws_alloc(ctx, (size_t)L * round16(K) * round16(m) * 2) : nullptr;
   int32_t *tc_err = bf16 ? static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4)) : nullptr;
-  float *Gex = bf16 ? static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)L * K * K)) : nullptr;
   float *a0c = bf16 ? static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n))) : nullptr;
-  if (bf16 && (!img || !tc_err || !Gex || !a0c)) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  if (bf16 && (!img || !tc_err || !a0c)) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
   if (bf16) SDL_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int32_t), ctx->stream), "err clear");
   T *G = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)L * K * K));
   int32_t *idx = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * s));
@@ -492,7 +488,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
     for (int it = 0; it < iters; ++it) {
       cudaError_t e;
       if (bf16) {
-        e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), Gex, tc_err, a0c);
+        e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c);
       } else {
         SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
         e = timed(ctx, "omp", 1, [&] { return launch_omp<T>(oa, ctx->num_sms, sm); });
@@ -662,11 +658,10 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
   if (bf16) {
     void *img = ws_alloc(ctx, (size_t)L * round16(K) * round16(m) * 2);
     int32_t *err = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
-    float *Gex = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)L * K * K));
     float *a0c = static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n)));
-    if (!img || !err || !Gex || !a0c) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+    if (!img || !err || !a0c) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
     SDL_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream), "err clear");
-    cudaError_t e = run_omp_bf16(ctx, a, img, static_cast<float *>(G), Gex, err, a0c);
+    cudaError_t e = run_omp_bf16(ctx, a, img, static_cast<float *>(G), err, a0c);
     if (e == cudaErrorInvalidConfiguration)
       return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
     SDL_CUDA(e, "omp bf16");

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (KPL <= 16 ? 3 : 2)
   __syncthreads();   // staging is dead from here; the union holds G columns
 
   T *Ls = reinterpret_cast<T *>(smem + lay.ls) + (size_t)warp * a.s * lay.lp;
-  code_warp_signals<T, KPL, MU, false>(a, a0, yt, yp, warp * SPW, SPW, nsig, row0, Dt, Gt, Ls, Ls,
+  code_warp_signals<T, KPL, MU, false>(a, a0, yt, yp, warp * SPW, SPW, nsig, row0, Dt, Gt, Ls,
                                        uni + (size_t)warp * a.s * K, lay.lp, lay.gcache);
 }
 

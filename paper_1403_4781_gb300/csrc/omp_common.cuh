@@ -124,17 +124,22 @@ __device__ __forceinline__ void support_residual(const T *Dt, const T *ysig, int
 // The selection loop (Sec. 1 greedy choice, Batch-OMP form), refinement on the
 // support and the ELL write-out for signals sig_begin .. sig_begin+sig_count-1
 // of a tile, run by one warp.
-//   a0     correlation tile alpha0 [tile signals][K] (shared memory)
+//   a0     correlation tile alpha0 [tile signals][K] (shared or global memory)
 //   ybase  signal 0 of the tile, row stride ypitch (shared or global memory)
 //   MU     ceil(m / 32): signal entries per lane
-//   Ls, Gx per-warp [s][lp] factor scratch;  gc per-warp [s][K] G-column cache
-//   EXACT  refit the coefficients from the exact Gram entries (a.Gexact, the Gram
-//          of D in T) and D_S^T y before the correction step (used when G and
-//          alpha0 came from reduced-precision products)
+//   Gt     the Gram matrix of D in T (FP32 or FP64 products)
+//   Ls     per-warp [s][lp] factor scratch;  gc per-warp [s][K] G-column cache
+//   EXACT  alpha0 came from reduced-precision products: the refit takes D_S^T y
+//          in T instead of alpha0 on the support
+// Per step the correlations are kept as a running vector alpha = alpha0 -
+// G[:, S] x_S in registers: after the support grows, alpha -= G[:, S] dx with dx
+// the change of every coefficient.  The forward-solved vector z = L^{-1}
+// alpha0_S grows by one entry per step, (alpha0_j - w^T z) / l for the new
+// factor row [w^T, l], so only x = L^{-T} z is solved again.
 template <typename T, int KPL, int MU, bool EXACT>
 __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase, int ypitch, int sig_begin,
                                   int sig_count, int nsig, int64_t row0, const T *__restrict__ Dt,
-                                  const T *__restrict__ Gt, T *Ls, T *Gx, T *gc, int lp, bool gcache) {
+                                  const T *__restrict__ Gt, T *Ls, T *gc, int lp, bool gcache) {
   constexpr int M32 = MU;
   const int K = a.K, m = a.m, s = a.s;
   const int lane = threadIdx.x & 31;
@@ -152,9 +157,9 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
     const int64_t gi = row0 + sig;
     const T *ysig = ybase + (size_t)sig * ypitch;
     const T *arow = a0 + (size_t)sig * K;
-    T a0r[KPL];
+    T av[KPL];   // running correlations of this lane's atoms
 #pragma unroll
-    for (int c = 0; c < KPL; ++c) a0r[c] = (valid >> c) & 1u ? arow[lane + 32 * c] : T(0);
+    for (int c = 0; c < KPL; ++c) av[c] = (valid >> c) & 1u ? arow[lane + 32 * c] : T(0);
 
     T yn2 = T(0);
 #pragma unroll
@@ -165,26 +170,11 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
     uint32_t avail = valid;   // unselected existing atoms of this lane
     int k = 0;
     int Sl = -1;              // lane p: p-th selected atom
-    T a0Sl = T(0), xl = T(0); // lane p: its alpha0 and coefficient
+    T zl = T(0), xl = T(0);   // lane p: z_p and the coefficient x_p
     T rn2 = yn2;
     while (k < s) {
       if (eps > T(0) && tsqrt(rn2) <= eps) break;
-      // alpha = alpha0 - G[:, S] x_S, masked argmax |alpha| (lowest index on ties)
-      T av[KPL];
-#pragma unroll
-      for (int c = 0; c < KPL; ++c) av[c] = a0r[c];
-      for (int p = 0; p < k; ++p) {
-        const T xp = __shfl_sync(0xffffffffu, xl, p);
-        const T *gp = gcache ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
-        if (full) {
-#pragma unroll
-          for (int c = 0; c < KPL; ++c) av[c] = fma(-gp[lane + 32 * c], xp, av[c]);
-        } else {
-#pragma unroll
-          for (int c = 0; c < KPL; ++c)
-            if ((valid >> c) & 1u) av[c] = fma(-gp[lane + 32 * c], xp, av[c]);
-        }
-      }
+      // masked argmax |alpha| (lowest index on ties)
       T bestv = T(-1);
       int best = -1;
 #pragma unroll
@@ -194,11 +184,7 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
       }
       warp_argmax<T>(bestv, best);
       if (best < 0 || !(bestv > T(0))) break;
-      T a0b = T(0);
-#pragma unroll
-      for (int c = 0; c < KPL; ++c)
-        if (c == (best >> 5)) a0b = a0r[c];
-      a0b = __shfl_sync(0xffffffffu, a0b, best & 31);
+      const T a0b = arow[best];
       // column `best` of G (= row, G symmetric); the cached copy serves the
       // updates of later steps only, so the last step reads it from L2
       const T *gcol = Gt + (size_t)best * K;
@@ -214,22 +200,41 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
       const T gbb = gcol[best];
       const T piv2 = gbb - warp_sum(lane < k ? w * w : T(0));
       if (!(piv2 > PivotRel<T>::v * gbb) || !(piv2 > T(0))) break;
+      const T wz = warp_sum(lane < k ? w * zl : T(0));
+      const T rl = T(1) / tsqrt(piv2);
       if (lane < k) Ls[k * lp + lane] = w;
       if (lane == k) {
-        Ls[k * lp + k] = T(1) / tsqrt(piv2);
+        Ls[k * lp + k] = rl;
         Sl = best;
-        a0Sl = a0b;
+        zl = (a0b - wz) * rl;
       }
       if ((best & 31) == lane) avail &= ~(1u << (best >> 5));
       __syncwarp();
       ++k;
-      xl = upper_solve(Ls, lp, k, lower_solve(Ls, lp, k, a0Sl, lane), lane);
+      const T xn = upper_solve(Ls, lp, k, zl, lane);
+      if (k < s) {
+        // alpha -= G[:, S] (x_new - x_old); the new atom's old coefficient is 0
+        const T dl = xn - xl;
+        for (int p = 0; p < k; ++p) {
+          const T dp = __shfl_sync(0xffffffffu, dl, p);
+          const T *gp = gcache ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
+          if (full) {
+#pragma unroll
+            for (int c = 0; c < KPL; ++c) av[c] = fma(-gp[lane + 32 * c], dp, av[c]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < KPL; ++c)
+              if ((valid >> c) & 1u) av[c] = fma(-gp[lane + 32 * c], dp, av[c]);
+          }
+        }
+      }
+      xl = xn;
       if (eps > T(0) && k < s) {   // explicit residual for the error-constrained stop
-        T rl[M32];
-        support_residual(Dt, ysig, m, mu, k, Sl, xl, rl, lane);
+        T rl2[M32];
+        support_residual(Dt, ysig, m, mu, k, Sl, xl, rl2, lane);
         T acc = T(0);
 #pragma unroll
-        for (int u = 0; u < M32; ++u) acc = fma(rl[u], rl[u], acc);
+        for (int u = 0; u < M32; ++u) acc = fma(rl2[u], rl2[u], acc);
         rn2 = warp_sum(acc);
       }
     }
@@ -237,45 +242,18 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
     // ---- refinement on the support
     T res2 = yn2;
     if (k > 0) {
-      const T *F = Ls;   // factor used for the correction step
-      if (EXACT) {
-        // exact Gram entries of the support (FP32 Gram of D) and D_S^T y, fresh factor
-        const T *Gex = static_cast<const T *>(a.Gexact) + (size_t)(Dt - static_cast<const T *>(a.D)) / m * K;
-        for (int p = 0; p < k; ++p) {
-          const int Sp = __shfl_sync(0xffffffffu, Sl, p);
-          if (lane <= p) Gx[p * lp + lane] = Gex[(size_t)Sp * K + Sl];
-        }
+      if (EXACT) {   // x = G_SS^{-1} D_S^T y with D_S^T y in T
         T yl[M32];
 #pragma unroll
         for (int u = 0; u < M32; ++u) yl[u] = (u < mu && lane + 32 * u < m) ? ysig[lane + 32 * u] : T(0);
         const T bl = support_dots(Dt, m, mu, k, Sl, yl, lane);
-        __syncwarp();
-        // column-sweep Cholesky of Gx (lane r owns row r)
-        bool ok = true;
-        for (int c = 0; c < k; ++c) {
-          const T d = Gx[c * lp + c];
-          if (!(d > T(0))) { ok = false; break; }
-          const T inv = T(1) / tsqrt(d);
-          __syncwarp();
-          if (lane == c) Gx[c * lp + c] = inv;
-          if (lane > c && lane < k) Gx[lane * lp + c] *= inv;
-          __syncwarp();
-          if (lane > c && lane < k) {
-            const T lr = Gx[lane * lp + c];
-            for (int q2 = c + 1; q2 <= lane; ++q2) Gx[lane * lp + q2] = fma(-lr, Gx[q2 * lp + c], Gx[lane * lp + q2]);
-          }
-          __syncwarp();
-        }
-        if (ok) {
-          F = Gx;
-          xl = upper_solve(Gx, lp, k, lower_solve(Gx, lp, k, bl, lane), lane);
-        }
+        xl = upper_solve(Ls, lp, k, lower_solve(Ls, lp, k, bl, lane), lane);
       }
-      // one correction step x += F^{-T} F^{-1} D_S^T (y - D_S x), then ||y - D_S x||^2
+      // one correction step x += L^{-T} L^{-1} D_S^T (y - D_S x), then ||y - D_S x||^2
       T rloc[M32];
       support_residual(Dt, ysig, m, mu, k, Sl, xl, rloc, lane);
       const T cl = support_dots(Dt, m, mu, k, Sl, rloc, lane);
-      xl += upper_solve(F, lp, k, lower_solve(F, lp, k, cl, lane), lane);
+      xl += upper_solve(Ls, lp, k, lower_solve(Ls, lp, k, cl, lane), lane);
       support_residual(Dt, ysig, m, mu, k, Sl, xl, rloc, lane);
       T racc = T(0);
 #pragma unroll

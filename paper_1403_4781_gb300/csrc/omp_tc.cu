@@ -1,16 +1,19 @@
-// BF16 tensor-core front end of OMP (Sec. 1) and of the Gram matrix.
+// BF16 tensor-core front end of OMP (Sec. 1).
 //
-// The correlations alpha0 = D^T y and the Gram G = D^T D are dense contractions,
-// so the BF16 path runs them on the 5th-generation tensor cores: tcgen05.mma
+// The correlations alpha0 = D^T y are the dense contraction of the coding pass
+// (2 m K products per signal), so the BF16 path runs them on the 5th-generation
+// tensor cores: tcgen05.mma
 // (kind::f16, BF16 operands, FP32 accumulation) with the accumulator tile in
 // tensor memory, operands in shared memory in the canonical K-major layout.
 // Dictionary tiles are streamed in by bulk TMA copies of a pre-laid-out BF16
 // image of D; the signal tile is converted from FP32 in the kernel.  The
 // correlation kernel writes alpha0 of 128-signal tiles to a global scratch (in
 // chunks of at most 1 GiB); the selection kernel then runs the shared selection
-// loop from there with little shared memory per block, and refits the
-// coefficients on the support exactly in FP32 from D (one refinement step), so
-// the BF16 rounding affects only which atoms are chosen.
+// loop from there with little shared memory per block.  The selection updates
+// the correlations with the FP32 Gram (O(K^2 m) per dictionary, small beside
+// the n K m of the correlations), so its Cholesky factor of G_SS is FP32-exact
+// and serves the refit of the coefficients on the support from D_S^T y in FP32
+// (one refinement step): the BF16 rounding affects only which atoms are chosen.
 #include "omp_common.cuh"
 #include "tc_ptx.cuh"
 
@@ -45,68 +48,6 @@ __global__ void bf16_image_kernel(const float *__restrict__ D, int K, int m, int
     *reinterpret_cast<uint4 *>(img + (size_t)t * Kp * mp * 2 + tc::image_offset(r, kc * 8, mp)) =
         make_uint4(packed[0], packed[1], packed[2], packed[3]);
   }
-}
-
-// G tile [128 rows][NG cols] of subset blockIdx.z from the BF16 image.
-__global__ void __launch_bounds__(128) gram_tc_kernel(const unsigned char *__restrict__ img, int K, int Kp, int mp,
-                                                      int NG, float *__restrict__ G, int32_t *err) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  const int t = blockIdx.z, bx = blockIdx.x, by = blockIdx.y;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  unsigned char *Aim = smem;
-  unsigned char *Bim = smem + (size_t)128 * mp * 2;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + (size_t)(128 + NG) * mp * 2);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
-  const uint32_t ncols = NG <= 128 ? 128u : 256u;
-  if (warp == 0) tc::tmem_alloc(tslot, ncols);
-  if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
-    tc::mbar_fence_init();
-  }
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t tbase = *tslot;
-  const unsigned char *sub = img + (size_t)t * Kp * mp * 2;
-  const int rowsA = min(128, Kp - 128 * bx), rowsB = min(NG, Kp - NG * by);
-  if (tid == 0) {
-    tc::mbar_expect_tx(&mbar[0], (uint32_t)(rowsA + rowsB) * mp * 2);
-    tc::bulk_g2s(Aim, sub + (size_t)128 * bx * mp * 2, (uint32_t)rowsA * mp * 2, &mbar[0]);
-    tc::bulk_g2s(Bim, sub + (size_t)NG * by * mp * 2, (uint32_t)rowsB * mp * 2, &mbar[0]);
-  }
-  bool ok = tc::mbar_wait(&mbar[0], 0, kWaitLimit);
-  if (ok && tid == 0) {
-    const uint32_t idesc = tc::idesc_bf16(128, NG);
-    const uint32_t sbo = (uint32_t)(mp >> 3) * 128;
-    for (int ks = 0; ks < (mp >> 4); ++ks)
-      tc::mma_bf16(tbase, tc::smem_desc(tc::smem_u32(Aim) + ks * 256, 128, sbo),
-                   tc::smem_desc(tc::smem_u32(Bim) + ks * 256, 128, sbo), idesc, ks > 0);
-    tc::mma_commit(&mbar[1]);
-  }
-  __syncthreads();
-  if (ok) ok = tc::mbar_wait(&mbar[1], 0, kWaitLimit);
-  tc::fence_after();
-  if (ok) {
-    const int row = 128 * bx + 32 * warp + lane;
-    for (int c0 = 0; c0 < NG; c0 += 32) {
-      float v[32];
-      tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + c0, v);
-      if (row < K) {
-        float *grow = G + ((size_t)t * K + row) * K;
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          const int col = NG * by + c0 + e;
-          if (col < K) grow[col] = v[e];
-        }
-      }
-    }
-  } else if (tid == 0) {
-    atomicOr(err, 1);
-  }
-  tc::fence_before();
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, ncols);
 }
 
 // ---- correlations: alpha0 = Y D^T of 128-signal tiles into global memory ----
@@ -253,7 +194,7 @@ constexpr int kSelThreads = 256;
 struct SelLayout {
   int lp;
   bool gcache;
-  size_t ls, gx, gc, total;
+  size_t ls, gc, total;
 };
 
 inline SelLayout sel_layout(int K, int s) {
@@ -263,7 +204,6 @@ inline SelLayout sel_layout(int K, int s) {
   L.gcache = gcol <= 48 * 1024;
   size_t off = 0;
   L.ls = off; off += align16(sizeof(float) * (size_t)8 * s * L.lp);
-  L.gx = off; off += align16(sizeof(float) * (size_t)8 * s * L.lp);
   L.gc = off; off += L.gcache ? align16(gcol) : 0;
   L.total = off;
   return L;
@@ -286,10 +226,9 @@ __global__ void __launch_bounds__(kSelThreads) omp_select_kernel(OmpArgs a, SelL
   const float *__restrict__ Gt = static_cast<const float *>(a.G) + (size_t)t * K * K;
   const float *a0 = a0c + ((size_t)(g - tile0) * 128 + quarter * 32) * K;
   float *Ls = reinterpret_cast<float *>(smem + lay.ls) + (size_t)warp * s * lay.lp;
-  float *Gx = reinterpret_cast<float *>(smem + lay.gx) + (size_t)warp * s * lay.lp;
   float *gc = lay.gcache ? reinterpret_cast<float *>(smem + lay.gc) + (size_t)warp * s * K : nullptr;
   code_warp_signals<float, KPL, MU, true>(a, a0, static_cast<const float *>(a.Y) + (size_t)row0 * m, m, warp * 4, 4,
-                                          nsig, row0, Dt, Gt, Ls, Gx, gc, lay.lp, lay.gcache);
+                                          nsig, row0, Dt, Gt, Ls, gc, lay.lp, lay.gcache);
 }
 
 template <int KPL, int MU>
@@ -311,17 +250,6 @@ cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, cu
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   bf16_image_kernel<<<blocks, 256, 0, st>>>(D, K, m, Kp, mp, L, static_cast<unsigned char *>(img));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gram_tc(const void *img, int K, int m, int L, float *G, int32_t *err, cudaStream_t st) {
-  const int Kp = round16(K), mp = round16(m);
-  const int NG = Kp > 128 ? 256 : 128;
-  const size_t smem = tc::smem_for_tmem((size_t)(128 + NG) * mp * 2 + 64, NG <= 128 ? 128 : 256);
-  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((Kp + 127) / 128, (Kp + NG - 1) / NG, L);
-  gram_tc_kernel<<<grid, 128, smem, st>>>(static_cast<const unsigned char *>(img), K, Kp, mp, NG, G, err);
   return cudaGetLastError();
 }
 

@@ -121,7 +121,6 @@ struct OmpArgs {
   void *resid2;           // may be null
   // tensor-core (BF16) path only
   const void *Dimg;       // [L][Kp][mp] BF16 canonical K-major image of D
-  const void *Gexact;     // [L][K][K] Gram of D in FP32 (refit on the support)
   int Kp, mp;             // K and m rounded up to multiples of 16
   int32_t *err;           // device word: bit 0 set when a bounded wait gave up
 };
@@ -132,7 +131,6 @@ int omp_tile_signals();
 // BF16 tensor-core path (tcgen05 + TMEM, operands fed by bulk TMA copies).
 inline int round16(int x) { return (x + 15) & ~15; }
 cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, cudaStream_t st);
-cudaError_t launch_gram_tc(const void *img, int K, int m, int L, float *G, int32_t *err, cudaStream_t st);
 // Correlations of 128-signal tiles on the tensor cores into the scratch a0c
 // (omp_tc_chunk_tiles tiles of 128 x K floats at a time), then the selection
 // loop from there.
