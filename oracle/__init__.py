@@ -15,6 +15,10 @@ Readings of the paper fixed here (Sec. 1, 2, 3.1, Algorithm 1):
     least squares on the support, stop at s atoms or ||r|| <= eps.
   * MOD: D = Y X^T (X X^T)^{-1} over the used atoms, unused atoms kept,
     columns renormalised.
+  * Atom replacement (not in the paper; off unless min_use > 0): after the MOD
+    update, atoms used by fewer than min_use signals become the worst-coded
+    training signals, normalised.  Parity unpinned against the paper, which has
+    no such step: its pins are hand-worked cases and the definition above.
 """
 from __future__ import annotations
 
@@ -59,13 +63,15 @@ def _load():
             lib.orc_omp.argtypes = [_dp, i32, i32, _dp, i64, i32, dbl, _ip, _dp, _ip, _dp, _dp, i32]
             lib.orc_mod.argtypes = [_dp, i32, i64, _ip, _dp, i32, _dp, i32, i32, _dp, _ip,
                                     ctypes.POINTER(ctypes.c_int)]
-            lib.orc_train.argtypes = [_dp, i32, i64, _dp, i32, i32, dbl, i32, _dp, _dp, _ip, _dp,
-                                      _ip, i32]
+            lib.orc_train.argtypes = [_dp, i32, i64, _dp, i32, i32, dbl, i32, i32, _dp, _dp, _ip,
+                                      _dp, _ip, i32]
             lib.orc_split.argtypes = [_dp, i32, i64, _lp, _dp]
-            lib.orc_local_train.argtypes = [_dp, i32, _lp, i32, _dp, i32, i32, dbl, i32, _dp, _dp,
-                                            i32]
-            lib.orc_merge.argtypes = [_dp, _dp, i32, i32, i32, _ip, i32, i32, dbl, i32, _dp, _dp,
-                                      _dp, i32]
+            lib.orc_local_train.argtypes = [_dp, i32, _lp, i32, _dp, i32, i32, dbl, i32, i32, _dp,
+                                            _dp, i32]
+            lib.orc_merge.argtypes = [_dp, _dp, i32, i32, i32, _ip, i32, i32, dbl, i32, i32, _dp,
+                                      _dp, _dp, i32]
+            lib.orc_replace_atoms.argtypes = [_dp, i32, i64, _ip, _dp, i32, _dp, i32, _ip,
+                                              ctypes.POINTER(ctypes.c_int)]
             lib.orc_residual.argtypes = [_dp, i32, i64, _dp, i32, _ip, _dp, i32, _dp, _dp]
             lib.orc_recovery.argtypes = [_dp, i32, _dp, i32, i32, dbl, ctypes.POINTER(ctypes.c_int)]
             lib.orc_mlp_forward.argtypes = [_dp, i32, i32, i32, i32, _dp, i64, _dp]
@@ -74,7 +80,8 @@ def _load():
             lib.orc_patch_average.argtypes = [_dp, i32, _ip, _dp, i32, i32, i32, i32, _dp]
             for f in ("orc_omp", "orc_mod", "orc_train", "orc_split", "orc_local_train",
                       "orc_merge", "orc_residual", "orc_recovery", "orc_mlp_forward",
-                      "orc_mlp_loss_grad", "orc_extract_patches", "orc_patch_average"):
+                      "orc_mlp_loss_grad", "orc_extract_patches", "orc_patch_average",
+                      "orc_replace_atoms"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -149,8 +156,26 @@ def mod(Y, idx, val, Dprev, normalise=True):
     return Dout, usage, bool(ridge.value), rc
 
 
-def train(Y, D0, s, iters, eps=0.0, nthreads=None):
-    """Standard alternating OMP/MOD training; returns dict(D, rmse, xfro, idx, val, nnz, status)."""
+def replace_atoms(Y, usage, resid2, min_use, D):
+    """Atom replacement (not in the paper): atoms used by fewer than min_use
+    signals become the worst-coded signals, normalised.  Returns (D (K,m), rep (K,), count)."""
+    lib = _load()
+    Y = _f64(Y)
+    n, m = Y.shape
+    D = _f64(D).copy()
+    K = D.shape[0]
+    usage = np.ascontiguousarray(usage, np.int32)
+    resid2 = _f64(resid2)
+    rep = np.empty((K,), np.int32)
+    cnt = ctypes.c_int(0)
+    _check(lib.orc_replace_atoms(_d(Y), m, n, _i(usage), _d(resid2), int(min_use), _d(D), K, _i(rep),
+                                 ctypes.byref(cnt)), "orc_replace_atoms")
+    return D, rep, cnt.value
+
+
+def train(Y, D0, s, iters, eps=0.0, nthreads=None, min_use=0):
+    """Standard alternating OMP/MOD training (min_use > 0: atom replacement after
+    every MOD update); returns dict(D, rmse, xfro, idx, val, nnz, status)."""
     lib = _load()
     Y = _f64(Y)
     D = _f64(D0).copy()
@@ -161,7 +186,7 @@ def train(Y, D0, s, iters, eps=0.0, nthreads=None):
     idx = np.empty((n, s), np.int32)
     val = np.empty((n, s), np.float64)
     nnz = np.empty((n,), np.int32)
-    rc = lib.orc_train(_d(Y), m, n, _d(D), K, s, float(eps), iters, _d(rmse),
+    rc = lib.orc_train(_d(Y), m, n, _d(D), K, s, float(eps), iters, int(min_use), _d(rmse),
                        ctypes.cast(ctypes.byref(xf), _dp), _i(idx), _d(val), _i(nnz),
                        nthreads or default_threads())
     _check(rc, "orc_train")
@@ -178,7 +203,7 @@ def split(Y, perm):
     return out
 
 
-def local_train(Y, offsets, Dloc0, s1, iters, eps=0.0, nthreads=None):
+def local_train(Y, offsets, Dloc0, s1, iters, eps=0.0, nthreads=None, min_use=0):
     """Algorithm 1 step 2 over every subset; returns dict(D (L,K1,m), xfro (L,), rmse (L,iters))."""
     lib = _load()
     Y = _f64(Y)
@@ -188,12 +213,12 @@ def local_train(Y, offsets, Dloc0, s1, iters, eps=0.0, nthreads=None):
     xfro = np.empty((L,), np.float64)
     rmse = np.empty((L, iters), np.float64)
     rc = lib.orc_local_train(_d(Y), m, _l(offsets), L, _d(D), K1, s1, float(eps), iters,
-                             _d(xfro), _d(rmse), nthreads or default_threads())
+                             int(min_use), _d(xfro), _d(rmse), nthreads or default_threads())
     _check(rc, "orc_local_train")
     return dict(D=D, xfro=xfro, rmse=rmse, status=rc)
 
 
-def merge(Dloc, xfro, pick, K, s2, iters, eps=0.0, nthreads=None):
+def merge(Dloc, xfro, pick, K, s2, iters, eps=0.0, nthreads=None, min_use=0):
     """Algorithm 1 step 3; returns dict(D (K,m), rmse (iters,), Ytilde (K1 L, m))."""
     lib = _load()
     Dloc = _f64(Dloc)
@@ -203,7 +228,8 @@ def merge(Dloc, xfro, pick, K, s2, iters, eps=0.0, nthreads=None):
     D = np.empty((K, m), np.float64)
     rmse = np.empty((iters,), np.float64)
     Yt = np.empty((K1 * L, m), np.float64)
-    rc = lib.orc_merge(_d(Dloc), _d(xfro), m, K1, L, _i(pick), K, s2, float(eps), iters, _d(D),
+    rc = lib.orc_merge(_d(Dloc), _d(xfro), m, K1, L, _i(pick), K, s2, float(eps), iters,
+                       int(min_use), _d(D),
                        _d(rmse), _d(Yt), nthreads or default_threads())
     _check(rc, "orc_merge")
     return dict(D=D, rmse=rmse, Ytilde=Yt, status=rc)

@@ -226,8 +226,41 @@ int orc_mod(const double *Y, int m, int64_t n, const int32_t *idx,
 
 /* -------------------------------------------------------------- train --- */
 
+/* Atom replacement (not in the paper, which keeps unused atoms).  Atoms are
+   visited in increasing index; atom j with usage[j] < min_use becomes the unit
+   vector along the training signal with the largest squared residual resid2[i]
+   among those not yet taken, ties to the lower signal index.  Only signals with
+   resid2 > 0 qualify (such a signal is nonzero); once none is left, the
+   remaining atoms keep their value.  rep[j] = i for a replaced atom, else -1. */
+int orc_replace_atoms(const double *Y, int m, int64_t n, const int32_t *usage,
+                      const double *resid2, int min_use, double *D, int K, int32_t *rep,
+                      int *nrep) {
+  if (m <= 0 || K <= 0 || n < 0 || !usage || !D || (n > 0 && (!Y || !resid2))) return 1;
+  unsigned char *taken = (unsigned char *)calloc((size_t)(n > 0 ? n : 1), 1);
+  int count = 0;
+  for (int j = 0; j < K; ++j) {
+    if (rep) rep[j] = -1;
+    if (usage[j] >= min_use) continue;
+    int64_t best = -1;
+    for (int64_t i = 0; i < n; ++i) {
+      if (taken[i] || !(resid2[i] > 0.0)) continue;
+      if (best < 0 || resid2[i] > resid2[best]) best = i;
+    }
+    if (best < 0) continue;
+    taken[best] = 1;
+    const double *y = Y + (size_t)best * m;
+    const double nrm = sqrt(dot(y, y, m));
+    for (int r = 0; r < m; ++r) D[(size_t)j * m + r] = y[r] / nrm;
+    if (rep) rep[j] = (int32_t)best;
+    ++count;
+  }
+  free(taken);
+  if (nrep) *nrep = count;
+  return 0;
+}
+
 int orc_train(const double *Y, int m, int64_t n, double *D, int K, int s,
-              double eps, int iters, double *rmse, double *xfro,
+              double eps, int iters, int min_use, double *rmse, double *xfro,
               int32_t *idx, double *val, int32_t *nnz, int nthreads) {
   if (m <= 0 || K <= 0 || n <= 0 || s <= 0 || iters < 0 || !Y || !D) return 1;
   int32_t *ix = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * s);
@@ -235,6 +268,7 @@ int orc_train(const double *Y, int m, int64_t n, double *D, int K, int s,
   int32_t *nz = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
   double *r2 = (double *)malloc(sizeof(double) * (size_t)n);
   double *Dn = (double *)malloc(sizeof(double) * (size_t)K * m);
+  int32_t *use = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
   int status = 0;
   double fro2 = 0.0;
   for (int it = 0; it < iters; ++it) {
@@ -244,8 +278,9 @@ int orc_train(const double *Y, int m, int64_t n, double *D, int K, int s,
     if (rmse) rmse[it] = sqrt(acc / ((double)m * (double)n));
     fro2 = 0.0;
     for (int64_t e = 0; e < n * s; ++e) fro2 += vx[e] * vx[e];
-    int st = orc_mod(Y, m, n, ix, vx, s, D, K, 1, Dn, NULL, NULL);
+    int st = orc_mod(Y, m, n, ix, vx, s, D, K, 1, Dn, use, NULL);
     if (st) status = st;
+    if (min_use > 0) orc_replace_atoms(Y, m, n, use, r2, min_use, Dn, K, NULL, NULL);
     memcpy(D, Dn, sizeof(double) * (size_t)K * m);
   }
   if (xfro) *xfro = sqrt(fro2);
@@ -259,6 +294,7 @@ int orc_train(const double *Y, int m, int64_t n, double *D, int K, int s,
   free(nz);
   free(r2);
   free(Dn);
+  free(use);
   return status;
 }
 
@@ -274,7 +310,7 @@ int orc_split(const double *Y, int m, int64_t N, const int64_t *perm, double *Yp
 }
 
 int orc_local_train(const double *Y, int m, const int64_t *offsets, int L,
-                    double *Dloc, int K1, int s1, double eps, int iters,
+                    double *Dloc, int K1, int s1, double eps, int iters, int min_use,
                     double *xfro, double *rmse, int nthreads) {
   if (m <= 0 || L <= 0 || K1 <= 0 || s1 <= 0 || !offsets || !Dloc || !xfro) return 1;
   for (int t = 0; t < L; ++t)
@@ -284,7 +320,7 @@ int orc_local_train(const double *Y, int m, const int64_t *offsets, int L,
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
   for (int t = 0; t < L; ++t) {
     int st = orc_train(Y + (size_t)offsets[t] * m, m, offsets[t + 1] - offsets[t],
-                       Dloc + (size_t)t * K1 * m, K1, s1, eps, iters,
+                       Dloc + (size_t)t * K1 * m, K1, s1, eps, iters, min_use,
                        rmse ? rmse + (size_t)t * iters : NULL, xfro + t, NULL, NULL,
                        NULL, 1);
     if (st) {
@@ -296,7 +332,7 @@ int orc_local_train(const double *Y, int m, const int64_t *offsets, int L,
 }
 
 int orc_merge(const double *Dloc, const double *xfro, int m, int K1, int L,
-              const int32_t *pick, int K, int s2, double eps, int iters,
+              const int32_t *pick, int K, int s2, double eps, int iters, int min_use,
               double *D, double *rmse, double *Ytilde_out, int nthreads) {
   if (m <= 0 || K1 <= 0 || L <= 0 || K <= 0 || s2 <= 0 || !Dloc || !xfro || !pick || !D)
     return 1;
@@ -316,7 +352,8 @@ int orc_merge(const double *Dloc, const double *xfro, int m, int K1, int L,
     for (int r = 0; r < m; ++r) D[(size_t)j * m + r] = nrm > 0.0 ? c[r] / nrm : 0.0;
   }
   double xf;
-  int st = orc_train(Yt, m, nt, D, K, s2, eps, iters, rmse, &xf, NULL, NULL, NULL, nthreads);
+  int st = orc_train(Yt, m, nt, D, K, s2, eps, iters, min_use, rmse, &xf, NULL, NULL, NULL,
+                     nthreads);
   if (Ytilde_out) memcpy(Ytilde_out, Yt, sizeof(double) * (size_t)nt * m);
   free(Yt);
   return st;

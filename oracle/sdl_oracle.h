@@ -51,13 +51,25 @@ int orc_mod(const double *Y, int m, int64_t n, const int32_t *idx,
             const double *val, int s, const double *Dprev, int K, int normalise,
             double *Dout, int32_t *usage, int *ridge);
 
+/* Atom replacement, an alternative dictionary-update policy (not in the paper,
+ * whose reading keeps unused atoms): atoms are visited in increasing index and
+ * atom j with usage[j] < min_use becomes y_i / ||y_i|| for the signal i with the
+ * largest resid2[i] not yet taken (lower i on ties; only resid2 > 0 qualifies;
+ * when none is left the remaining atoms keep their value).  rep[K] (may be
+ * NULL) receives i or -1 per atom, nrep (may be NULL) the number replaced. */
+int orc_replace_atoms(const double *Y, int m, int64_t n, const int32_t *usage,
+                      const double *resid2, int min_use, double *D, int K, int32_t *rep,
+                      int *nrep);
+
 /* Alternating minimisation (Sec. 1, "standard approach"): for it in 0..iters-1
  * { X = OMP(D, Y, s, eps); rmse[it] = ||Y - D X||_F / sqrt(m n); D = MOD(Y, X) }.
+ * With min_use > 0 every MOD update is followed by orc_replace_atoms with the
+ * usage counts of X and the squared residuals of that coding pass.
  * D is the initial dictionary on entry and the trained one on exit.
  * xfro receives ||X||_F of the last coding pass.  idx/val/nnz (may be NULL)
  * receive that last coding.  rmse may be NULL. */
 int orc_train(const double *Y, int m, int64_t n, double *D, int K, int s,
-              double eps, int iters, double *rmse, double *xfro,
+              double eps, int iters, int min_use, double *rmse, double *xfro,
               int32_t *idx, double *val, int32_t *nnz, int nthreads);
 
 /* Algorithm 1 step 1: Yp[:, i] = Y[:, perm[i]] (the random partition is the
@@ -68,7 +80,7 @@ int orc_split(const double *Y, int m, int64_t N, const int64_t *perm, double *Yp
  * trained independently with K1 atoms and sparsity s1.  Dloc is [L][K1][m]
  * (init on entry, trained on exit); xfro[L]; rmse [L][iters] (may be NULL). */
 int orc_local_train(const double *Y, int m, const int64_t *offsets, int L,
-                    double *Dloc, int K1, int s1, double eps, int iters,
+                    double *Dloc, int K1, int s1, double eps, int iters, int min_use,
                     double *xfro, double *rmse, int nthreads);
 
 /* Algorithm 1 step 3: Ytilde = [ xfro[0] D^(0) ... xfro[L-1] D^(L-1) ]
@@ -76,7 +88,7 @@ int orc_local_train(const double *Y, int m, const int64_t *offsets, int L,
  * and trained on Ytilde with K atoms and sparsity s2.  D is [K][m] out.
  * Ytilde_out [K1 L][m] may be NULL. */
 int orc_merge(const double *Dloc, const double *xfro, int m, int K1, int L,
-              const int32_t *pick, int K, int s2, double eps, int iters,
+              const int32_t *pick, int K, int s2, double eps, int iters, int min_use,
               double *D, double *rmse, double *Ytilde_out, int nthreads);
 
 /* ||Y - D X||_F^2 and ||Y||_F^2 with X in ELL form (Table 1's MSE_train is
