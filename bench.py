@@ -536,6 +536,8 @@ def run_denoise(args):
     dictionaries with 20 (+20) iterations; a new noisy image (sigma = 20/255)
     denoised with each and with the DCT itself (every overlapping patch coded
     to ||r|| <= 8.5 sigma, at most 32 atoms, estimates averaged per pixel).
+    Both trainings are repeated with atom replacement (atoms no training patch
+    uses become the worst-coded patches after every MOD update).
     A measurement of a widening workload, printed as its own line."""
     import torch
 
@@ -576,9 +578,23 @@ def run_denoise(args):
         sdl.local_train(Y, [0, len(train)], D, 8, 20, with_rmse=False)
         return D[0]
 
+    ctx = sdl.context(0)
     split_merge(), standard()   # warm-up: autotuner, workspace
     t_sm, D_sm = timed(split_merge)
     t_std, D_std = timed(standard)
+    # the same trainings with atom replacement after every MOD update (min_use 1)
+    ctx.set_option(sdl.OPT_REPLACE, 1)
+    try:
+        split_merge(), standard()
+        t_smr, D_smr = timed(split_merge)
+        t_stdr, D_stdr = timed(standard)
+        ctx.profile(True)
+        ctx.profile_reset()
+        split_merge()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+    finally:
+        ctx.set_option(sdl.OPT_REPLACE, 0)
     ng = torch.from_numpy(noisy).to(dev)
     cg = torch.from_numpy(clean.astype(np.float32)).to(dev)
 
@@ -586,12 +602,22 @@ def run_denoise(args):
         e2 = sdl.sq_error(img, cg).cpu().numpy()[0]
         return float(10 * np.log10(img.numel() / e2))
 
-    out = {"train_s": {"split_merge": t_sm, "standard": t_std}, "psnr_noisy": psnr(ng)}
-    for name, D in (("split_merge", D_sm), ("standard", D_std), ("dct", torch.from_numpy(D_mer0).to(dev))):
+    def unused_atoms(D, s):
+        idx = sdl.omp(D, Y, s, with_resid=False)[0]
+        return int(D.shape[0] - torch.unique(idx[idx >= 0]).numel())
+
+    out = {"train_s": {"split_merge": t_sm, "standard": t_std, "split_merge_replace": t_smr,
+                       "standard_replace": t_stdr},
+           "replace_kernel": {"ms_per_launch": prof["replace"][2] / max(prof["replace"][0], 1),
+                              "launches": prof["replace"][0],
+                              "share_of_training": prof["replace"][2] / sum(v[2] for v in prof.values())},
+           "psnr_noisy": psnr(ng)}
+    for name, D, s_tr in (("split_merge", D_sm, 2), ("standard", D_std, 8), ("split_merge_replace", D_smr, 2),
+                          ("standard_replace", D_stdr, 8), ("dct", torch.from_numpy(D_mer0).to(dev), 8)):
         sdl.denoise(ng, D, 8, 8.5 * sigma)
         t, (den, (idx, val, nnz)) = timed(lambda: sdl.denoise(ng, D, 8, 8.5 * sigma))
         out[name] = {"psnr": psnr(den), "denoise_s": t, "patches_per_s": idx.shape[0] / t,
-                     "mean_atoms": float(nnz.float().mean())}
+                     "mean_atoms": float(nnz.float().mean()), "atoms_unused_on_training_patches": unused_atoms(D, s_tr)}
     res = {"metric": METRIC, "workload": "denoise_synthetic_512x512_sigma20", "train_patches": len(train),
            "data": "synthetic piecewise-smooth images (seeded), pixel values in [0, 1]", **out}
     print(json.dumps(res), flush=True)

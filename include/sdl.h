@@ -122,6 +122,27 @@ sdl_status sdl_mod_update_batched(sdl_ctx *ctx, sdl_precision prec, const void *
                                   const int64_t *offsets, int L, const int32_t *idx,
                                   const void *val, int s, void *D, int K, int32_t *usage);
 
+/* Atom replacement, an alternative dictionary-update policy.  The paper has no
+ * counterpart: its MOD (Sec. 1) leaves unused atoms as they are.  For every
+ * subset t (signals offsets[t] .. offsets[t+1]-1, dictionary D + t*K*m), the
+ * atoms j with usage[t][j] < min_use are visited in increasing j, and each
+ * becomes y_i / ||y_i||.  Signal i is the one of the subset with the largest
+ * resid2[i] that no earlier atom took, the lower i on ties.  Only signals with
+ * resid2 > 0 qualify.  Once none is left, the remaining atoms keep their value.
+ *   prec    F32 or F64 (the data type of Y, resid2 and D)
+ *   Y       device [n][m];  resid2 device [n], squared residuals of the coding
+ *           pass that produced the usage counts (sdl_omp's resid2)
+ *   offsets HOST int64 [L+1];  usage device int32 [L][K] (sdl_mod_update's)
+ *   D       device [L][K][m], updated in place
+ *   rep     device int32 [L][K] out (the signal row that replaced an atom, or
+ *           -1), may be NULL
+ * min_use = 0 replaces nothing.  SDL_OPT_REPLACE applies the same step after
+ * every MOD update of sdl_local_train and sdl_merge.  Errors:
+ * SDL_EINVAL for a bad shape, precision or pointer. */
+sdl_status sdl_replace_atoms(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m,
+                             const int64_t *offsets, int L, const int32_t *usage,
+                             const void *resid2, int min_use, void *D, int K, int32_t *rep);
+
 /* Algorithm 1 step 1: Yp[:, i] = Y[:, perm[i]].  perm device int64 [N], a
  * permutation of 0..N-1 drawn by the caller; consecutive ranges of Yp given by
  * the caller's offsets are the random subsets. */
@@ -252,8 +273,9 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
                            int s, double eps, int32_t *idx, float *val, int32_t *nnz,
                            float *resid2);
 
-/* Execution options (the paper has no counterpart; they select between
- * implementations of the FP64 MOD solve that compute the same result):
+/* Execution options (the paper has no counterpart; the first six select
+ * between implementations that compute the same result, the last one enables
+ * an alternative dictionary-update policy):
  *   SDL_OPT_MOD_SOLVE: 0 = automatic (default: the tiled solve with an
  *     automatic tile and cluster size), 1 = one thread-block cluster per subset
  *     holding the factor in distributed shared memory (K <= 512), 2 = one
@@ -280,6 +302,10 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     run eagerly.  Graphs refer to the caller's buffers: do not free a buffer
  *     that a cached graph uses while the option is on (turning it off, or a
  *     workspace reallocation, drops the cache).  0 (default) = always eager.
+ *   SDL_OPT_REPLACE: min_use of the atom replacement (sdl_replace_atoms) run
+ *     after every MOD update of the training loops.  0 (default) = off, the
+ *     paper's reading: unused atoms keep their value.  This option changes the
+ *     result; the others above do not.
  * Returns SDL_EINVAL for an unknown option or value. */
 typedef enum {
   SDL_OPT_MOD_SOLVE = 1,
@@ -287,7 +313,8 @@ typedef enum {
   SDL_OPT_MOD_TILE = 3,
   SDL_OPT_AUTOTUNE = 4,
   SDL_OPT_GRAPH = 5,
-  SDL_OPT_SM_BLOCKS = 6
+  SDL_OPT_SM_BLOCKS = 6,
+  SDL_OPT_REPLACE = 7
 } sdl_option;
 sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
 

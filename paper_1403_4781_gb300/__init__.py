@@ -63,6 +63,7 @@ _SIGS = {
                                _vp]),
     "sdl_mod_update": (_i32, [_vp, _i32, _vp, _i32, _i64, _vp, _vp, _i32, _vp, _i32, _vp]),
     "sdl_mod_update_batched": (_i32, [_vp, _i32, _vp, _i32, _vp, _i32, _vp, _vp, _i32, _vp, _i32, _vp]),
+    "sdl_replace_atoms": (_i32, [_vp, _i32, _vp, _i32, _vp, _i32, _vp, _vp, _i32, _vp, _i32, _vp]),
     "sdl_split": (_i32, [_vp, _i32, _vp, _i32, _i64, _vp, _vp]),
     "sdl_init_dict": (_i32, [_vp, _i32, _vp, _i32, _i64, _vp, _vp, _i64, _vp]),
     "sdl_local_train": (_i32, [_vp, _i32, _vp, _i32, _vp, _i32, _i32, _i32, _dbl, _i32, _vp, _vp, _vp]),
@@ -89,7 +90,7 @@ _SIGS = {
     "sdl_omp_proposed": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp,
                                 ctypes.POINTER(_i64)]),
 }
-OPT_MOD_SOLVE, OPT_CLUSTER, OPT_MOD_TILE, OPT_AUTOTUNE, OPT_GRAPH, OPT_SM_BLOCKS = 1, 2, 3, 4, 5, 6
+OPT_MOD_SOLVE, OPT_CLUSTER, OPT_MOD_TILE, OPT_AUTOTUNE, OPT_GRAPH, OPT_SM_BLOCKS, OPT_REPLACE = 1, 2, 3, 4, 5, 6, 7
 
 
 def lib() -> ctypes.CDLL:
@@ -275,6 +276,21 @@ def mod_update_batched(Y, offsets, idx, val, D, prec=None):
     _call("sdl_mod_update_batched", ctx.bind_stream(), prec, _ptr(Y), m, op, L, _ptr(idx), _ptr(val), s,
           _ptr(D), K, _ptr(usage))
     return usage
+
+
+def replace_atoms(Y, offsets, usage, resid2, min_use, D, prec=None):
+    """Atom replacement in place on D (L, K, m): per subset, atoms used by fewer
+    than min_use signals become the worst-coded signals (largest resid2),
+    normalised.  Returns rep (L, K) int32: the signal row per replaced atom, else -1."""
+    import torch
+    prec = _prec_of(D, prec)
+    L, K, m = D.shape
+    oh, op = _offsets_host(offsets)
+    rep = torch.empty((L, K), dtype=torch.int32, device=D.device)
+    ctx = context(D.device.index)
+    _call("sdl_replace_atoms", ctx.bind_stream(), prec, _ptr(Y), m, op, L, _ptr(usage), _ptr(resid2),
+          int(min_use), _ptr(D), K, _ptr(rep))
+    return rep
 
 
 def split(Y, perm, prec=None, out=None):

@@ -503,6 +503,11 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
       SDL_CUDA(timed(ctx, "mod_accum", mod_accum_kernels(sizeof(T) == 4, ma.total_tiles),
                      [&] { return launch_mod_accum<T>(ma, sm); }), "mod accumulate");
       SDL_CUDA(run_mod_solve<T>(ctx, ma), "mod solve");
+      if (ctx->opt_replace > 0)
+        SDL_CUDA(timed(ctx, "replace", 1, [&] {
+                   return launch_replace_atoms<T>(Y, m, ma.offsets, L, ma.usage, res2, ctx->opt_replace, D, K,
+                                                  nullptr, sm);
+                 }), "atom replacement");
       if (!tiled_folds_status)   // the other solve implementations only write status[]
         SDL_CUDA(timed(ctx, "status", 1, [&] { return launch_status_max(ma.status, L, worst + it, sm); }),
                  "status");
@@ -518,11 +523,11 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
     if ((st = run_loop()) != SDL_OK) return st;
   } else {
     char kb[512];
-    snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d",
+    snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d:%d",
              sizeof(T), (int)bf16, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
              (void *)d_off, m, K, s, L, (long long)n, (long long)tiles, (long long)ma.total_tiles, eps, iters,
              ctx->opt_mod_solve, ctx->opt_tile, ctx->opt_cluster * 4 + ctx->opt_sm_blocks, ctx->opt_autotune,
-             (int)ctx->tuned.size());
+             (int)ctx->tuned.size(), ctx->opt_replace);
     const std::string key(kb);
     auto hit = ctx->graphs.find(key);
     if (hit != ctx->graphs.end()) {
@@ -725,6 +730,48 @@ sdl_status sdl_mod_update_batched(sdl_ctx *ctx, sdl_precision prec, const void *
   if (prec == SDL_PREC_F64) SDL_CUDA(run_mod_solve<double>(ctx, a), "mod solve");
   else SDL_CUDA(run_mod_solve<float>(ctx, a), "mod solve");
   return mod_status(ctx, a.status, L, d_max);
+}
+
+sdl_status sdl_replace_atoms(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, const int64_t *offsets,
+                             int L, const int32_t *usage, const void *resid2, int min_use, void *D, int K,
+                             int32_t *rep) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  SDL_REQUIRE(prec != SDL_PREC_BF16, "atom replacement takes F32 or F64 data");
+  SDL_REQUIRE(m >= 1 && m <= kMaxM, "m must be in [1, 256]");
+  SDL_REQUIRE(K >= 1 && K <= kMaxK, "K must be in [1, 1024]");
+  SDL_REQUIRE(min_use >= 0, "min_use must be >= 0");
+  if ((st = check_offsets(ctx, offsets, L, false)) != SDL_OK) return st;
+  const int64_t n = offsets[L];
+  SDL_REQUIRE(n < ((int64_t)1 << 31), "more than 2^31 - 1 signals");
+  SDL_REQUIRE(aligned16(D) && aligned16(usage) && (n == 0 || (aligned16(Y) && aligned16(resid2))) &&
+                  (rep == nullptr || aligned16(rep)),
+              "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  if ((st = ws_reserve(ctx, 2 * round256(sizeof(int64_t) * (L + 1)) + 1024)) != SDL_OK) return st;
+  int64_t *d_off = nullptr;
+  int32_t *d_tiles = nullptr;
+  int64_t tiles = 0;
+  if ((st = upload_plan(ctx, offsets, L, 128, &d_off, &d_tiles, &tiles)) != SDL_OK) return st;
+  cudaStream_t sm = ctx->stream;
+  if (rep && min_use == 0)
+    SDL_CUDA(cudaMemsetAsync(rep, 0xff, sizeof(int32_t) * (size_t)L * K, sm), "rep clear");
+  if (prec == SDL_PREC_F64)
+    SDL_CUDA(timed(ctx, "replace", min_use > 0 ? 1 : 0, [&] {
+               return launch_replace_atoms<double>(static_cast<const double *>(Y), m, d_off, L, usage,
+                                                   static_cast<const double *>(resid2), min_use,
+                                                   static_cast<double *>(D), K, rep, sm);
+             }), "atom replacement");
+  else
+    SDL_CUDA(timed(ctx, "replace", min_use > 0 ? 1 : 0, [&] {
+               return launch_replace_atoms<float>(static_cast<const float *>(Y), m, d_off, L, usage,
+                                                  static_cast<const float *>(resid2), min_use,
+                                                  static_cast<float *>(D), K, rep, sm);
+             }), "atom replacement");
+  return SDL_OK;
 }
 
 sdl_status sdl_mod_update(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t n,
@@ -1086,6 +1133,11 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
     case SDL_OPT_SM_BLOCKS:
       if (value < 0 || value > 3) return set_error(ctx, SDL_EINVAL, "SDL_OPT_SM_BLOCKS takes 0 to 3");
       ctx->opt_sm_blocks = (int)value;
+      return SDL_OK;
+    case SDL_OPT_REPLACE:
+      if (value < 0 || value > ((int64_t)1 << 30))
+        return set_error(ctx, SDL_EINVAL, "SDL_OPT_REPLACE takes 0 to 2^30");
+      ctx->opt_replace = (int)value;
       return SDL_OK;
     case SDL_OPT_GRAPH:
       if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_GRAPH takes 0 or 1");

@@ -75,6 +75,7 @@ struct sdl_ctx {
   };
   std::map<std::string, TunedSolve> tuned;   // shape key -> chosen tile, cluster size, blocks-per-SM cap
   int opt_graph = 0;             // replay training loops as captured CUDA graphs
+  int opt_replace = 0;           // atom replacement after every MOD update: min_use (0 = off)
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
@@ -209,6 +210,12 @@ template <typename T>
 cudaError_t launch_recovery(const T *D0, int K0, const T *D, int K, int m, double thresh,
                             int32_t *count, cudaStream_t st);
 cudaError_t launch_status_max(const int32_t *status, int L, int32_t *out, cudaStream_t st);
+// Atom replacement (replace.cu): atoms of subset t used by fewer than min_use
+// signals become the worst-coded signals of the subset, normalised; rep[L][K]
+// (may be null) receives the signal row or -1.  offsets on the device.  K <= 1024.
+template <typename T>
+cudaError_t launch_replace_atoms(const T *Y, int m, const int64_t *offsets, int L, const int32_t *usage,
+                                 const T *resid2, int min_use, T *D, int K, int32_t *rep, cudaStream_t st);
 // Denoising (denoise.cu).
 template <typename T>
 cudaError_t launch_extract_patches(const T *img, int H, int W, int p, T *out, cudaStream_t st);
