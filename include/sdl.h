@@ -273,8 +273,8 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
                            int s, double eps, int32_t *idx, float *val, int32_t *nnz,
                            float *resid2);
 
-/* Execution options (the paper has no counterpart; the first six select
- * between implementations that compute the same result, the last one enables
+/* Execution options (the paper has no counterpart; all but SDL_OPT_REPLACE
+ * select between implementations that compute the same result, which enables
  * an alternative dictionary-update policy):
  *   SDL_OPT_MOD_SOLVE: 0 = automatic (default: the tiled solve with an
  *     automatic tile and cluster size), 1 = one thread-block cluster per subset
@@ -302,6 +302,11 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     run eagerly.  Graphs refer to the caller's buffers: do not free a buffer
  *     that a cached graph uses while the option is on (turning it off, or a
  *     workspace reallocation, drops the cache).  0 (default) = always eager.
+ *   SDL_OPT_OMP_FORM: FP32 OMP kernels.  0 = automatic (default): form 2.
+ *     1 = one fused kernel per pass, the correlations of 32-signal tiles in
+ *     shared memory.  2 = a correlation GEMM of 128-signal tiles into a
+ *     workspace scratch, then the selection kernel.  Both compute the same
+ *     correlations (FMAs over the signal entries in order).
  *   SDL_OPT_REPLACE: min_use of the atom replacement (sdl_replace_atoms) run
  *     after every MOD update of the training loops.  0 (default) = off, the
  *     paper's reading: unused atoms keep their value.  This option changes the
@@ -314,7 +319,8 @@ typedef enum {
   SDL_OPT_AUTOTUNE = 4,
   SDL_OPT_GRAPH = 5,
   SDL_OPT_SM_BLOCKS = 6,
-  SDL_OPT_REPLACE = 7
+  SDL_OPT_REPLACE = 7,
+  SDL_OPT_OMP_FORM = 8
 } sdl_option;
 sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
 

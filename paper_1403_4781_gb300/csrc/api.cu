@@ -278,6 +278,17 @@ sdl_status check_prec(sdl_ctx *ctx, sdl_precision prec) {
   return set_error(ctx, SDL_EINVAL, "unknown precision");
 }
 
+// FP32 OMP form: the fused kernel (correlation tile in shared memory) or the
+// correlation GEMM + selection kernel pair.  Automatic: the pair, which was
+// the faster of the two at every shape measured (m 64..256, K 256..1024,
+// s 2..16), by 1.2x at m = 64, K = 256, s = 2 and 2.2x at m = 256, K = 512.
+bool omp_split_f32(const sdl_ctx *ctx, int K, int m, int s) {
+  (void)K;
+  (void)m;
+  (void)s;
+  return ctx->opt_omp_form != 1;
+}
+
 // Workspace of the BF16 tensor-core coding pass over n signals in L subsets:
 // BF16 image of D, error word, and the correlation scratch (one chunk of
 // 128-signal tiles).  The FP32 Gram lives in the caller's G.
@@ -288,6 +299,13 @@ size_t tc_a0_bytes(int L, int K, int64_t n) {
 size_t tc_ws_bytes(int L, int K, int m, int64_t n) {
   return round256((size_t)L * round16(K) * round16(m) * 2) + round256(sizeof(int32_t) * 4) +
          round256(tc_a0_bytes(L, K, n));
+}
+
+// Kernels of one two-kernel coding pass: a correlation and a selection launch
+// per chunk of the scratch.
+int split_kernels(const OmpArgs &oa) {
+  const int64_t chunk = omp_tc_chunk_tiles(oa.K, oa.total_tiles);
+  return oa.total_tiles > 0 ? 2 * (int)((oa.total_tiles + chunk - 1) / chunk) : 0;
 }
 
 // One BF16 coding pass: BF16 image of D, FP32 Gram, correlations on the tensor
@@ -307,9 +325,7 @@ cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t
     return launch_gram<float>(static_cast<const float *>(oa.D), oa.m, oa.K, oa.L, G, sm);
   });
   if (e != cudaSuccess) return e;
-  const int64_t chunk = omp_tc_chunk_tiles(oa.K, oa.total_tiles);
-  const int nk = oa.total_tiles > 0 ? 2 * (int)((oa.total_tiles + chunk - 1) / chunk) : 0;
-  return timed(ctx, "omp_tc", nk, [&] { return launch_omp_tc(oa, a0c, sm); });
+  return timed(ctx, "omp_tc", split_kernels(oa), [&] { return launch_omp_tc(oa, a0c, sm); });
 }
 
 // Read back the error word of the tensor-core kernels (synchronises).
@@ -453,14 +469,15 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   int64_t *d_off = nullptr;
   int32_t *d_tiles = nullptr;
   int64_t tiles = 0;
-  const int tile = bf16 ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
+  const bool split = !bf16 && sizeof(T) == 4 && omp_split_f32(ctx, K, m, s);
+  const int tile = bf16 || split ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
   if (tile <= 0) return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
   if ((st = upload_plan(ctx, offsets, L, tile, &d_off, &d_tiles, &tiles)) != SDL_OK)
     return st;
   void *img = bf16 ? ws_alloc(ctx, (size_t)L * round16(K) * round16(m) * 2) : nullptr;
   int32_t *tc_err = bf16 ? static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4)) : nullptr;
-  float *a0c = bf16 ? static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n))) : nullptr;
-  if (bf16 && (!img || !tc_err || !a0c)) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  float *a0c = bf16 || split ? static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n))) : nullptr;
+  if ((split && !a0c) || (bf16 && (!img || !tc_err || !a0c))) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
   if (bf16) SDL_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int32_t), ctx->stream), "err clear");
   T *G = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)L * K * K));
   int32_t *idx = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * s));
@@ -489,6 +506,9 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
       cudaError_t e;
       if (bf16) {
         e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c);
+      } else if (split) {
+        SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
+        e = timed(ctx, "omp_split", split_kernels(oa), [&] { return launch_omp_split_f32(oa, a0c, sm); });
       } else {
         SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
         e = timed(ctx, "omp", 1, [&] { return launch_omp<T>(oa, ctx->num_sms, sm); });
@@ -527,7 +547,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
              sizeof(T), (int)bf16, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
              (void *)d_off, m, K, s, L, (long long)n, (long long)tiles, (long long)ma.total_tiles, eps, iters,
              ctx->opt_mod_solve, ctx->opt_tile, ctx->opt_cluster * 4 + ctx->opt_sm_blocks, ctx->opt_autotune,
-             (int)ctx->tuned.size(), ctx->opt_replace);
+             (int)ctx->tuned.size(), ctx->opt_replace * 4 + ctx->opt_omp_form);
     const std::string key(kb);
     auto hit = ctx->graphs.find(key);
     if (hit != ctx->graphs.end()) {
@@ -651,7 +671,8 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
   int32_t *d_tiles = nullptr;
   int64_t tiles = 0;
   const bool bf16 = prec == SDL_PREC_BF16;
-  const int tile = bf16 ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
+  const bool split = prec == SDL_PREC_F32 && omp_split_f32(ctx, K, m, s);
+  const int tile = bf16 || split ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
   if (tile <= 0) return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
   if ((st = upload_plan(ctx, offsets, L, tile, &d_off, &d_tiles, &tiles)) != SDL_OK)
     return st;
@@ -679,6 +700,13 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
     if (e == cudaErrorInvalidConfiguration)
       return set_error(ctx, SDL_EINVAL, "shape too large for the FP64 OMP kernel's shared memory");
     SDL_CUDA(e, "omp");
+  } else if (split) {
+    float *a0c = static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n)));
+    if (!a0c) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+    SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<float>(static_cast<const float *>(D), m, K, L, static_cast<float *>(G),
+                                ctx->stream); }), "gram");
+    SDL_CUDA(timed(ctx, "omp_split", split_kernels(a), [&] { return launch_omp_split_f32(a, a0c, ctx->stream); }),
+             "omp");
   } else {
     SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<float>(static_cast<const float *>(D), m, K, L, static_cast<float *>(G),
                                 ctx->stream); }), "gram");
@@ -1138,6 +1166,10 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
       if (value < 0 || value > ((int64_t)1 << 30))
         return set_error(ctx, SDL_EINVAL, "SDL_OPT_REPLACE takes 0 to 2^30");
       ctx->opt_replace = (int)value;
+      return SDL_OK;
+    case SDL_OPT_OMP_FORM:
+      if (value < 0 || value > 2) return set_error(ctx, SDL_EINVAL, "SDL_OPT_OMP_FORM takes 0, 1 or 2");
+      ctx->opt_omp_form = (int)value;
       return SDL_OK;
     case SDL_OPT_GRAPH:
       if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_GRAPH takes 0 or 1");

@@ -1,0 +1,146 @@
+// OMP in two kernels for FP32 data (Sec. 1; error-constrained stop of Sec.
+// 3.2.2): an FFMA correlation GEMM writes alpha0 = D^T y of 128-signal tiles
+// to the same global scratch the BF16 path uses, then the shared selection
+// kernel codes the signals from there.  The fused kernel (omp.cu) keeps a
+// 32-signal correlation tile in shared memory, which at large K and m leaves
+// one block per SM for the latency-bound selection loop; here the selection
+// runs with little shared memory at full occupancy and the GEMM runs with
+// full-size register tiles.  The products are FP32 FMAs over the signal
+// entries in order, like the fused kernel's, so no refit is needed.
+#include "omp_common.cuh"
+
+namespace sdl {
+namespace {
+
+using namespace omp_detail;
+
+constexpr int kGThreads = 256;
+constexpr int kGM = 128;      // signals per block (the tile of the plan)
+constexpr int kGN = 128;      // atoms per block
+constexpr int kGK = 16;       // signal entries per stage
+constexpr int kGPitch = 132;  // staged row pitch (floats): 16-byte aligned rows
+
+// alpha0 of one 128-signal tile against 128 atoms.  Thread (ty, tx) of a 16 x
+// 16 grid owns signals 4 ty + {0..3} and 64 + 4 ty + {0..3} and atoms 4 tx +
+// {0..3} and 64 + 4 tx + {0..3}: an 8 x 8 register tile fed by four 16-byte
+// shared-memory reads per entry.  Stages of 16 entries are double-buffered,
+// the next stage's global loads held in registers during the products.
+__global__ void __launch_bounds__(kGThreads) corr_f32_kernel(OmpArgs a, float *a0c, int64_t tile0) {
+  __shared__ __align__(16) float Ys[2][kGK][kGPitch];
+  __shared__ __align__(16) float Ds[2][kGK][kGPitch];
+  const int K = a.K, m = a.m;
+  const int64_t g = tile0 + blockIdx.x;
+  const int t = find_subset(a.tile_start, a.L, g);
+  const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)kGM;
+  const int64_t rows_left = a.offsets[t + 1] - row0;
+  const int nsig = rows_left < kGM ? (int)rows_left : kGM;
+  const int j0 = blockIdx.y * kGN;
+  const float *__restrict__ Y = static_cast<const float *>(a.Y);
+  const float *__restrict__ Dt = static_cast<const float *>(a.D) + (size_t)t * K * m;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const bool vec = (m & 3) == 0;
+
+  // loader: thread tid stages row (tid >> 1) of both operands, entries
+  // 8 (tid & 1) .. 8 (tid & 1) + 7 of the stage
+  const int lrow = tid >> 1, lk = (tid & 1) * 8;
+  const bool yok = lrow < nsig, dok = j0 + lrow < K;
+  const float *ysrc = Y + (size_t)(row0 + (yok ? lrow : 0)) * m;
+  const float *dsrc = Dt + (size_t)(dok ? j0 + lrow : 0) * m;
+  float yr[8], dr[8];
+  auto fetch = [&](int k0) {
+    const int kb = k0 + lk;
+    if (vec && kb + 8 <= m) {
+      const float4 y0 = yok ? *reinterpret_cast<const float4 *>(ysrc + kb) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 y1 = yok ? *reinterpret_cast<const float4 *>(ysrc + kb + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 d0 = dok ? *reinterpret_cast<const float4 *>(dsrc + kb) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 d1 = dok ? *reinterpret_cast<const float4 *>(dsrc + kb + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      yr[0] = y0.x; yr[1] = y0.y; yr[2] = y0.z; yr[3] = y0.w;
+      yr[4] = y1.x; yr[5] = y1.y; yr[6] = y1.z; yr[7] = y1.w;
+      dr[0] = d0.x; dr[1] = d0.y; dr[2] = d0.z; dr[3] = d0.w;
+      dr[4] = d1.x; dr[5] = d1.y; dr[6] = d1.z; dr[7] = d1.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        yr[e] = (yok && kb + e < m) ? ysrc[kb + e] : 0.f;
+        dr[e] = (dok && kb + e < m) ? dsrc[kb + e] : 0.f;
+      }
+    }
+  };
+  auto stage = [&](int buf) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      Ys[buf][lk + e][lrow] = yr[e];
+      Ds[buf][lk + e][lrow] = dr[e];
+    }
+  };
+
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+
+  const int nst = (m + kGK - 1) / kGK;
+  fetch(0);
+  stage(0);
+  __syncthreads();
+  for (int st = 0; st < nst; ++st) {
+    const int buf = st & 1;
+    if (st + 1 < nst) fetch((st + 1) * kGK);
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      const float4 ya = *reinterpret_cast<const float4 *>(&Ys[buf][kk][4 * ty]);
+      const float4 yb = *reinterpret_cast<const float4 *>(&Ys[buf][kk][64 + 4 * ty]);
+      const float4 da = *reinterpret_cast<const float4 *>(&Ds[buf][kk][4 * tx]);
+      const float4 db = *reinterpret_cast<const float4 *>(&Ds[buf][kk][64 + 4 * tx]);
+      const float yv[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+      const float dv[8] = {da.x, da.y, da.z, da.w, db.x, db.y, db.z, db.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(yv[r], dv[c], acc[r][c]);
+    }
+    if (st + 1 < nst) stage(buf ^ 1);
+    __syncthreads();
+  }
+
+  // rows of the tile's scratch block: signal r of the tile at a0 + r * K
+  float *out = a0c + (size_t)(g - tile0) * kGM * K;
+  const bool vstore = (K & 3) == 0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int sig = (r < 4 ? 4 * ty : 64 + 4 * ty) + (r & 3);
+    if (sig >= nsig) continue;
+    float *orow = out + (size_t)sig * K;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = j0 + (h == 0 ? 4 * tx : 64 + 4 * tx);
+      if (vstore && j + 4 <= K) {
+        *reinterpret_cast<float4 *>(orow + j) =
+            make_float4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (j + e < K) orow[j + e] = acc[r][4 * h + e];
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_omp_split_f32(const OmpArgs &a, float *a0c, cudaStream_t st) {
+  if (a.total_tiles <= 0) return cudaSuccess;
+  const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles);
+  for (int64_t g0 = 0; g0 < a.total_tiles; g0 += chunk) {
+    const int64_t nt = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
+    dim3 grid((unsigned)nt, (unsigned)((a.K + kGN - 1) / kGN));
+    corr_f32_kernel<<<grid, kGThreads, 0, st>>>(a, a0c, g0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = launch_omp_select(a, a0c, g0, nt, false, st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace sdl

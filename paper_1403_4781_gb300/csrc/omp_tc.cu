@@ -209,7 +209,7 @@ inline SelLayout sel_layout(int K, int s) {
   return L;
 }
 
-template <int KPL, int MU>
+template <int KPL, int MU, bool EXACT>
 __global__ void __launch_bounds__(kSelThreads) omp_select_kernel(OmpArgs a, SelLayout lay, const float *a0c,
                                                                  int64_t tile0) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -227,18 +227,34 @@ __global__ void __launch_bounds__(kSelThreads) omp_select_kernel(OmpArgs a, SelL
   const float *a0 = a0c + ((size_t)(g - tile0) * 128 + quarter * 32) * K;
   float *Ls = reinterpret_cast<float *>(smem + lay.ls) + (size_t)warp * s * lay.lp;
   float *gc = lay.gcache ? reinterpret_cast<float *>(smem + lay.gc) + (size_t)warp * s * K : nullptr;
-  code_warp_signals<float, KPL, MU, true>(a, a0, static_cast<const float *>(a.Y) + (size_t)row0 * m, m, warp * 4, 4,
+  code_warp_signals<float, KPL, MU, EXACT>(a, a0, static_cast<const float *>(a.Y) + (size_t)row0 * m, m, warp * 4, 4,
                                           nsig, row0, Dt, Gt, Ls, gc, lay.lp, lay.gcache);
 }
 
-template <int KPL, int MU>
+template <int KPL, int MU, bool EXACT>
 cudaError_t launch_select(const OmpArgs &a, const SelLayout &lay, const float *a0c, int64_t tile0, int64_t ntile,
                           cudaStream_t st) {
-  auto kern = omp_select_kernel<KPL, MU>;
+  auto kern = omp_select_kernel<KPL, MU, EXACT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)(ntile * 4), kSelThreads, lay.total, st>>>(a, lay, a0c, tile0);
   return cudaGetLastError();
+}
+
+template <bool EXACT>
+cudaError_t select_dispatch(const OmpArgs &a, const float *a0c, int64_t g0, int64_t nt, cudaStream_t st) {
+  const SelLayout sl = sel_layout(a.K, a.s);
+  const int kpl = (a.K + 31) / 32;
+  if (a.m <= 64) {
+    return kpl <= 4 ? launch_select<4, 2, EXACT>(a, sl, a0c, g0, nt, st)
+         : kpl <= 8 ? launch_select<8, 2, EXACT>(a, sl, a0c, g0, nt, st)
+         : kpl <= 16 ? launch_select<16, 2, EXACT>(a, sl, a0c, g0, nt, st)
+                     : launch_select<32, 2, EXACT>(a, sl, a0c, g0, nt, st);
+  }
+  return kpl <= 4 ? launch_select<4, 8, EXACT>(a, sl, a0c, g0, nt, st)
+       : kpl <= 8 ? launch_select<8, 8, EXACT>(a, sl, a0c, g0, nt, st)
+       : kpl <= 16 ? launch_select<16, 8, EXACT>(a, sl, a0c, g0, nt, st)
+                   : launch_select<32, 8, EXACT>(a, sl, a0c, g0, nt, st);
 }
 
 }  // namespace
@@ -251,6 +267,11 @@ cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, cu
   if (blocks < 1) blocks = 1;
   bf16_image_kernel<<<blocks, 256, 0, st>>>(D, K, m, Kp, mp, L, static_cast<unsigned char *>(img));
   return cudaGetLastError();
+}
+
+cudaError_t launch_omp_select(const OmpArgs &a, const float *a0c, int64_t tile0, int64_t ntile, bool exact,
+                              cudaStream_t st) {
+  return exact ? select_dispatch<true>(a, a0c, tile0, ntile, st) : select_dispatch<false>(a, a0c, tile0, ntile, st);
 }
 
 int omp_tc_tile_signals(int K, int m, int s) {
@@ -275,23 +296,12 @@ cudaError_t launch_omp_tc(const OmpArgs &a, float *a0c, cudaStream_t st) {
   if (csm > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
   if (e != cudaSuccess) return e;
-  const SelLayout sl = sel_layout(a.K, a.s);
-  const int kpl = (a.K + 31) / 32;
   const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles);
   for (int64_t g0 = 0; g0 < a.total_tiles; g0 += chunk) {
     const int64_t nt = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
     corr_tc_kernel<<<(unsigned)nt, kCorrThreads, csm, st>>>(a, cl, a0c, g0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (a.m <= 64) {
-      e = kpl <= 4 ? launch_select<4, 2>(a, sl, a0c, g0, nt, st)
-        : kpl <= 8 ? launch_select<8, 2>(a, sl, a0c, g0, nt, st)
-        : kpl <= 16 ? launch_select<16, 2>(a, sl, a0c, g0, nt, st) : launch_select<32, 2>(a, sl, a0c, g0, nt, st);
-    } else {
-      e = kpl <= 4 ? launch_select<4, 8>(a, sl, a0c, g0, nt, st)
-        : kpl <= 8 ? launch_select<8, 8>(a, sl, a0c, g0, nt, st)
-        : kpl <= 16 ? launch_select<16, 8>(a, sl, a0c, g0, nt, st) : launch_select<32, 8>(a, sl, a0c, g0, nt, st);
-    }
-    if (e != cudaSuccess) return e;
+    if ((e = select_dispatch<true>(a, a0c, g0, nt, st)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

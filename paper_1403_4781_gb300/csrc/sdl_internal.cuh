@@ -76,6 +76,7 @@ struct sdl_ctx {
   std::map<std::string, TunedSolve> tuned;   // shape key -> chosen tile, cluster size, blocks-per-SM cap
   int opt_graph = 0;             // replay training loops as captured CUDA graphs
   int opt_replace = 0;           // atom replacement after every MOD update: min_use (0 = off)
+  int opt_omp_form = 0;          // FP32 OMP: 0 automatic, 1 fused kernel, 2 correlation GEMM + selection
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
@@ -137,6 +138,14 @@ cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, cu
 // loop from there.
 cudaError_t launch_omp_tc(const OmpArgs &a, float *a0c, cudaStream_t st);
 int omp_tc_tile_signals(int K, int m, int s);
+// The selection kernel over 128-signal tiles tile0 .. tile0+ntile-1 whose
+// alpha0 rows are in a0c (FP32 data).  exact: alpha0 came from BF16 products,
+// so the coefficients are refitted from D_S^T y.
+cudaError_t launch_omp_select(const OmpArgs &a, const float *a0c, int64_t tile0, int64_t ntile, bool exact,
+                              cudaStream_t st);
+// FP32 OMP in two kernels: FFMA correlation GEMM of 128-signal tiles into a0c,
+// then the selection kernel (same plan and scratch as the BF16 path).
+cudaError_t launch_omp_split_f32(const OmpArgs &a, float *a0c, cudaStream_t st);
 int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles);
 
 struct ModArgs {
