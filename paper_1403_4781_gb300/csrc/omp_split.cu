@@ -25,16 +25,18 @@ constexpr int kGPitch = 132;  // staged row pitch (floats): 16-byte aligned rows
 // {0..3} and 64 + 4 tx + {0..3}: an 8 x 8 register tile fed by four 16-byte
 // shared-memory reads per entry.  Stages of 16 entries are double-buffered,
 // the next stage's global loads held in registers during the products.
-__global__ void __launch_bounds__(kGThreads) corr_f32_kernel(OmpArgs a, float *a0c, int64_t tile0) {
+__global__ void __launch_bounds__(kGThreads) corr_f32_kernel(OmpArgs a, float *a0c, int64_t tile0, int nb) {
   __shared__ __align__(16) float Ys[2][kGK][kGPitch];
   __shared__ __align__(16) float Ds[2][kGK][kGPitch];
   const int K = a.K, m = a.m;
-  const int64_t g = tile0 + blockIdx.x;
+  // consecutive blocks share a tile (its nb atom blocks), so the tile's signals
+  // come from DRAM once and from L2 for the other atom blocks
+  const int64_t g = tile0 + blockIdx.x / nb;
   const int t = find_subset(a.tile_start, a.L, g);
   const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)kGM;
   const int64_t rows_left = a.offsets[t + 1] - row0;
   const int nsig = rows_left < kGM ? (int)rows_left : kGM;
-  const int j0 = blockIdx.y * kGN;
+  const int j0 = (int)(blockIdx.x % nb) * kGN;
   const float *__restrict__ Y = static_cast<const float *>(a.Y);
   const float *__restrict__ Dt = static_cast<const float *>(a.D) + (size_t)t * K * m;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -134,8 +136,8 @@ cudaError_t launch_omp_split_f32(const OmpArgs &a, float *a0c, cudaStream_t st) 
   const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles);
   for (int64_t g0 = 0; g0 < a.total_tiles; g0 += chunk) {
     const int64_t nt = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
-    dim3 grid((unsigned)nt, (unsigned)((a.K + kGN - 1) / kGN));
-    corr_f32_kernel<<<grid, kGThreads, 0, st>>>(a, a0c, g0);
+    const int nb = (a.K + kGN - 1) / kGN;
+    corr_f32_kernel<<<(unsigned)(nt * nb), kGThreads, 0, st>>>(a, a0c, g0, nb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if ((e = launch_omp_select(a, a0c, g0, nt, false, st)) != cudaSuccess) return e;
