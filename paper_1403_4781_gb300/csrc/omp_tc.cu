@@ -51,12 +51,14 @@ __global__ void bf16_image_kernel(const float *__restrict__ D, int K, int m, int
 }
 
 // ---- correlations: alpha0 = Y D^T of 128-signal tiles into global memory ----
-// One block per tile of 128 signals (the MMA's M), 4 warps.  The signal tile is
-// converted to a BF16 K-major image once; dictionary tiles of 128 atoms stream
-// in by bulk copies into two buffers, and their products go to two TMEM
-// accumulators, so the MMA of tile nt+1 runs while tile nt is read out.  Row r
-// of the tile's alpha0 block (atoms in order) is written to a0 + r * K.
-constexpr int kCorrThreads = 128;
+// One block per tile of 128 signals (the MMA's M), 8 warps.  The signal tile is
+// converted to a BF16 K-major image once (16-byte loads, eight warps so many
+// loads are in flight); dictionary tiles of 128 atoms stream in by bulk copies
+// into two buffers, and their products go to two TMEM accumulators, so the MMA
+// of tile nt+1 runs while tile nt is read out.  Warps w and w + 4 read the TMEM
+// lanes of rows 32 (w mod 4) .. + 31, each half of the columns.  Row r of the
+// tile's alpha0 block (atoms in order) is written to a0 + r * K.
+constexpr int kCorrThreads = 256;
 constexpr int kCorrNT = 128;
 
 struct CorrLayout {
@@ -89,43 +91,64 @@ __global__ void __launch_bounds__(kCorrThreads) corr_tc_kernel(OmpArgs a, CorrLa
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + lay.bar);   // [0,1] loads, [2,3] MMA commits
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 4);
   int *fail = reinterpret_cast<int *>(bar + 5);
-  const size_t btile = (size_t)kCorrNT * mp * 2;
-  const int ntiles = (K + kCorrNT - 1) / kCorrNT;
-  auto tile_bytes = [&](int nt) { return (uint32_t)min(kCorrNT, Kp - nt * kCorrNT) * (uint32_t)mp * 2u; };
+  constexpr int NT = kCorrNT;
+  const size_t btile = (size_t)NT * mp * 2;
+  const int ntiles = (K + NT - 1) / NT;
+  auto tile_bytes = [&](int nt) { return (uint32_t)min(NT, Kp - nt * NT) * (uint32_t)mp * 2u; };
 
-  if (warp == 0) tc::tmem_alloc(tslot, 2 * kCorrNT);
+  if (warp == 0) tc::tmem_alloc(tslot, 2 * NT);
   if (tid == 0) {
     for (int q = 0; q < 4; ++q) tc::mbar_init(&bar[q], 1);
     tc::mbar_fence_init();
     *fail = 0;
     for (int nt = 0; nt < 2 && nt < ntiles; ++nt) {
       tc::mbar_expect_tx(&bar[nt], tile_bytes(nt));
-      tc::bulk_g2s(Bim + nt * btile, sub + (size_t)nt * kCorrNT * mp * 2, tile_bytes(nt), &bar[nt]);
+      tc::bulk_g2s(Bim + nt * btile, sub + (size_t)nt * NT * mp * 2, tile_bytes(nt), &bar[nt]);
     }
   }
-  // signal tile -> BF16 A image (rows beyond the tile are zero)
+  // signal tile -> BF16 A image (rows beyond the tile are zero); item q is
+  // entries 8 kc .. 8 kc + 7 of row r
   const int kc8 = mp >> 3;
-  for (int q = tid; q < 128 * kc8; q += kCorrThreads) {
-    const int r = q / kc8, kc = q - r * kc8;
-    const float *yr = Y + (size_t)(row0 + r) * m;
-    uint32_t packed[4];
+  const bool vec = (m & 3) == 0;   // 16-byte aligned rows
+  constexpr int kU = 4;            // items whose loads are in flight together
+  for (int q0 = tid; q0 < 128 * kc8; q0 += kU * kCorrThreads) {
+    float f[kU][8];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int k0 = kc * 8 + 2 * e;
-      const float lo = (r < nsig && k0 < m) ? yr[k0] : 0.f;
-      const float hi = (r < nsig && k0 + 1 < m) ? yr[k0 + 1] : 0.f;
-      __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
-      packed[e] = *reinterpret_cast<uint32_t *>(&b2);
+    for (int u = 0; u < kU; ++u) {
+      const int q = q0 + u * kCorrThreads;
+      const int r = q / kc8, k0 = (q - r * kc8) * 8;
+      const float *yr = Y + (size_t)(row0 + r) * m + k0;
+      if (q < 128 * kc8 && r < nsig && vec && k0 + 8 <= m) {
+        const float4 u0 = *reinterpret_cast<const float4 *>(yr);
+        const float4 u1 = *reinterpret_cast<const float4 *>(yr + 4);
+        f[u][0] = u0.x; f[u][1] = u0.y; f[u][2] = u0.z; f[u][3] = u0.w;
+        f[u][4] = u1.x; f[u][5] = u1.y; f[u][6] = u1.z; f[u][7] = u1.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[u][e] = (q < 128 * kc8 && r < nsig && k0 + e < m) ? yr[e] : 0.f;
+      }
     }
-    *reinterpret_cast<uint4 *>(Aim + tc::image_offset(r, kc * 8, mp)) =
-        make_uint4(packed[0], packed[1], packed[2], packed[3]);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int q = q0 + u * kCorrThreads;
+      if (q >= 128 * kc8) break;
+      const int r = q / kc8, kc = q - r * kc8;
+      uint32_t packed[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(f[u][2 * e], f[u][2 * e + 1]);
+        packed[e] = *reinterpret_cast<uint32_t *>(&b2);
+      }
+      *reinterpret_cast<uint4 *>(Aim + tc::image_offset(r, kc * 8, mp)) =
+          make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    }
   }
   tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = *tslot;
-  const uint32_t idesc = tc::idesc_bf16(128, kCorrNT);
+  const uint32_t idesc = tc::idesc_bf16(128, NT);
   const uint32_t sbo = (uint32_t)kc8 * 128;
   // tile nt's product into TMEM columns (nt & 1) * 128 (thread 0)
   auto issue = [&](int nt) {
@@ -134,12 +157,13 @@ __global__ void __launch_bounds__(kCorrThreads) corr_tc_kernel(OmpArgs a, CorrLa
     tc::fence_after();
     const uint32_t bsm = tc::smem_u32(Bim + b * btile);
     for (int ks = 0; ks < (mp >> 4); ++ks)
-      tc::mma_bf16(tbase + (uint32_t)(b * kCorrNT), tc::smem_desc(tc::smem_u32(Aim) + ks * 256, 128, sbo),
+      tc::mma_bf16(tbase + (uint32_t)(b * NT), tc::smem_desc(tc::smem_u32(Aim) + ks * 256, 128, sbo),
                    tc::smem_desc(bsm + ks * 256, 128, sbo), idesc, ks > 0);
     tc::mma_commit(&bar[2 + b]);
   };
   if (tid == 0) issue(0);
-  const int row = 32 * warp + lane;
+  const int quarter = warp & 3, half = warp >> 2;   // TMEM lanes 32 quarter .. + 31
+  const int row = 32 * quarter + lane;
   float *arow = a0c + ((size_t)(g - tile0) * 128 + row) * K;
   int nt = 0;
   for (; nt < ntiles; ++nt) {
@@ -149,10 +173,10 @@ __global__ void __launch_bounds__(kCorrThreads) corr_tc_kernel(OmpArgs a, CorrLa
     __syncthreads();
     if (*fail) break;
     tc::fence_after();
-    for (int c0 = 0; c0 < kCorrNT; c0 += 32) {
+    for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += 32) {
       float v[32];
-      tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * kCorrNT + c0), v);
-      const int col0 = nt * kCorrNT + c0;
+      tc::tmem_ld32(tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * NT + c0), v);
+      const int col0 = nt * NT + c0;
       if (row < nsig) {
         if (col0 + 32 <= K && (K & 3) == 0) {
 #pragma unroll
@@ -169,7 +193,7 @@ __global__ void __launch_bounds__(kCorrThreads) corr_tc_kernel(OmpArgs a, CorrLa
     __syncthreads();   // buffer b (TMEM columns and B image) is free again
     if (tid == 0 && nt + 2 < ntiles) {
       tc::mbar_expect_tx(&bar[b], tile_bytes(nt + 2));
-      tc::bulk_g2s(Bim + b * btile, sub + (size_t)(nt + 2) * kCorrNT * mp * 2, tile_bytes(nt + 2), &bar[b]);
+      tc::bulk_g2s(Bim + b * btile, sub + (size_t)(nt + 2) * NT * mp * 2, tile_bytes(nt + 2), &bar[b]);
     }
   }
   if (*fail) {
@@ -182,7 +206,7 @@ __global__ void __launch_bounds__(kCorrThreads) corr_tc_kernel(OmpArgs a, CorrLa
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, 2 * kCorrNT);
+  if (warp == 0) tc::tmem_dealloc(tbase, 2 * NT);
 }
 
 // ---- selection: the Batch-OMP loop and exact refit from alpha0 in global memory
