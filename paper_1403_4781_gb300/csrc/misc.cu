@@ -71,7 +71,32 @@ __global__ void pick_init_kernel(const T *__restrict__ Yt, int m, const int32_t 
     D[(size_t)j * m + r] = nrm > 0.0 ? (T)((double)src[r] / nrm) : T(0);
 }
 
-// Per-subset RMSE of a coding pass and Frobenius norm of its codes, FP64 sums.
+// Compensated FP32 sum (a hi + lo pair): each term, or each exact product
+// x y = p + e (one FMA gives e), is added with TwoSum and the rounding error
+// carried in lo, so about 48 significant bits survive.  Accumulating FP32
+// values this way runs on the FP32 pipe; FP64 additions of every term would
+// load one SM's narrow FP64 pipe when a single subset has many codes.
+struct CSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float p, float e) {
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
+    const float l = lo + (e + err);
+    hi = s + l;
+    lo = l - (hi - s);
+  }
+  __device__ __forceinline__ void add(float x) { add(x, 0.f); }
+  __device__ __forceinline__ void add_sq(float x) {
+    const float p = x * x;
+    add(p, fmaf(x, x, -p));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Per-subset sums: rmse[t] = sqrt(sum resid2 / (m n_t)), xfro[t] = ||val||_F.
+// One block per subset.  FP32 codes: per-thread compensated FP32 sums, added
+// in FP64 across threads; FP64 codes: FP64 sums.
 template <typename T>
 __global__ void __launch_bounds__(1024) subset_stats_kernel(const T *__restrict__ resid2,
                                                            const T *__restrict__ val,
@@ -82,12 +107,21 @@ __global__ void __launch_bounds__(1024) subset_stats_kernel(const T *__restrict_
   const int t = blockIdx.x;
   const int64_t a = offsets[t], b = offsets[t + 1];
   double r2 = 0.0, v2 = 0.0;
-  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) r2 += (double)resid2[i];
-  if (xfro_out)
-    for (int64_t e = a * s + threadIdx.x; e < b * s; e += blockDim.x) {
-      const double v = (double)val[e];
-      v2 = fma(v, v, v2);
-    }
+  if constexpr (sizeof(T) == 4) {
+    CSum cr, cv;
+    for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) cr.add((float)resid2[i]);
+    if (xfro_out)
+      for (int64_t e = a * s + threadIdx.x; e < b * s; e += blockDim.x) cv.add_sq((float)val[e]);
+    r2 = cr.value();
+    v2 = cv.value();
+  } else {
+    for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) r2 += (double)resid2[i];
+    if (xfro_out)
+      for (int64_t e = a * s + threadIdx.x; e < b * s; e += blockDim.x) {
+        const double v = (double)val[e];
+        v2 = fma(v, v, v2);
+      }
+  }
   r2 = warp_sum(r2);
   v2 = warp_sum(v2);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;

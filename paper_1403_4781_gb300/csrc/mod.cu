@@ -35,15 +35,26 @@ __device__ __forceinline__ int find_subset_tiles(const int32_t *__restrict__ til
 }
 
 // ---- 1 + 2: usage counts, scan, fill --------------------------------------
+// Counts of one tile of signals are gathered in a shared-memory histogram first,
+// so the global counters take one atomic per (tile, atom) instead of one per
+// code entry (the merge's single subset would otherwise serialise many atomics
+// on each of its K counters).
 __global__ void mod_count_kernel(ModArgs a) {
+  __shared__ int hist[1024];   // K <= 1024
   const int64_t g = blockIdx.x;
   const int t = find_subset_tiles(a.tile_start, a.L, g);
+  const int K = a.K;
+  for (int j = threadIdx.x; j < K; j += kModTile) hist[j] = 0;
+  __syncthreads();
   const int64_t i = a.offsets[t] + (g - a.tile_start[t]) * kModTile + threadIdx.x;
-  if (i >= a.offsets[t + 1]) return;
-  for (int k = 0; k < a.s; ++k) {
-    const int j = a.idx[(size_t)i * a.s + k];
-    if (j >= 0 && j < a.K) atomicAdd(&a.usage[(size_t)t * a.K + j], 1);
-  }
+  if (i < a.offsets[t + 1])
+    for (int k = 0; k < a.s; ++k) {
+      const int j = a.idx[(size_t)i * a.s + k];
+      if (j >= 0 && j < K) atomicAdd_block(&hist[j], 1);
+    }
+  __syncthreads();
+  for (int j = threadIdx.x; j < K; j += kModTile)
+    if (hist[j] > 0) atomicAdd(&a.usage[(size_t)t * K + j], hist[j]);
 }
 
 // Exclusive scan of usage[t][0..K) -> ptr[t][0..K]; cursor = ptr.  K <= 1024.
@@ -228,12 +239,28 @@ __global__ void __launch_bounds__(256) mod_accum_ds_kernel(ModArgs a) {
     const bool ok = e < e_hi;
     const int i = ok ? a.lsig[base + e] : 0;
     const int j = ok ? a.latom[base + e] : -1;
-    const float x = ok ? vt[(size_t)i * s + a.lslot[base + e]] : 0.f;
+    const int slot = ok ? a.lslot[base + e] : 0;
+    const float x = ok ? vt[(size_t)i * s + slot] : 0.f;
     if (ok)
       for (int k = 0; k < s; ++k) {
         const int j2 = it[(size_t)i * s + k];
-        if (j2 >= 0 && j2 <= j) atomicAdd(&At[(size_t)j * K + j2], (double)x * (double)vt[(size_t)i * s + k]);
+        if (j2 >= 0 && (j2 < j || (j2 == j && k != slot)))
+          atomicAdd(&At[(size_t)j * K + j2], (double)x * (double)vt[(size_t)i * s + k]);
       }
+    // the diagonal term x^2 of every entry, summed over the lanes of a run of
+    // equal atoms (contiguous: the entries are atom-major) and added once, so
+    // the diagonal counters do not serialise one atomic per entry
+    {
+      double d = (double)x * (double)x;
+      const unsigned grp = __match_any_sync(0xffffffffu, j);
+      const int lo = __ffs(grp) - 1, hi = 31 - __clz(grp);
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, d, off);
+        if (lane + off <= hi) d += o;
+      }
+      if (ok && lane == lo) atomicAdd(&At[(size_t)j * K + j], d);
+    }
     const int nq = e_hi - e0 < 32 ? (int)(e_hi - e0) : 32;
     for (int q = 0; q < nq; ++q) {
       const int jq = __shfl_sync(0xffffffffu, j, q);
