@@ -1,12 +1,14 @@
 // OMP in two kernels for FP32 data (Sec. 1; error-constrained stop of Sec.
-// 3.2.2): an FFMA correlation GEMM writes alpha0 = D^T y of 128-signal tiles
-// to the same global scratch the BF16 path uses, then the shared selection
-// kernel codes the signals from there.  The fused kernel (omp.cu) keeps a
-// 32-signal correlation tile in shared memory, which at large K and m leaves
-// one block per SM for the latency-bound selection loop; here the selection
-// runs with little shared memory at full occupancy and the GEMM runs with
-// full-size register tiles.  The products are FP32 FMAs over the signal
-// entries in order, like the fused kernel's, so no refit is needed.
+// 3.2.2), the default FP32 form: an FFMA correlation GEMM writes alpha0 = D^T y
+// of 128-signal tiles to the same global scratch the BF16 path uses, then the
+// shared selection kernel codes the signals from there.  The fused kernel
+// (omp.cu) keeps a 32-signal correlation tile in shared memory, which leaves
+// one to three blocks per SM for the latency-bound selection loop; here the
+// selection runs with little shared memory at full occupancy and the GEMM runs
+// with full-size register tiles, at the cost of writing and reading alpha0
+// (4K bytes per signal each way).  The products are FP32 FMAs over the signal
+// entries in order, like the fused kernel's, so the codes are the same and no
+// refit is needed.
 #include "omp_common.cuh"
 
 namespace sdl {
