@@ -249,16 +249,19 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
         const T bl = support_dots(Dt, m, mu, k, Sl, yl, lane);
         xl = upper_solve(Ls, lp, k, lower_solve(Ls, lp, k, bl, lane), lane);
       }
-      // one correction step x += L^{-T} L^{-1} D_S^T (y - D_S x), then ||y - D_S x||^2
+      // one correction step x += G_SS^{-1} c, c = D_S^T r, r = y - D_S x.  The
+      // corrected residual's energy follows without another pass over D_S:
+      // ||r - D_S G_SS^{-1} c||^2 = ||r||^2 - c^T G_SS^{-1} c = ||r||^2 - ||L^{-1} c||^2
       T rloc[M32];
-      support_residual(Dt, ysig, m, mu, k, Sl, xl, rloc, lane);
-      const T cl = support_dots(Dt, m, mu, k, Sl, rloc, lane);
-      xl += upper_solve(Ls, lp, k, lower_solve(Ls, lp, k, cl, lane), lane);
       support_residual(Dt, ysig, m, mu, k, Sl, xl, rloc, lane);
       T racc = T(0);
 #pragma unroll
       for (int u = 0; u < M32; ++u) racc = fma(rloc[u], rloc[u], racc);
-      res2 = warp_sum(racc);
+      const T cl = support_dots(Dt, m, mu, k, Sl, rloc, lane);
+      const T wl = lower_solve(Ls, lp, k, cl, lane);
+      xl += upper_solve(Ls, lp, k, wl, lane);
+      const T r2 = warp_sum(racc) - warp_sum(lane < k ? wl * wl : T(0));
+      res2 = r2 > T(0) ? r2 : T(0);
     }
 
     // ---- write the ELL row (lane p holds entry p)
