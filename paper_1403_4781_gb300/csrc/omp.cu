@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (KPL <= 16 ? 3 : 2)
 
   T *Ls = reinterpret_cast<T *>(smem + lay.ls) + (size_t)warp * a.s * lay.lp;
   code_warp_signals<T, KPL, MU, false>(a, a0, yt, yp, warp * SPW, SPW, nsig, row0, Dt, Gt, Ls,
-                                       uni + (size_t)warp * a.s * K, lay.lp, lay.gcache);
+                                       uni + (size_t)warp * a.s * K, lay.lp, lay.gcache ? a.s : 0);
 }
 
 }  // namespace

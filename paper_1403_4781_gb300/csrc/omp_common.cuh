@@ -128,7 +128,9 @@ __device__ __forceinline__ void support_residual(const T *Dt, const T *ysig, int
 //   ybase  signal 0 of the tile, row stride ypitch (shared or global memory)
 //   MU     ceil(m / 32): signal entries per lane
 //   Gt     the Gram matrix of D in T (FP32 or FP64 products)
-//   Ls     per-warp [s][lp] factor scratch;  gc per-warp [s][K] G-column cache
+//   Ls     per-warp [s][lp] factor scratch;  gc per-warp [gcn][K] cache of the
+//          first gcn G columns of the support (the earliest picks are re-read by
+//          the most later updates)
 //   EXACT  alpha0 came from reduced-precision products: the refit takes D_S^T y
 //          in T instead of alpha0 on the support
 // Per step the correlations are kept as a running vector alpha = alpha0 -
@@ -139,7 +141,7 @@ __device__ __forceinline__ void support_residual(const T *Dt, const T *ysig, int
 template <typename T, int KPL, int MU, bool EXACT>
 __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase, int ypitch, int sig_begin,
                                   int sig_count, int nsig, int64_t row0, const T *__restrict__ Dt,
-                                  const T *__restrict__ Gt, T *Ls, T *gc, int lp, bool gcache) {
+                                  const T *__restrict__ Gt, T *Ls, T *gc, int lp, int gcn) {
   constexpr int M32 = MU;
   const int K = a.K, m = a.m, s = a.s;
   const int lane = threadIdx.x & 31;
@@ -188,7 +190,7 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
       // column `best` of G (= row, G symmetric); the cached copy serves the
       // updates of later steps only, so the last step reads it from L2
       const T *gcol = Gt + (size_t)best * K;
-      if (gcache && k + 1 < s) {
+      if (k < gcn && k + 1 < s) {
         T *dst = gc + (size_t)k * K;
         for (int j = lane; j < K; j += 32) dst[j] = gcol[j];
         __syncwarp();
@@ -217,7 +219,7 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
         const T dl = xn - xl;
         for (int p = 0; p < k; ++p) {
           const T dp = __shfl_sync(0xffffffffu, dl, p);
-          const T *gp = gcache ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
+          const T *gp = p < gcn ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
           if (full) {
 #pragma unroll
             for (int c = 0; c < KPL; ++c) av[c] = fma(-gp[lane + 32 * c], dp, av[c]);

@@ -217,18 +217,28 @@ constexpr int kSelThreads = 256;
 
 struct SelLayout {
   int lp;
-  bool gcache;
+  int gcn;   // G columns of the support cached per warp
   size_t ls, gc, total;
 };
 
-inline SelLayout sel_layout(int K, int s) {
+// Per-warp factor scratch, then as many of the support's G columns per warp as
+// fit the shared memory one block gets at the occupancy its registers allow
+// (the first picks' columns: column p is re-read by the s - 1 - p later
+// updates, so caching the first few saves most of the L2 reads).
+inline SelLayout sel_layout(int K, int s, int regs) {
+  const int rr = (regs + 7) & ~7;
+  int blocks = 65536 / (kSelThreads * (rr > 0 ? rr : 8));
+  blocks = blocks < 1 ? 1 : (blocks > 8 ? 8 : blocks);
+  const size_t budget = (size_t)228 * 1024 / blocks - 1024;
   SelLayout L{};
   L.lp = odd_pitch(s);
-  const size_t gcol = sizeof(float) * (size_t)8 * s * K;
-  L.gcache = gcol <= 48 * 1024;
+  const size_t ls = align16(sizeof(float) * (size_t)8 * s * L.lp);
+  const size_t col = sizeof(float) * (size_t)8 * K;   // one column for every warp
+  const int fit = budget > ls ? (int)((budget - ls) / col) : 0;
+  L.gcn = fit < s - 1 ? fit : (s > 1 ? s - 1 : 0);
   size_t off = 0;
-  L.ls = off; off += align16(sizeof(float) * (size_t)8 * s * L.lp);
-  L.gc = off; off += L.gcache ? align16(gcol) : 0;
+  L.ls = off; off += ls;
+  L.gc = off; off += align16(col * L.gcn);
   L.total = off;
   return L;
 }
@@ -250,16 +260,19 @@ __global__ void __launch_bounds__(kSelThreads) omp_select_kernel(OmpArgs a, SelL
   const float *__restrict__ Gt = static_cast<const float *>(a.G) + (size_t)t * K * K;
   const float *a0 = a0c + ((size_t)(g - tile0) * 128 + quarter * 32) * K;
   float *Ls = reinterpret_cast<float *>(smem + lay.ls) + (size_t)warp * s * lay.lp;
-  float *gc = lay.gcache ? reinterpret_cast<float *>(smem + lay.gc) + (size_t)warp * s * K : nullptr;
+  float *gc = lay.gcn > 0 ? reinterpret_cast<float *>(smem + lay.gc) + (size_t)warp * lay.gcn * K : nullptr;
   code_warp_signals<float, KPL, MU, EXACT>(a, a0, static_cast<const float *>(a.Y) + (size_t)row0 * m, m, warp * 4, 4,
-                                          nsig, row0, Dt, Gt, Ls, gc, lay.lp, lay.gcache);
+                                          nsig, row0, Dt, Gt, Ls, gc, lay.lp, lay.gcn);
 }
 
 template <int KPL, int MU, bool EXACT>
-cudaError_t launch_select(const OmpArgs &a, const SelLayout &lay, const float *a0c, int64_t tile0, int64_t ntile,
-                          cudaStream_t st) {
+cudaError_t launch_select(const OmpArgs &a, const float *a0c, int64_t tile0, int64_t ntile, cudaStream_t st) {
   auto kern = omp_select_kernel<KPL, MU, EXACT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  const SelLayout lay = sel_layout(a.K, a.s, fa.numRegs);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)(ntile * 4), kSelThreads, lay.total, st>>>(a, lay, a0c, tile0);
   return cudaGetLastError();
@@ -267,18 +280,17 @@ cudaError_t launch_select(const OmpArgs &a, const SelLayout &lay, const float *a
 
 template <bool EXACT>
 cudaError_t select_dispatch(const OmpArgs &a, const float *a0c, int64_t g0, int64_t nt, cudaStream_t st) {
-  const SelLayout sl = sel_layout(a.K, a.s);
   const int kpl = (a.K + 31) / 32;
   if (a.m <= 64) {
-    return kpl <= 4 ? launch_select<4, 2, EXACT>(a, sl, a0c, g0, nt, st)
-         : kpl <= 8 ? launch_select<8, 2, EXACT>(a, sl, a0c, g0, nt, st)
-         : kpl <= 16 ? launch_select<16, 2, EXACT>(a, sl, a0c, g0, nt, st)
-                     : launch_select<32, 2, EXACT>(a, sl, a0c, g0, nt, st);
+    return kpl <= 4 ? launch_select<4, 2, EXACT>(a, a0c, g0, nt, st)
+         : kpl <= 8 ? launch_select<8, 2, EXACT>(a, a0c, g0, nt, st)
+         : kpl <= 16 ? launch_select<16, 2, EXACT>(a, a0c, g0, nt, st)
+                     : launch_select<32, 2, EXACT>(a, a0c, g0, nt, st);
   }
-  return kpl <= 4 ? launch_select<4, 8, EXACT>(a, sl, a0c, g0, nt, st)
-       : kpl <= 8 ? launch_select<8, 8, EXACT>(a, sl, a0c, g0, nt, st)
-       : kpl <= 16 ? launch_select<16, 8, EXACT>(a, sl, a0c, g0, nt, st)
-                   : launch_select<32, 8, EXACT>(a, sl, a0c, g0, nt, st);
+  return kpl <= 4 ? launch_select<4, 8, EXACT>(a, a0c, g0, nt, st)
+       : kpl <= 8 ? launch_select<8, 8, EXACT>(a, a0c, g0, nt, st)
+       : kpl <= 16 ? launch_select<16, 8, EXACT>(a, a0c, g0, nt, st)
+                   : launch_select<32, 8, EXACT>(a, a0c, g0, nt, st);
 }
 
 }  // namespace
