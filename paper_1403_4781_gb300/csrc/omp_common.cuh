@@ -121,6 +121,52 @@ __device__ __forceinline__ void support_residual(const T *Dt, const T *ysig, int
   }
 }
 
+// Atom of entry c of a lane's KPL correlations: groups of four consecutive
+// atoms, lane l holding atoms 4 l .. 4 l + 3 of every 128 (so a warp's 16-byte
+// loads of one group cover 512 contiguous bytes).
+__device__ __forceinline__ int lane_atom(int lane, int c) { return 128 * (c >> 2) + 4 * lane + (c & 3); }
+
+// This lane's entries of a row (bit c of `valid`: entry c exists; missing
+// entries read as zero); p points at the row's atom 4 lane.  vec: the rows are
+// 16-byte aligned (K a multiple of 4), so each group loads as one vector.
+template <int KPL>
+__device__ __forceinline__ void span_load(const float *p, float (&v)[KPL], uint32_t valid, bool vec) {
+#pragma unroll
+  for (int c = 0; c < KPL; c += 4) {
+    const float *q = p + 128 * (c >> 2);
+    if (vec) {
+      if ((valid >> c) & 1u) {
+        const float4 t = *reinterpret_cast<const float4 *>(q);
+        v[c] = t.x; v[c + 1] = t.y; v[c + 2] = t.z; v[c + 3] = t.w;
+      } else {
+        v[c] = v[c + 1] = v[c + 2] = v[c + 3] = 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[c + e] = (valid >> (c + e)) & 1u ? q[e] : 0.f;
+    }
+  }
+}
+template <int KPL>
+__device__ __forceinline__ void span_load(const double *p, double (&v)[KPL], uint32_t valid, bool vec) {
+#pragma unroll
+  for (int c = 0; c < KPL; c += 4) {
+    const double *q = p + 128 * (c >> 2);
+    if (vec) {
+      if ((valid >> c) & 1u) {
+        const double2 t0 = *reinterpret_cast<const double2 *>(q);
+        const double2 t1 = *reinterpret_cast<const double2 *>(q + 2);
+        v[c] = t0.x; v[c + 1] = t0.y; v[c + 2] = t1.x; v[c + 3] = t1.y;
+      } else {
+        v[c] = v[c + 1] = v[c + 2] = v[c + 3] = 0.0;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[c + e] = (valid >> (c + e)) & 1u ? q[e] : 0.0;
+    }
+  }
+}
+
 // The selection loop (Sec. 1 greedy choice, Batch-OMP form), refinement on the
 // support and the ELL write-out for signals sig_begin .. sig_begin+sig_count-1
 // of a tile, run by one warp.
@@ -133,6 +179,8 @@ __device__ __forceinline__ void support_residual(const T *Dt, const T *ysig, int
 //          the most later updates)
 //   EXACT  alpha0 came from reduced-precision products: the refit takes D_S^T y
 //          in T instead of alpha0 on the support
+// Lane l owns the atoms lane_atom(l, c), c < KPL: its correlations and the
+// matching entries of each G column load as 16-byte vectors.
 // Per step the correlations are kept as a running vector alpha = alpha0 -
 // G[:, S] x_S in registers: after the support grows, alpha -= G[:, S] dx with dx
 // the change of every coefficient.  The forward-solved vector z = L^{-1}
@@ -147,11 +195,12 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
   const int lane = threadIdx.x & 31;
   constexpr int mu = MU;
   const T eps = (T)a.eps;
-  uint32_t valid = 0;   // bit c: atom lane + 32 c exists
+  uint32_t valid = 0;   // bit c: atom lane_atom(lane, c) exists
 #pragma unroll
   for (int c = 0; c < KPL; ++c)
-    if (lane + 32 * c < K) valid |= 1u << c;
-  const bool full = K == 32 * KPL;   // every lane holds KPL atoms (warp-uniform)
+    if (lane_atom(lane, c) < K) valid |= 1u << c;
+  const bool vec = (K & 3) == 0;   // 16-byte aligned rows of alpha0 and G (warp-uniform)
+  const int j0 = 4 * lane;         // this lane's first atom
 
   for (int q = 0; q < sig_count; ++q) {
     const int sig = sig_begin + q;
@@ -160,8 +209,7 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
     const T *ysig = ybase + (size_t)sig * ypitch;
     const T *arow = a0 + (size_t)sig * K;
     T av[KPL];   // running correlations of this lane's atoms
-#pragma unroll
-    for (int c = 0; c < KPL; ++c) av[c] = (valid >> c) & 1u ? arow[lane + 32 * c] : T(0);
+    span_load<KPL>(arow + j0, av, valid, vec);
 
     T yn2 = T(0);
 #pragma unroll
@@ -182,7 +230,7 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
 #pragma unroll
       for (int c = 0; c < KPL; ++c) {
         const T v = fabs(av[c]);
-        if (((avail >> c) & 1u) && v > bestv) { bestv = v; best = lane + 32 * c; }
+        if (((avail >> c) & 1u) && v > bestv) { bestv = v; best = lane_atom(lane, c); }
       }
       warp_argmax<T>(bestv, best);
       if (best < 0 || !(bestv > T(0))) break;
@@ -210,7 +258,7 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
         Sl = best;
         zl = (a0b - wz) * rl;
       }
-      if ((best & 31) == lane) avail &= ~(1u << (best >> 5));
+      if (((best & 127) >> 2) == lane) avail &= ~(1u << (4 * (best >> 7) + (best & 3)));
       __syncwarp();
       ++k;
       const T xn = upper_solve(Ls, lp, k, zl, lane);
@@ -220,14 +268,10 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
         for (int p = 0; p < k; ++p) {
           const T dp = __shfl_sync(0xffffffffu, dl, p);
           const T *gp = p < gcn ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
-          if (full) {
+          T g[KPL];
+          span_load<KPL>(gp + j0, g, valid, vec);
 #pragma unroll
-            for (int c = 0; c < KPL; ++c) av[c] = fma(-gp[lane + 32 * c], dp, av[c]);
-          } else {
-#pragma unroll
-            for (int c = 0; c < KPL; ++c)
-              if ((valid >> c) & 1u) av[c] = fma(-gp[lane + 32 * c], dp, av[c]);
-          }
+          for (int c = 0; c < KPL; ++c) av[c] = fma(-g[c], dp, av[c]);
         }
       }
       xl = xn;

@@ -244,7 +244,7 @@ inline SelLayout sel_layout(int K, int s, int regs) {
 }
 
 template <int KPL, int MU, bool EXACT>
-__global__ void __launch_bounds__(kSelThreads) omp_select_kernel(OmpArgs a, SelLayout lay, const float *a0c,
+__global__ void __launch_bounds__(kSelThreads, KPL <= 8 ? 4 : (KPL <= 16 ? 3 : 2)) omp_select_kernel(OmpArgs a, SelLayout lay, const float *a0c,
                                                                  int64_t tile0) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int K = a.K, m = a.m, s = a.s;
