@@ -2,8 +2,8 @@
 products with FP32 accumulation) through the C ABI, against the FP64 oracle.
 
 Gradients: BF16 rounding of weights and activations (u = 2^-9 per operand)
-bounds the relative error of each parameter block's gradient by the
-the benchmark spec's BF16 tolerance 2e-2.  Restricted OMP: for every signal it is OMP
+keeps the relative error of each parameter block's gradient within the BF16
+tolerance 2e-2 used for every BF16 result.  Restricted OMP: for every signal it is OMP
 on the sub-dictionary of its candidates, so it is compared with the oracle's
 OMP on exactly that sub-dictionary."""
 import numpy as np
