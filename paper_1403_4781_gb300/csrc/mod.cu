@@ -261,26 +261,43 @@ __global__ void __launch_bounds__(256) mod_accum_ds_kernel(ModArgs a) {
       }
       if (ok && lane == lo) atomicAdd(&At[(size_t)j * K + j], d);
     }
+    // the entries' signal rows are loaded kB at a time (their loads in flight
+    // together), then added in entry order
+    constexpr int kB = MU <= 2 ? 8 : 1;   // wider rows: registers would cost occupancy
     const int nq = e_hi - e0 < 32 ? (int)(e_hi - e0) : 32;
-    for (int q = 0; q < nq; ++q) {
-      const int jq = __shfl_sync(0xffffffffu, j, q);
-      const int iq = __shfl_sync(0xffffffffu, i, q);
-      const float xq = __shfl_sync(0xffffffffu, x, q);
-      if (jq != cur) {   // warp-uniform
-        if (cur >= 0)
+    for (int q0 = 0; q0 < nq; q0 += kB) {
+      float yb[kB][MU], xb[kB];
+      int jb[kB];
 #pragma unroll
-          for (int u = 0; u < MU; ++u) {
-            const int r = lane + 32 * u;
-            if (r < m) atomicAdd(&Bt[(size_t)cur * m + r], (double)acc[u].hi + (double)acc[u].lo);
-            acc[u] = DSum{0.f, 0.f};
-          }
-        cur = jq;
+      for (int b = 0; b < kB; ++b) {
+        const int q = q0 + b;   // < 32: kB divides 32
+        const int jq = __shfl_sync(0xffffffffu, j, q);
+        const int iq = __shfl_sync(0xffffffffu, i, q);
+        xb[b] = __shfl_sync(0xffffffffu, x, q);
+        jb[b] = q < nq ? jq : -2;   // -2: past the range
+        const float *yr = Yt + (size_t)iq * m;
+#pragma unroll
+        for (int u = 0; u < MU; ++u) {
+          const int r = lane + 32 * u;
+          yb[b][u] = (q < nq && r < m) ? yr[r] : 0.f;
+        }
       }
-      const float *yr = Yt + (size_t)iq * m;
 #pragma unroll
-      for (int u = 0; u < MU; ++u) {
-        const int r = lane + 32 * u;
-        if (r < m) ds_add_product(acc[u], xq, yr[r]);
+      for (int b = 0; b < kB; ++b) {
+        if (jb[b] == -2) break;   // warp-uniform
+        if (jb[b] != cur) {       // warp-uniform
+          if (cur >= 0)
+#pragma unroll
+            for (int u = 0; u < MU; ++u) {
+              const int r = lane + 32 * u;
+              if (r < m) atomicAdd(&Bt[(size_t)cur * m + r], (double)acc[u].hi + (double)acc[u].lo);
+              acc[u] = DSum{0.f, 0.f};
+            }
+          cur = jb[b];
+        }
+#pragma unroll
+        for (int u = 0; u < MU; ++u)
+          if (lane + 32 * u < m) ds_add_product(acc[u], xb[b], yb[b][u]);
       }
     }
   }
