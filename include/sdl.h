@@ -58,9 +58,9 @@ typedef enum {
   /* FP32 data; correlations, Gram and the OMP loop in FP32 (CUDA cores);
      coefficients recomputed on the support with one refinement step. */
   SDL_PREC_F32 = 1,
-  /* FP32 data; correlations and Gram from BF16 operands on the tensor cores
-     with FP32 accumulation; coefficients recomputed in FP32 on the support
-     with one refinement step. */
+  /* FP32 data; correlations from BF16 operands on the tensor cores with
+     FP32 accumulation; the selection updates with the FP32 Gram; coefficients
+     recomputed in FP32 on the support from D_S^T y with one refinement step. */
   SDL_PREC_BF16 = 2
 } sdl_precision;
 
