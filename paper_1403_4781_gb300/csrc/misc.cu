@@ -145,16 +145,43 @@ __global__ void __launch_bounds__(256) residual_kernel(const T *__restrict__ Y, 
   __shared__ double red[2][8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double r2 = 0.0, y2 = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
-    for (int r = lane; r < m; r += 32) {
-      const double y = (double)Y[(size_t)i * m + r];
-      double v = y;
-      for (int k = 0; k < s; ++k) {
-        const int j = idx[(size_t)i * s + k];
-        if (j >= 0) v = fma(-(double)D[(size_t)j * m + r], (double)val[(size_t)i * s + k], v);
+  if constexpr (sizeof(T) == 4) {
+    // FP32 data: the residual entry y - sum_k d x_k and the two energies in
+    // compensated FP32 (each product split exactly by an FMA), about 48
+    // significant bits, on the FP32 pipe rather than the narrow FP64 one
+    CSum cr, cy;
+    for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
+      for (int r = lane; r < m; r += 32) {
+        const float y = (float)Y[(size_t)i * m + r];
+        CSum v;
+        v.hi = y;
+        for (int k = 0; k < s; ++k) {
+          const int j = idx[(size_t)i * s + k];
+          if (j >= 0) {
+            const float d = (float)D[(size_t)j * m + r], x = (float)val[(size_t)i * s + k];
+            const float p = d * x;
+            v.add(-p, -fmaf(d, x, -p));
+          }
+        }
+        const float h = v.hi, l = v.lo, p2 = h * h;
+        cr.add(p2, fmaf(h, h, -p2) + 2.f * h * l);
+        cy.add_sq(y);
       }
-      r2 = fma(v, v, r2);
-      y2 = fma(y, y, y2);
+    }
+    r2 = cr.value();
+    y2 = cy.value();
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
+      for (int r = lane; r < m; r += 32) {
+        const double y = (double)Y[(size_t)i * m + r];
+        double v = y;
+        for (int k = 0; k < s; ++k) {
+          const int j = idx[(size_t)i * s + k];
+          if (j >= 0) v = fma(-(double)D[(size_t)j * m + r], (double)val[(size_t)i * s + k], v);
+        }
+        r2 = fma(v, v, r2);
+        y2 = fma(y, y, y2);
+      }
     }
   }
   r2 = warp_sum(r2);
