@@ -206,6 +206,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (KPL <= 16 ? 3 : 2)
 template <typename T>
 cudaError_t launch_gram(const T *D, int m, int K, int L, T *G, cudaStream_t st) {
   if (L <= 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    // 128 x 128 tiles when they give at least one block per SM of the GB300
+    // (152: the batched local dictionaries), 64 x 64 tiles otherwise (a single
+    // dictionary, where the smaller tiles spread over more SMs)
+    constexpr int64_t kMinBigBlocks = 152;
+    const int64_t big = (int64_t)L * ((K + 127) / 128) * ((K + 127) / 128);
+    if (big >= kMinBigBlocks) return launch_gram_f32_tiles(reinterpret_cast<const float *>(D), m, K, L,
+                                                 reinterpret_cast<float *>(G), st);
+  }
   dim3 grid((K + 63) / 64, (K + 63) / 64, L);
   gram_kernel<T><<<grid, 256, 0, st>>>(D, m, K, G);
   return cudaGetLastError();

@@ -22,25 +22,18 @@ constexpr int kGN = 128;      // atoms per block
 constexpr int kGK = 16;       // signal entries per stage
 constexpr int kGPitch = 132;  // staged row pitch (floats): 16-byte aligned rows
 
-// alpha0 of one 128-signal tile against 128 atoms.  Thread (ty, tx) of a 16 x
-// 16 grid owns signals 4 ty + {0..3} and 64 + 4 ty + {0..3} and atoms 4 tx +
-// {0..3} and 64 + 4 tx + {0..3}: an 8 x 8 register tile fed by four 16-byte
-// shared-memory reads per entry.  Stages of 16 entries are double-buffered,
-// the next stage's global loads held in registers during the products.
-__global__ void __launch_bounds__(kGThreads) corr_f32_kernel(OmpArgs a, float *a0c, int64_t tile0, int nb) {
+// out[r][j0 + c] = <y_r, d_(j0 + c)> for the rows r < nsig of a 128-row tile
+// (row r at Yt + r m) against atoms j0 .. j0 + 127 of Dt ([K][m]); row r of the
+// output at out + r ldo.  Thread (ty, tx) of a 16 x 16 grid owns rows 4 ty +
+// {0..3} and 64 + 4 ty + {0..3} and atoms 4 tx + {0..3} and 64 + 4 tx + {0..3}:
+// an 8 x 8 register tile fed by four 16-byte shared-memory reads per entry.
+// Stages of 16 entries are double-buffered, the next stage's global loads held
+// in registers during the products.  Each product is an ordered chain of FP32
+// FMAs over the entries, as in the fused OMP kernel.
+__device__ __forceinline__ void tile_products(const float *__restrict__ Yt, int nsig, const float *__restrict__ Dt,
+                                              int K, int m, int j0, float *out, int64_t ldo) {
   __shared__ __align__(16) float Ys[2][kGK][kGPitch];
   __shared__ __align__(16) float Ds[2][kGK][kGPitch];
-  const int K = a.K, m = a.m;
-  // consecutive blocks share a tile (its nb atom blocks), so the tile's signals
-  // come from DRAM once and from L2 for the other atom blocks
-  const int64_t g = tile0 + blockIdx.x / nb;
-  const int t = find_subset(a.tile_start, a.L, g);
-  const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)kGM;
-  const int64_t rows_left = a.offsets[t + 1] - row0;
-  const int nsig = rows_left < kGM ? (int)rows_left : kGM;
-  const int j0 = (int)(blockIdx.x % nb) * kGN;
-  const float *__restrict__ Y = static_cast<const float *>(a.Y);
-  const float *__restrict__ Dt = static_cast<const float *>(a.D) + (size_t)t * K * m;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const bool vec = (m & 3) == 0;
 
@@ -48,7 +41,7 @@ __global__ void __launch_bounds__(kGThreads) corr_f32_kernel(OmpArgs a, float *a
   // 8 (tid & 1) .. 8 (tid & 1) + 7 of the stage
   const int lrow = tid >> 1, lk = (tid & 1) * 8;
   const bool yok = lrow < nsig, dok = j0 + lrow < K;
-  const float *ysrc = Y + (size_t)(row0 + (yok ? lrow : 0)) * m;
+  const float *ysrc = Yt + (size_t)(yok ? lrow : 0) * m;
   const float *dsrc = Dt + (size_t)(dok ? j0 + lrow : 0) * m;
   float yr[8], dr[8];
   auto fetch = [&](int k0) {
@@ -108,14 +101,12 @@ __global__ void __launch_bounds__(kGThreads) corr_f32_kernel(OmpArgs a, float *a
     __syncthreads();
   }
 
-  // rows of the tile's scratch block: signal r of the tile at a0 + r * K
-  float *out = a0c + (size_t)(g - tile0) * kGM * K;
-  const bool vstore = (K & 3) == 0;
+  const bool vstore = (K & 3) == 0 && (ldo & 3) == 0;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    const int sig = (r < 4 ? 4 * ty : 64 + 4 * ty) + (r & 3);
-    if (sig >= nsig) continue;
-    float *orow = out + (size_t)sig * K;
+    const int row = (r < 4 ? 4 * ty : 64 + 4 * ty) + (r & 3);
+    if (row >= nsig) continue;
+    float *orow = out + (size_t)row * ldo;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int j = j0 + (h == 0 ? 4 * tx : 64 + 4 * tx);
@@ -131,7 +122,46 @@ __global__ void __launch_bounds__(kGThreads) corr_f32_kernel(OmpArgs a, float *a
   }
 }
 
+// alpha0 of one 128-signal tile of the plan against 128 atoms, into the
+// scratch (signal r of the tile at a0c + ((g - tile0) 128 + r) K).  The atom
+// blocks of a tile are consecutive blocks, so the tile's signals come from
+// DRAM once and from L2 for the other atom blocks.
+__global__ void __launch_bounds__(kGThreads) corr_f32_kernel(OmpArgs a, float *a0c, int64_t tile0, int nb) {
+  const int K = a.K, m = a.m;
+  const int64_t g = tile0 + blockIdx.x / nb;
+  const int t = find_subset(a.tile_start, a.L, g);
+  const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)kGM;
+  const int64_t rows_left = a.offsets[t + 1] - row0;
+  const int nsig = rows_left < kGM ? (int)rows_left : kGM;
+  const int j0 = (int)(blockIdx.x % nb) * kGN;
+  tile_products(static_cast<const float *>(a.Y) + (size_t)row0 * m, nsig,
+                static_cast<const float *>(a.D) + (size_t)t * K * m, K, m, j0,
+                a0c + (size_t)(g - tile0) * kGM * K, K);
+}
+
+// The Gram matrices G_t = D_t D_t^T of L dictionaries [L][K][m] into [L][K][K]:
+// the same tile products with the atoms of D_t as the rows.  Block b covers
+// subset b / (nt nb), row tile (b / nb) mod nt and atom block b mod nb.
+__global__ void __launch_bounds__(kGThreads) gram_f32_kernel(const float *__restrict__ D, int K, int m, int nt,
+                                                             int nb, float *G) {
+  const int64_t b = blockIdx.x;
+  const int t = (int)(b / ((int64_t)nt * nb));
+  const int rt = (int)((b / nb) % nt);
+  const int j0 = (int)(b % nb) * kGN;
+  const int r0 = rt * kGM;
+  const int nrow = K - r0 < kGM ? K - r0 : kGM;
+  const float *Dt = D + (size_t)t * K * m;
+  tile_products(Dt + (size_t)r0 * m, nrow, Dt, K, m, j0, G + ((size_t)t * K + r0) * K, K);
+}
+
 }  // namespace
+
+cudaError_t launch_gram_f32_tiles(const float *D, int m, int K, int L, float *G, cudaStream_t st) {
+  if (L <= 0) return cudaSuccess;
+  const int nt = (K + kGM - 1) / kGM, nb = (K + kGN - 1) / kGN;
+  gram_f32_kernel<<<(unsigned)((int64_t)L * nt * nb), kGThreads, 0, st>>>(D, K, m, nt, nb, G);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_omp_split_f32(const OmpArgs &a, float *a0c, cudaStream_t st) {
   if (a.total_tiles <= 0) return cudaSuccess;

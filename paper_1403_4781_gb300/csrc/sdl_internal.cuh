@@ -146,6 +146,9 @@ cudaError_t launch_omp_select(const OmpArgs &a, const float *a0c, int64_t tile0,
 // FP32 OMP in two kernels: FFMA correlation GEMM of 128-signal tiles into a0c,
 // then the selection kernel (same plan and scratch as the BF16 path).
 cudaError_t launch_omp_split_f32(const OmpArgs &a, float *a0c, cudaStream_t st);
+// G_t = D_t D_t^T with the correlation GEMM's 128 x 128 register-tiled blocks
+// (used by launch_gram<float> when there are enough blocks to fill the GPU).
+cudaError_t launch_gram_f32_tiles(const float *D, int m, int K, int L, float *G, cudaStream_t st);
 int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles);
 
 struct ModArgs {
