@@ -417,9 +417,21 @@ def proposer_bench(sdl, dev, flush, stream):
     t_prop, (qi, qv, qn, qr, nf) = timed(lambda: prop.omp(D, Yev, s, ncand, eps_fb))
     same = (torch.sort(pi, dim=1).values == torch.sort(qi, dim=1).values).all(dim=1).float().mean().item()
     met = (torch.sqrt(qr) <= eps_fb).float().mean().item()
+    # one more epoch, after the evaluation, with each training step bracketed
+    # by events: the device time of training alone (the timed loop above also
+    # holds the gaps while Python issues each step)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(0, n_train, B)]
+    for q, a in enumerate(range(0, n_train, B)):
+        evs[q][0].record(stream)
+        prop.train_step(Ytr[a:a + B], labels[a:a + B], 1e-4, loss)
+        evs[q][1].record(stream)
+    evs[-1][1].synchronize()
+    dev_ms = sum(b.elapsed_time(e) for b, e in evs)
     prop.close()
     return {"train_pairs": n_train, "epochs": epochs, "batch": B, "train_s": train_s,
-            "train_samples_per_s": epochs * n_train / train_s, "loss_first": first, "loss_last": last,
+            "train_samples_per_s": epochs * n_train / train_s,
+            "train_device_samples_per_s": n_train / (dev_ms / 1e3), "loss_first": first, "loss_last": last,
             "eval_signals": n_eval, "plain_omp_signals_per_s": n_eval / t_plain,
             "proposed_omp_signals_per_s": n_eval / t_prop, "fallback_rate": nf / n_eval,
             "support_agreement_with_plain": same, "residual_within_eps_fb": met,
