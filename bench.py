@@ -324,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
     kernels = {k: {"ms_per_step": v[2] / args.steps, "launches_per_step": v[0] / args.steps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}
     # the OMP stage alone: Gram, correlations, selection loop (every coding pass)
-    omp_names = ("omp", "omp_split", "gram", "omp_tc", "bf16_image")
+    omp_names = ("omp", "omp_split", "gram", "omp_tc", "gram_tc", "bf16_image")
     omp_ms = sum(v[2] for k, v in prof.items() if k in omp_names) / args.steps
 
     res = {

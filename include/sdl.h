@@ -59,8 +59,9 @@ typedef enum {
      coefficients recomputed on the support with one refinement step. */
   SDL_PREC_F32 = 1,
   /* FP32 data; correlations from BF16 operands on the tensor cores with
-     FP32 accumulation; the selection updates with the FP32 Gram; coefficients
-     recomputed in FP32 on the support from D_S^T y with one refinement step. */
+     FP32 accumulation; the Gram on the tensor cores from a two-term BF16 split
+     of D (about 2^-16); coefficients recomputed in FP32 on the support from
+     D_S^T y with one refinement step. */
   SDL_PREC_BF16 = 2
 } sdl_precision;
 
@@ -185,6 +186,17 @@ sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, cons
 sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t n,
                         const void *D, int K, const int32_t *idx, const void *val, int s,
                         double *out2);
+
+/* Gram matrices G_t = D_t D_t^T of L dictionaries, the products the
+ * Batch-OMP update uses (Sec. 1).  D device [L][K][m] (the data type), G device
+ * [L][K][K] (the data type; FP32 for BF16).  F64 and F32: FMA chains over the
+ * m entries on the CUDA cores.  BF16: FP32 data split as d = hi + lo + r with
+ * hi = bf16(d), lo = bf16(d - hi), and G = hi hi^T + hi lo^T + lo hi^T on the
+ * tensor cores with FP32 accumulation, about 2^-16 of |d_i||d_j| from the
+ * exact Gram (synchronises to read the tensor-core kernels' error word).
+ * Errors: SDL_EINVAL for a bad shape or pointer, SDL_ETIMEOUT when a bounded
+ * wait of the tensor-core kernel gave up. */
+sdl_status sdl_gram(sdl_ctx *ctx, sdl_precision prec, const void *D, int m, int K, int L, void *G);
 
 /* Atom recovery (Sec. 3.1): count device int32 [1] receives the number of atoms
  * of D0 (K0 x m) for which some atom of D (K x m) has |d0_i^T d_j| >= thresh. */

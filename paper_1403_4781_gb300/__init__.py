@@ -70,6 +70,7 @@ _SIGS = {
     "sdl_merge": (_i32, [_vp, _i32, _vp, _vp, _i32, _i32, _i32, _vp, _i32, _i32, _dbl, _i32, _vp, _vp]),
     "sdl_residual": (_i32, [_vp, _i32, _vp, _i32, _i64, _vp, _i32, _vp, _vp, _i32, _vp]),
     "sdl_recovery": (_i32, [_vp, _i32, _vp, _i32, _vp, _i32, _i32, _dbl, _vp]),
+    "sdl_gram": (_i32, [_vp, _i32, _vp, _i32, _i32, _i32, _vp]),
     "sdl_profile_enable": (_i32, [_vp, _i32]),
     "sdl_profile_reset": (_i32, [_vp]),
     "sdl_profile_count": (_i32, [_vp]),
@@ -408,6 +409,18 @@ def denoise(noisy, D, p, eps, s_max=32, prec=None):
     P = extract_patches(noisy, p, prec=prec)
     idx, val, nnz, _ = omp(D, P, s_max, eps=eps, prec=prec, with_resid=False)
     return patch_average(D, idx, val, H, W, p, prec=None if prec == PREC_BF16 else prec), (idx, val, nnz)
+
+
+def gram(D, prec=None):
+    """Gram matrices of D (L, K, m) or (K, m): D_t D_t^T, shape (L, K, K) or (K, K)."""
+    import torch
+    prec = _prec_of(D, prec)
+    Db = D if D.dim() == 3 else D[None]
+    L, K, m = Db.shape
+    G = torch.empty((L, K, K), dtype=torch.float64 if prec == PREC_F64 else torch.float32, device=D.device)
+    ctx = context(D.device.index)
+    _call("sdl_gram", ctx.bind_stream(), prec, _ptr(Db), m, K, L, _ptr(G))
+    return G if D.dim() == 3 else G[0]
 
 
 def recovery(D0, D, thresh=0.98, prec=None):

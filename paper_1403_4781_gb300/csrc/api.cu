@@ -290,15 +290,16 @@ bool omp_split_f32(const sdl_ctx *ctx, int K, int m, int s) {
 }
 
 // Workspace of the BF16 tensor-core coding pass over n signals in L subsets:
-// BF16 image of D, error word, and the correlation scratch (one chunk of
-// 128-signal tiles).  The FP32 Gram lives in the caller's G.
+// the two BF16 images of D (hi, then lo), error word, and the correlation
+// scratch (one chunk of 128-signal tiles).  The FP32 Gram lives in the
+// caller's G.
+size_t tc_image_bytes(int L, int K, int m) { return (size_t)L * round16(K) * round16(m) * 2; }
 size_t tc_a0_bytes(int L, int K, int64_t n) {
   const int64_t tiles = (n + 127) / 128 + L;
   return sizeof(float) * (size_t)omp_tc_chunk_tiles(K, tiles) * 128 * K;
 }
 size_t tc_ws_bytes(int L, int K, int m, int64_t n) {
-  return round256((size_t)L * round16(K) * round16(m) * 2) + round256(sizeof(int32_t) * 4) +
-         round256(tc_a0_bytes(L, K, n));
+  return round256(2 * tc_image_bytes(L, K, m)) + round256(sizeof(int32_t) * 4) + round256(tc_a0_bytes(L, K, n));
 }
 
 // Kernels of one two-kernel coding pass: a correlation and a selection launch
@@ -308,22 +309,21 @@ int split_kernels(const OmpArgs &oa) {
   return oa.total_tiles > 0 ? 2 * (int)((oa.total_tiles + chunk - 1) / chunk) : 0;
 }
 
-// One BF16 coding pass: BF16 image of D, FP32 Gram, correlations on the tensor
-// cores, selection loop, FP32 refit on the support.
+// One BF16 coding pass: BF16 images of D (img holds hi, then lo), Gram and
+// correlations on the tensor cores, selection loop, FP32 refit on the support.
 cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *err, float *a0c) {
   cudaStream_t sm = ctx->stream;
+  void *lo = static_cast<unsigned char *>(img) + tc_image_bytes(oa.L, oa.K, oa.m);
   oa.Dimg = img;
   oa.Kp = round16(oa.K);
   oa.mp = round16(oa.m);
   oa.err = err;
   oa.G = G;
   cudaError_t e = timed(ctx, "bf16_image", 1, [&] {
-    return launch_bf16_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, img, sm);
+    return launch_bf16_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, img, lo, sm);
   });
   if (e != cudaSuccess) return e;
-  e = timed(ctx, "gram", 1, [&] {
-    return launch_gram<float>(static_cast<const float *>(oa.D), oa.m, oa.K, oa.L, G, sm);
-  });
+  e = timed(ctx, "gram_tc", 1, [&] { return launch_gram_tc(img, lo, oa.K, oa.m, oa.L, G, err, sm); });
   if (e != cudaSuccess) return e;
   return timed(ctx, "omp_tc", split_kernels(oa), [&] { return launch_omp_tc(oa, a0c, sm); });
 }
@@ -474,7 +474,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   if (tile <= 0) return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
   if ((st = upload_plan(ctx, offsets, L, tile, &d_off, &d_tiles, &tiles)) != SDL_OK)
     return st;
-  void *img = bf16 ? ws_alloc(ctx, (size_t)L * round16(K) * round16(m) * 2) : nullptr;
+  void *img = bf16 ? ws_alloc(ctx, 2 * tc_image_bytes(L, K, m)) : nullptr;
   int32_t *tc_err = bf16 ? static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4)) : nullptr;
   float *a0c = bf16 || split ? static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n))) : nullptr;
   if ((split && !a0c) || (bf16 && (!img || !tc_err || !a0c))) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
@@ -682,7 +682,7 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
   a.L = L; a.m = m; a.K = K; a.s = s; a.eps = eps;
   a.idx = idx; a.val = val; a.nnz = nnz; a.resid2 = resid2;
   if (bf16) {
-    void *img = ws_alloc(ctx, (size_t)L * round16(K) * round16(m) * 2);
+    void *img = ws_alloc(ctx, 2 * tc_image_bytes(L, K, m));
     int32_t *err = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
     float *a0c = static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n)));
     if (!img || !err || !a0c) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
@@ -938,6 +938,49 @@ sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, 
     SDL_CUDA(timed(ctx, "residual", 1, [&] { return launch_residual<float>(static_cast<const float *>(Y), m, n, static_cast<const float *>(D), idx,
                                     static_cast<const float *>(val), s, out2, ctx->stream); }), "residual");
   return SDL_OK;
+}
+
+sdl_status sdl_gram(sdl_ctx *ctx, sdl_precision prec, const void *D, int m, int K, int L, void *G) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
+  SDL_REQUIRE(m >= 1 && m <= kMaxM, "m must be in [1, 256]");
+  SDL_REQUIRE(K >= 1 && K <= kMaxK, "K must be in [1, 1024]");
+  SDL_REQUIRE(L >= 1, "L must be >= 1");
+  SDL_REQUIRE(aligned16(D) && aligned16(G), "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  cudaStream_t sm = ctx->stream;
+  if (prec == SDL_PREC_F64) {
+    SDL_CUDA(timed(ctx, "gram", 1, [&] {
+               return launch_gram<double>(static_cast<const double *>(D), m, K, L, static_cast<double *>(G), sm);
+             }), "gram");
+    return SDL_OK;
+  }
+  if (prec == SDL_PREC_F32) {
+    SDL_CUDA(timed(ctx, "gram", 1, [&] {
+               return launch_gram<float>(static_cast<const float *>(D), m, K, L, static_cast<float *>(G), sm);
+             }), "gram");
+    return SDL_OK;
+  }
+  if ((st = ws_reserve(ctx, round256(2 * tc_image_bytes(L, K, m)) + round256(sizeof(int32_t) * 4) + 1024)) !=
+      SDL_OK)
+    return st;
+  void *img = ws_alloc(ctx, 2 * tc_image_bytes(L, K, m));
+  int32_t *err = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
+  if (!img || !err) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  void *lo = static_cast<unsigned char *>(img) + tc_image_bytes(L, K, m);
+  SDL_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), sm), "err clear");
+  SDL_CUDA(timed(ctx, "bf16_image", 1, [&] {
+             return launch_bf16_image(static_cast<const float *>(D), K, m, L, img, lo, sm);
+           }), "bf16 image");
+  cudaError_t e = timed(ctx, "gram_tc", 1, [&] {
+    return launch_gram_tc(img, lo, K, m, L, static_cast<float *>(G), err, sm);
+  });
+  if (e == cudaErrorInvalidConfiguration) return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core Gram");
+  SDL_CUDA(e, "gram tc");
+  return tc_status(ctx, err);
 }
 
 sdl_status sdl_recovery(sdl_ctx *ctx, sdl_precision prec, const void *D0, int K0, const void *D, int K, int m,

@@ -1,19 +1,21 @@
-// BF16 tensor-core front end of OMP (Sec. 1).
+// BF16 tensor-core front end of OMP (Sec. 1) and of the Gram matrix.
 //
 // The correlations alpha0 = D^T y are the dense contraction of the coding pass
-// (2 m K products per signal), so the BF16 path runs them on the 5th-generation
-// tensor cores: tcgen05.mma
+// (2 m K products per signal) and G = D^T D that of each dictionary, so the
+// BF16 path runs both on the 5th-generation tensor cores: tcgen05.mma
 // (kind::f16, BF16 operands, FP32 accumulation) with the accumulator tile in
 // tensor memory, operands in shared memory in the canonical K-major layout.
 // Dictionary tiles are streamed in by bulk TMA copies of a pre-laid-out BF16
 // image of D; the signal tile is converted from FP32 in the kernel.  The
 // correlation kernel writes alpha0 of 128-signal tiles to a global scratch (in
 // chunks of at most 1 GiB); the selection kernel then runs the shared selection
-// loop from there with little shared memory per block.  The selection updates
-// the correlations with the FP32 Gram (O(K^2 m) per dictionary, small beside
-// the n K m of the correlations), so its Cholesky factor of G_SS is FP32-exact
-// and serves the refit of the coefficients on the support from D_S^T y in FP32
-// (one refinement step): the BF16 rounding affects only which atoms are chosen.
+// loop from there with little shared memory per block.  The Gram is formed
+// from a two-term BF16 split of D (hi + lo, three products), accurate to about
+// 2^-16 where one BF16 product would give 2^-8, so the selection's Cholesky
+// factor of G_SS also serves the refit of the coefficients on the support from
+// D_S^T y in FP32, whose refinement step (residuals from D_S and y in FP32)
+// removes the factor's remaining error: the BF16 rounding of alpha0 affects
+// only which atoms are chosen.
 #include "omp_common.cuh"
 #include "tc_ptx.cuh"
 
@@ -26,9 +28,11 @@ using namespace omp_detail;
 
 constexpr int kWaitLimit = 1 << 22;   // polls of a bounded mbarrier wait
 
-// D [L][K][m] FP32 -> BF16 image [L][Kp][mp]; zero padding rows / columns.
+// D [L][K][m] FP32 -> BF16 images [L][Kp][mp] (zero padding rows / columns):
+// hi = bf16(d) and, when lo is not null, lo = bf16(d - hi), the next eight
+// significant bits, so that hi + lo carries d to about 2^-16.
 __global__ void bf16_image_kernel(const float *__restrict__ D, int K, int m, int Kp, int mp, int L,
-                                  unsigned char *__restrict__ img) {
+                                  unsigned char *__restrict__ img, unsigned char *__restrict__ lo_img) {
   const int kc8 = mp >> 3;
   const int64_t total = (int64_t)L * Kp * kc8;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
@@ -36,18 +40,106 @@ __global__ void bf16_image_kernel(const float *__restrict__ D, int K, int m, int
     const int rem = (int)(q - t * Kp * kc8);
     const int r = rem / kc8, kc = rem - r * kc8;
     const float *src = D + ((size_t)t * K + r) * m;
-    uint32_t packed[4];
+    uint32_t packed[4], packed_lo[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int k0 = kc * 8 + 2 * e;
-      const float lo = (r < K && k0 < m) ? src[k0] : 0.f;
-      const float hi = (r < K && k0 + 1 < m) ? src[k0 + 1] : 0.f;
-      __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
-      packed[e] = *reinterpret_cast<uint32_t *>(&b2);
+      const float x0 = (r < K && k0 < m) ? src[k0] : 0.f;
+      const float x1 = (r < K && k0 + 1 < m) ? src[k0 + 1] : 0.f;
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+      packed[e] = *reinterpret_cast<const uint32_t *>(&h);
+      packed_lo[e] = *reinterpret_cast<const uint32_t *>(&l);
     }
-    *reinterpret_cast<uint4 *>(img + (size_t)t * Kp * mp * 2 + tc::image_offset(r, kc * 8, mp)) =
-        make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    const size_t off = (size_t)t * Kp * mp * 2 + tc::image_offset(r, kc * 8, mp);
+    *reinterpret_cast<uint4 *>(img + off) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    if (lo_img)
+      *reinterpret_cast<uint4 *>(lo_img + off) = make_uint4(packed_lo[0], packed_lo[1], packed_lo[2], packed_lo[3]);
   }
+}
+
+// Gram tile G[128 rows][128 cols] of subset blockIdx.z on the tensor cores from
+// the split images: hi hi^T + hi lo^T + lo hi^T accumulated in one TMEM tile
+// (the dropped lo lo^T is about 2^-16 of each product), three rounds of bulk
+// loads of the row tile and the column tile, each round's products finished
+// before the next round's loads overwrite the operands.
+constexpr int kGramNG = 128;
+
+__global__ void __launch_bounds__(128) gram_tc_kernel(const unsigned char *__restrict__ hi,
+                                                      const unsigned char *__restrict__ lo, int K, int Kp, int mp,
+                                                      float *__restrict__ G, int32_t *err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int t = blockIdx.z, bx = blockIdx.x, by = blockIdx.y;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char *Aim = smem;
+  unsigned char *Bim = smem + (size_t)128 * mp * 2;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + (size_t)(128 + kGramNG) * mp * 2);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+  if (warp == 0) tc::tmem_alloc(tslot, kGramNG);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *tslot;
+  const size_t sub = (size_t)t * Kp * mp * 2;
+  const int rowsA = min(128, Kp - 128 * bx), rowsB = min(kGramNG, Kp - kGramNG * by);
+  const uint32_t idesc = tc::idesc_bf16(128, kGramNG);
+  const uint32_t sbo = (uint32_t)(mp >> 3) * 128;
+  bool ok = true;
+  for (int round = 0; round < 3; ++round) {
+    const unsigned char *a = (round == 2 ? lo : hi) + sub;
+    const unsigned char *b = (round == 1 ? lo : hi) + sub;
+    const uint32_t par = (uint32_t)(round & 1);
+    if (tid == 0) {
+      tc::mbar_expect_tx(&mbar[0], (uint32_t)(rowsA + rowsB) * mp * 2);
+      tc::bulk_g2s(Aim, a + (size_t)128 * bx * mp * 2, (uint32_t)rowsA * mp * 2, &mbar[0]);
+      tc::bulk_g2s(Bim, b + (size_t)kGramNG * by * mp * 2, (uint32_t)rowsB * mp * 2, &mbar[0]);
+    }
+    // every decision below is made block-wide (barrier with a vote), so all
+    // threads leave the loop together
+    if (__syncthreads_or(!tc::mbar_wait(&mbar[0], par, kWaitLimit))) {
+      if (tid == 0) tc::mbar_wait(&mbar[0], par, kWaitLimit);   // drain copies in flight (bounded)
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      tc::fence_after();
+      for (int ks = 0; ks < (mp >> 4); ++ks)
+        tc::mma_bf16(tbase, tc::smem_desc(tc::smem_u32(Aim) + ks * 256, 128, sbo),
+                     tc::smem_desc(tc::smem_u32(Bim) + ks * 256, 128, sbo), idesc, round > 0 || ks > 0);
+      tc::mma_commit(&mbar[1]);
+    }
+    // the products have read the operands: the next round may overwrite them
+    if (__syncthreads_or(!tc::mbar_wait(&mbar[1], par, kWaitLimit))) {
+      ok = false;
+      break;
+    }
+  }
+  tc::fence_after();
+  if (ok) {
+    const int row = 128 * bx + 32 * warp + lane;
+    for (int c0 = 0; c0 < kGramNG; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + c0, v);
+      if (row < K) {
+        float *grow = G + ((size_t)t * K + row) * K;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          const int col = kGramNG * by + c0 + e;
+          if (col < K) grow[col] = v[e];
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(err, 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, kGramNG);
 }
 
 // ---- correlations: alpha0 = Y D^T of 128-signal tiles into global memory ----
@@ -295,13 +387,28 @@ cudaError_t select_dispatch(const OmpArgs &a, const float *a0c, int64_t g0, int6
 
 }  // namespace
 
-cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, cudaStream_t st) {
+cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, void *lo_img, cudaStream_t st) {
   const int Kp = round16(K), mp = round16(m);
   const int64_t total = (int64_t)L * Kp * (mp >> 3);
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  bf16_image_kernel<<<blocks, 256, 0, st>>>(D, K, m, Kp, mp, L, static_cast<unsigned char *>(img));
+  bf16_image_kernel<<<blocks, 256, 0, st>>>(D, K, m, Kp, mp, L, static_cast<unsigned char *>(img),
+                                            static_cast<unsigned char *>(lo_img));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc(const void *hi, const void *lo, int K, int m, int L, float *G, int32_t *err,
+                           cudaStream_t st) {
+  if (L <= 0) return cudaSuccess;
+  const int Kp = round16(K), mp = round16(m);
+  const size_t smem = tc::smem_for_tmem((size_t)(128 + kGramNG) * mp * 2 + 64, kGramNG);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((Kp + 127) / 128, (Kp + kGramNG - 1) / kGramNG, L);
+  gram_tc_kernel<<<grid, 128, smem, st>>>(static_cast<const unsigned char *>(hi),
+                                          static_cast<const unsigned char *>(lo), K, Kp, mp, G, err);
   return cudaGetLastError();
 }
 

@@ -132,7 +132,12 @@ int omp_tile_signals();
 
 // BF16 tensor-core path (tcgen05 + TMEM, operands fed by bulk TMA copies).
 inline int round16(int x) { return (x + 15) & ~15; }
-cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, cudaStream_t st);
+// BF16 images of D: hi = bf16(d) and (lo_img not null) lo = bf16(d - hi).
+cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, void *lo_img, cudaStream_t st);
+// G = hi hi^T + hi lo^T + lo hi^T per dictionary on the tensor cores (FP32
+// accumulation, about 2^-16 relative to the exact Gram of D).
+cudaError_t launch_gram_tc(const void *hi, const void *lo, int K, int m, int L, float *G, int32_t *err,
+                           cudaStream_t st);
 // Correlations of 128-signal tiles on the tensor cores into the scratch a0c
 // (omp_tc_chunk_tiles tiles of 128 x K floats at a time), then the selection
 // loop from there.
