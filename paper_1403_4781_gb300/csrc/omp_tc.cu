@@ -60,20 +60,24 @@ __global__ void bf16_image_kernel(const float *__restrict__ D, int K, int m, int
 
 // Gram tile G[128 rows][128 cols] of subset blockIdx.z on the tensor cores from
 // the split images: hi hi^T + hi lo^T + lo hi^T accumulated in one TMEM tile
-// (the dropped lo lo^T is about 2^-16 of each product), three rounds of bulk
-// loads of the row tile and the column tile, each round's products finished
-// before the next round's loads overwrite the operands.
+// (the dropped terms are about 2^-18 of each product).  all4: the hi and lo
+// row and column tiles are loaded in one round of bulk copies; otherwise three
+// rounds through one pair of buffers, each round's products finished before the
+// next round's loads overwrite the operands.
 constexpr int kGramNG = 128;
 
 __global__ void __launch_bounds__(128) gram_tc_kernel(const unsigned char *__restrict__ hi,
                                                       const unsigned char *__restrict__ lo, int K, int Kp, int mp,
-                                                      float *__restrict__ G, int32_t *err) {
+                                                      bool all4, float *__restrict__ G, int32_t *err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int t = blockIdx.z, bx = blockIdx.x, by = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const size_t tile = (size_t)128 * mp * 2;   // one 128-row operand tile (kGramNG == 128)
   unsigned char *Aim = smem;
-  unsigned char *Bim = smem + (size_t)128 * mp * 2;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + (size_t)(128 + kGramNG) * mp * 2);
+  unsigned char *Bim = smem + tile;
+  unsigned char *Alo = smem + 2 * tile;   // all4: the lo tiles too, one round of loads
+  unsigned char *Blo = smem + 3 * tile;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + (all4 ? 4 : 2) * tile);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
   if (warp == 0) tc::tmem_alloc(tslot, kGramNG);
   if (tid == 0) {
@@ -90,33 +94,61 @@ __global__ void __launch_bounds__(128) gram_tc_kernel(const unsigned char *__res
   const uint32_t idesc = tc::idesc_bf16(128, kGramNG);
   const uint32_t sbo = (uint32_t)(mp >> 3) * 128;
   bool ok = true;
-  for (int round = 0; round < 3; ++round) {
-    const unsigned char *a = (round == 2 ? lo : hi) + sub;
-    const unsigned char *b = (round == 1 ? lo : hi) + sub;
-    const uint32_t par = (uint32_t)(round & 1);
+  auto mma_tiles = [&](const unsigned char *A, const unsigned char *B, bool acc) {
+    for (int ks = 0; ks < (mp >> 4); ++ks)
+      tc::mma_bf16(tbase, tc::smem_desc(tc::smem_u32(A) + ks * 256, 128, sbo),
+                   tc::smem_desc(tc::smem_u32(B) + ks * 256, 128, sbo), idesc, acc || ks > 0);
+  };
+  const size_t arow = (size_t)128 * bx * mp * 2, brow = (size_t)kGramNG * by * mp * 2;
+  const uint32_t abytes = (uint32_t)rowsA * mp * 2, bbytes = (uint32_t)rowsB * mp * 2;
+  // every decision below is made block-wide (barrier with a vote), so all
+  // threads leave together
+  if (all4) {   // the four tiles at once, then the three products
     if (tid == 0) {
-      tc::mbar_expect_tx(&mbar[0], (uint32_t)(rowsA + rowsB) * mp * 2);
-      tc::bulk_g2s(Aim, a + (size_t)128 * bx * mp * 2, (uint32_t)rowsA * mp * 2, &mbar[0]);
-      tc::bulk_g2s(Bim, b + (size_t)kGramNG * by * mp * 2, (uint32_t)rowsB * mp * 2, &mbar[0]);
+      tc::mbar_expect_tx(&mbar[0], 2 * (abytes + bbytes));
+      tc::bulk_g2s(Aim, hi + sub + arow, abytes, &mbar[0]);
+      tc::bulk_g2s(Bim, hi + sub + brow, bbytes, &mbar[0]);
+      tc::bulk_g2s(Alo, lo + sub + arow, abytes, &mbar[0]);
+      tc::bulk_g2s(Blo, lo + sub + brow, bbytes, &mbar[0]);
     }
-    // every decision below is made block-wide (barrier with a vote), so all
-    // threads leave the loop together
-    if (__syncthreads_or(!tc::mbar_wait(&mbar[0], par, kWaitLimit))) {
-      if (tid == 0) tc::mbar_wait(&mbar[0], par, kWaitLimit);   // drain copies in flight (bounded)
+    if (__syncthreads_or(!tc::mbar_wait(&mbar[0], 0, kWaitLimit))) {
+      if (tid == 0) tc::mbar_wait(&mbar[0], 0, kWaitLimit);   // drain copies in flight (bounded)
       ok = false;
-      break;
+    } else {
+      if (tid == 0) {
+        tc::fence_after();
+        mma_tiles(Aim, Bim, false);
+        mma_tiles(Aim, Blo, true);
+        mma_tiles(Alo, Bim, true);
+        tc::mma_commit(&mbar[1]);
+      }
+      ok = !__syncthreads_or(!tc::mbar_wait(&mbar[1], 0, kWaitLimit));
     }
-    if (tid == 0) {
-      tc::fence_after();
-      for (int ks = 0; ks < (mp >> 4); ++ks)
-        tc::mma_bf16(tbase, tc::smem_desc(tc::smem_u32(Aim) + ks * 256, 128, sbo),
-                     tc::smem_desc(tc::smem_u32(Bim) + ks * 256, 128, sbo), idesc, round > 0 || ks > 0);
-      tc::mma_commit(&mbar[1]);
-    }
-    // the products have read the operands: the next round may overwrite them
-    if (__syncthreads_or(!tc::mbar_wait(&mbar[1], par, kWaitLimit))) {
-      ok = false;
-      break;
+  } else {   // three rounds through one pair of tile buffers
+    for (int round = 0; round < 3; ++round) {
+      const unsigned char *a = (round == 2 ? lo : hi) + sub;
+      const unsigned char *b = (round == 1 ? lo : hi) + sub;
+      const uint32_t par = (uint32_t)(round & 1);
+      if (tid == 0) {
+        tc::mbar_expect_tx(&mbar[0], abytes + bbytes);
+        tc::bulk_g2s(Aim, a + arow, abytes, &mbar[0]);
+        tc::bulk_g2s(Bim, b + brow, bbytes, &mbar[0]);
+      }
+      if (__syncthreads_or(!tc::mbar_wait(&mbar[0], par, kWaitLimit))) {
+        if (tid == 0) tc::mbar_wait(&mbar[0], par, kWaitLimit);   // drain copies in flight (bounded)
+        ok = false;
+        break;
+      }
+      if (tid == 0) {
+        tc::fence_after();
+        mma_tiles(Aim, Bim, round > 0);
+        tc::mma_commit(&mbar[1]);
+      }
+      // the products have read the operands: the next round may overwrite them
+      if (__syncthreads_or(!tc::mbar_wait(&mbar[1], par, kWaitLimit))) {
+        ok = false;
+        break;
+      }
     }
   }
   tc::fence_after();
@@ -402,13 +434,15 @@ cudaError_t launch_gram_tc(const void *hi, const void *lo, int K, int m, int L, 
                            cudaStream_t st) {
   if (L <= 0) return cudaSuccess;
   const int Kp = round16(K), mp = round16(m);
-  const size_t smem = tc::smem_for_tmem((size_t)(128 + kGramNG) * mp * 2 + 64, kGramNG);
+  const size_t tile = (size_t)128 * mp * 2;
+  const bool all4 = 4 * tile + 64 <= 200 * 1024;   // the four tiles fit: one round of loads
+  const size_t smem = tc::smem_for_tmem((all4 ? 4 : 2) * tile + 64, kGramNG);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((Kp + 127) / 128, (Kp + kGramNG - 1) / kGramNG, L);
   gram_tc_kernel<<<grid, 128, smem, st>>>(static_cast<const unsigned char *>(hi),
-                                          static_cast<const unsigned char *>(lo), K, Kp, mp, G, err);
+                                          static_cast<const unsigned char *>(lo), K, Kp, mp, all4, G, err);
   return cudaGetLastError();
 }
 
