@@ -235,7 +235,10 @@ sdl_status sdl_sq_error(sdl_ctx *ctx, sdl_precision prec, const void *a, const v
 typedef struct sdl_proposer sdl_proposer;
 
 /* Create a proposer with initial parameters `params` (device, packed as above).
- * h1, h2, K multiples of 8; 1 <= m <= 256; K <= 1024.  Synchronises. */
+ * m is the input size: the signal length for a proposer that reads signals,
+ * the atom count K for one that reads correlation features |D^T y| (see
+ * sdl_corr_features).  h1, h2, K multiples of 8; 1 <= m <= 1024; K <= 1024.
+ * Synchronises. */
 sdl_status sdl_proposer_create(sdl_ctx *ctx, int m, int h1, int h2, int K, const float *params,
                                sdl_proposer **out);
 sdl_status sdl_proposer_destroy(sdl_proposer *p);
@@ -262,6 +265,38 @@ sdl_status sdl_proposer_scores(sdl_ctx *ctx, sdl_proposer *p, const float *Y, in
 sdl_status sdl_omp_proposed(sdl_ctx *ctx, sdl_proposer *p, const float *D, int m, int K, const float *Y,
                             int64_t n, int s, int ncand, double eps_fb, int32_t *idx, float *val,
                             int32_t *nnz, float *resid2, int64_t *n_fallback);
+
+/* Correlation features (the input of a dictionary-conditioned proposer, which
+ * reads |D_t^T y| instead of y so that one network serves every dictionary of a
+ * batch): F[i][j] = |<d_(t(i), j), y_i>| for signal i of subset t(i), each an
+ * ordered chain of FP32 FMAs over the m entries (the correlation of OMP's first
+ * step, Sec. 1, before the argmax).
+ *   D        device float [L][K][m] (row-major, atoms as rows), 16-byte aligned
+ *   Y        device float [n][m], n = offsets[L]; offsets host int64 [L+1] as in
+ *            sdl_omp_batched (empty subsets allowed)
+ *   F        device float [n][K] out, 16-byte aligned
+ * 1 <= m <= 256, 1 <= K <= 1024.  Errors: SDL_EINVAL on bad sizes, offsets or
+ * pointers (nothing is written).  Does not synchronise beyond the upload of the
+ * offsets. */
+sdl_status sdl_corr_features(sdl_ctx *ctx, const float *D, int m, int K, const float *Y, const int64_t *offsets,
+                             int L, float *F);
+
+/* Proposer input for sdl_omp_proposed_batched. */
+#define SDL_FEATURES_SIGNAL 0   /* the proposer reads y (m inputs) */
+#define SDL_FEATURES_CORR 1     /* the proposer reads |D_t^T y| (K inputs) */
+
+/* Proposer-assisted OMP over L subsets, each coded against its own dictionary
+ * D_t (FP32 data): candidates are the top `ncand` atoms of the proposer's scores
+ * of y (SDL_FEATURES_SIGNAL) or of |D_t^T y| (SDL_FEATURES_CORR; one network
+ * for every dictionary), OMP runs over them with D_t's Gram and refits on the
+ * support, and each signal whose residual norm exceeds eps_fb is recoded by the
+ * full OMP of sdl_omp_batched against its own D_t.  D, m, K, Y, offsets, L, s
+ * and the outputs as sdl_omp_batched (eps = 0); ncand, eps_fb, *n_fallback as
+ * sdl_omp_proposed.  The proposer must have K outputs and m (signal) or K
+ * (correlation) inputs.  Synchronises once. */
+sdl_status sdl_omp_proposed_batched(sdl_ctx *ctx, sdl_proposer *p, int features, const float *D, int m, int K,
+                                    const float *Y, const int64_t *offsets, int L, int s, int ncand, double eps_fb,
+                                    int32_t *idx, float *val, int32_t *nnz, float *resid2, int64_t *n_fallback);
 
 /* OMP without any allocation (the paper has no counterpart: this is a service
  * entry point).  For callers that cannot call cudaMalloc where they code signals:

@@ -19,6 +19,9 @@ Readings of the paper fixed here (Sec. 1, 2, 3.1, Algorithm 1):
     update, atoms used by fewer than min_use signals become the worst-coded
     training signals, normalised.  Parity unpinned against the paper, which has
     no such step: its pins are hand-worked cases and the definition above.
+  * Dictionary-conditioned proposer input (not in the paper): |D_t^T y| of each
+    signal against its own subset's dictionary, the magnitudes OMP's first
+    greedy step ranks.
 """
 from __future__ import annotations
 
@@ -78,10 +81,11 @@ def _load():
             lib.orc_mlp_loss_grad.argtypes = [_dp, i32, i32, i32, i32, _dp, _ip, i32, i64, _dp, _dp]
             lib.orc_extract_patches.argtypes = [_dp, i32, i32, i32, _dp]
             lib.orc_patch_average.argtypes = [_dp, i32, _ip, _dp, i32, i32, i32, i32, _dp]
+            lib.orc_corr_features.argtypes = [_dp, i32, i32, _dp, _lp, i32, _dp]
             for f in ("orc_omp", "orc_mod", "orc_train", "orc_split", "orc_local_train",
                       "orc_merge", "orc_residual", "orc_recovery", "orc_mlp_forward",
                       "orc_mlp_loss_grad", "orc_extract_patches", "orc_patch_average",
-                      "orc_replace_atoms"):
+                      "orc_replace_atoms", "orc_corr_features"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -257,6 +261,18 @@ def recovery(D0, D, thresh=0.98):
     _check(lib.orc_recovery(_d(D0), D0.shape[0], _d(D), D.shape[0], D.shape[1], float(thresh),
                             ctypes.byref(c)), "orc_recovery")
     return c.value
+
+
+def corr_features(D, offsets, Y):
+    """|d_(t,j)^T y_i| of every row i of Y against the dictionary D[t] (D: (L, K, m))
+    of its subset (rows offsets[t] .. offsets[t+1]-1): shape (n, K)."""
+    lib = _load()
+    D, Y = _f64(D), _f64(Y)
+    L, K, m = D.shape
+    off = np.ascontiguousarray(offsets, np.int64)
+    F = np.empty((Y.shape[0], K))
+    _check(lib.orc_corr_features(_d(D), m, K, _d(Y), _l(off), L, _d(F)), "orc_corr_features")
+    return F
 
 
 def mlp_sizes(m, h1, h2, K):

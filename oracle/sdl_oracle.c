@@ -401,6 +401,18 @@ int orc_recovery(const double *D0, int K0, const double *D, int K, int m,
   return 0;
 }
 
+int orc_corr_features(const double *D, int m, int K, const double *Y, const int64_t *offsets, int L,
+                      double *F) {
+  if (m <= 0 || K <= 0 || L <= 0 || !D || !offsets || (offsets[L] > 0 && (!Y || !F))) return 1;
+  for (int t = 0; t < L; ++t) {
+    if (offsets[t + 1] < offsets[t]) return 1;
+    const double *Dt = D + (size_t)t * K * m;
+    for (int64_t i = offsets[t]; i < offsets[t + 1]; ++i)
+      for (int j = 0; j < K; ++j) F[(size_t)i * K + j] = fabs(dot(Dt + (size_t)j * m, Y + (size_t)i * m, m));
+  }
+  return 0;
+}
+
 /* ------------------------------------------------------- MLP proposer --- */
 
 static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }

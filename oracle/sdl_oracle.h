@@ -102,6 +102,13 @@ int orc_residual(const double *Y, int m, int64_t n, const double *D, int K,
 int orc_recovery(const double *D0, int K0, const double *D, int K, int m,
                  double thresh, int *count);
 
+/* Input of a dictionary-conditioned support proposer (an extension beyond the
+ * paper): F[i][j] = |d_(t,j)^T y_i| for every signal i of subset t (rows
+ * offsets[t] .. offsets[t+1]-1 of Y), D [L][K][m].  These are the magnitudes
+ * OMP's first greedy step ranks (Sec. 1), written out as plain dot products. */
+int orc_corr_features(const double *D, int m, int K, const double *Y, const int64_t *offsets, int L,
+                      double *F);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,7 +90,11 @@ _SIGS = {
     "sdl_proposer_scores": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "sdl_omp_proposed": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp,
                                 ctypes.POINTER(_i64)]),
+    "sdl_corr_features": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _i32, _vp]),
+    "sdl_omp_proposed_batched": (_i32, [_vp, _vp, _i32, _vp, _i32, _i32, _vp, _vp, _i32, _i32, _i32, _dbl, _vp, _vp,
+                                        _vp, _vp, ctypes.POINTER(_i64)]),
 }
+FEATURES_SIGNAL, FEATURES_CORR = 0, 1
 OPT_MOD_SOLVE, OPT_CLUSTER, OPT_MOD_TILE, OPT_AUTOTUNE, OPT_GRAPH, OPT_SM_BLOCKS, OPT_REPLACE = 1, 2, 3, 4, 5, 6, 7
 OPT_OMP_FORM = 8
 
@@ -164,6 +168,24 @@ class Context:
 
     def workspace_bytes(self) -> int:
         return int(lib().sdl_workspace_bytes(self.handle))
+
+    def omp_batched(self, D, Y, offsets, s, ncand, eps_fb, features=FEATURES_CORR, with_resid=True):
+        """Proposer-assisted OMP over subsets (D: (L, K, m)), the network reading
+        |D_t^T y| (FEATURES_CORR) or y (FEATURES_SIGNAL); returns (idx, val, nnz,
+        resid2, n_fallback)."""
+        import torch
+        L, K, m = D.shape
+        n = Y.shape[0]
+        oh, op = _offsets_host(offsets)
+        assert len(oh) == L + 1 and oh[-1] == n
+        idx = torch.empty((n, s), dtype=torch.int32, device=self.device)
+        val = torch.empty((n, s), dtype=torch.float32, device=self.device)
+        nnz = torch.empty((n,), dtype=torch.int32, device=self.device)
+        r2 = torch.empty((n,), dtype=torch.float32, device=self.device) if with_resid else None
+        nf = ctypes.c_int64(0)
+        _call("sdl_omp_proposed_batched", self.ctx.bind_stream(), self.handle, features, _ptr(D), m, K, _ptr(Y), op,
+              L, s, ncand, float(eps_fb), _ptr(idx), _ptr(val), _ptr(nnz), _ptr(r2), ctypes.byref(nf))
+        return idx, val, nnz, r2, int(nf.value)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -411,6 +433,20 @@ def denoise(noisy, D, p, eps, s_max=32, prec=None):
     return patch_average(D, idx, val, H, W, p, prec=None if prec == PREC_BF16 else prec), (idx, val, nnz)
 
 
+def corr_features(D, Y, offsets):
+    """|D_t^T y| of every row of Y against its subset's dictionary (D: (L, K, m),
+    FP32), shape (n, K): the input of a dictionary-conditioned proposer."""
+    import torch
+    L, K, m = D.shape
+    n = Y.shape[0]
+    oh, op = _offsets_host(offsets)
+    assert len(oh) == L + 1 and oh[-1] == n
+    F = torch.empty((n, K), dtype=torch.float32, device=D.device)
+    ctx = context(D.device.index)
+    _call("sdl_corr_features", ctx.bind_stream(), _ptr(D), m, K, _ptr(Y), op, L, _ptr(F))
+    return F
+
+
 def gram(D, prec=None):
     """Gram matrices of D (L, K, m) or (K, m): D_t D_t^T, shape (L, K, K) or (K, K)."""
     import torch
@@ -488,6 +524,24 @@ class Proposer:
         nf = ctypes.c_int64(0)
         _call("sdl_omp_proposed", self.ctx.bind_stream(), self.handle, _ptr(D), m, K, _ptr(Y), n, s, ncand,
               float(eps_fb), _ptr(idx), _ptr(val), _ptr(nnz), _ptr(r2), ctypes.byref(nf))
+        return idx, val, nnz, r2, int(nf.value)
+
+    def omp_batched(self, D, Y, offsets, s, ncand, eps_fb, features=FEATURES_CORR, with_resid=True):
+        """Proposer-assisted OMP over subsets (D: (L, K, m)), the network reading
+        |D_t^T y| (FEATURES_CORR) or y (FEATURES_SIGNAL); returns (idx, val, nnz,
+        resid2, n_fallback)."""
+        import torch
+        L, K, m = D.shape
+        n = Y.shape[0]
+        oh, op = _offsets_host(offsets)
+        assert len(oh) == L + 1 and oh[-1] == n
+        idx = torch.empty((n, s), dtype=torch.int32, device=self.device)
+        val = torch.empty((n, s), dtype=torch.float32, device=self.device)
+        nnz = torch.empty((n,), dtype=torch.int32, device=self.device)
+        r2 = torch.empty((n,), dtype=torch.float32, device=self.device) if with_resid else None
+        nf = ctypes.c_int64(0)
+        _call("sdl_omp_proposed_batched", self.ctx.bind_stream(), self.handle, features, _ptr(D), m, K, _ptr(Y), op,
+              L, s, ncand, float(eps_fb), _ptr(idx), _ptr(val), _ptr(nnz), _ptr(r2), ctypes.byref(nf))
         return idx, val, nnz, r2, int(nf.value)
 
     def close(self):

@@ -1116,7 +1116,8 @@ sdl_status sdl_omp_proposed(sdl_ctx *ctx, sdl_proposer *p, const float *D, int m
   SDL_CUDA(timed(ctx, "proposer_topk", 4, [&] { return proposer_topk(p, Y, n, ncand, cand, sm); }), "proposer scores");
   SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<float>(D, m, K, 1, G, sm); }), "gram");
   SDL_CUDA(timed(ctx, "omp_restricted", 1, [&] {
-             return launch_romp(D, G, m, K, Y, n, s, ncand, cand, (float)eps_fb, idx, val, nnz, r2, flag, sm);
+             return launch_romp(D, G, m, K, Y, n, s, ncand, cand, (float)eps_fb, idx, val, nnz, r2, flag, nullptr, 1,
+                                sm);
            }), "restricted omp");
   SDL_CUDA(timed(ctx, "fallback_compact", 1, [&] { return launch_compact(flag, n, list, count, sm); }), "compact");
   SDL_CUDA(cudaMemcpyAsync(ctx->h_status, count, sizeof(int32_t), cudaMemcpyDeviceToHost, sm), "count read");
@@ -1139,6 +1140,159 @@ sdl_status sdl_omp_proposed(sdl_ctx *ctx, sdl_proposer *p, const float *D, int m
   SDL_CUDA(timed(ctx, "omp", 1, [&] { return launch_omp<float>(a, ctx->num_sms, sm); }), "fallback omp");
   SDL_CUDA(timed(ctx, "fallback_scatter", 1, [&] {
              return launch_scatter_codes(list, count, nf, s, fi, fv, fn, fr, idx, val, nnz, resid2, sm);
+           }), "scatter");
+  return SDL_OK;
+}
+
+sdl_status sdl_corr_features(sdl_ctx *ctx, const float *D, int m, int K, const float *Y, const int64_t *offsets,
+                             int L, float *F) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  SDL_REQUIRE(m >= 1 && m <= kMaxM, "m must be in [1, 256]");
+  SDL_REQUIRE(K >= 1 && K <= kMaxK, "K must be in [1, 1024]");
+  if ((st = check_offsets(ctx, offsets, L, false)) != SDL_OK) return st;
+  const int64_t n = offsets[L];
+  if (n == 0) return SDL_OK;
+  SDL_REQUIRE(aligned16(D) && aligned16(Y) && aligned16(F), "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  if ((st = ws_reserve(ctx, 2 * round256(sizeof(int64_t) * (L + 1)) + 1024)) != SDL_OK) return st;
+  OmpArgs a{};
+  int64_t *d_off = nullptr;
+  int32_t *d_tiles = nullptr;
+  int64_t tiles = 0;
+  if ((st = upload_plan(ctx, offsets, L, 128, &d_off, &d_tiles, &tiles)) != SDL_OK) return st;
+  a.D = D; a.Y = Y; a.offsets = d_off; a.tile_start = d_tiles; a.total_tiles = tiles;
+  a.L = L; a.m = m; a.K = K;
+  SDL_CUDA(timed(ctx, "corr_features", 1, [&] { return launch_corr_features(a, 0, tiles, 0, F, ctx->stream); }),
+           "correlation features");
+  return SDL_OK;
+}
+
+sdl_status sdl_omp_proposed_batched(sdl_ctx *ctx, sdl_proposer *p, int features, const float *D, int m, int K,
+                                    const float *Y, const int64_t *offsets, int L, int s, int ncand, double eps_fb,
+                                    int32_t *idx, float *val, int32_t *nnz, float *resid2, int64_t *n_fallback) {
+  if (!ctx) return SDL_EINVAL;
+  ctx->err.clear();
+  sdl_status st;
+  SDL_REQUIRE(p != nullptr && n_fallback != nullptr, "proposer and n_fallback must be given");
+  SDL_REQUIRE(features == SDL_FEATURES_SIGNAL || features == SDL_FEATURES_CORR,
+              "features must be SDL_FEATURES_SIGNAL or SDL_FEATURES_CORR");
+  if ((st = check_omp_shape(ctx, m, K, s, 0.0)) != SDL_OK) return st;
+  const bool corr = features == SDL_FEATURES_CORR;
+  SDL_REQUIRE(proposer_m(p) == (corr ? K : m) && proposer_K(p) == K,
+              "the proposer's sizes do not match: K outputs and m (signal) or K (correlation) inputs");
+  SDL_REQUIRE(ncand >= s && ncand <= 32 && ncand <= K, "ncand must be in [s, min(32, K)]");
+  SDL_REQUIRE(eps_fb >= 0.0 && isfinite(eps_fb), "eps_fb must be finite and >= 0");
+  if ((st = check_offsets(ctx, offsets, L, false)) != SDL_OK) return st;
+  *n_fallback = 0;
+  const int64_t n = offsets[L];
+  if (n == 0) return SDL_OK;
+  SDL_REQUIRE(aligned16(D) && aligned16(Y) && aligned16(idx) && aligned16(val) && aligned16(nnz) &&
+                  (resid2 == nullptr || aligned16(resid2)),
+              "device pointers must be non-NULL and 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  SDL_REQUIRE(g.ok, "cannot select the context device");
+  const bool split = omp_split_f32(ctx, K, m, s);
+  const int ftile = split ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
+  // correlation features are formed per chunk of 512 tiles of 128 signals
+  const int64_t kChunkTiles = 512;
+  const int64_t frows = corr ? (n < kChunkTiles * 128 ? n : kChunkTiles * 128) : 0;
+  const size_t plan_b = round256(sizeof(int64_t) * (L + 1)) + round256(sizeof(int32_t) * (L + 1));
+  const size_t need = round256(sizeof(float) * (size_t)L * K * K) + round256(sizeof(int32_t) * (size_t)n * ncand) +
+                      4 * round256(sizeof(int32_t) * (size_t)n) + round256(sizeof(int32_t) * (size_t)(2 * L + 1)) +
+                      round256(sizeof(float) * (size_t)n * m) + 2 * round256(sizeof(int32_t) * (size_t)n * s) +
+                      round256(sizeof(float) * (size_t)frows * K) + (split ? round256(tc_a0_bytes(L, K, n)) : 0) +
+                      2 * plan_b + 4096;
+  if ((st = ws_reserve(ctx, need)) != SDL_OK) return st;
+  int64_t *d_off = nullptr;
+  int32_t *d_tiles = nullptr;
+  int64_t tiles = 0;
+  if ((st = upload_plan(ctx, offsets, L, 128, &d_off, &d_tiles, &tiles)) != SDL_OK) return st;
+  float *G = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)L * K * K));
+  int32_t *cand = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * ncand));
+  int32_t *flag = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n));
+  int32_t *list = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n));
+  int32_t *fn = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n));
+  float *fr = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)n));
+  int32_t *cnt = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)(2 * L + 1)));
+  float *Yf = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)n * m));
+  int32_t *fi = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * s));
+  float *fv = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)n * s));
+  float *F = corr ? static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)frows * K)) : nullptr;
+  float *a0c = split ? static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n))) : nullptr;
+  if (!G || !cand || !flag || !list || !fn || !fr || !cnt || !Yf || !fi || !fv || (corr && !F) || (split && !a0c))
+    return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  int32_t *pos = cnt + L + 1;
+  float *r2 = resid2 ? resid2 : fr;
+  cudaStream_t sm = ctx->stream;
+  if (!corr) {
+    SDL_CUDA(timed(ctx, "proposer_topk", 5 * (int)((n + 65535) / 65536),
+                   [&] { return proposer_topk(p, Y, n, ncand, cand, sm); }), "proposer scores");
+  } else {
+    // the rows of consecutive tiles are consecutive rows of Y
+    const TilePlan plan = make_tiles(offsets, L, 128);
+    auto subset_of_tile = [&](int64_t gt) {
+      int lo = 0, hi = L - 1;   // largest t with tile_start[t] <= gt
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (plan.tile_start[mid] <= gt) lo = mid; else hi = mid - 1;
+      }
+      return lo;
+    };
+    OmpArgs fa{};
+    fa.D = D; fa.Y = Y; fa.offsets = d_off; fa.tile_start = d_tiles; fa.total_tiles = tiles;
+    fa.L = L; fa.m = m; fa.K = K;
+    for (int64_t g0 = 0; g0 < tiles; g0 += kChunkTiles) {
+      const int64_t g1 = tiles - g0 < kChunkTiles ? tiles : g0 + kChunkTiles;
+      const int t0 = subset_of_tile(g0), t1 = subset_of_tile(g1 - 1);
+      const int64_t r0 = offsets[t0] + (g0 - plan.tile_start[t0]) * 128;
+      const int64_t e1 = offsets[t1] + (g1 - plan.tile_start[t1]) * 128;
+      const int64_t r1 = e1 < offsets[t1 + 1] ? e1 : offsets[t1 + 1];
+      SDL_CUDA(timed(ctx, "corr_features", 1, [&] { return launch_corr_features(fa, g0, g1 - g0, r0, F, sm); }),
+               "correlation features");
+      SDL_CUDA(timed(ctx, "proposer_topk", 5, [&] { return proposer_topk(p, F, r1 - r0, ncand, cand + r0 * ncand, sm); }),
+               "proposer scores");
+    }
+  }
+  SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<float>(D, m, K, L, G, sm); }), "gram");
+  SDL_CUDA(timed(ctx, "omp_restricted", 1, [&] {
+             return launch_romp(D, G, m, K, Y, n, s, ncand, cand, (float)eps_fb, idx, val, nnz, r2, flag, d_off, L,
+                                sm);
+           }), "restricted omp");
+  SDL_CUDA(timed(ctx, "fallback_compact", 1, [&] { return launch_count_flags(flag, d_off, L, n, cnt, sm); }),
+           "fallback count");
+  std::vector<int32_t> hc((size_t)L + 1);
+  SDL_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * (L + 1), cudaMemcpyDeviceToHost, sm), "count read");
+  SDL_CUDA(cudaStreamSynchronize(sm), "count sync");
+  const int64_t nf = hc[L];
+  *n_fallback = nf;
+  if (nf == 0) return SDL_OK;
+  // full OMP on the flagged signals of each subset against its own dictionary
+  std::vector<int64_t> fo((size_t)L + 1, 0);
+  for (int t = 0; t < L; ++t) fo[t + 1] = fo[t] + hc[t];
+  if (fo[L] != nf) return set_error(ctx, SDL_EINVAL, "fallback counts are inconsistent");
+  int64_t *d_foff = nullptr;
+  int32_t *d_ftiles = nullptr;
+  int64_t ftiles = 0;
+  if ((st = upload_plan(ctx, fo.data(), L, ftile, &d_foff, &d_ftiles, &ftiles)) != SDL_OK) return st;
+  SDL_CUDA(timed(ctx, "fallback_compact", 1,
+                 [&] { return launch_place_flags(flag, d_off, L, n, d_foff, pos, list, sm); }), "fallback place");
+  SDL_CUDA(timed(ctx, "fallback_gather", 1, [&] { return launch_gather_rows(Y, m, list, cnt + L, nf, Yf, sm); }),
+           "gather");
+  OmpArgs a{};
+  a.D = D; a.G = G; a.Y = Yf; a.offsets = d_foff; a.tile_start = d_ftiles; a.total_tiles = ftiles;
+  a.L = L; a.m = m; a.K = K; a.s = s; a.eps = 0.0;
+  a.idx = fi; a.val = fv; a.nnz = fn; a.resid2 = fr;
+  if (split) {
+    SDL_CUDA(timed(ctx, "omp_split", split_kernels(a), [&] { return launch_omp_split_f32(a, a0c, sm); }),
+             "fallback omp");
+  } else {
+    SDL_CUDA(timed(ctx, "omp", 1, [&] { return launch_omp<float>(a, ctx->num_sms, sm); }), "fallback omp");
+  }
+  SDL_CUDA(timed(ctx, "fallback_scatter", 1, [&] {
+             return launch_scatter_codes(list, cnt + L, nf, s, fi, fv, fn, fr, idx, val, nnz, resid2, sm);
            }), "scatter");
   return SDL_OK;
 }

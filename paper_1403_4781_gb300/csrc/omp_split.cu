@@ -29,7 +29,8 @@ constexpr int kGPitch = 132;  // staged row pitch (floats): 16-byte aligned rows
 // an 8 x 8 register tile fed by four 16-byte shared-memory reads per entry.
 // Stages of 16 entries are double-buffered, the next stage's global loads held
 // in registers during the products.  Each product is an ordered chain of FP32
-// FMAs over the entries, as in the fused OMP kernel.
+// FMAs over the entries, as in the fused OMP kernel.  kAbs: store |product|.
+template <bool kAbs = false>
 __device__ __forceinline__ void tile_products(const float *__restrict__ Yt, int nsig, const float *__restrict__ Dt,
                                               int K, int m, int j0, float *out, int64_t ldo) {
   __shared__ __align__(16) float Ys[2][kGK][kGPitch];
@@ -101,6 +102,12 @@ __device__ __forceinline__ void tile_products(const float *__restrict__ Yt, int 
     __syncthreads();
   }
 
+  if (kAbs) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[r][c] = fabsf(acc[r][c]);
+  }
   const bool vstore = (K & 3) == 0 && (ldo & 3) == 0;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
@@ -139,6 +146,24 @@ __global__ void __launch_bounds__(kGThreads) corr_f32_kernel(OmpArgs a, float *a
                 a0c + (size_t)(g - tile0) * kGM * K, K);
 }
 
+// Correlation features F[i][j] = |<d_(t(i), j), y_i>| of every signal against
+// its own subset's dictionary (the input of a dictionary-conditioned support
+// proposer): the same tile products, stored as absolute values straight into
+// row i - row_base of F (pitch K), no scratch.
+__global__ void __launch_bounds__(kGThreads) corr_abs_kernel(OmpArgs a, float *F, int64_t tile0, int64_t row_base,
+                                                              int nb) {
+  const int K = a.K, m = a.m;
+  const int64_t g = tile0 + blockIdx.x / nb;
+  const int t = find_subset(a.tile_start, a.L, g);
+  const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)kGM;
+  const int64_t rows_left = a.offsets[t + 1] - row0;
+  const int nsig = rows_left < kGM ? (int)rows_left : kGM;
+  const int j0 = (int)(blockIdx.x % nb) * kGN;
+  tile_products<true>(static_cast<const float *>(a.Y) + (size_t)row0 * m, nsig,
+                      static_cast<const float *>(a.D) + (size_t)t * K * m, K, m, j0,
+                      F + (size_t)(row0 - row_base) * K, K);
+}
+
 // The Gram matrices G_t = D_t D_t^T of L dictionaries [L][K][m] into [L][K][K]:
 // the same tile products with the atoms of D_t as the rows.  Block b covers
 // subset b / (nt nb), row tile (b / nb) mod nt and atom block b mod nb.
@@ -160,6 +185,14 @@ cudaError_t launch_gram_f32_tiles(const float *D, int m, int K, int L, float *G,
   if (L <= 0) return cudaSuccess;
   const int nt = (K + kGM - 1) / kGM, nb = (K + kGN - 1) / kGN;
   gram_f32_kernel<<<(unsigned)((int64_t)L * nt * nb), kGThreads, 0, st>>>(D, K, m, nt, nb, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corr_features(const OmpArgs &a, int64_t tile0, int64_t ntile, int64_t row_base, float *F,
+                                 cudaStream_t st) {
+  if (ntile <= 0) return cudaSuccess;
+  const int nb = (a.K + kGN - 1) / kGN;
+  corr_abs_kernel<<<(unsigned)(ntile * nb), kGThreads, 0, st>>>(a, F, tile0, row_base, nb);
   return cudaGetLastError();
 }
 

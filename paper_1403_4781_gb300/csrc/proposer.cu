@@ -272,12 +272,27 @@ __global__ void topk_kernel(const float *__restrict__ Z, int64_t n, int K, int c
   }
 }
 
+// Subset of row i under offsets [L+1]: the largest t with offsets[t] <= i (an
+// empty subset never qualifies, since the next one starts at the same row).
+__device__ __forceinline__ int subset_of_row(const int64_t *__restrict__ offsets, int L, int64_t i) {
+  int lo = 0, hi = L - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (offsets[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // OMP restricted to c candidate atoms (lane j < c holds candidate j), Batch-OMP
 // with the FP32 Gram of D, exact refit and one correction step on the support;
 // flags signals whose residual norm exceeds eps_fb for the full-OMP fallback.
+// offsets (device [L+1], or null for one dictionary): signal i is coded
+// against dictionary t(i) of D [L][K][m] with Gram G [L][K][K], and its
+// candidates are atom indices of that dictionary.
 __global__ void romp_kernel(const float *__restrict__ D, const float *__restrict__ G, int m, int K,
                             const float *__restrict__ Y, int64_t n, int s, int c, const int32_t *__restrict__ cand,
-                            float eps_fb, int32_t *idx, float *val, int32_t *nnz, float *resid2, int32_t *flag) {
+                            float eps_fb, int32_t *idx, float *val, int32_t *nnz, float *resid2, int32_t *flag,
+                            const int64_t *__restrict__ offsets, int L) {
   extern __shared__ __align__(16) float Lshared[];
   using namespace omp_detail;
   constexpr int M32 = kMaxM / 32;
@@ -285,6 +300,11 @@ __global__ void romp_kernel(const float *__restrict__ D, const float *__restrict
   const int lane = threadIdx.x & 31;
   if (warp_g >= n) return;
   const int64_t b = warp_g;
+  if (offsets) {
+    const int t = subset_of_row(offsets, L, b);
+    D += (size_t)t * K * m;
+    G += (size_t)t * K * K;
+  }
   const int lp = odd_pitch(s);
   float *Ls = Lshared + (size_t)(threadIdx.x >> 5) * s * lp;   // per-warp factor scratch
   const int mu = (m + 31) >> 5;
@@ -366,6 +386,49 @@ __global__ void romp_kernel(const float *__restrict__ D, const float *__restrict
 __global__ void compact_kernel(const int32_t *__restrict__ flag, int64_t n, int32_t *list, int32_t *count) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
     if (flag[q]) list[atomicAdd(count, 1)] = (int32_t)q;
+}
+
+// Fallback signals grouped by subset.  Pass 1 counts the flagged signals of
+// each subset into cnt[t] and their total into cnt[L]; pass 2 places flagged
+// signal i at list[foff[t] + k], k its arrival rank within subset t (the order
+// inside a subset is free: every signal is coded on its own).  The lanes of a
+// warp that flag signals of one subset share one atomic (rows of a warp are
+// consecutive, so they are nearly always in one subset).
+__global__ void count_flags_kernel(const int32_t *__restrict__ flag, const int64_t *__restrict__ offsets, int L,
+                                   int64_t n, int32_t *cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n_up = (n + 31) / 32 * 32;    // whole warps stay in the loop together
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_up; q += stride) {
+    const bool f = q < n && flag[q] != 0;
+    const unsigned act = __ballot_sync(0xffffffffu, f);
+    if (f) {
+      const int t = subset_of_row(offsets, L, q);
+      const unsigned grp = __match_any_sync(act, t);
+      if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&cnt[t], __popc(grp));
+    }
+    if ((threadIdx.x & 31) == 0 && act) atomicAdd(&cnt[L], __popc(act));
+  }
+}
+
+__global__ void place_flags_kernel(const int32_t *__restrict__ flag, const int64_t *__restrict__ offsets, int L,
+                                   int64_t n, const int64_t *__restrict__ foff, int32_t *pos, int32_t *list) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n_up = (n + 31) / 32 * 32;
+  const int lane = threadIdx.x & 31;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_up; q += stride) {
+    const bool f = q < n && flag[q] != 0;
+    const unsigned act = __ballot_sync(0xffffffffu, f);
+    if (f) {
+      const int t = subset_of_row(offsets, L, q);
+      const unsigned grp = __match_any_sync(act, t);
+      const int leader = __ffs(grp) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(&pos[t], __popc(grp));
+      base = __shfl_sync(grp, base, leader);
+      const int rank = __popc(grp & ((1u << lane) - 1u));
+      list[foff[t] + base + rank] = (int32_t)q;
+    }
+  }
 }
 
 __global__ void gather_rows_kernel(const float *__restrict__ Y, int m, const int32_t *__restrict__ list,
@@ -583,8 +646,8 @@ sdl_status sdl_proposer_create(sdl_ctx *ctx, int m, int h1, int h2, int K, const
                                sdl_proposer **out) {
   if (!ctx || !out) return SDL_EINVAL;
   *out = nullptr;
-  if (m < 1 || m > kMaxM || h1 < 8 || h2 < 8 || K < 1 || K > kMaxK || h1 % 8 || h2 % 8 || K % 8)
-    return perr(ctx, SDL_EINVAL, "proposer sizes: 1 <= m <= 256, h1, h2 multiples of 8, K <= 1024 multiple of 8");
+  if (m < 1 || m > kMaxK || h1 < 8 || h2 < 8 || K < 1 || K > kMaxK || h1 % 8 || h2 % 8 || K % 8)
+    return perr(ctx, SDL_EINVAL, "proposer sizes: 1 <= m <= 1024, h1, h2 multiples of 8, K <= 1024 multiple of 8");
   if (!al16(params)) return perr(ctx, SDL_EINVAL, "params must be a 16-byte aligned device pointer");
   sdl_proposer *p = new sdl_proposer();
   p->device = ctx->device;
@@ -707,12 +770,30 @@ cudaError_t proposer_topk(sdl_proposer *p, const float *Y, int64_t n, int c, int
 
 cudaError_t launch_romp(const float *D, const float *G, int m, int K, const float *Y, int64_t n, int s, int c,
                         const int32_t *cand, float eps_fb, int32_t *idx, float *val, int32_t *nnz, float *resid2,
-                        int32_t *flag, cudaStream_t st) {
+                        int32_t *flag, const int64_t *offsets, int L, cudaStream_t st) {
   using namespace prop;
   if (n <= 0) return cudaSuccess;
   const size_t smem = sizeof(float) * 8 * (size_t)s * omp_detail::odd_pitch(s);
   romp_kernel<<<nblocks(n, 8, 1u << 30), 256, smem, st>>>(D, G, m, K, Y, n, s, c, cand, eps_fb, idx, val, nnz,
-                                                           resid2, flag);
+                                                           resid2, flag, offsets, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_flags(const int32_t *flag, const int64_t *offsets, int L, int64_t n, int32_t *cnt,
+                               cudaStream_t st) {
+  using namespace prop;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (L + 1), st);
+  if (e != cudaSuccess || n <= 0) return e;
+  count_flags_kernel<<<nblocks(n, 256, 4096), 256, 0, st>>>(flag, offsets, L, n, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_place_flags(const int32_t *flag, const int64_t *offsets, int L, int64_t n, const int64_t *foff,
+                               int32_t *pos, int32_t *list, cudaStream_t st) {
+  using namespace prop;
+  cudaError_t e = cudaMemsetAsync(pos, 0, sizeof(int32_t) * L, st);
+  if (e != cudaSuccess || n <= 0) return e;
+  place_flags_kernel<<<nblocks(n, 256, 4096), 256, 0, st>>>(flag, offsets, L, n, foff, pos, list);
   return cudaGetLastError();
 }
 

@@ -155,6 +155,10 @@ cudaError_t launch_omp_split_f32(const OmpArgs &a, float *a0c, cudaStream_t st);
 // (used by launch_gram<float> when there are enough blocks to fill the GPU).
 cudaError_t launch_gram_f32_tiles(const float *D, int m, int K, int L, float *G, cudaStream_t st);
 int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles);
+// Correlation features F = |D_t^T y| (FP32 FMA chains) of the 128-signal tiles
+// tile0 .. tile0+ntile-1 of the plan; signal row r goes to row r - row_base of F.
+cudaError_t launch_corr_features(const OmpArgs &a, int64_t tile0, int64_t ntile, int64_t row_base, float *F,
+                                 cudaStream_t st);
 
 struct ModArgs {
   const void *Y;          // [n][m]
@@ -248,9 +252,16 @@ int proposer_K(const sdl_proposer *p);
 // Scores of n signals (chunked forward passes) and their top-c atoms cand [n][c].
 cudaError_t proposer_topk(sdl_proposer *p, const float *Y, int64_t n, int c, int32_t *cand, cudaStream_t st);
 // OMP restricted to the candidates; flag[i] = 1 where ||r|| > eps_fb.
+// offsets (device [L+1]) null: one dictionary; else signal i uses D_t(i), G_t(i).
 cudaError_t launch_romp(const float *D, const float *G, int m, int K, const float *Y, int64_t n, int s, int c,
                         const int32_t *cand, float eps_fb, int32_t *idx, float *val, int32_t *nnz, float *resid2,
-                        int32_t *flag, cudaStream_t st);
+                        int32_t *flag, const int64_t *offsets, int L, cudaStream_t st);
+// Flagged signals by subset: cnt[t] (device [L+1], cnt[L] = total), then
+// list[foff[t] + k] for the k-th flagged signal of subset t (pos: device [L]).
+cudaError_t launch_count_flags(const int32_t *flag, const int64_t *offsets, int L, int64_t n, int32_t *cnt,
+                               cudaStream_t st);
+cudaError_t launch_place_flags(const int32_t *flag, const int64_t *offsets, int L, int64_t n, const int64_t *foff,
+                               int32_t *pos, int32_t *list, cudaStream_t st);
 cudaError_t launch_compact(const int32_t *flag, int64_t n, int32_t *list, int32_t *count, cudaStream_t st);
 cudaError_t launch_gather_rows(const float *Y, int m, const int32_t *list, const int32_t *count, int64_t nmax,
                                float *Yf, cudaStream_t st);
