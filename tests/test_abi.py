@@ -24,6 +24,9 @@ def test_null_context_and_bad_arguments_are_rejected_without_a_gpu():
     assert lib.sdl_omp(None, 1, None, 64, 256, None, 10, 6, 0.0, None, None, None, None) == 1
     assert lib.sdl_destroy(None) == 0
     h = ctypes.c_void_p()
+    assert lib.sdl_corr_features(None, None, 64, 256, None, None, 1, None) == 1
+    assert lib.sdl_omp_proposed_batched(None, None, 1, None, 64, 256, None, None, 1, 6, 12, 0.1,
+                                        None, None, None, None, None) == 1
     # no CUDA device in this container: sdl_create must fail cleanly, not crash
     rc = lib.sdl_create(ctypes.byref(h), 0, None)
     assert rc in (0, 1, 4)
