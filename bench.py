@@ -786,12 +786,13 @@ def run_coding(args):
 
 
 # ------------------------------------------------------------ CPU oracle ------
-def _oracle_sample(p, Y, n_sub, final_n, merge_iters):
+def _oracle_sample(p, Y, n_sub, final_n, merge_iters, threads=None):
     """Run the oracle on a bounded sample of the workload: local training of the
     first n_sub subsets (all iterations), a merge of their stacked atoms, and the
-    final coding of final_n signals.  Returns (coded signals, seconds, threads)."""
+    final coding of final_n signals, on `threads` host threads (default: all).
+    Returns (coded signals, seconds, threads)."""
     import oracle
-    th = oracle.default_threads()
+    th = threads or oracle.default_threads()
     Yp = Y[p.perm[: p.offsets[n_sub]]].astype(np.float64)
     off = p.offsets[: n_sub + 1]
     Dl = np.stack([Yp[q] / np.linalg.norm(Yp[q], axis=1, keepdims=True) for q in p.picks[:n_sub]])
@@ -808,10 +809,17 @@ def _oracle_sample(p, Y, n_sub, final_n, merge_iters):
 def cpu_baseline(p, Y):
     n_sub, final_n, merge_iters = p.L, p.N, p.iters_merge   # one whole step of the workload
     coded, dt, th = _oracle_sample(p, Y, n_sub=n_sub, final_n=final_n, merge_iters=merge_iters)
+    # the same oracle on one thread, on a smaller sample (4 subsets, 4 merge
+    # iterations, 8,000 final signals) to keep the run short
+    c1, d1, _ = _oracle_sample(p, Y, n_sub=4, final_n=8000, merge_iters=4, threads=1)
     return {"value": coded / dt, "unit": UNIT, "cores": th, "kind": "oracle",
             "sample": f"{n_sub} of {p.L} subsets x {p.iters_local} local iterations, merge of their "
                       f"{n_sub * p.K1} atoms x {merge_iters} iterations, final coding of {final_n:,} signals "
-                      f"({coded} coded signals in {dt:.1f} s)"}
+                      f"({coded} coded signals in {dt:.1f} s)",
+            "single_thread": {"value": c1 / d1, "unit": UNIT, "cores": 1,
+                              "sample": f"4 subsets x {p.iters_local} local iterations, merge of their "
+                                        f"{4 * p.K1} atoms x 4 iterations, final coding of 8,000 signals "
+                                        f"({c1} coded signals in {d1:.1f} s)"}}
 
 
 def run_reference(args, rank, world):
