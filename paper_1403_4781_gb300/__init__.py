@@ -169,24 +169,6 @@ class Context:
     def workspace_bytes(self) -> int:
         return int(lib().sdl_workspace_bytes(self.handle))
 
-    def omp_batched(self, D, Y, offsets, s, ncand, eps_fb, features=FEATURES_CORR, with_resid=True):
-        """Proposer-assisted OMP over subsets (D: (L, K, m)), the network reading
-        |D_t^T y| (FEATURES_CORR) or y (FEATURES_SIGNAL); returns (idx, val, nnz,
-        resid2, n_fallback)."""
-        import torch
-        L, K, m = D.shape
-        n = Y.shape[0]
-        oh, op = _offsets_host(offsets)
-        assert len(oh) == L + 1 and oh[-1] == n
-        idx = torch.empty((n, s), dtype=torch.int32, device=self.device)
-        val = torch.empty((n, s), dtype=torch.float32, device=self.device)
-        nnz = torch.empty((n,), dtype=torch.int32, device=self.device)
-        r2 = torch.empty((n,), dtype=torch.float32, device=self.device) if with_resid else None
-        nf = ctypes.c_int64(0)
-        _call("sdl_omp_proposed_batched", self.ctx.bind_stream(), self.handle, features, _ptr(D), m, K, _ptr(Y), op,
-              L, s, ncand, float(eps_fb), _ptr(idx), _ptr(val), _ptr(nnz), _ptr(r2), ctypes.byref(nf))
-        return idx, val, nnz, r2, int(nf.value)
-
     def close(self):
         if getattr(self, "handle", None):
             lib().sdl_destroy(self.handle)
