@@ -1074,74 +1074,16 @@ sdl_status sdl_sq_error(sdl_ctx *ctx, sdl_precision prec, const void *a, const v
   return SDL_OK;
 }
 
+// One dictionary: the batched path with L = 1 and the proposer reading y.
 sdl_status sdl_omp_proposed(sdl_ctx *ctx, sdl_proposer *p, const float *D, int m, int K, const float *Y, int64_t n,
                             int s, int ncand, double eps_fb, int32_t *idx, float *val, int32_t *nnz, float *resid2,
                             int64_t *n_fallback) {
   if (!ctx) return SDL_EINVAL;
   ctx->err.clear();
-  sdl_status st;
-  SDL_REQUIRE(p != nullptr && n_fallback != nullptr, "proposer and n_fallback must be given");
-  if ((st = check_omp_shape(ctx, m, K, s, 0.0)) != SDL_OK) return st;
-  SDL_REQUIRE(proposer_m(p) == m && proposer_K(p) == K, "the proposer was built for another (m, K)");
-  SDL_REQUIRE(ncand >= s && ncand <= 32 && ncand <= K, "ncand must be in [s, min(32, K)]");
-  SDL_REQUIRE(eps_fb >= 0.0 && isfinite(eps_fb), "eps_fb must be finite and >= 0");
-  SDL_REQUIRE(n >= 0 && n < ((int64_t)1 << 31), "0 <= n < 2^31");
-  *n_fallback = 0;
-  if (n == 0) return SDL_OK;
-  SDL_REQUIRE(aligned16(D) && aligned16(Y) && aligned16(idx) && aligned16(val) && aligned16(nnz) &&
-                  (resid2 == nullptr || aligned16(resid2)),
-              "device pointers must be non-NULL and 16-byte aligned");
-  DeviceGuard g(ctx->device);
-  SDL_REQUIRE(g.ok, "cannot select the context device");
-  const size_t need = round256(sizeof(float) * (size_t)K * K) + round256(sizeof(int32_t) * (size_t)n * ncand) +
-                      3 * round256(sizeof(int32_t) * (size_t)n) + round256(sizeof(float) * (size_t)n) +
-                      round256(sizeof(int32_t) * 4) + round256(sizeof(float) * (size_t)n * m) +
-                      round256(sizeof(int32_t) * (size_t)n * s) + round256(sizeof(float) * (size_t)n * s) +
-                      2 * round256(sizeof(int64_t) * 2) + 4096;
-  if ((st = ws_reserve(ctx, need)) != SDL_OK) return st;
-  float *G = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)K * K));
-  int32_t *cand = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * ncand));
-  int32_t *flag = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n));
-  int32_t *list = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n));
-  int32_t *fn = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n));
-  float *fr = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)n));
-  int32_t *count = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
-  float *Yf = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)n * m));
-  int32_t *fi = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * s));
-  float *fv = static_cast<float *>(ws_alloc(ctx, sizeof(float) * (size_t)n * s));
-  float *r2 = resid2 ? resid2 : fr;   // romp needs somewhere to write residuals
-  if (!G || !cand || !flag || !list || !fn || !fr || !count || !Yf || !fi || !fv)
-    return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
-  cudaStream_t sm = ctx->stream;
-  SDL_CUDA(timed(ctx, "proposer_topk", 4, [&] { return proposer_topk(p, Y, n, ncand, cand, sm); }), "proposer scores");
-  SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<float>(D, m, K, 1, G, sm); }), "gram");
-  SDL_CUDA(timed(ctx, "omp_restricted", 1, [&] {
-             return launch_romp(D, G, m, K, Y, n, s, ncand, cand, (float)eps_fb, idx, val, nnz, r2, flag, nullptr, 1,
-                                sm);
-           }), "restricted omp");
-  SDL_CUDA(timed(ctx, "fallback_compact", 1, [&] { return launch_compact(flag, n, list, count, sm); }), "compact");
-  SDL_CUDA(cudaMemcpyAsync(ctx->h_status, count, sizeof(int32_t), cudaMemcpyDeviceToHost, sm), "count read");
-  SDL_CUDA(cudaStreamSynchronize(sm), "count sync");
-  const int64_t nf = *ctx->h_status;
-  *n_fallback = nf;
-  if (nf == 0) return SDL_OK;
-  // full OMP on the flagged signals (same Gram), then scatter the codes back
-  SDL_CUDA(timed(ctx, "fallback_gather", 1, [&] { return launch_gather_rows(Y, m, list, count, nf, Yf, sm); }),
-           "gather");
-  const int64_t offs[2] = {0, nf};
-  OmpArgs a{};
-  int64_t *d_off = nullptr;
-  int32_t *d_tiles = nullptr;
-  int64_t tiles = 0;
-  if ((st = upload_plan(ctx, offs, 1, omp_tile_signals(), &d_off, &d_tiles, &tiles)) != SDL_OK) return st;
-  a.D = D; a.G = G; a.Y = Yf; a.offsets = d_off; a.tile_start = d_tiles; a.total_tiles = tiles;
-  a.L = 1; a.m = m; a.K = K; a.s = s; a.eps = 0.0;
-  a.idx = fi; a.val = fv; a.nnz = fn; a.resid2 = fr;
-  SDL_CUDA(timed(ctx, "omp", 1, [&] { return launch_omp<float>(a, ctx->num_sms, sm); }), "fallback omp");
-  SDL_CUDA(timed(ctx, "fallback_scatter", 1, [&] {
-             return launch_scatter_codes(list, count, nf, s, fi, fv, fn, fr, idx, val, nnz, resid2, sm);
-           }), "scatter");
-  return SDL_OK;
+  if (n < 0) return set_error(ctx, SDL_EINVAL, "n must be >= 0");
+  const int64_t offsets[2] = {0, n};
+  return sdl_omp_proposed_batched(ctx, p, SDL_FEATURES_SIGNAL, D, m, K, Y, offsets, 1, s, ncand, eps_fb, idx, val,
+                                  nnz, resid2, n_fallback);
 }
 
 sdl_status sdl_corr_features(sdl_ctx *ctx, const float *D, int m, int K, const float *Y, const int64_t *offsets,

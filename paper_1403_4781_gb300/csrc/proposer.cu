@@ -382,13 +382,7 @@ __global__ void romp_kernel(const float *__restrict__ D, const float *__restrict
   }
 }
 
-// Fallback bookkeeping: list of flagged signals, gather, scatter.
-__global__ void compact_kernel(const int32_t *__restrict__ flag, int64_t n, int32_t *list, int32_t *count) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-    if (flag[q]) list[atomicAdd(count, 1)] = (int32_t)q;
-}
-
-// Fallback signals grouped by subset.  Pass 1 counts the flagged signals of
+// Fallback bookkeeping.  Signals grouped by subset.  Pass 1 counts the flagged signals of
 // each subset into cnt[t] and their total into cnt[L]; pass 2 places flagged
 // signal i at list[foff[t] + k], k its arrival rank within subset t (the order
 // inside a subset is free: every signal is coded on its own).  The lanes of a
@@ -794,14 +788,6 @@ cudaError_t launch_place_flags(const int32_t *flag, const int64_t *offsets, int 
   cudaError_t e = cudaMemsetAsync(pos, 0, sizeof(int32_t) * L, st);
   if (e != cudaSuccess || n <= 0) return e;
   place_flags_kernel<<<nblocks(n, 256, 4096), 256, 0, st>>>(flag, offsets, L, n, foff, pos, list);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_compact(const int32_t *flag, int64_t n, int32_t *list, int32_t *count, cudaStream_t st) {
-  using namespace prop;
-  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t), st);
-  if (e != cudaSuccess || n <= 0) return e;
-  compact_kernel<<<nblocks(n, 256, 4096), 256, 0, st>>>(flag, n, list, count);
   return cudaGetLastError();
 }
 

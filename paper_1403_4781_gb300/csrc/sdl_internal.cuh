@@ -262,7 +262,6 @@ cudaError_t launch_count_flags(const int32_t *flag, const int64_t *offsets, int 
                                cudaStream_t st);
 cudaError_t launch_place_flags(const int32_t *flag, const int64_t *offsets, int L, int64_t n, const int64_t *foff,
                                int32_t *pos, int32_t *list, cudaStream_t st);
-cudaError_t launch_compact(const int32_t *flag, int64_t n, int32_t *list, int32_t *count, cudaStream_t st);
 cudaError_t launch_gather_rows(const float *Y, int m, const int32_t *list, const int32_t *count, int64_t nmax,
                                float *Yf, cudaStream_t st);
 cudaError_t launch_scatter_codes(const int32_t *list, const int32_t *count, int64_t nmax, int s, const int32_t *fi,
