@@ -535,6 +535,13 @@ def conditioned_bench(sdl, dev, flush, stream):
     t_plain, (pi, *_) = timed(lambda: sdl.omp_batched(Dg, Yev, off, s))
     t_prop, (qi, qv, qn, qr, nf) = timed(lambda: prop.omp_batched(Dg, Yev, off, s, ncand, eps_fb))
     same = (torch.sort(pi, dim=1).values == torch.sort(qi, dim=1).values).all(dim=1).float().mean().item()
+    # one more pass with the library's per-kernel events: where the time goes
+    ctx = sdl.context(dev.index or 0)
+    ctx.profile(True)
+    ctx.profile_reset()
+    prop.omp_batched(Dg, Yev, off, s, ncand, eps_fb)
+    prof = ctx.profile_read()
+    ctx.profile(False)
     prop.close()
     ne = Yev.shape[0]
     return {"dictionaries": L, "signals_per_dictionary": n_t, "train_pairs": n, "epochs": epochs,
@@ -543,7 +550,22 @@ def conditioned_bench(sdl, dev, flush, stream):
             "recall_at_12_unseen_dictionaries": {"network_on_abs_Dty": u_net, "abs_Dty_ranking": u_corr},
             "eval_signals": ne, "plain_batched_omp_signals_per_s": ne / t_plain,
             "proposed_batched_omp_signals_per_s": ne / t_prop, "fallback_rate": nf / ne,
-            "support_agreement_with_plain": same, "candidates": ncand, "eps_fb": eps_fb}
+            "support_agreement_with_plain": same, "candidates": ncand, "eps_fb": eps_fb,
+            "proposed_pass_kernel_ms": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}
+
+
+def run_conditioned(args):
+    """The dictionary-conditioned proposer workload alone, printed as its own line."""
+    import torch
+
+    import paper_1403_4781_gb300 as sdl
+
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    res = {"metric": METRIC, "workload": "conditioned_proposer_L64_m64_K256_s6_n8192",
+           "data": "synthetic (seeded; Sec. 3.1 data model, one dictionary per subset)",
+           **conditioned_bench(sdl, dev, flush, torch.cuda.current_stream(dev))}
+    print(json.dumps(res), flush=True)
 
 
 def run_uneven(args, shape):
@@ -857,7 +879,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposer sub-benchmark")
-    ap.add_argument("--workload", choices=["splitmerge", "uneven-A", "uneven-B", "patches", "denoise", "coding"],
+    ap.add_argument("--workload", choices=["splitmerge", "uneven-A", "uneven-B", "patches", "denoise", "coding",
+                                           "conditioned"],
                     default="splitmerge",
                     help="the bench workload (default) or one of the parity workloads, measured alone")
     ap.add_argument("--plain-steps", type=int, default=1,
@@ -877,6 +900,9 @@ def main():
     elif args.workload == "coding":
         if rank == 0:
             run_coding(args)
+    elif args.workload == "conditioned":
+        if rank == 0:
+            run_conditioned(args)
     elif args.workload != "splitmerge":
         if rank == 0:
             run_uneven(args, args.workload[-1])

@@ -102,37 +102,55 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(GemmArgs g) {
     __syncthreads();   // the images may be overwritten by the next chunk
   }
   tc::fence_after();
+  ok = __syncthreads_and(ok) != 0;   // one verdict per block: the TMEM loads below are warp-wide
   if (ok && c_end > c_begin) {
-    const int row = m0 + 32 * warp + lane;
+    // The accumulator leaves TMEM with one row per lane.  Each warp stages its
+    // 32 x 32 blocks in shared memory (the operand images are free now; pitch 33
+    // keeps both access directions free of bank conflicts), so that C and H are
+    // written along rows and the transposed copy HT along columns: every
+    // global access of a warp covers consecutive addresses.
+    float *buf = reinterpret_cast<float *>(smem) + warp * 32 * 33;
+    const int rbase = m0 + 32 * warp;
     for (int c0 = 0; c0 < kNT; c0 += 32) {
       float v[32];
       tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + c0, v);
-      if (row >= g.M) continue;
 #pragma unroll
-      for (int e = 0; e < 32; ++e) {
-        const int col = n0 + c0 + e;
-        if (col >= g.N) continue;
-        float x = v[e];
-        switch (g.mode) {
-          case kStore: g.C[(size_t)row * g.ldc + col] = x; break;
-          case kAtomic: atomicAdd(&g.C[(size_t)row * g.ldc + col], x); break;
-          case kBias: g.C[(size_t)row * g.ldc + col] = x + g.bias[col]; break;
-          case kBiasGelu: {
-            const float p = x + g.bias[col];
-            g.C[(size_t)row * g.ldc + col] = p;
-            const bf16 h = __float2bfloat16_rn(gelu(p));
-            if (g.H) g.H[(size_t)row * g.ldh + col] = h;
-            if (g.HT) g.HT[(size_t)col * g.ldt + row] = h;
-          } break;
-          case kDGelu: {
-            const float d = x * gelu_prime(g.pre[(size_t)row * g.ldp + col]);
-            g.C[(size_t)row * g.ldc + col] = d;
-            const bf16 h = __float2bfloat16_rn(d);
-            if (g.H) g.H[(size_t)row * g.ldh + col] = h;
-            if (g.HT) g.HT[(size_t)col * g.ldt + row] = h;
-          } break;
+      for (int e = 0; e < 32; ++e) buf[lane * 33 + e] = v[e];
+      __syncwarp();
+      const int col = n0 + c0 + lane;
+      const bool cok = col < g.N;
+      for (int r = 0; r < 32 && rbase + r < g.M; ++r) {
+        const int row = rbase + r;
+        float x = buf[r * 33 + lane];
+        if (cok) {
+          switch (g.mode) {
+            case kStore: g.C[(size_t)row * g.ldc + col] = x; break;
+            case kAtomic: atomicAdd(&g.C[(size_t)row * g.ldc + col], x); break;
+            case kBias: g.C[(size_t)row * g.ldc + col] = x + g.bias[col]; break;
+            case kBiasGelu: {
+              const float p = x + g.bias[col];
+              g.C[(size_t)row * g.ldc + col] = p;
+              x = gelu(p);
+              if (g.H) g.H[(size_t)row * g.ldh + col] = __float2bfloat16_rn(x);
+            } break;
+            case kDGelu: {
+              x *= gelu_prime(g.pre[(size_t)row * g.ldp + col]);
+              g.C[(size_t)row * g.ldc + col] = x;
+              if (g.H) g.H[(size_t)row * g.ldh + col] = __float2bfloat16_rn(x);
+            } break;
+          }
+        }
+        buf[r * 33 + lane] = x;   // the value HT receives (rounded to BF16 there)
+      }
+      __syncwarp();
+      if (g.HT && (g.mode == kBiasGelu || g.mode == kDGelu) && rbase + lane < g.M) {
+#pragma unroll 4
+        for (int e = 0; e < 32; ++e) {
+          const int ce = n0 + c0 + e;
+          if (ce < g.N) g.HT[(size_t)ce * g.ldt + rbase + lane] = __float2bfloat16_rn(buf[lane * 33 + e]);
         }
       }
+      __syncwarp();
     }
   } else if (!ok && tid == 0 && g.err) {
     atomicOr(g.err, 1);

@@ -187,3 +187,67 @@ def test_bad_arguments_are_rejected():
     with pytest.raises(sdl.SdlError):
         prop.omp_batched(_t(Ds), _t(Y), off, s, s - 1, 0.1, features=sdl.FEATURES_SIGNAL)
     prop.close()
+
+
+def test_largest_shapes_restricted_omp():
+    """m = 256, K = 1024 (the largest compiled sizes), 32 candidates (the most a
+    warp holds), s = 16, a network with 1,024 inputs: restricted OMP per subset
+    against the oracle on each candidate sub-dictionary."""
+    m, K, s, nc = 256, 1024, 16, 32
+    rng, Ds, Y, off = _batch(966, m, K, s, [150, 0, 90])
+    prop = sdl.Proposer(_t(si.mlp_init(rng, K, 64, 64, K, s)), K, 64, 64, K)
+    Dg, Yg = _t(Ds), _t(Y)
+    cand = np.argsort(-prop.scores(sdl.corr_features(Dg, Yg, off)).cpu().numpy(), axis=1, kind="stable")[:, :nc]
+    gi, gv, gn, gr, nf = prop.omp_batched(Dg, Yg, off, s, nc, 1e30)
+    assert nf == 0
+    gi, gv, gn, gr = (a.cpu().numpy() for a in (gi, gv, gn, gr))
+    for t in range(len(off) - 1):
+        D64 = Ds[t].astype(np.float64)
+        for i in range(off[t], off[t + 1]):
+            y = Y[i:i + 1].astype(np.float64)
+            o = oracle.omp(D64[cand[i]], y, s, nthreads=1)
+            o["idx"] = np.where(o["idx"] >= 0, cand[i][np.maximum(o["idx"], 0)], -1)
+            compare_codes(D64, y, gi[i:i + 1], gv[i:i + 1], gn[i:i + 1], gr[i:i + 1], o,
+                          fp32_gap_tol(m, np.linalg.norm(y, axis=1)), 1e-3)
+    prop.close()
+
+
+def test_full_size_conditioned_sampled():
+    """The bench's conditioned workload at full size: 64 dictionaries of 64 x 256,
+    8,192 signals each (2^19 in all).  Sampled signals: features within
+    gamma_m ||y|| of the oracle and restricted codes equal to the oracle's OMP
+    on their candidate sub-dictionaries.  Every signal: with eps_fb = 8.5 sigma,
+    the accepted ones keep their restricted code and the others carry plain
+    batched OMP's code, bit for bit."""
+    m, K, s, L, n_t = 64, 256, 6, 64, 8192
+    rng, Ds, Y, off = _batch(967, m, K, s, [n_t] * L)
+    prop = sdl.Proposer(_t(si.mlp_init(rng, K, H1, H2, K, s)), K, H1, H2, K)
+    Dg, Yg = _t(Ds), _t(Y)
+    F = sdl.corr_features(Dg, Yg, off)
+    cand_all = torch.topk(prop.scores(F), 2 * s, dim=1).indices.cpu().numpy()
+    F = F.cpu().numpy()
+    ri, rv, rn, rr, nf0 = prop.omp_batched(Dg, Yg, off, s, 2 * s, 1e30)
+    assert nf0 == 0
+    ri, rv, rn, rr = (a.cpu().numpy() for a in (ri, rv, rn, rr))
+    sample = np.sort(rng.choice(len(Y), 400, replace=False))
+    for i in sample:
+        t = int(np.searchsorted(off, i, side="right") - 1)
+        D64, y = Ds[t].astype(np.float64), Y[i:i + 1].astype(np.float64)
+        want = oracle.corr_features(D64[None], np.array([0, 1], np.int64), y)[0]
+        assert (np.abs(F[i] - want) <= _gamma(m) * np.linalg.norm(y) + 1e-30).all()
+        c = np.sort(cand_all[i])        # the candidate set (its order does not matter to OMP)
+        o = oracle.omp(D64[c], y, s, nthreads=1)
+        o["idx"] = np.where(o["idx"] >= 0, c[np.maximum(o["idx"], 0)], -1)
+        compare_codes(D64, y, ri[i:i + 1], rv[i:i + 1], rn[i:i + 1], rr[i:i + 1], o,
+                      fp32_gap_tol(m, np.linalg.norm(y, axis=1)), 1e-4)
+    eps_fb = 8.5 * 0.01
+    fi, fv, fn, fr, nf = prop.omp_batched(Dg, Yg, off, s, 2 * s, eps_fb)
+    pi, pv, pn, pr = sdl.omp_batched(Dg, Yg, off, s)
+    fi, fv, pi, pv = (a.cpu().numpy() for a in (fi, fv, pi, pv))
+    acc = np.sqrt(rr.astype(np.float64)) <= eps_fb
+    assert nf == int((~acc).sum())
+    np.testing.assert_array_equal(fi[acc], ri[acc])
+    np.testing.assert_array_equal(fv[acc], rv[acc])
+    np.testing.assert_array_equal(fi[~acc], pi[~acc])
+    np.testing.assert_array_equal(fv[~acc], pv[~acc])
+    prop.close()
