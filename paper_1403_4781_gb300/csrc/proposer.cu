@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(GemmArgs g) {
             case kBias: g.C[(size_t)row * g.ldc + col] = x + g.bias[col]; break;
             case kBiasGelu: {
               const float p = x + g.bias[col];
-              g.C[(size_t)row * g.ldc + col] = p;
+              if (g.C) g.C[(size_t)row * g.ldc + col] = p;   // the pre-activation, kept for training
               x = gelu(p);
               if (g.H) g.H[(size_t)row * g.ldh + col] = __float2bfloat16_rn(x);
             } break;
@@ -570,13 +570,13 @@ cudaError_t forward(sdl_proposer *p, const float *Y, int64_t B, bool training, c
   GemmArgs g{};
   g.err = p->err;
   g.A = p->X; g.lda = p->mp; g.B = p->W1b; g.ldb = p->mp; g.M = (int)B; g.N = p->h1; g.Kd = p->mp;
-  g.mode = kBiasGelu; g.C = p->A1; g.ldc = p->h1; g.bias = p->params + o.b1;
+  g.mode = kBiasGelu; g.C = training ? p->A1 : nullptr; g.ldc = p->h1; g.bias = p->params + o.b1;
   g.H = p->H1; g.ldh = p->h1; g.HT = training ? p->H1T : nullptr; g.ldt = ldt;
   if ((e = gemm(g, 1, st)) != cudaSuccess) return e;
   g = GemmArgs{};
   g.err = p->err;
   g.A = p->H1; g.lda = p->h1; g.B = p->W2b; g.ldb = p->h1; g.M = (int)B; g.N = p->h2; g.Kd = p->h1;
-  g.mode = kBiasGelu; g.C = p->A2; g.ldc = p->h2; g.bias = p->params + o.b2;
+  g.mode = kBiasGelu; g.C = training ? p->A2 : nullptr; g.ldc = p->h2; g.bias = p->params + o.b2;
   g.H = p->H2; g.ldh = p->h2; g.HT = training ? p->H2T : nullptr; g.ldt = ldt;
   if ((e = gemm(g, 1, st)) != cudaSuccess) return e;
   g = GemmArgs{};
