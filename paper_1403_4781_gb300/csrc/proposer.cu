@@ -37,6 +37,7 @@ struct GemmArgs {
   bf16 *H; int ldh;          // BF16 [M][N] output (may be null)
   bf16 *HT; int ldt;         // BF16 [N][M] output (may be null)
   int32_t *err;
+  int staged;                // epilogue through shared memory (large grids) or straight from registers
 };
 
 constexpr int kGemmThreads = 128;
@@ -103,7 +104,42 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(GemmArgs g) {
   }
   tc::fence_after();
   ok = __syncthreads_and(ok) != 0;   // one verdict per block: the TMEM loads below are warp-wide
-  if (ok && c_end > c_begin) {
+  if (ok && c_end > c_begin && !g.staged) {
+    // Straight from registers, one row per lane: fewest instructions, for
+    // grids of about one block per SM, where each warp's stores are issued
+    // and left to the memory system while the block has little else to do.
+    const int row = m0 + 32 * warp + lane;
+    for (int c0 = 0; c0 < kNT; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + c0, v);
+      if (row >= g.M) continue;
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        const int col = n0 + c0 + e;
+        if (col >= g.N) continue;
+        float x = v[e];
+        switch (g.mode) {
+          case kStore: g.C[(size_t)row * g.ldc + col] = x; break;
+          case kAtomic: atomicAdd(&g.C[(size_t)row * g.ldc + col], x); break;
+          case kBias: g.C[(size_t)row * g.ldc + col] = x + g.bias[col]; break;
+          case kBiasGelu: {
+            const float p = x + g.bias[col];
+            if (g.C) g.C[(size_t)row * g.ldc + col] = p;
+            const bf16 h = __float2bfloat16_rn(gelu(p));
+            if (g.H) g.H[(size_t)row * g.ldh + col] = h;
+            if (g.HT) g.HT[(size_t)col * g.ldt + row] = h;
+          } break;
+          case kDGelu: {
+            const float d = x * gelu_prime(g.pre[(size_t)row * g.ldp + col]);
+            g.C[(size_t)row * g.ldc + col] = d;
+            const bf16 h = __float2bfloat16_rn(d);
+            if (g.H) g.H[(size_t)row * g.ldh + col] = h;
+            if (g.HT) g.HT[(size_t)col * g.ldt + row] = h;
+          } break;
+        }
+      }
+    }
+  } else if (ok && c_end > c_begin) {
     // The accumulator leaves TMEM with one row per lane.  Each warp stages its
     // 32 x 32 blocks in shared memory (the operand images are free now; pitch 33
     // keeps both access directions free of bank conflicts), so that C and H are
@@ -171,6 +207,9 @@ cudaError_t gemm(const GemmArgs &a0, int split, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.M + 127) / 128, (a.N + kNT - 1) / kNT, split);
+  // staged (coalesced) stores pay once the grid fills the SMs several times
+  // over (inference chunks); training batches launch about a block per SM
+  a.staged = (int64_t)grid.x * grid.y * grid.z >= 1024 ? 1 : 0;
   gemm_bf16_kernel<<<grid, kGemmThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
