@@ -28,9 +28,14 @@ def test_reference_arm_prints_one_contract_line():
     assert r["impl"] == "reference" and r["value"] > 0 and r["ms_per_step"] > 0
     assert (r["n_gpus"], r["steps"], r["warmup"]) == (1, 1, 1)
     assert r["higher_is_better"] is True and r["scaling"] == "weak"
-    assert r["config"]["workload"].startswith("splitmerge")
+    # the default workload is the large image-patch one, with our arm's config
+    sys.path.insert(0, ROOT)
+    import bench
+    assert r["config"]["workload"] == bench.WORKLOADS["patches"]
+    assert (r["config"]["m"], r["config"]["K"], r["config"]["K1"], r["config"]["L"]) == (256, 1024, 512, 256)
     cb = r["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == r["value"]
+    assert cb["extrapolated"] is True
     assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
