@@ -22,6 +22,9 @@ Readings of the paper fixed here (Sec. 1, 2, 3.1, Algorithm 1):
   * Dictionary-conditioned proposer input (not in the paper): |D_t^T y| of each
     signal against its own subset's dictionary, the magnitudes OMP's first
     greedy step ranks.
+  * Proposer training (not in the paper): binary cross-entropy of the MLP's
+    logits against support labels, minimised by Adam (Kingma & Ba 2015,
+    Algorithm 1: bias-corrected moment estimates, beta1 0.9, beta2 0.999).
 """
 from __future__ import annotations
 
@@ -78,6 +81,7 @@ def _load():
             lib.orc_residual.argtypes = [_dp, i32, i64, _dp, i32, _ip, _dp, i32, _dp, _dp]
             lib.orc_recovery.argtypes = [_dp, i32, _dp, i32, i32, dbl, ctypes.POINTER(ctypes.c_int)]
             lib.orc_mlp_forward.argtypes = [_dp, i32, i32, i32, i32, _dp, i64, _dp]
+            lib.orc_adam_step.argtypes = [_dp, _dp, _dp, _dp, i64, i32, dbl, dbl, dbl, dbl]
             lib.orc_mlp_loss_grad.argtypes = [_dp, i32, i32, i32, i32, _dp, _ip, i32, i64, _dp, _dp]
             lib.orc_extract_patches.argtypes = [_dp, i32, i32, i32, _dp]
             lib.orc_patch_average.argtypes = [_dp, i32, _ip, _dp, i32, i32, i32, i32, _dp]
@@ -301,6 +305,18 @@ def mlp_loss_grad(params, m, h1, h2, K, Y, idx, with_grad=True):
     _check(lib.orc_mlp_loss_grad(_d(params), m, h1, h2, K, _d(Y), _i(idx), idx.shape[1], Y.shape[0],
                                  ctypes.cast(ctypes.byref(loss), _dp), _d(grad)), "orc_mlp_loss_grad")
     return loss.value, grad
+
+
+def adam_step(theta, g, m, v, t, alpha, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba 2015, Algorithm 1); returns new (theta, m, v)."""
+    lib = _load()
+    theta, g = _f64(theta).copy(), _f64(g)
+    m, v = _f64(m).copy(), _f64(v).copy()
+    n = theta.size
+    assert g.size == n and m.size == n and v.size == n
+    _check(lib.orc_adam_step(_d(theta), _d(g), _d(m), _d(v), n, int(t), float(alpha), float(beta1), float(beta2),
+                             float(eps)), "orc_adam_step")
+    return theta, m, v
 
 
 def extract_patches(img, p):

@@ -494,6 +494,25 @@ int orc_mlp_loss_grad(const double *params, int m, int h1, int h2, int K, const 
   return 0;
 }
 
+/* Adam (Kingma & Ba 2015, Algorithm 1), the optimiser the proposer trains
+ * with (the paper has no learned part): step t >= 1 on n parameters theta with
+ * gradient g.  The first and second moment estimates are exponential moving
+ * averages of g and g^2 (rates beta1, beta2) held in m and v; their initial
+ * bias towards zero is removed by dividing by 1 - beta^t; theta moves by
+ * alpha * mhat / (sqrt(vhat) + eps). */
+int orc_adam_step(double *theta, const double *g, double *m, double *v, int64_t n, int t, double alpha,
+                  double beta1, double beta2, double eps) {
+  if (n < 0 || t < 1 || (n > 0 && (!theta || !g || !m || !v))) return 1;
+  const double c1 = 1.0 - pow(beta1, (double)t), c2 = 1.0 - pow(beta2, (double)t);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+    v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+    const double mhat = m[i] / c1, vhat = v[i] / c2;
+    theta[i] -= alpha * mhat / (sqrt(vhat) + eps);
+  }
+  return 0;
+}
+
 /* ------------------------------------------------- image denoising --- */
 
 int orc_extract_patches(const double *img, int H, int W, int p, double *out) {

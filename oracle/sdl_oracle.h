@@ -132,6 +132,11 @@ int orc_mlp_forward(const double *params, int m, int h1, int h2, int K, const do
                     double *Z);
 int orc_mlp_loss_grad(const double *params, int m, int h1, int h2, int K, const double *Y,
                       const int32_t *idx, int s, int64_t B, double *loss, double *grad);
+
+/* One Adam step (Kingma & Ba 2015, Algorithm 1) of the proposer's optimiser:
+ * theta, m, v updated in place; t >= 1 is the step number (bias correction). */
+int orc_adam_step(double *theta, const double *g, double *m, double *v, int64_t n, int t, double alpha,
+                  double beta1, double beta2, double eps);
 #ifdef __cplusplus
 }
 #endif
