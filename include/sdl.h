@@ -301,11 +301,14 @@ sdl_status sdl_omp_proposed_batched(sdl_ctx *ctx, sdl_proposer *p, int features,
 /* OMP without any allocation (the paper has no counterpart: this is a service
  * entry point).  For callers that cannot call cudaMalloc where they code signals:
  * processes whose device memory is entirely owned by another allocator, or loops
- * that must not take the implicit synchronisation of an allocation.  It computes
- * exactly what sdl_omp computes for SDL_PREC_F32 (same kernels), but keeps its
- * scratch -- the K x K Gram matrix and a small launch plan -- in a fixed array
- * of 1 MiB + 256 bytes inside the library, which every GPU that loads the
- * library holds until the process exits.  The call allocates nothing: no
+ * that must not take the implicit synchronisation of an allocation.  It runs the
+ * fused FP32 OMP kernel, the form sdl_omp runs for SDL_PREC_F32 under
+ * SDL_OPT_OMP_FORM = 1, and returns the same codes bit for bit; sdl_omp's
+ * default two-kernel form forms every correlation as the same ordered chain of
+ * FP32 FMAs and gives the same codes too.  It keeps its scratch -- the K x K
+ * Gram matrix and a small launch plan -- in a fixed array of 1 MiB + 256 bytes
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits.  The call allocates nothing: no
  * cudaMalloc, no cudaFree, no context workspace.
  *   stream  cudaStream_t on the calling thread's current device (NULL = legacy)
  *   D, Y, idx, val, nnz, resid2: as sdl_omp with float data; resid2 may be NULL

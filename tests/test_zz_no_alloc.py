@@ -12,7 +12,9 @@ pointers) and compares its codes with sdl_omp's on the same inputs, using the
 tolerances of the OMP parity tests: identical supports and nnz, coefficients
 within 1e-4 relative, residual energies within 1e-4 relative.  Two calls of
 different shapes run back to back, so stale scratch from the first would show
-up in the second.
+up in the second.  At the array's size limit (K = 512, m = 256) the codes are
+compared bit for bit with sdl_omp's fused FP32 form (the same kernels) and,
+once, with the FP64 oracle under the FP32 parity rule.
 """
 import ctypes
 
@@ -20,8 +22,10 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_1403_4781_gb300 as sdl
 import sdl_inputs as si
+from _parity import compare_codes, fp32_gap_tol
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -66,6 +70,35 @@ def test_noalloc_matches_sdl_omp_on_two_calls_in_a_row():
     assert first[0] == 0 and second[0] == 0
     _same_codes(first[1:], sdl.omp(D1, Y1, 6))
     _same_codes(second[1:], sdl.omp(D2, Y2, 4, eps=0.05))
+
+
+@pytest.mark.parametrize("s", [16, 32])
+def test_noalloc_at_its_size_limit(s):
+    """K = 512 and m = 256 fill the Gram part of the array exactly; n = 1,000
+    leaves a ragged last tile of 8 signals.  A smaller call first leaves other
+    contents in the array."""
+    Ds, Ys = _inputs(303, 40, 100, 77, 3)
+    assert _noalloc(Ds, Ys, 3)[0] == 0
+    D, Y = _inputs(304 + s, 256, 512, 1000, 12)
+    rc, *got = _noalloc(D, Y, s)
+    assert rc == 0
+    ctx = sdl.context(0)
+    ctx.set_option(sdl.OPT_OMP_FORM, 1)
+    try:
+        fused = sdl.omp(D, Y, s)
+    finally:
+        ctx.set_option(sdl.OPT_OMP_FORM, 0)
+    for a, b in zip(got, fused):
+        assert torch.equal(a, b)
+    _same_codes(got, sdl.omp(D, Y, s))
+    gi, gv, gn, gr = (t.cpu().numpy() for t in got)
+    D64, Y64 = D.cpu().numpy().astype(np.float64), Y.cpu().numpy().astype(np.float64)
+    orc = oracle.omp(D64, Y64, s)
+    # picks past the signals' 12-atom supports code the noise, whose largest
+    # correlations lie close together: more near-ties than the default cap allows
+    st = compare_codes(D64, Y64, gi, gv, gn, gr, orc, fp32_gap_tol(256, np.linalg.norm(Y64, axis=1)), 1e-4,
+                       max_excused=0.05)
+    print(f"noalloc K=512 m=256 s={s}: {st['same']} of 1000 codes equal the oracle's, {st['excused']} near-ties")
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
