@@ -3,13 +3,38 @@
 Greedy OMP is discontinuous in its inputs: where two atoms tie for the largest
 |d_j^T r| (to within rounding) either choice is a correct execution of the
 definition.  So a signal's support must equal the oracle's unless, at the
-first step where they differ, the oracle's top-two gap is below `gap_tol`;
-such a signal is then checked for validity on its own support (coefficients
-are the least-squares fit, the reported residual is that fit's residual).
+first step k where they differ, both hold:
+  (a) the oracle's top-two gap there is below the path's rounding bound;
+  (b) the GPU's atom g was near-maximal under the oracle's residual r_k (the
+      least-squares residual of y on the common prefix, recomputed here in
+      FP64): max_j |d_j^T r_k| - |d_g^T r_k| is within that bound too.
+Such a signal is then checked for validity on its own support (coefficients
+are the least-squares fit, the reported residual is that fit's residual), and
+a test caps how many signals may be excused this way.  Differences at a
+rounding-level step, where even the oracle's largest correlation is within the
+bound (the prefix already fits y to rounding, as when a signal is itself an
+atom of the dictionary, or what is left is noise below the path's
+resolution), are counted apart and not capped: there every atom is a correct
+choice at that precision.
+
+Rounding bounds.  A correlation the GPU forms at step k is
+alpha0_j - g_j^T G_SS^-1 alpha0_S (Batch-OMP, Sec. 1 greedy choice): with
+alpha0 = D^T y off by delta, the compared value is off by
+delta_j - w_j^T delta_S, w_j = G_SS^-1 D_S^T d_j the coefficients of d_j on the
+prefix atoms.  |delta_j| <= e sum_i |d_ji y_i| with e = gamma_m for FP32
+products (u = 2^-24) and e = 2u_b + u_b^2 + gamma_m for BF16 operands
+(round to nearest, u_b = 2^-9, exact products, FP32 accumulation).
 """
 from __future__ import annotations
 
 import numpy as np
+
+U32 = 2.0 ** -24
+UB16 = 2.0 ** -9
+
+
+def gamma(m: int, u: float = U32) -> float:
+    return m * u / (1 - m * u)
 
 
 def fp32_gap_tol(m: int, ynorm: np.ndarray) -> np.ndarray:
@@ -17,24 +42,89 @@ def fp32_gap_tol(m: int, ynorm: np.ndarray) -> np.ndarray:
     m-term dot product of unit-norm d_j with y is at most gamma_m ||y||,
     gamma_m = m u / (1 - m u), u = 2^-24; two correlations must move for their
     order to flip, so ties closer than 2 gamma_m ||y|| are undecidable in FP32."""
-    u = 2.0 ** -24
-    gm = m * u / (1 - m * u)
-    return np.maximum(1e-6, 2 * gm * ynorm)
+    return np.maximum(1e-6, 2 * gamma(m) * ynorm)
 
 
-def compare_codes(D, Y, gpu_idx, gpu_val, gpu_nnz, gpu_r2, orc, gap_tol, coef_rtol, r2_rtol=None, eps=None):
+def bf16_unit(m: int) -> float:
+    """Relative error bound of one BF16-operand correlation term sum."""
+    return 2 * UB16 + UB16 ** 2 + gamma(m) * (1 + 2 * UB16)
+
+
+def step_correlations(D, y, S):
+    """|d_j^T r| of every atom, r the FP64 least-squares residual of y on the
+    atoms S (selected atoms masked to -inf), and the coefficients W (|S| x K)
+    of every atom on D_S."""
+    if len(S):
+        B = D[S].T
+        x, *_ = np.linalg.lstsq(B, y, rcond=None)
+        r = y - B @ x
+        W, *_ = np.linalg.lstsq(B, D.T, rcond=None)
+    else:
+        r, W = y, np.zeros((0, D.shape[0]))
+    c = np.abs(D @ r)
+    c[list(S)] = -np.inf
+    return c, W
+
+
+def corr_error_bound(D, y, S, W, e):
+    """Per-atom bound e (a_j + |w_j|^T a_S), a_j = sum_i |d_ji y_i|, on the
+    error of the correlation the GPU compares at a step with prefix S."""
+    a = np.abs(D) @ np.abs(y)
+    return e * (a + (np.abs(W).T @ a[list(S)] if len(S) else 0.0))
+
+
+def _first_difference(gi, gn, oi, on):
+    k = int(np.argmax(gi != oi)) if (gi != oi).any() else int(min(gn, on))
+    g = int(gi[k]) if k < len(gi) and k < gn else -1
+    o = int(oi[k]) if k < len(oi) and k < on else -1
+    return k, g, o
+
+
+def _near_tie(D, y, gi, gn, oi, on, orc_gap_k, tol_a, tol_b, e):
+    """Checks (a) with tolerance tol_a(E, o, g) and (b) with tol_b(E, o, g) at
+    the first differing step (E: the per-atom bound there); returns whether
+    that step is at rounding level (the largest correlation within tol_b)."""
+    k, g, o = _first_difference(gi, gn, oi, on)
+    S = [int(v) for v in gi[:k]]
+    c, W = step_correlations(D, y, S)
+    E = corr_error_bound(D, y, S, W, e)
+    if o >= 0 and g >= 0:
+        assert orc_gap_k < tol_a(E, o, g), (
+            f"support differs at step {k} (gpu {gi.tolist()} orc {oi.tolist()}) but the oracle gap there is "
+            f"{orc_gap_k:.3e} >= {tol_a(E, o, g):.3e}")
+        lag = c[o] - c[g]
+        assert lag <= tol_b(E, o, g), (
+            f"step {k}: the GPU's atom {g} trails the oracle's {o} by {lag:.3e} under the oracle's residual, "
+            f"beyond the rounding bound {tol_b(E, o, g):.3e} (gpu {gi.tolist()} orc {oi.tolist()})")
+        return bool(c[o] <= tol_b(E, o, o))
+    else:
+        # one side stopped where the other went on: the atom it went on with
+        # must have a correlation within rounding of zero
+        j = o if o >= 0 else g
+        assert j >= 0 and c[j] <= tol_b(E, j, j), (
+            f"step {k}: one side stops (gpu {gi.tolist()} orc {oi.tolist()}) while atom {j} still has "
+            f"|d^T r| = {c[j]:.3e}")
+        return True
+
+
+def compare_codes(D, Y, gpu_idx, gpu_val, gpu_nnz, gpu_r2, orc, gap_tol, coef_rtol, r2_rtol=None, eps=None,
+                  max_excused=0.002):
     """Returns a dict of counts; raises AssertionError on a real mismatch.
 
     D (K, m) and Y (n, m) are float64 numpy arrays of the inputs both sides saw.
-    gap_tol: scalar or per-signal array.  eps: the error-constrained stop, if
-    any; a code that agrees with the oracle's on their common prefix but stops
-    at another length is then a near-tie on the stop itself when the prefix's
-    least-squares residual norm is eps to within 1e-4 eps."""
+    gap_tol: scalar or per-signal array (the FP32 rule of fp32_gap_tol, or the
+    stated 1e-6 on FP64).  eps: the error-constrained stop, if any; a code that
+    agrees with the oracle's on their common prefix but stops at another length
+    is then a near-tie on the stop itself when the prefix's least-squares
+    residual norm is eps to within 1e-4 eps.  At most max_excused of the
+    signals may be excused near-ties (stop near-ties and rounding-level steps
+    are counted apart, as excused_eps and excused_rounding)."""
     n, s = gpu_idx.shape
+    m = D.shape[1]
     gap_tol = np.broadcast_to(np.asarray(gap_tol, dtype=np.float64), (n,))
     r2_rtol = coef_rtol if r2_rtol is None else r2_rtol
     same = (gpu_idx == orc["idx"]).all(axis=1) & (gpu_nnz == orc["nnz"])
-    stats = dict(n=n, same=int(same.sum()), excused=0)
+    stats = dict(n=n, same=int(same.sum()), excused=0, excused_eps=0, excused_rounding=0)
     # identical supports: coefficients and residual energies
     if same.any():
         xo, xg = orc["val"][same], gpu_val[same].astype(np.float64)
@@ -49,7 +139,9 @@ def compare_codes(D, Y, gpu_idx, gpu_val, gpu_nnz, gpu_r2, orc, gap_tol, coef_rt
         err = np.abs(rg - ro) / np.maximum(ro, 1e-6 * yn2 + 1e-300)
         assert err.max() <= max(r2_rtol, 1e-4) * 10, f"resid2 rel err {err.max():.3e}"
         stats["coef_rel_max"] = float(rel.max())
-    # differing supports: must be a near-tie in the oracle, and valid on its own
+    # differing supports: a near-tie in the oracle at which the GPU's atom was
+    # near-maximal, and a valid code on its own support
+    e32 = gamma(m)
     for i in np.nonzero(~same)[0]:
         gi, oi = gpu_idx[i], orc["idx"][i]
         kmin = int(min(gpu_nnz[i], orc["nnz"][i]))
@@ -62,28 +154,41 @@ def compare_codes(D, Y, gpu_idx, gpu_val, gpu_nnz, gpu_r2, orc, gap_tol, coef_rt
                 rk = np.linalg.norm(Y[i])
             assert abs(rk - eps) <= 1e-4 * eps, (
                 f"signal {i}: stops at {gpu_nnz[i]} (oracle {orc['nnz'][i]}) with ||r|| {rk:.8e} vs eps {eps:.8e}")
-            stats["excused"] += 1
+            stats["excused_eps"] += 1
             continue
-        k = int(np.argmax(gi != oi)) if (gi != oi).any() else kmin
-        g = orc["gap"][i][k] if k < s else np.inf
-        assert g < gap_tol[i], (
-            f"signal {i}: support differs at step {k} (gpu {gi.tolist()} orc {oi.tolist()}) "
-            f"but the oracle gap there is {g:.3e} >= {gap_tol[i]:.3e}")
+        k, _, _ = _first_difference(gi, gpu_nnz[i], oi, orc["nnz"][i])
+        gk = orc["gap"][i][k] if k < s else np.inf
+        # (a) with the gap rule as given; (b) with it widened by the
+        # running-correlation term where that is larger
+        t = gap_tol[i]
+        rounding = _near_tie(D, Y[i], gi, int(gpu_nnz[i]), oi, int(orc["nnz"][i]), gk, lambda E, o, g: t,
+                             lambda E, o, g: 2.0 * max(t, E[o] + E[g]), e32)
         S = gi[: gpu_nnz[i]]
         assert len(set(S.tolist())) == len(S) and (gi[gpu_nnz[i]:] == -1).all()
         if len(S):
             x, *_ = np.linalg.lstsq(D[S].T, Y[i], rcond=None)
             xg = gpu_val[i][: len(S)].astype(np.float64)
             assert np.abs(xg - x).max() <= 10 * coef_rtol * max(1.0, np.abs(x).max()), (i, xg, x)
-        stats["excused"] += 1
+        stats["excused_rounding" if rounding else "excused"] += 1
+    assert stats["excused"] + stats["excused_eps"] <= max(2, max_excused * n), (
+        f"{stats['excused']} + {stats['excused_eps']} (stop) of {n} signals differ at near-ties, above the cap "
+        f"{max_excused:.2%} ({stats['excused_rounding']} more at rounding-level steps)")
     return stats
 
 
-def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2):
+def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0.05):
+    """BF16-operand correlations (tcgen05) with FP32 refits: every code is valid
+    on its own support (exact least squares within coef_rtol, the reported
+    residual that fit's); a support may differ from the oracle's only at a step
+    where the oracle's top-two gap and the GPU atom's lag are both within
+    1.25 (E_o + E_g), the BF16 bound of the module docstring (the factor covers
+    the FP32 Gram and solve, about 2^-16 against 2^-8); at most max_excused of
+    the signals may differ at steps that are not at rounding level.  Returns
+    (signals that differ there, signals that differ at rounding-level steps)."""
     D64, Y64 = D.astype(np.float64), Y.astype(np.float64)
     n, s = idx.shape
-    tol = 2 * 2.0 ** -8 * (np.linalg.norm(Y64, axis=1) + 2 * np.abs(orc["val"]).sum(axis=1))
-    excused = 0
+    e16 = bf16_unit(D.shape[1])
+    excused = rounding = 0
     for i in range(n):
         k = int(nnz[i])
         S = idx[i, :k]
@@ -95,9 +200,14 @@ def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2):
             res = Y64[i] - D64[S].T @ x
             assert abs(r2[i] - res @ res) <= 1e-3 * (Y64[i] @ Y64[i]) + 1e-6
         if not ((idx[i] == orc["idx"][i]).all() and nnz[i] == orc["nnz"][i]):
-            diff = np.nonzero(idx[i] != orc["idx"][i])[0]
-            step = int(diff[0]) if len(diff) else min(int(nnz[i]), int(orc["nnz"][i]))
-            g = orc["gap"][i][step] if step < s else np.inf
-            assert g < tol[i], (i, step, g, tol[i], idx[i], orc["idx"][i])
-            excused += 1
-    return excused
+            kk, _, _ = _first_difference(idx[i], k, orc["idx"][i], int(orc["nnz"][i]))
+            gk = orc["gap"][i][kk] if kk < s else np.inf
+            tol = lambda E, o, g: 1.25 * (E[o] + E[g])  # noqa: E731
+            if _near_tie(D64, Y64[i], idx[i], k, orc["idx"][i], int(orc["nnz"][i]), gk, tol, tol, e16):
+                rounding += 1
+            else:
+                excused += 1
+    assert excused <= max(2, max_excused * n), (
+        f"{excused} of {n} BF16 supports differ at near-ties, above the cap {max_excused:.2%} "
+        f"({rounding} more at rounding-level steps)")
+    return excused, rounding

@@ -2,14 +2,19 @@
 against the FP64 oracle, through the C ABI.
 
 Tolerances (derived from the arithmetic): BF16 rounds each operand to 8
-significant bits (u = 2^-9), products are exact and accumulate in FP32, so a
-correlation of a unit atom with y is off by at most about 2^-8 ||y||, and a
-Batch-OMP update alpha0 - G_S x adds 2^-8 ||x||_1 per Gram factor.  Supports may
-therefore differ from the oracle's only where the oracle's top-two gap is below
-2 * 2^-8 (||y|| + 2 ||x||_1).  Whatever support the GPU chose, its coefficients
-are refitted in FP32 on that support from D and y, so they must equal the exact
-least-squares fit on that support within the BF16 coefficient tolerance 2e-2,
-and the reported residual must be that fit's residual.
+significant bits (round to nearest, u = 2^-9), products are exact and
+accumulate in FP32, so alpha0_j = d_j^T y is off by at most
+e sum_i |d_ji y_i|, e = 2u + u^2 + gamma_m.  The selection compares running
+correlations alpha0_j - g_j^T G_SS^-1 alpha0_S (FP32 Gram from a BF16 hi/lo
+split, about 2^-16), which inherit that error as delta_j - w_j^T delta_S with
+w_j the coefficients of d_j on the support so far.  A support may differ from
+the oracle's only at a step where the oracle's top-two gap, and the amount by
+which the GPU's atom trails the oracle's under the oracle's own residual, are
+both below 1.25 (E_o + E_g), E the per-atom bound (tests/_parity.py); each test
+caps the share of signals that differ.  Whatever support the GPU chose, its
+coefficients are refitted in FP32 on that support from D and y, so they must
+equal the exact least-squares fit on that support within the BF16 coefficient
+tolerance 2e-2, and the reported residual must be that fit's residual.
 """
 import numpy as np
 import pytest
@@ -18,10 +23,16 @@ import torch
 import oracle
 import paper_1403_4781_gb300 as sdl
 import sdl_inputs as si
-from _parity import check_bf16_codes
+from _parity import check_bf16_codes, compare_codes, fp32_gap_tol
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
+# Share of signals allowed to differ at near-ties that are not at rounding
+# level, about twice what these seeded inputs gave (2.2 %, 0.9 %, 28 %, 1.8 %,
+# 50 %).  The signals hold at most 6 atoms: coding them with s = 10 or 16 atoms
+# spends the last picks on noise whose largest correlations lie within the
+# BF16 bound of one another, hence the two high shares.
+CAPS = {(64, 256): 0.04, (64, 128): 0.02, (144, 512): 0.40, (30, 60): 0.04, (256, 1024): 0.65}
 
 
 def _t(a):
@@ -42,26 +53,32 @@ def test_bf16_omp_matches_oracle(m, K, n, s):
     idx, val, nnz, r2 = sdl.omp(_t(D), _t(Y), s, prec=sdl.PREC_BF16)
     torch.cuda.synchronize()
     orc = oracle.omp(D.astype(np.float64), Y.astype(np.float64), s)
-    excused = check_bf16_codes(D, Y, idx.cpu().numpy(), val.cpu().numpy(), nnz.cpu().numpy(),
-                               r2.cpu().numpy(), orc)
+    excused, rounding = check_bf16_codes(D, Y, idx.cpu().numpy(), val.cpu().numpy(), nnz.cpu().numpy(),
+                                         r2.cpu().numpy(), orc, max_excused=CAPS[(m, K)])
     # near-tie picks cost little: mean residual energy within 5 % of the oracle's
     # (measured 2.7 % at m=30, K=60 where ties are most frequent)
     assert r2.cpu().numpy().astype(np.float64).mean() <= 1.05 * orc["resid2"].mean() + 1e-9
-    print(f"m={m} K={K}: {excused} of {n} supports differ at near-ties")
+    print(f"m={m} K={K}: {excused} of {n} supports differ at near-ties, {rounding} more at rounding-level steps")
 
 
 def test_bf16_gram_and_correlation_exact_on_bf16_representable_inputs():
-    """With inputs that BF16 represents exactly (dyadic values), the tensor-core
-    products are exact, so the codes must equal the FP64 oracle's exactly."""
+    """With inputs that BF16 represents exactly (multiples of 1/8 in [-1, 1]),
+    the tensor-core products are exact: alpha0 = D^T y and the split Gram carry
+    no BF16 rounding at all, so the BF16 path must meet the FP32 bar against the
+    FP64 oracle (supports equal except at FP32 near-ties, coefficients within
+    1e-4).  The atoms are not unit norm here; the FP32 gap rule is scaled by the
+    largest atom norm."""
     rng = np.random.default_rng(410)
     m, K, n, s = 64, 256, 300, 4
     D = (rng.integers(-8, 9, size=(K, m)) / 8.0).astype(np.float32)
     Y = (rng.integers(-8, 9, size=(n, m)) / 8.0).astype(np.float32)
-    idx, val, nnz, r2 = sdl.omp(_t(D), _t(Y), s, prec=sdl.PREC_BF16)
-    fidx, fval, fnnz, fr2 = sdl.omp(_t(D), _t(Y), s, prec=sdl.PREC_F32)
-    # atoms are not unit norm here, which both paths handle identically
-    same = (idx.cpu().numpy() == fidx.cpu().numpy()).all(axis=1).mean()
-    assert same > 0.99, same
+    idx, val, nnz, r2 = (x.cpu().numpy() for x in sdl.omp(_t(D), _t(Y), s, prec=sdl.PREC_BF16))
+    D64, Y64 = D.astype(np.float64), Y.astype(np.float64)
+    orc = oracle.omp(D64, Y64, s)
+    dmax = np.linalg.norm(D64, axis=1).max()
+    st = compare_codes(D64, Y64, idx, val, nnz, r2, orc, fp32_gap_tol(m, np.linalg.norm(Y64, axis=1) * dmax), 1e-4,
+                       max_excused=0.01)
+    print(f"BF16 on BF16-exact inputs: {st['same']} of {n} supports equal the oracle's, {st['excused']} near-ties")
 
 
 def test_bf16_batched_uneven_subsets():
@@ -79,23 +96,29 @@ def test_bf16_batched_uneven_subsets():
         if a == b:
             continue
         orc = oracle.omp(Ds[t].astype(np.float64), Y[a:b].astype(np.float64), s)
-        check_bf16_codes(Ds[t], Y[a:b], idx[a:b], val[a:b], nnz[a:b], r2[a:b], orc)
+        # the signals are Gaussian noise, not sparse: measured at most 4.6 % per subset
+        ex, ro = check_bf16_codes(Ds[t], Y[a:b], idx[a:b], val[a:b], nnz[a:b], r2[a:b], orc, max_excused=0.08)
+        print(f"batched subset {t} ({b - a} signals): {ex} differ at near-ties, {ro} at rounding-level steps")
 
 
 def test_bf16_local_training_per_iteration():
     """One training iteration from a shared dictionary: the BF16 coding pass's RMSE
     is within 1e-3 of the oracle's (its refit coefficients are exact least
-    squares; only near-tie supports may differ), and the MOD update that follows
-    stays close to the oracle's."""
+    squares; only near-tie supports may differ), and the updated atoms equal the
+    oracle's MOD of the GPU's own codes within the FP32 atom tolerance 2e-5."""
     p = si.split_merge_problem("t", 64, 256, 6, 2, 3, 256, [2000, 1500, 2500], 4, 4, 0.01,
                                np.random.default_rng(412))
     Yp = p.Y[p.perm]
     Dl = np.stack([Yp[q] / np.linalg.norm(Yp[q], axis=1, keepdims=True) for q in p.picks]).astype(np.float32)
-    Dg = _t(Dl.copy())
-    _, rmse = sdl.local_train(_t(Yp), p.offsets, Dg, p.s1, 1, prec=sdl.PREC_BF16)
+    Dg, Ypg = _t(Dl.copy()), _t(Yp)
+    idx, val, nnz, r2 = (x.cpu().numpy() for x in sdl.omp_batched(Dg, Ypg, p.offsets, p.s1, prec=sdl.PREC_BF16))
+    _, rmse = sdl.local_train(Ypg, p.offsets, Dg, p.s1, 1, prec=sdl.PREC_BF16)
     orc = oracle.local_train(Yp.astype(np.float64), p.offsets, Dl.astype(np.float64), p.s1, 1)
     rel = np.abs(rmse.cpu().numpy()[:, 0] - orc["rmse"][:, 0]) / orc["rmse"][:, 0]
     assert rel.max() < 1e-3, rel
-    # atoms used by signals whose near-tie support changed move; the rest agree
-    per_atom = np.abs(Dg.cpu().numpy() - orc["D"]).max(axis=2).ravel()
-    assert np.quantile(per_atom, 0.9) < 0.02, np.quantile(per_atom, [0.5, 0.9, 0.99])
+    after = Dg.cpu().numpy()
+    for t in range(p.L):
+        a, b = p.offsets[t], p.offsets[t + 1]
+        Dm, *_ = oracle.mod(Yp[a:b].astype(np.float64), idx[a:b], val[a:b].astype(np.float64),
+                            Dl[t].astype(np.float64), True)
+        np.testing.assert_allclose(after[t], Dm, rtol=0, atol=2e-5, err_msg=f"subset {t}")

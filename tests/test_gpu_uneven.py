@@ -28,6 +28,10 @@ from _parity import check_bf16_codes
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 ITERS = 4
+# share of a subset's signals allowed to differ at near-ties not at rounding
+# level, per iteration (measured at most 7.4 % on shape A and 15.5 % on shape
+# B, both on their smallest subsets)
+CAP = {"A": 0.12, "B": 0.25}
 
 
 def _t(a):
@@ -43,7 +47,7 @@ def test_uneven_bf16_training_full_size_sampled_subsets(shape):
     Yg = sdl.split(_t(p.Y), _t(p.perm))
     Dg = sdl.init_dict(Yg, _t(p.picks.reshape(-1)), _t(p.fill.reshape(-1, p.m))).reshape(p.L, p.K1, p.m)
     Yp = Yg.cpu().numpy().astype(np.float64)
-    worst, excused, coded = 0.0, 0, 0
+    worst, excused, rounding, coded = 0.0, 0, 0, 0
     for it in range(ITERS):
         before = Dg.cpu().numpy()
         idx, val, nnz, r2 = (x.cpu().numpy() for x in
@@ -56,8 +60,10 @@ def test_uneven_bf16_training_full_size_sampled_subsets(shape):
             a, b = p.offsets[t], p.offsets[t + 1]
             Dt = before[t].astype(np.float64)
             orc = oracle.omp(Dt, Yp[a:b], p.s1)
-            excused += check_bf16_codes(before[t], Yp[a:b].astype(np.float32), idx[a:b], val[a:b], nnz[a:b],
-                                        r2[a:b], orc)
+            ex, ro = check_bf16_codes(before[t], Yp[a:b].astype(np.float32), idx[a:b], val[a:b], nnz[a:b],
+                                      r2[a:b], orc, max_excused=CAP[shape])
+            excused, rounding = excused + ex, rounding + ro
+            print(f"shape {shape} it {it} subset {t} ({b - a} signals): {ex} differ, {ro} at rounding level")
             coded += b - a
             o = oracle.train(Yp[a:b], Dt, p.s1, 1)
             rel = abs(rmse[t] - o["rmse"][0]) / o["rmse"][0]
@@ -66,4 +72,5 @@ def test_uneven_bf16_training_full_size_sampled_subsets(shape):
             Dm, *_ = oracle.mod(Yp[a:b], idx[a:b], val[a:b].astype(np.float64), Dt, True)
             np.testing.assert_allclose(after[t], Dm, rtol=0, atol=2e-5, err_msg=f"{shape} it {it} subset {t}")
     print(f"shape {shape}: sampled subsets {sample} (sizes {sizes[sample].tolist()}), "
-          f"worst per-iteration RMSE error {worst:.2e}, {excused} of {coded} codes differ at near-ties")
+          f"worst per-iteration RMSE error {worst:.2e}, {excused} of {coded} codes differ at near-ties, "
+          f"{rounding} more at rounding-level steps")
