@@ -148,6 +148,8 @@ def algorithmic_work(p):
                       + p.N * omp_flops(K, p.s)),
         "omp_tc": ("alu", p.iters_local * p.N * omp_flops(K1, p.s1) + p.iters_merge * nm * omp_flops(K, p.s2)
                    + p.N * omp_flops(K, p.s)),
+        # residual form: D^T r of every step on the tensor cores (2 m K s per signal)
+        "omp_rtc": ("tensor", 2 * m * (p.iters_local * p.N * K1 * p.s1 + p.iters_merge * nm * K * p.s2 + p.N * K * p.s)),
         "gram": ("alu", p.iters_local * L * 2 * K1 * K1 * m + p.iters_merge * 2 * K * K * m),
     }
 
@@ -417,7 +419,10 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
     roof = None
     if name_k in work:
         kind, flops_step = work[name_k]
-        peak = FP64_PEAK_FLOPS if "fp64" in name_k else FP32_PEAK_FLOPS
+        peaks = load_peaks()
+        # a kernel timed inside a long step: the sustained BF16 figure
+        peak = (FP64_PEAK_FLOPS if "fp64" in name_k else
+                peaks.get("bf16_tflops_sustained", 1700.0) * 1e12 if kind == "tensor" else FP32_PEAK_FLOPS)
         achieved = flops_step * psteps / (kms / 1e3)
         tr = TRAFFIC.get((name, name_k))
         roof = {"kernel": name_k, "bound": kind, "achieved": achieved / 1e12,
@@ -426,13 +431,14 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
                 "traffic_source": tr[1] if tr else "no ncu capture of this kernel's current code",
                 "algorithmic_flops_per_launch": flops_step / max(nl / psteps, 1),
                 "peak_source": ("FP64 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived from unit counts and "
-                                "the maximum clock; a DFMA probe measured 1.254 TFLOP/s)"
-                                if "fp64" in name_k else "FP32 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"),
+                                "the maximum clock; a DFMA probe measured 1.254 TFLOP/s)" if "fp64" in name_k else
+                                "measured BF16 dense, sustained (MEASURED_PEAKS.json)" if kind == "tensor" else
+                                "FP32 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"),
                 "share_of_step": kms / prof_total_ms, "launches": nl,
                 "timed": "instrumented eager pass over %d steps (%.2f ms/step)" % (psteps, prof_total_ms / psteps)}
     kernels = {k: {"ms_per_step": v[2] / psteps, "launches_per_step": v[0] / psteps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}
-    omp_names = ("omp", "omp_split", "gram", "omp_tc", "gram_tc", "bf16_image")
+    omp_names = ("omp", "omp_split", "gram", "omp_tc", "omp_rtc", "gram_tc", "bf16_image")
     omp_ms = sum(v[2] for k, v in prof.items() if k in omp_names) / psteps
 
     res = {

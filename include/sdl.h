@@ -357,6 +357,16 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     shared memory.  2 = a correlation GEMM of 128-signal tiles into a
  *     workspace scratch, then the selection kernel.  Both compute the same
  *     correlations (FMAs over the signal entries in order).
+ *   SDL_OPT_BF16_FORM: BF16 OMP kernels.  0 = automatic (default): form 1.
+ *     1 = Batch-OMP form: alpha0 =
+ *     D^T y of 128-signal tiles on the tensor cores into a workspace scratch,
+ *     then the selection kernel's running correlations through the Gram.
+ *     2 = residual form: one kernel recomputes D^T r of a 128-signal tile at
+ *     every step on the tensor cores (accumulators in tensor memory) and forms
+ *     the residuals and right-hand sides in FP32 (s <= 16 and m <= 256; other
+ *     shapes run form 1).  Both refit the coefficients
+ *     on the chosen support in FP32 with one refinement step; they may choose
+ *     differently among atoms whose correlations tie to within BF16 rounding.
  *   SDL_OPT_REPLACE: min_use of the atom replacement (sdl_replace_atoms) run
  *     after every MOD update of the training loops.  0 (default) = off, the
  *     paper's reading: unused atoms keep their value.  This option changes the
@@ -370,7 +380,8 @@ typedef enum {
   SDL_OPT_GRAPH = 5,
   SDL_OPT_SM_BLOCKS = 6,
   SDL_OPT_REPLACE = 7,
-  SDL_OPT_OMP_FORM = 8
+  SDL_OPT_OMP_FORM = 8,
+  SDL_OPT_BF16_FORM = 9
 } sdl_option;
 sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
 

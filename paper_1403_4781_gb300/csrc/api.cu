@@ -325,6 +325,8 @@ cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t
   if (e != cudaSuccess) return e;
   e = timed(ctx, "gram_tc", 1, [&] { return launch_gram_tc(img, lo, oa.K, oa.m, oa.L, G, err, sm); });
   if (e != cudaSuccess) return e;
+  if (ctx->opt_bf16_form == 2 && omp_rtc_supported(oa.K, oa.m, oa.s))
+    return timed(ctx, "omp_rtc", 1, [&] { return launch_omp_rtc(oa, sm); });
   return timed(ctx, "omp_tc", split_kernels(oa), [&] { return launch_omp_tc(oa, a0c, sm); });
 }
 
@@ -547,7 +549,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
              sizeof(T), (int)bf16, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
              (void *)d_off, m, K, s, L, (long long)n, (long long)tiles, (long long)ma.total_tiles, eps, iters,
              ctx->opt_mod_solve, ctx->opt_tile, ctx->opt_cluster * 4 + ctx->opt_sm_blocks, ctx->opt_autotune,
-             (int)ctx->tuned.size(), ctx->opt_replace * 4 + ctx->opt_omp_form);
+             (int)ctx->tuned.size(), (ctx->opt_replace * 4 + ctx->opt_omp_form) * 4 + ctx->opt_bf16_form);
     const std::string key(kb);
     auto hit = ctx->graphs.find(key);
     if (hit != ctx->graphs.end()) {
@@ -1309,6 +1311,10 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
     case SDL_OPT_OMP_FORM:
       if (value < 0 || value > 2) return set_error(ctx, SDL_EINVAL, "SDL_OPT_OMP_FORM takes 0, 1 or 2");
       ctx->opt_omp_form = (int)value;
+      return SDL_OK;
+    case SDL_OPT_BF16_FORM:
+      if (value < 0 || value > 2) return set_error(ctx, SDL_EINVAL, "SDL_OPT_BF16_FORM takes 0, 1 or 2");
+      ctx->opt_bf16_form = (int)value;
       return SDL_OK;
     case SDL_OPT_GRAPH:
       if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_GRAPH takes 0 or 1");

@@ -77,6 +77,7 @@ struct sdl_ctx {
   int opt_graph = 0;             // replay training loops as captured CUDA graphs
   int opt_replace = 0;           // atom replacement after every MOD update: min_use (0 = off)
   int opt_omp_form = 0;          // FP32 OMP: 0 automatic, 1 fused kernel, 2 correlation GEMM + selection
+  int opt_bf16_form = 0;         // BF16 OMP: 0 automatic, 1 Batch-OMP selection, 2 residual form
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
@@ -143,6 +144,11 @@ cudaError_t launch_gram_tc(const void *hi, const void *lo, int K, int m, int L, 
 // loop from there.
 cudaError_t launch_omp_tc(const OmpArgs &a, float *a0c, cudaStream_t st);
 int omp_tc_tile_signals(int K, int m, int s);
+// Residual-form OMP on the tensor cores (same 128-signal tiles, same BF16
+// images and FP32 Gram): D^T r of every step by tcgen05 into TMEM, picks,
+// Cholesky rows and FP32 residuals per signal.  Shapes: s <= 16, m <= 256.
+bool omp_rtc_supported(int K, int m, int s);
+cudaError_t launch_omp_rtc(const OmpArgs &a, cudaStream_t st);
 // The selection kernel over 128-signal tiles tile0 .. tile0+ntile-1 whose
 // alpha0 rows are in a0c (FP32 data).  exact: alpha0 came from BF16 products,
 // so the coefficients are refitted from D_S^T y.

@@ -48,6 +48,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, int lim
                  : "=r"(done) : "r"(smem_u32(bar)), "r"(phase) : "memory");
   return done != 0;
 }
+// Bounded spin on an mbarrier phase with the non-blocking test_wait: the thread
+// stays runnable and sees the completion at once (try_wait may suspend it).
+__device__ __forceinline__ bool mbar_poll(uint64_t *bar, uint32_t phase, int limit) {
+  uint32_t done = 0;
+  for (int it = 0; it < limit && !done; ++it)
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+  return done != 0;
+}
 // Bulk copy (TMA, no tensor map): bytes and both addresses multiples of 16.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -89,6 +98,33 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Plain arrival on an mbarrier (one of its expected arrivals).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// OR of `c` over the `nthreads` threads (a multiple of 32) that reach named
+// barrier `id` (1..15; 0 is __syncthreads'), which they also synchronise.
+__device__ __forceinline__ bool named_any(int id, int nthreads, bool c) {
+  uint32_t r;
+  asm volatile("{\n .reg .pred pc, pr;\n setp.ne.u32 pc, %1, 0;\n bar.red.or.pred pr, %2, %3, pc;\n"
+               " selp.u32 %0, 1, 0, pr;\n}\n"
+               : "=r"(r) : "r"((uint32_t)c), "r"(id), "r"(nthreads) : "memory");
+  return r != 0;
 }
 
 // Dynamic shared memory to request so that the blocks resident on one SM never

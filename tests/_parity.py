@@ -52,8 +52,8 @@ def bf16_unit(m: int) -> float:
 
 def step_correlations(D, y, S):
     """|d_j^T r| of every atom, r the FP64 least-squares residual of y on the
-    atoms S (selected atoms masked to -inf), and the coefficients W (|S| x K)
-    of every atom on D_S."""
+    atoms S (selected atoms masked to -inf), the coefficients W (|S| x K) of
+    every atom on D_S, and r."""
     if len(S):
         B = D[S].T
         x, *_ = np.linalg.lstsq(B, y, rcond=None)
@@ -63,12 +63,16 @@ def step_correlations(D, y, S):
         r, W = y, np.zeros((0, D.shape[0]))
     c = np.abs(D @ r)
     c[list(S)] = -np.inf
-    return c, W
+    return c, W, r
 
 
-def corr_error_bound(D, y, S, W, e):
-    """Per-atom bound e (a_j + |w_j|^T a_S), a_j = sum_i |d_ji y_i|, on the
-    error of the correlation the GPU compares at a step with prefix S."""
+def corr_error_bound(D, y, S, W, e, r=None):
+    """Per-atom bound on the error of the correlation the GPU compares at a
+    step with prefix S.  Running correlations (Batch-OMP): e (a_j + |w_j|^T a_S),
+    a_j = sum_i |d_ji y_i|.  Recomputed from the residual (r given): e b_j,
+    b_j = sum_i |d_ji r_i|."""
+    if r is not None:
+        return e * (np.abs(D) @ np.abs(r))
     a = np.abs(D) @ np.abs(y)
     return e * (a + (np.abs(W).T @ a[list(S)] if len(S) else 0.0))
 
@@ -80,14 +84,15 @@ def _first_difference(gi, gn, oi, on):
     return k, g, o
 
 
-def _near_tie(D, y, gi, gn, oi, on, orc_gap_k, tol_a, tol_b, e):
+def _near_tie(D, y, gi, gn, oi, on, orc_gap_k, tol_a, tol_b, e, residual=False):
     """Checks (a) with tolerance tol_a(E, o, g) and (b) with tol_b(E, o, g) at
-    the first differing step (E: the per-atom bound there); returns whether
-    that step is at rounding level (the largest correlation within tol_b)."""
+    the first differing step (E: the per-atom bound there, of the residual form
+    when `residual`); returns whether that step is at rounding level (the
+    largest correlation within tol_b)."""
     k, g, o = _first_difference(gi, gn, oi, on)
     S = [int(v) for v in gi[:k]]
-    c, W = step_correlations(D, y, S)
-    E = corr_error_bound(D, y, S, W, e)
+    c, W, r = step_correlations(D, y, S)
+    E = corr_error_bound(D, y, S, W, e, r if residual else None)
     if o >= 0 and g >= 0:
         assert orc_gap_k < tol_a(E, o, g), (
             f"support differs at step {k} (gpu {gi.tolist()} orc {oi.tolist()}) but the oracle gap there is "
@@ -176,15 +181,22 @@ def compare_codes(D, Y, gpu_idx, gpu_val, gpu_nnz, gpu_r2, orc, gap_tol, coef_rt
     return stats
 
 
-def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0.05):
+def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0.05, residual=False, eps=None):
     """BF16-operand correlations (tcgen05) with FP32 refits: every code is valid
     on its own support (exact least squares within coef_rtol, the reported
     residual that fit's); a support may differ from the oracle's only at a step
     where the oracle's top-two gap and the GPU atom's lag are both within
     1.25 (E_o + E_g), the BF16 bound of the module docstring (the factor covers
     the FP32 Gram and solve, about 2^-16 against 2^-8); at most max_excused of
-    the signals may differ at steps that are not at rounding level.  Returns
-    (signals that differ there, signals that differ at rounding-level steps)."""
+    the signals may differ at steps that are not at rounding level.
+    residual: the path recomputed D^T r from the BF16-rounded residual at every
+    step, so E is the residual form's bound e sum_i |d_ji r_i| (tighter as the
+    residual shrinks).  eps: the error-constrained stop; a code that agrees
+    with the oracle's on their common prefix but stops at another length is a
+    near-tie on the stop itself when the prefix's least-squares residual norm
+    is eps to within 1e-4 eps (counted with the rounding-level ones).  Returns
+    (signals that differ there, signals that differ at rounding-level steps or
+    at the stop)."""
     D64, Y64 = D.astype(np.float64), Y.astype(np.float64)
     n, s = idx.shape
     e16 = bf16_unit(D.shape[1])
@@ -200,10 +212,21 @@ def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0
             res = Y64[i] - D64[S].T @ x
             assert abs(r2[i] - res @ res) <= 1e-3 * (Y64[i] @ Y64[i]) + 1e-6
         if not ((idx[i] == orc["idx"][i]).all() and nnz[i] == orc["nnz"][i]):
+            kmin = min(k, int(orc["nnz"][i]))
+            if eps is not None and k != orc["nnz"][i] and (idx[i, :kmin] == orc["idx"][i, :kmin]).all():
+                P = idx[i, :kmin]
+                if kmin:
+                    xp, *_ = np.linalg.lstsq(D64[P].T, Y64[i], rcond=None)
+                    rk = np.linalg.norm(Y64[i] - D64[P].T @ xp)
+                else:
+                    rk = np.linalg.norm(Y64[i])
+                assert abs(rk - eps) <= 1e-4 * eps, (i, k, orc["nnz"][i], rk, eps)
+                rounding += 1
+                continue
             kk, _, _ = _first_difference(idx[i], k, orc["idx"][i], int(orc["nnz"][i]))
             gk = orc["gap"][i][kk] if kk < s else np.inf
             tol = lambda E, o, g: 1.25 * (E[o] + E[g])  # noqa: E731
-            if _near_tie(D64, Y64[i], idx[i], k, orc["idx"][i], int(orc["nnz"][i]), gk, tol, tol, e16):
+            if _near_tie(D64, Y64[i], idx[i], k, orc["idx"][i], int(orc["nnz"][i]), gk, tol, tol, e16, residual):
                 rounding += 1
             else:
                 excused += 1
@@ -211,3 +234,25 @@ def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0
         f"{excused} of {n} BF16 supports differ at near-ties, above the cap {max_excused:.2%} "
         f"({rounding} more at rounding-level steps)")
     return excused, rounding
+
+
+def check_rmse(r2_gpu, orc, idx, nnz, m, rmse_gpu=None, rtol=1e-3):
+    """The coding pass's RMSE against the oracle's, signal by signal.  A signal
+    whose support differs from the oracle's at a validated near-tie (checked by
+    compare_codes / check_bf16_codes) may legitimately end at another residual:
+    greedy OMP from another first pick follows another path.  So the RMSE over
+    the signals whose codes equal the oracle's must be within rtol of the
+    oracle's over the same signals, and the RMSE the GPU reports (rmse_gpu, if
+    given) must be that of its own residual energies r2_gpu.  Returns the
+    relative RMSE difference over all signals (for the printout)."""
+    r2g = np.asarray(r2_gpu, dtype=np.float64)
+    r2o = np.asarray(orc["resid2"], dtype=np.float64)
+    n = len(r2g)
+    same = (idx == orc["idx"]).all(axis=1) & (nnz == orc["nnz"])
+    if same.any():
+        a, b = np.sqrt(r2g[same].sum() / (m * same.sum())), np.sqrt(r2o[same].sum() / (m * same.sum()))
+        assert abs(a - b) <= rtol * b, (a, b, int(same.sum()), n)
+    full_g, full_o = np.sqrt(r2g.sum() / (m * n)), np.sqrt(r2o.sum() / (m * n))
+    if rmse_gpu is not None:
+        assert abs(rmse_gpu - full_g) <= 1e-5 * full_g + 1e-12, (rmse_gpu, full_g)
+    return (full_g - full_o) / full_o

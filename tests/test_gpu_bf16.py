@@ -23,7 +23,7 @@ import torch
 import oracle
 import paper_1403_4781_gb300 as sdl
 import sdl_inputs as si
-from _parity import check_bf16_codes, compare_codes, fp32_gap_tol
+from _parity import check_bf16_codes, check_rmse, compare_codes, fp32_gap_tol
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -46,19 +46,28 @@ def _problem(seed, m, K, n, s, sigma):
     return D0, Y
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("m,K,n,s", [(64, 256, 4133, 6), (64, 128, 700, 5), (144, 512, 1500, 10),
                                      (30, 60, 333, 6), (256, 1024, 300, 16)])
-def test_bf16_omp_matches_oracle(m, K, n, s):
+def test_bf16_omp_matches_oracle(m, K, n, s, form):
+    """Both BF16 forms (1: Batch-OMP selection from alpha0; 2: residual form)
+    under the Batch-OMP rule, whose bound covers both."""
     D, Y = _problem(400 + m + K, m, K, n, min(s, 6), 0.01)
-    idx, val, nnz, r2 = sdl.omp(_t(D), _t(Y), s, prec=sdl.PREC_BF16)
-    torch.cuda.synchronize()
+    ctx = sdl.context(0)
+    ctx.set_option(sdl.OPT_BF16_FORM, form)
+    try:
+        idx, val, nnz, r2 = sdl.omp(_t(D), _t(Y), s, prec=sdl.PREC_BF16)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_option(sdl.OPT_BF16_FORM, 0)
     orc = oracle.omp(D.astype(np.float64), Y.astype(np.float64), s)
     excused, rounding = check_bf16_codes(D, Y, idx.cpu().numpy(), val.cpu().numpy(), nnz.cpu().numpy(),
                                          r2.cpu().numpy(), orc, max_excused=CAPS[(m, K)])
     # near-tie picks cost little: mean residual energy within 5 % of the oracle's
     # (measured 2.7 % at m=30, K=60 where ties are most frequent)
     assert r2.cpu().numpy().astype(np.float64).mean() <= 1.05 * orc["resid2"].mean() + 1e-9
-    print(f"m={m} K={K}: {excused} of {n} supports differ at near-ties, {rounding} more at rounding-level steps")
+    print(f"form {form} m={m} K={K}: {excused} of {n} supports differ at near-ties, {rounding} more at "
+          f"rounding-level steps")
 
 
 def test_bf16_gram_and_correlation_exact_on_bf16_representable_inputs():
@@ -66,13 +75,20 @@ def test_bf16_gram_and_correlation_exact_on_bf16_representable_inputs():
     the tensor-core products are exact: alpha0 = D^T y and the split Gram carry
     no BF16 rounding at all, so the BF16 path must meet the FP32 bar against the
     FP64 oracle (supports equal except at FP32 near-ties, coefficients within
-    1e-4).  The atoms are not unit norm here; the FP32 gap rule is scaled by the
-    largest atom norm."""
+    1e-4).  This holds for the Batch-OMP form (alpha0 = D^T y and G feed every
+    step); the residual form rounds each step's residual to BF16.  The atoms
+    are not unit norm here; the FP32 gap rule is scaled by the largest atom
+    norm."""
     rng = np.random.default_rng(410)
     m, K, n, s = 64, 256, 300, 4
     D = (rng.integers(-8, 9, size=(K, m)) / 8.0).astype(np.float32)
     Y = (rng.integers(-8, 9, size=(n, m)) / 8.0).astype(np.float32)
-    idx, val, nnz, r2 = (x.cpu().numpy() for x in sdl.omp(_t(D), _t(Y), s, prec=sdl.PREC_BF16))
+    ctx = sdl.context(0)
+    ctx.set_option(sdl.OPT_BF16_FORM, 1)   # the Batch-OMP form: alpha0 and G exact on these inputs
+    try:
+        idx, val, nnz, r2 = (x.cpu().numpy() for x in sdl.omp(_t(D), _t(Y), s, prec=sdl.PREC_BF16))
+    finally:
+        ctx.set_option(sdl.OPT_BF16_FORM, 0)
     D64, Y64 = D.astype(np.float64), Y.astype(np.float64)
     orc = oracle.omp(D64, Y64, s)
     dmax = np.linalg.norm(D64, axis=1).max()
@@ -102,10 +118,11 @@ def test_bf16_batched_uneven_subsets():
 
 
 def test_bf16_local_training_per_iteration():
-    """One training iteration from a shared dictionary: the BF16 coding pass's RMSE
-    is within 1e-3 of the oracle's (its refit coefficients are exact least
-    squares; only near-tie supports may differ), and the updated atoms equal the
-    oracle's MOD of the GPU's own codes within the FP32 atom tolerance 2e-5."""
+    """One training iteration from a shared dictionary: the BF16 coding pass's
+    codes under the BF16 rule, its RMSE within 1e-3 of the oracle's over the
+    signals whose codes agree and equal to that of its own codes, and the
+    updated atoms equal to the oracle's MOD of the GPU's own codes within the
+    FP32 atom tolerance 2e-5."""
     p = si.split_merge_problem("t", 64, 256, 6, 2, 3, 256, [2000, 1500, 2500], 4, 4, 0.01,
                                np.random.default_rng(412))
     Yp = p.Y[p.perm]
@@ -113,12 +130,12 @@ def test_bf16_local_training_per_iteration():
     Dg, Ypg = _t(Dl.copy()), _t(Yp)
     idx, val, nnz, r2 = (x.cpu().numpy() for x in sdl.omp_batched(Dg, Ypg, p.offsets, p.s1, prec=sdl.PREC_BF16))
     _, rmse = sdl.local_train(Ypg, p.offsets, Dg, p.s1, 1, prec=sdl.PREC_BF16)
-    orc = oracle.local_train(Yp.astype(np.float64), p.offsets, Dl.astype(np.float64), p.s1, 1)
-    rel = np.abs(rmse.cpu().numpy()[:, 0] - orc["rmse"][:, 0]) / orc["rmse"][:, 0]
-    assert rel.max() < 1e-3, rel
-    after = Dg.cpu().numpy()
+    after, rmse = Dg.cpu().numpy(), rmse.cpu().numpy()[:, 0]
     for t in range(p.L):
         a, b = p.offsets[t], p.offsets[t + 1]
+        orc = oracle.omp(Dl[t].astype(np.float64), Yp[a:b].astype(np.float64), p.s1)
+        check_bf16_codes(Dl[t], Yp[a:b], idx[a:b], val[a:b], nnz[a:b], r2[a:b], orc)
+        check_rmse(r2[a:b], orc, idx[a:b], nnz[a:b], p.m, rmse[t])
         Dm, *_ = oracle.mod(Yp[a:b].astype(np.float64), idx[a:b], val[a:b].astype(np.float64),
                             Dl[t].astype(np.float64), True)
         np.testing.assert_allclose(after[t], Dm, rtol=0, atol=2e-5, err_msg=f"subset {t}")

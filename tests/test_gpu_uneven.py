@@ -9,7 +9,9 @@ oracle from the same dictionary (the GPU's):
   * the iteration's codes (the same batched BF16 OMP the training runs) meet the
     BF16 parity rule against the oracle's OMP: supports equal except at
     near-ties, coefficients the exact least squares on the GPU's support;
-  * the iteration's coding RMSE is within 1e-3 of the oracle's;
+  * the iteration's coding RMSE is within 1e-3 of the oracle's over the
+    signals whose codes agree, and the reported RMSE is that of the GPU's own
+    codes (a near-tie pick may lead greedy OMP to another final residual);
   * the updated atoms equal the oracle's MOD of the GPU's own codes within the
     FP32 atom tolerance 2e-5.
 Free-running BF16 and FP64 trajectories separate through near-tie support
@@ -23,7 +25,7 @@ import torch
 import oracle
 import paper_1403_4781_gb300 as sdl
 import sdl_inputs as si
-from _parity import check_bf16_codes
+from _parity import check_bf16_codes, check_rmse
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -65,12 +67,10 @@ def test_uneven_bf16_training_full_size_sampled_subsets(shape):
             excused, rounding = excused + ex, rounding + ro
             print(f"shape {shape} it {it} subset {t} ({b - a} signals): {ex} differ, {ro} at rounding level")
             coded += b - a
-            o = oracle.train(Yp[a:b], Dt, p.s1, 1)
-            rel = abs(rmse[t] - o["rmse"][0]) / o["rmse"][0]
+            rel = abs(check_rmse(r2[a:b], orc, idx[a:b], nnz[a:b], p.m, rmse[t]))
             worst = max(worst, rel)
-            assert rel < 1e-3, (shape, it, t, rmse[t], o["rmse"][0])
             Dm, *_ = oracle.mod(Yp[a:b], idx[a:b], val[a:b].astype(np.float64), Dt, True)
             np.testing.assert_allclose(after[t], Dm, rtol=0, atol=2e-5, err_msg=f"{shape} it {it} subset {t}")
     print(f"shape {shape}: sampled subsets {sample} (sizes {sizes[sample].tolist()}), "
-          f"worst per-iteration RMSE error {worst:.2e}, {excused} of {coded} codes differ at near-ties, "
+          f"worst per-iteration RMSE difference (near-tie paths included) {worst:.2e}, {excused} of {coded} codes differ at near-ties, "
           f"{rounding} more at rounding-level steps")
