@@ -330,9 +330,14 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     automatic tile and cluster size), 1 = one thread-block cluster per subset
  *     holding the factor in distributed shared memory (K <= 512), 2 = one
  *     thread block per subset for the factorisation, then a separate solve,
- *     3 = the tiled solve with the tile and cluster size set below.
+ *     3 = the tiled solve with the tile and cluster size set below, 4 = the
+ *     wide form of the tiled solve: each subset's tile tasks spread over
+ *     SDL_OPT_CLUSTER blocks (0: the SM count over the number of subsets) of a
+ *     cooperative launch anywhere on the GPU, meeting at barriers in global
+ *     memory whose waits are bounded (SDL_ETIMEOUT when one gives up).  The
+ *     automatic choice also times the wide form for fewer subsets than SMs / 16.
  *   SDL_OPT_CLUSTER: cluster size, 0 = automatic (default); 4, 8 or 16 for
- *     option 1, 1 to 16 for option 3.
+ *     option 1, 1 to 16 for option 3; blocks per subset for option 4.
  *   SDL_OPT_MOD_TILE: tile edge of the tiled solve: 0 = automatic (default),
  *     16 or 32.
  *   SDL_OPT_SM_BLOCKS: with the tile or cluster size set by hand, at most this

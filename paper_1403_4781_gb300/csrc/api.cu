@@ -175,10 +175,12 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
     cudaGetLastError();
     capst = cudaStreamCaptureStatusActive;
   }
+  int wide = 0;
   if (!manual && it != ctx->tuned.end()) {
     ts = it->second.ts;
     C = it->second.C;
     cap = it->second.cap;
+    wide = it->second.wide;
   } else if (manual || !ctx->opt_autotune || capst != cudaStreamCaptureStatusNone) {
     pick_tiled<T>(ctx, ma.L, &ts, &C);
     if (manual) cap = ctx->opt_sm_blocks;
@@ -210,6 +212,28 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
         }
         if (e == cudaSuccess && ms_best < best) { best = ms_best; best_ts = t; best_c = c; best_cap = cp; }
       }
+    // few subsets: the wide form, each subset's tile tasks over G blocks
+    // anywhere on the GPU (its largest cluster holds at most 16 SMs)
+    int best_wide = 0;
+    if ((int64_t)ma.L * 16 < ctx->num_sms)
+      for (int a = 0; a < 2 && e == cudaSuccess; ++a)
+        for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
+          const int t = tiles[a];
+          const int G = (int)((int64_t)ctx->num_sms * (f == 0 ? 1 : (f == 1 ? 2 : 4)) / (2 * ma.L));
+          if (G <= 16 || (int64_t)ma.L * G > mod_wide_max_blocks<T>(t, ctx->num_sms)) continue;
+          float ms_best = 3.4e38f;
+          for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(e0, sm);
+            if (e == cudaSuccess) e = launch_mod_wide<T>(ma, t, G, sm);
+            if (e == cudaSuccess) ctx->launches += 1;
+            if (e == cudaSuccess) e = cudaEventRecord(e1, sm);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < ms_best) ms_best = ms;
+          }
+          if (e == cudaSuccess && ms_best < best) { best = ms_best; best_ts = t; best_c = G; best_cap = 0; best_wide = 1; }
+        }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return e;
@@ -219,12 +243,14 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
       ts = best_ts;
       C = best_c;
       cap = best_cap;
+      wide = best_wide;
     }
-    ctx->tuned[key] = sdl_ctx::TunedSolve{ts, C, cap};
+    ctx->tuned[key] = sdl_ctx::TunedSolve{ts, C, cap, wide};
   }
   // the batched solve and the single-system (merge) solve are reported apart
-  return timed(ctx, ma.L > 1 ? "mod_solve_fp64" : "mod_solve_fp64_single", 1,
-               [&] { return launch_mod_tiled<T>(ma, ts, C, cap, ctx->num_sms, sm); });
+  return timed(ctx, ma.L > 1 ? "mod_solve_fp64" : "mod_solve_fp64_single", 1, [&] {
+    return wide ? launch_mod_wide<T>(ma, ts, C, sm) : launch_mod_tiled<T>(ma, ts, C, cap, ctx->num_sms, sm);
+  });
 }
 
 // FP64 Cholesky + solve + renormalisation: the tiled cluster kernel unless an
@@ -234,6 +260,11 @@ cudaError_t run_mod_solve(sdl_ctx *ctx, const ModArgs &ma) {
   cudaStream_t sm = ctx->stream;
   cudaError_t e = cudaErrorNotSupported;
   if (ctx->opt_mod_solve == 0 || ctx->opt_mod_solve == 3) return run_tiled_tuned<T>(ctx, ma);
+  if (ctx->opt_mod_solve == 4)   // the wide form, tile edge and blocks per subset from the options
+    return timed(ctx, ma.L > 1 ? "mod_solve_fp64" : "mod_solve_fp64_single", 1, [&] {
+      const int G = ctx->opt_cluster > 0 ? ctx->opt_cluster : (ctx->num_sms + ma.L - 1) / ma.L;
+      return launch_mod_wide<T>(ma, ctx->opt_tile ? ctx->opt_tile : 16, G, sm);
+    });
   if (ma.K <= 512 && ctx->opt_mod_solve == 1)
     e = timed(ctx, "mod_solve_fp64", 1, [&] {
       return launch_mod_solve_cluster<T>(ma, ctx->opt_cluster ? ctx->opt_cluster : 16, sm);
@@ -435,6 +466,7 @@ sdl_status mod_status(sdl_ctx *ctx, const int32_t *status, int L, int32_t *d_max
   SDL_CUDA(cudaMemcpyAsync(ctx->h_status, d_max, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
            "status read");
   SDL_CUDA(cudaStreamSynchronize(ctx->stream), "status sync");
+  if (*ctx->h_status >= 3) return set_error(ctx, SDL_ETIMEOUT, "a bounded barrier wait of the FP64 solve gave up");
   if (*ctx->h_status >= 2)
     return set_error(ctx, SDL_ENOTPD,
                      "MOD normal equations not positive definite after the ridge retry");
@@ -1282,11 +1314,12 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
   if (!ctx) return SDL_EINVAL;
   switch (option) {
     case SDL_OPT_MOD_SOLVE:
-      if (value < 0 || value > 3) return set_error(ctx, SDL_EINVAL, "SDL_OPT_MOD_SOLVE takes 0, 1, 2 or 3");
+      if (value < 0 || value > 4) return set_error(ctx, SDL_EINVAL, "SDL_OPT_MOD_SOLVE takes 0 to 4");
       ctx->opt_mod_solve = (int)value;
       return SDL_OK;
     case SDL_OPT_CLUSTER:
-      if (value < 0 || value > 16) return set_error(ctx, SDL_EINVAL, "SDL_OPT_CLUSTER takes 0 to 16");
+      if (value < 0 || value > 1024)
+        return set_error(ctx, SDL_EINVAL, "SDL_OPT_CLUSTER takes 0 to 1024 (above 16: the wide form only)");
       ctx->opt_cluster = (int)value;
       return SDL_OK;
     case SDL_OPT_MOD_TILE:

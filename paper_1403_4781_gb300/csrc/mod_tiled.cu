@@ -407,12 +407,220 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
   }
 }
 
+// ---- the wide form: one subset's tile tasks spread over G blocks anywhere on
+// the GPU (a cooperative launch keeps them all resident), for few subsets, where
+// a cluster of at most 16 SMs leaves the rest of the GPU idle while the
+// single system's FP64 work runs on its 2 DFMA per clock per SM.  The steps and
+// their tile tasks are the cluster form's; the blocks of a subset meet at a
+// barrier in global memory instead of the cluster barrier, and the inverse of
+// each diagonal factor and its breakdown verdict travel through global memory
+// (every block loads the inverse into its shared memory after the barrier).
+
+// Barrier words of one subset's group of blocks (zeroed before the launch).
+struct WideSync {
+  unsigned int count, gen;
+  int verdict[2];
+  int fail;
+  int pad[3];
+};
+constexpr long long kWideSpin = 1ll << 24;   // polls (64 ns sleeps) before a barrier gives up
+
+__device__ __forceinline__ unsigned int vload(const unsigned int *p) {
+  return *reinterpret_cast<const volatile unsigned int *>(p);
+}
+__device__ __forceinline__ int vload(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
+
+// Barrier of the nb blocks of a group: the arrivals count up, the last one
+// resets the count and moves the generation on, the others wait (bounded) for
+// the generation to change.  Global writes before it are visible to every
+// block of the group after it.  False when some block of the group gave up.
+__device__ bool wide_sync(WideSync *w, int nb) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int g = vload(&w->gen);
+    __threadfence();
+    if (atomicAdd(&w->count, 1u) == (unsigned int)nb - 1) {
+      atomicExch(&w->count, 0u);
+      __threadfence();
+      atomicAdd(&w->gen, 1u);
+    } else {
+      long long it = 0;
+      while (vload(&w->gen) == g) {
+        if (++it > kWideSpin || vload(&w->fail)) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (!ok) atomicExch(&w->fail, 1);
+    ok_s = ok && !vload(&w->fail);
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <typename T, int TS>
+__global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__restrict__ A,
+                                                                const double *__restrict__ B,
+                                                                const int32_t *__restrict__ usage, int K, int m,
+                                                                int G, double *M, double *V, WideSync *sync, T *D,
+                                                                int32_t *status, int32_t *status_max) {
+  __shared__ TiledSmem<TS> sm;
+  __shared__ double red[2][kTThreads / 32];
+  const int rank = blockIdx.x % G;
+  const int t = blockIdx.x / G;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  TGeom g;
+  g.K = K; g.m = m; g.TS = TS;
+  g.R = (K + TS - 1) / TS;
+  g.RT = g.R + (m + TS - 1) / TS;
+  const int R = g.R, RT = g.RT, Rm = RT - R;
+  const double *At = A + (size_t)t * K * K;
+  const double *Bt = B + (size_t)t * K * m;
+  const int32_t *ut = usage + (size_t)t * K;
+  double *Mt = M + (size_t)t * (K + m) * K;
+  double *Vt = V + (size_t)t * R * TS * TS;
+  WideSync *ws = sync + t;
+
+  double tr = 0.0, nu = 0.0;
+  for (int j = tid; j < K; j += kTThreads)
+    if (ut[j] > 0) { tr += At[(size_t)j * K + j]; nu += 1.0; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    nu += __shfl_xor_sync(0xffffffffu, nu, o);
+  }
+  if (lane == 0) { red[0][warp] = tr; red[1][warp] = nu; }
+  __syncthreads();
+  double T0 = 0.0, N0 = 0.0;
+  for (int w = 0; w < kTThreads / 32; ++w) { T0 += red[0][w]; N0 += red[1][w]; }
+  const double lambda = N0 > 0.0 ? kModRidge * T0 / N0 : 0.0;
+
+  // factor diagonal tile kk; its inverse and verdict go to global memory
+  double ridge = 0.0;
+  auto own_diag = [&](int kk) {
+    const bool okd = factor_diag<TS>(sm, Mt, g, kk, At, ut, ridge);
+    for (int e = tid; e < TS * TS; e += kTThreads) Vt[(size_t)kk * TS * TS + e] = sm.b[e / TS][e % TS];
+    if (tid == 0) ws->verdict[kk & 1] = okd ? 0 : 1;
+  };
+  // every block's shared copy of the inverse of diagonal factor k
+  auto load_inv = [&](int k) {
+    for (int e = tid; e < TS * TS; e += kTThreads) sm.v[0][e / TS][e % TS] = __ldcg(Vt + (size_t)k * TS * TS + e);
+    __syncthreads();
+  };
+
+  bool alive = true;   // false once a barrier gave up: every block then leaves
+  int st = 2;
+  bool failed = true;
+  for (int attempt = 0; attempt < 2 && failed && alive; ++attempt) {
+    ridge = attempt == 0 ? 0.0 : lambda;
+    const int64_t total = (int64_t)(K + m) * K;
+    for (int64_t q = (int64_t)rank * kTThreads + tid; q < total; q += (int64_t)G * kTThreads) {
+      const int r = (int)(q / K), c = (int)(q % K);
+      if (r < K) {
+        if (c <= r) Mt[q] = At[(size_t)r * K + c] + ((r == c && ut[r] > 0) ? ridge : 0.0);
+      } else {
+        Mt[q] = Bt[(size_t)c * m + (r - K)];
+      }
+    }
+    if (!(alive = wide_sync(ws, G))) break;
+    if (rank == 0) own_diag(0);
+    if (!(alive = wide_sync(ws, G))) break;
+    failed = false;
+    for (int k = 0; k < R; ++k) {
+      if (vload(&ws->verdict[k & 1])) { failed = true; break; }   // the same value in every block
+      load_inv(k);
+      const double (*vk)[TS + 1] = sm.v[0];
+      run_step<TS>(sm, vk, RT - k - 1, rank, G, [&](int q) {
+        const Opnd p = tile_of<TS>(Mt, g, k + 1 + q, k);
+        return TileTask{p, p, p, false, true, false, false};
+      });
+      if (!(alive = wide_sync(ws, G))) break;
+      const int ntr = (R - k - 1) * (R - k) / 2 + Rm * (R - k - 1);
+      auto trail = [&](int q) {
+        int i = k + 1, w = 1;
+        while (q >= w) {
+          q -= w;
+          ++i;
+          w = (i < R ? i : R - 1) - k;
+        }
+        const int j = k + 1 + q;
+        return TileTask{tile_of<TS>(Mt, g, i, k), tile_of<TS>(Mt, g, j, k), tile_of<TS>(Mt, g, i, j), false, false,
+                        true, i == j};
+      };
+      if (ntr > 0) {
+        // the owner of the next diagonal tile updates and factors it and, with
+        // other blocks in the group, takes no other tile; they share the rest
+        const int owner = (k + 1) % G;
+        if (rank == owner) {
+          run_step<TS>(sm, vk, 1, 0, G, trail);
+          __syncthreads();   // the updated diagonal tile is in global memory
+          own_diag(k + 1);
+          if (G == 1) run_step<TS>(sm, vk, ntr, 1, 1, trail);
+        } else {
+          run_step<TS>(sm, vk, ntr, 1 + (rank - owner - 1 + G) % G, G - 1, trail);
+        }
+      }
+      if (!(alive = wide_sync(ws, G))) break;
+    }
+    if (!failed && alive) st = attempt;
+    if (alive && !(alive = wide_sync(ws, G))) break;
+  }
+
+  if (!failed && alive) {
+    // backward sweep on the right-hand-side rows: X^T = W L^{-1}
+    for (int k = R - 1; k >= 0 && alive; --k) {
+      run_step<TS>(sm, sm.v[0], Rm, rank, G, [&](int q) {
+        const Opnd w = tile_of<TS>(Mt, g, R + q, k);
+        return TileTask{w, Opnd{Vt + (size_t)k * TS * TS, TS, TS, TS}, w, true, false, false, false};
+      });
+      if (!(alive = wide_sync(ws, G))) break;
+      if (k > 0)
+        run_step<TS>(sm, sm.v[0], Rm * k, rank, G, [&](int q) {
+          const int rb = q / k, i = q % k;
+          return TileTask{tile_of<TS>(Mt, g, R + rb, k), tile_of<TS>(Mt, g, k, i), tile_of<TS>(Mt, g, R + rb, i),
+                          true, false, true, false};
+        });
+      if (!(alive = wide_sync(ws, G))) break;
+    }
+    if (alive) {
+      for (int j = rank * kTThreads + tid; j < K; j += G * kTThreads) {
+        if (ut[j] == 0) continue;   // unused: keeps the previous atom
+        const double *xj = Mt + (size_t)K * K + j;
+        double n2 = 0.0;
+        for (int r = 0; r < m; ++r) {
+          const double v = __ldcg(xj + (size_t)r * K);
+          n2 = fma(v, v, n2);
+        }
+        const double nrm = sqrt(n2);
+        if (!(nrm > 0.0) || !isfinite(nrm)) continue;
+        const double inv = 1.0 / nrm;
+        T *dj = D + ((size_t)t * K + j) * m;
+        for (int r = 0; r < m; ++r) dj[r] = (T)(__ldcg(xj + (size_t)r * K) * inv);
+      }
+    }
+  }
+  if (rank == 0 && tid == 0) {
+    // a barrier that gave up: status 3 (the atoms may be partly updated)
+    const int code = alive ? st : 3;
+    status[t] = code;
+    if (status_max) atomicMax(status_max, code);
+  }
+}
+
 }  // namespace
 
-size_t mod_tiled_scratch_doubles(int L, int K, int m) {
+// Scratch per subset: M ((K + m) x K), room for the inverses of either tile
+// edge, and the wide form's barrier words (4 doubles).
+static size_t tiled_sub_doubles(int K, int m) {
   const int R = (K + 15) / 16;   // the smaller tile needs the most inverse blocks
-  return (size_t)L * ((size_t)(K + m) * K + (size_t)R * 16 * 16 + (size_t)((K + 31) / 32) * 32 * 32);
+  return (size_t)(K + m) * K + (size_t)R * 16 * 16 + (size_t)((K + 31) / 32) * 32 * 32;
 }
+size_t mod_tiled_scratch_doubles(int L, int K, int m) { return (size_t)L * (tiled_sub_doubles(K, m) + 4); }
 
 // Dynamic shared memory that keeps at most `cap` blocks on an SM (0: no cap):
 // more than 1/(cap + 1) of the SM's 228 KB with the static part included.
@@ -492,6 +700,51 @@ cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, int num_s
   return ts == 16 ? launch_tiled_ts<T, 16>(a, C, cap, num_sms, st) : launch_tiled_ts<T, 32>(a, C, cap, num_sms, st);
 }
 
+template <typename T, int TS>
+static cudaError_t launch_wide_ts(const ModArgs &a, int G, cudaStream_t st) {
+  auto kern = mod_wide_kernel<T, TS>;
+  double *M = a.Lf;
+  double *V = a.Lf + (size_t)a.L * (a.K + a.m) * a.K;
+  WideSync *sync = reinterpret_cast<WideSync *>(a.Lf + (size_t)a.L * tiled_sub_doubles(a.K, a.m));
+  cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(WideSync) * (size_t)a.L, st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((int64_t)a.L * G));
+  cfg.blockDim = dim3(kTThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // every block resident: the barriers need it
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, (const double *)a.A, (const double *)a.B, (const int32_t *)a.usage, a.K,
+                            a.m, G, M, V, sync, static_cast<T *>(a.D), a.status, a.status_max);
+}
+
+template <typename T>
+int mod_wide_max_blocks(int ts, int num_sms) {
+  int per = 0;
+  const cudaError_t e = ts == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mod_wide_kernel<T, 16>, kTThreads, 0)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mod_wide_kernel<T, 32>, kTThreads, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per * num_sms;
+}
+
+template <typename T>
+cudaError_t launch_mod_wide(const ModArgs &a, int ts, int G, cudaStream_t st) {
+  if (a.L <= 0) return cudaSuccess;
+  if (G < 1 || (ts != 16 && ts != 32)) return cudaErrorInvalidValue;
+  return ts == 16 ? launch_wide_ts<T, 16>(a, G, st) : launch_wide_ts<T, 32>(a, G, st);
+}
+
+template cudaError_t launch_mod_wide<float>(const ModArgs &, int, int, cudaStream_t);
+template cudaError_t launch_mod_wide<double>(const ModArgs &, int, int, cudaStream_t);
+template int mod_wide_max_blocks<float>(int, int);
+template int mod_wide_max_blocks<double>(int, int);
 template cudaError_t launch_mod_tiled<float>(const ModArgs &, int, int, int, int, cudaStream_t);
 template cudaError_t launch_mod_tiled<double>(const ModArgs &, int, int, int, int, cudaStream_t);
 template int mod_tiled_max_clusters<float>(int, int, int);

@@ -72,6 +72,7 @@ struct sdl_ctx {
   int opt_autotune = 1;          // time candidate launch shapes on first use
   struct TunedSolve {
     int ts, C, cap;
+    int wide;   // 1: the wide form with C blocks per subset
   };
   std::map<std::string, TunedSolve> tuned;   // shape key -> chosen tile, cluster size, blocks-per-SM cap
   int opt_graph = 0;             // replay training loops as captured CUDA graphs
@@ -214,6 +215,13 @@ cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, int num_s
 template <typename T>
 int mod_tiled_max_clusters(int ts, int C, int cap);
 size_t mod_tiled_scratch_doubles(int L, int K, int m);
+// The wide form of the tiled solve for few subsets: the tile tasks of each
+// subset spread over G blocks of a cooperative launch that meet at barriers in
+// global memory.  Status 3 when a barrier wait gave up.
+template <typename T>
+cudaError_t launch_mod_wide(const ModArgs &a, int ts, int G, cudaStream_t st);
+template <typename T>
+int mod_wide_max_blocks(int ts, int num_sms);
 
 template <typename T>
 cudaError_t launch_split(const T *Y, int m, int64_t N, const int64_t *perm, T *Yp, cudaStream_t st);

@@ -131,3 +131,70 @@ def test_autotuned_choice_matches_oracle(ctx):
     for _ in range(3):
         got = _run(ctx, 0, 0, 0, offsets, Y, idx, val, D0)
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("K,m,s", [(60, 30, 4), (97, 33, 5), (256, 64, 6)])
+@pytest.mark.parametrize("ts,G", [(16, 1), (16, 7), (16, 100), (32, 40)])
+def test_wide_solve_fp64_matches_oracle(ctx, ts, G, K, m, s):
+    """The wide form (option 4): each subset's tile tasks over G blocks of a
+    cooperative launch meeting at barriers in global memory; the same steps as
+    the cluster form, so the same 1e-10 FP64 bound, unused atoms bit-exact."""
+    offsets, Y, idx, val, D0 = _problem(310 + K, [3 * K, 5 * K, 4 * K], m, K, s, np.float64)
+    want = _oracle_batched(offsets, Y, idx, val, D0)
+    got = _run(ctx, 4, ts, G, offsets, Y, idx, val, D0)
+    np.testing.assert_array_equal(got[:, K - 3:], D0[:, K - 3:])
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("ts,G", [(16, 8), (16, 64), (32, 30)])
+def test_wide_solve_ridge_retry(ctx, ts, G):
+    rng = np.random.default_rng(311)
+    m, K, n = 6, 5, 50
+    Y = rng.standard_normal((n, m))
+    third = rng.integers(2, K, size=n)
+    idx = np.stack([np.zeros(n), np.ones(n), third], axis=1).astype(np.int32)
+    c = rng.standard_normal(n)
+    val = np.stack([c, c, rng.standard_normal(n)], axis=1)
+    Dprev = si.unit_gaussian_atoms(rng, m, K)
+    Do, _, ridge, st = oracle.mod(Y, idx, val, Dprev, True)
+    assert ridge and st == 0
+    got = _run(ctx, 4, ts, G, np.array([0, n], np.int64), Y, idx, val, Dprev[None])
+    np.testing.assert_allclose(got[0], Do, atol=1e-5)
+
+
+@pytest.mark.parametrize("K,m,n", [(256, 64, 25600), (1024, 256, 12000)])
+def test_wide_solve_single_system_merge_shapes(ctx, K, m, n):
+    """The merge phase's single systems (K=256, m=64: the split-and-merge
+    workload; K=1024, m=256: the image-patch workload), FP32 atoms, against the
+    oracle; the wide form over every SM and the 16-block cluster form are timed
+    side by side (printed)."""
+    offsets, Y, idx, val, D0 = _problem(312 + K, [n], m, K, 4, np.float32, unused=0)
+    want = _oracle_batched(offsets, Y, idx, val, D0)
+    import time
+    times = {}
+    for path, ts, G in ((3, 16 if K <= 256 else 32, 16), (4, 16, 152), (4, 32, 152), (4, 16, 304)):
+        got = _run(ctx, path, ts, G, offsets, Y, idx, val, D0)
+        np.testing.assert_allclose(got, want, rtol=0, atol=2e-5, err_msg=f"path {path} ts {ts} G {G}")
+        Dg = _t(D0.copy())
+        Yg, ig, vg = _t(Y), _t(idx), _t(val)
+        sdl.mod_update_batched(Yg, offsets, ig, vg, Dg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            sdl.mod_update_batched(Yg, offsets, ig, vg, Dg)
+        torch.cuda.synchronize()
+        times[(path, ts, G)] = (time.perf_counter() - t0) / 5 * 1e3
+    print(f"K={K} m={m}: MOD update ms (accumulate + solve) by (path, tile, blocks): "
+          + ", ".join(f"{k}: {v:.3f}" for k, v in times.items()))
+
+
+def test_autotuned_single_system_matches_oracle(ctx):
+    """One subset: the autotuner times the cluster candidates and the wide
+    form; its cached choice agrees with the oracle on every call."""
+    offsets, Y, idx, val, D0 = _problem(313, [4000], 64, 256, 4, np.float64, unused=0)
+    ctx.set_option(sdl.OPT_AUTOTUNE, 0)
+    ctx.set_option(sdl.OPT_AUTOTUNE, 1)
+    want = _oracle_batched(offsets, Y, idx, val, D0)
+    for _ in range(3):
+        got = _run(ctx, 0, 0, 0, offsets, Y, idx, val, D0)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-10)
