@@ -55,7 +55,10 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
 # DRAM bytes (read + write) per launch of a kernel family, each from one ncu
 # capture named beside it; a family with no capture of its current code has none.
-TRAFFIC = {}
+TRAFFIC = {
+    ("patches", "mod_solve_fp64"): (17.835e9, "ncu capture, profiles/mod_tiled_fp64_patches_local_L256_K512.md"),
+    ("splitmerge", "mod_solve_fp64"): (53.3e6, "ncu capture, profiles/mod_tiled_fp64_splitmerge_local_L100_K256.md"),
+}
 
 def load_peaks():
     try:
@@ -829,9 +832,10 @@ def run_denoise(args):
 
 def run_coding(args):
     """One OMP coding pass of 2^19 signals (m=256, K=512, s=8, noise 0.02, one
-    dictionary) with FP32 CUDA-core correlations and with BF16 tensor-core ones:
-    the shape where the correlation GEMM is most of the arithmetic.  Printed as
-    its own line; also the small case the tensor-core kernels are profiled on."""
+    dictionary) with FP32 CUDA-core correlations, with BF16 tensor-core ones
+    (Batch-OMP selection) and with the BF16 residual form: the shape where the
+    correlation GEMM is most of the arithmetic.  Printed as its own line; also
+    the small case the tensor-core kernels are profiled on."""
     import torch
 
     import paper_1403_4781_gb300 as sdl
@@ -846,7 +850,9 @@ def run_coding(args):
     ctx = sdl.context(0)
     stream = torch.cuda.current_stream(dev)
     out = {}
-    for name, prec in (("fp32", sdl.PREC_F32), ("bf16", sdl.PREC_BF16)):
+    for name, prec, form in (("fp32", sdl.PREC_F32, 0), ("bf16", sdl.PREC_BF16, 1),
+                             ("bf16_residual_form", sdl.PREC_BF16, 2)):
+        ctx.set_option(sdl.OPT_BF16_FORM, form)
         sdl.omp(D, Yg, s, prec=prec)
         torch.cuda.synchronize()
         ctx.profile(True)
@@ -861,12 +867,91 @@ def run_coding(args):
         ms = e0.elapsed_time(e1)
         out[name] = {"signals_per_s": n / (ms / 1e3), "ms": ms,
                      "kernels": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}
+    ctx.set_option(sdl.OPT_BF16_FORM, 0)
     res = {"metric": METRIC, "workload": "coding_m256_K512_s8_n524288", "correlation_tflop": 2 * m * K * n / 1e12,
            "data": "synthetic (seeded; Sec. 3.1 data model)", **out}
     print(json.dumps(res), flush=True)
 
 
+def run_mod_local(args):
+    """The local MOD update of the image-patch workload's shape, alone: 256
+    subsets, K1=512 atoms, m=256, codes of s1=4 from the overcomplete DCT
+    (2,048 patches per subset: the FP64 solve's cost does not depend on n).
+    The third call is bracketed by cudaProfilerStart/Stop, so a profiler
+    started with profiling off captures exactly one accumulation and one solve
+    in the bench's launch configuration.  The small case the FP64 solve is
+    profiled on; printed as its own line."""
+    import torch
+
+    import paper_1403_4781_gb300 as sdl
+
+    dev = torch.device("cuda", 0)
+    p = si.config4(n_images=32, per_image=16384, L=256)
+    Yp = sdl.split(torch.from_numpy(p.Y).to(dev), torch.from_numpy(p.perm).to(dev))
+    D = torch.from_numpy(np.broadcast_to(p.extra["D_local0"], (p.L, p.K1, p.m)).copy()).to(dev)
+    idx, val, _, _ = sdl.omp_batched(D, Yp, p.offsets, p.s1, prec=sdl.PREC_BF16, with_resid=False)
+    for _ in range(2):   # the first call tunes the solve
+        sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    ctx = sdl.context(0)
+    ctx.profile(True)
+    ctx.profile_reset()
+    sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    flops = p.L * (p.K1 ** 3 / 3 + 2 * p.K1 ** 2 * p.m)
+    ms = prof["mod_solve_fp64"][2]
+    print(json.dumps({"metric": METRIC, "workload": f"mod_local_L{p.L}_K{p.K1}_m{p.m}_s{p.s1}",
+                      "solve_ms": ms, "solve_tflops": flops / (ms / 1e3) / 1e12,
+                      "fp64_frac": flops / (ms / 1e3) / FP64_PEAK_FLOPS,
+                      "kernels": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}),
+          flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle ------
+def run_mod_local(args):
+    """The local MOD update of the image-patch workload's shape, alone: 256
+    subsets, K1=512 atoms, m=256, codes of s1=4 from the overcomplete DCT
+    (2,048 patches per subset: the FP64 solve's cost does not depend on n).
+    The third call is bracketed by cudaProfilerStart/Stop, so a profiler
+    started with profiling off captures exactly one accumulation and one solve
+    in the bench's launch configuration.  The small case the FP64 solve is
+    profiled on; printed as its own line."""
+    import torch
+
+    import paper_1403_4781_gb300 as sdl
+
+    dev = torch.device("cuda", 0)
+    p = si.config4(n_images=32, per_image=16384, L=256)
+    Yp = sdl.split(torch.from_numpy(p.Y).to(dev), torch.from_numpy(p.perm).to(dev))
+    D = torch.from_numpy(np.broadcast_to(p.extra["D_local0"], (p.L, p.K1, p.m)).copy()).to(dev)
+    idx, val, _, _ = sdl.omp_batched(D, Yp, p.offsets, p.s1, prec=sdl.PREC_BF16, with_resid=False)
+    for _ in range(2):   # the first call tunes the solve
+        sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    ctx = sdl.context(0)
+    ctx.profile(True)
+    ctx.profile_reset()
+    sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    flops = p.L * (p.K1 ** 3 / 3 + 2 * p.K1 ** 2 * p.m)
+    ms = prof["mod_solve_fp64"][2]
+    print(json.dumps({"metric": METRIC, "workload": f"mod_local_L{p.L}_K{p.K1}_m{p.m}_s{p.s1}",
+                      "solve_ms": ms, "solve_tflops": flops / (ms / 1e3) / 1e12,
+                      "fp64_frac": flops / (ms / 1e3) / FP64_PEAK_FLOPS,
+                      "kernels": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}),
+          flush=True)
+
+
 # ------------------------------------------------------------ CPU oracle ------
 def _oracle_phases(p, name, Y, n_sub, local_iters, merge_iters, final_n, threads=None):
     """Run the oracle on a bounded sample of the workload, phase by phase: local
@@ -1006,7 +1091,7 @@ def main():
     ap.add_argument("--error-sample", type=int, default=2000,
                     help="signals of the final coding the oracle recodes for the precision error")
     ap.add_argument("--workload", choices=["patches", "splitmerge", "uneven-A", "uneven-B", "denoise", "coding",
-                                           "conditioned"],
+                                           "conditioned", "mod-local"],
                     default="patches",
                     help="the main line's workload (patches or splitmerge), or a parity workload measured alone")
     ap.add_argument("--plain-steps", type=int, default=1,
@@ -1020,7 +1105,8 @@ def main():
     elif args.workload in WORKLOADS:
         run_ours(args, rank, world, local_rank)
     elif rank == 0:
-        {"denoise": run_denoise, "coding": run_coding, "conditioned": run_conditioned}.get(
+        {"denoise": run_denoise, "coding": run_coding, "conditioned": run_conditioned,
+         "mod-local": run_mod_local}.get(
             args.workload, lambda a: run_uneven(a, args.workload[-1]))(args)
 
 
