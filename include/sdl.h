@@ -372,6 +372,12 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     shapes run form 1).  Both refit the coefficients
  *     on the chosen support in FP32 with one refinement step; they may choose
  *     differently among atoms whose correlations tie to within BF16 rounding.
+ *   SDL_OPT_WAIT_LIMIT: polls (64 ns apart) before a barrier wait of the wide
+ *     solve gives up, default 2^24; the call then returns SDL_ETIMEOUT with the
+ *     atoms unchanged and the context usable.
+ *   SDL_OPT_WAIT_TEST: 1 makes one block of every wide-solve group leave at
+ *     once, so that the others' first barrier wait runs out: the test of the
+ *     bounded waits (default 0).
  *   SDL_OPT_REPLACE: min_use of the atom replacement (sdl_replace_atoms) run
  *     after every MOD update of the training loops.  0 (default) = off, the
  *     paper's reading: unused atoms keep their value.  This option changes the
@@ -386,7 +392,9 @@ typedef enum {
   SDL_OPT_SM_BLOCKS = 6,
   SDL_OPT_REPLACE = 7,
   SDL_OPT_OMP_FORM = 8,
-  SDL_OPT_BF16_FORM = 9
+  SDL_OPT_BF16_FORM = 9,
+  SDL_OPT_WAIT_LIMIT = 10,
+  SDL_OPT_WAIT_TEST = 11
 } sdl_option;
 sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
 

@@ -98,6 +98,7 @@ FEATURES_SIGNAL, FEATURES_CORR = 0, 1
 OPT_MOD_SOLVE, OPT_CLUSTER, OPT_MOD_TILE, OPT_AUTOTUNE, OPT_GRAPH, OPT_SM_BLOCKS, OPT_REPLACE = 1, 2, 3, 4, 5, 6, 7
 OPT_OMP_FORM = 8
 OPT_BF16_FORM = 9
+OPT_WAIT_LIMIT, OPT_WAIT_TEST = 10, 11
 
 
 def lib() -> ctypes.CDLL:

@@ -224,7 +224,7 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
           float ms_best = 3.4e38f;
           for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
             e = cudaEventRecord(e0, sm);
-            if (e == cudaSuccess) e = launch_mod_wide<T>(ma, t, G, sm);
+            if (e == cudaSuccess) e = launch_mod_wide<T>(ma, t, G, ctx->opt_wait_limit, -1, sm);
             if (e == cudaSuccess) ctx->launches += 1;
             if (e == cudaSuccess) e = cudaEventRecord(e1, sm);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -249,7 +249,8 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
   }
   // the batched solve and the single-system (merge) solve are reported apart
   return timed(ctx, ma.L > 1 ? "mod_solve_fp64" : "mod_solve_fp64_single", 1, [&] {
-    return wide ? launch_mod_wide<T>(ma, ts, C, sm) : launch_mod_tiled<T>(ma, ts, C, cap, ctx->num_sms, sm);
+    return wide ? launch_mod_wide<T>(ma, ts, C, ctx->opt_wait_limit, ctx->opt_wait_test ? 1 : -1, sm)
+                : launch_mod_tiled<T>(ma, ts, C, cap, ctx->num_sms, sm);
   });
 }
 
@@ -263,7 +264,8 @@ cudaError_t run_mod_solve(sdl_ctx *ctx, const ModArgs &ma) {
   if (ctx->opt_mod_solve == 4)   // the wide form, tile edge and blocks per subset from the options
     return timed(ctx, ma.L > 1 ? "mod_solve_fp64" : "mod_solve_fp64_single", 1, [&] {
       const int G = ctx->opt_cluster > 0 ? ctx->opt_cluster : (ctx->num_sms + ma.L - 1) / ma.L;
-      return launch_mod_wide<T>(ma, ctx->opt_tile ? ctx->opt_tile : 16, G, sm);
+      return launch_mod_wide<T>(ma, ctx->opt_tile ? ctx->opt_tile : 16, G, ctx->opt_wait_limit,
+                                ctx->opt_wait_test ? 1 : -1, sm);
     });
   if (ma.K <= 512 && ctx->opt_mod_solve == 1)
     e = timed(ctx, "mod_solve_fp64", 1, [&] {
@@ -1344,6 +1346,14 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
     case SDL_OPT_OMP_FORM:
       if (value < 0 || value > 2) return set_error(ctx, SDL_EINVAL, "SDL_OPT_OMP_FORM takes 0, 1 or 2");
       ctx->opt_omp_form = (int)value;
+      return SDL_OK;
+    case SDL_OPT_WAIT_LIMIT:
+      if (value < 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_WAIT_LIMIT takes a positive poll count");
+      ctx->opt_wait_limit = (long long)value;
+      return SDL_OK;
+    case SDL_OPT_WAIT_TEST:
+      if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_WAIT_TEST takes 0 or 1");
+      ctx->opt_wait_test = (int)value;
       return SDL_OK;
     case SDL_OPT_BF16_FORM:
       if (value < 0 || value > 2) return set_error(ctx, SDL_EINVAL, "SDL_OPT_BF16_FORM takes 0, 1 or 2");

@@ -423,7 +423,6 @@ struct WideSync {
   int fail;
   int pad[3];
 };
-constexpr long long kWideSpin = 1ll << 24;   // polls (64 ns sleeps) before a barrier gives up
 
 __device__ __forceinline__ unsigned int vload(const unsigned int *p) {
   return *reinterpret_cast<const volatile unsigned int *>(p);
@@ -434,7 +433,7 @@ __device__ __forceinline__ int vload(const int *p) { return *reinterpret_cast<co
 // resets the count and moves the generation on, the others wait (bounded) for
 // the generation to change.  Global writes before it are visible to every
 // block of the group after it.  False when some block of the group gave up.
-__device__ bool wide_sync(WideSync *w, int nb) {
+__device__ bool wide_sync(WideSync *w, int nb, long long spin) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -448,7 +447,7 @@ __device__ bool wide_sync(WideSync *w, int nb) {
     } else {
       long long it = 0;
       while (vload(&w->gen) == g) {
-        if (++it > kWideSpin || vload(&w->fail)) {
+        if (++it > spin || vload(&w->fail)) {
           ok = 0;
           break;
         }
@@ -468,7 +467,8 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
                                                                 const double *__restrict__ B,
                                                                 const int32_t *__restrict__ usage, int K, int m,
                                                                 int G, double *M, double *V, WideSync *sync, T *D,
-                                                                int32_t *status, int32_t *status_max) {
+                                                                int32_t *status, int32_t *status_max,
+                                                                long long spin, int absent) {
   __shared__ TiledSmem<TS> sm;
   __shared__ double red[2][kTThreads / 32];
   const int rank = blockIdx.x % G;
@@ -485,6 +485,9 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
   double *Mt = M + (size_t)t * (K + m) * K;
   double *Vt = V + (size_t)t * R * TS * TS;
   WideSync *ws = sync + t;
+  // test of the bounded waits: the block of rank `absent` leaves at once, so
+  // the others' first barrier wait runs out (status 3, SDL_ETIMEOUT)
+  if (rank == absent) return;
 
   double tr = 0.0, nu = 0.0;
   for (int j = tid; j < K; j += kTThreads)
@@ -527,9 +530,9 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
         Mt[q] = Bt[(size_t)c * m + (r - K)];
       }
     }
-    if (!(alive = wide_sync(ws, G))) break;
+    if (!(alive = wide_sync(ws, G, spin))) break;
     if (rank == 0) own_diag(0);
-    if (!(alive = wide_sync(ws, G))) break;
+    if (!(alive = wide_sync(ws, G, spin))) break;
     failed = false;
     for (int k = 0; k < R; ++k) {
       if (vload(&ws->verdict[k & 1])) { failed = true; break; }   // the same value in every block
@@ -539,7 +542,7 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
         const Opnd p = tile_of<TS>(Mt, g, k + 1 + q, k);
         return TileTask{p, p, p, false, true, false, false};
       });
-      if (!(alive = wide_sync(ws, G))) break;
+      if (!(alive = wide_sync(ws, G, spin))) break;
       const int ntr = (R - k - 1) * (R - k) / 2 + Rm * (R - k - 1);
       auto trail = [&](int q) {
         int i = k + 1, w = 1;
@@ -565,10 +568,10 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
           run_step<TS>(sm, vk, ntr, 1 + (rank - owner - 1 + G) % G, G - 1, trail);
         }
       }
-      if (!(alive = wide_sync(ws, G))) break;
+      if (!(alive = wide_sync(ws, G, spin))) break;
     }
     if (!failed && alive) st = attempt;
-    if (alive && !(alive = wide_sync(ws, G))) break;
+    if (alive && !(alive = wide_sync(ws, G, spin))) break;
   }
 
   if (!failed && alive) {
@@ -578,14 +581,14 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
         const Opnd w = tile_of<TS>(Mt, g, R + q, k);
         return TileTask{w, Opnd{Vt + (size_t)k * TS * TS, TS, TS, TS}, w, true, false, false, false};
       });
-      if (!(alive = wide_sync(ws, G))) break;
+      if (!(alive = wide_sync(ws, G, spin))) break;
       if (k > 0)
         run_step<TS>(sm, sm.v[0], Rm * k, rank, G, [&](int q) {
           const int rb = q / k, i = q % k;
           return TileTask{tile_of<TS>(Mt, g, R + rb, k), tile_of<TS>(Mt, g, k, i), tile_of<TS>(Mt, g, R + rb, i),
                           true, false, true, false};
         });
-      if (!(alive = wide_sync(ws, G))) break;
+      if (!(alive = wide_sync(ws, G, spin))) break;
     }
     if (alive) {
       for (int j = rank * kTThreads + tid; j < K; j += G * kTThreads) {
@@ -701,7 +704,7 @@ cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, int num_s
 }
 
 template <typename T, int TS>
-static cudaError_t launch_wide_ts(const ModArgs &a, int G, cudaStream_t st) {
+static cudaError_t launch_wide_ts(const ModArgs &a, int G, long long spin, int absent, cudaStream_t st) {
   auto kern = mod_wide_kernel<T, TS>;
   double *M = a.Lf;
   double *V = a.Lf + (size_t)a.L * (a.K + a.m) * a.K;
@@ -719,7 +722,7 @@ static cudaError_t launch_wide_ts(const ModArgs &a, int G, cudaStream_t st) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, (const double *)a.A, (const double *)a.B, (const int32_t *)a.usage, a.K,
-                            a.m, G, M, V, sync, static_cast<T *>(a.D), a.status, a.status_max);
+                            a.m, G, M, V, sync, static_cast<T *>(a.D), a.status, a.status_max, spin, absent);
 }
 
 template <typename T>
@@ -735,14 +738,14 @@ int mod_wide_max_blocks(int ts, int num_sms) {
 }
 
 template <typename T>
-cudaError_t launch_mod_wide(const ModArgs &a, int ts, int G, cudaStream_t st) {
+cudaError_t launch_mod_wide(const ModArgs &a, int ts, int G, long long spin, int absent, cudaStream_t st) {
   if (a.L <= 0) return cudaSuccess;
-  if (G < 1 || (ts != 16 && ts != 32)) return cudaErrorInvalidValue;
-  return ts == 16 ? launch_wide_ts<T, 16>(a, G, st) : launch_wide_ts<T, 32>(a, G, st);
+  if (G < 1 || (ts != 16 && ts != 32) || spin < 1) return cudaErrorInvalidValue;
+  return ts == 16 ? launch_wide_ts<T, 16>(a, G, spin, absent, st) : launch_wide_ts<T, 32>(a, G, spin, absent, st);
 }
 
-template cudaError_t launch_mod_wide<float>(const ModArgs &, int, int, cudaStream_t);
-template cudaError_t launch_mod_wide<double>(const ModArgs &, int, int, cudaStream_t);
+template cudaError_t launch_mod_wide<float>(const ModArgs &, int, int, long long, int, cudaStream_t);
+template cudaError_t launch_mod_wide<double>(const ModArgs &, int, int, long long, int, cudaStream_t);
 template int mod_wide_max_blocks<float>(int, int);
 template int mod_wide_max_blocks<double>(int, int);
 template cudaError_t launch_mod_tiled<float>(const ModArgs &, int, int, int, int, cudaStream_t);

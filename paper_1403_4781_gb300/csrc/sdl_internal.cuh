@@ -79,6 +79,8 @@ struct sdl_ctx {
   int opt_replace = 0;           // atom replacement after every MOD update: min_use (0 = off)
   int opt_omp_form = 0;          // FP32 OMP: 0 automatic, 1 fused kernel, 2 correlation GEMM + selection
   int opt_bf16_form = 0;         // BF16 OMP: 0 automatic, 1 Batch-OMP selection, 2 residual form
+  long long opt_wait_limit = 1ll << 24;   // polls before a barrier wait of the wide solve gives up
+  int opt_wait_test = 0;         // 1: one block of each wide-solve group leaves at once
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
@@ -217,9 +219,11 @@ int mod_tiled_max_clusters(int ts, int C, int cap);
 size_t mod_tiled_scratch_doubles(int L, int K, int m);
 // The wide form of the tiled solve for few subsets: the tile tasks of each
 // subset spread over G blocks of a cooperative launch that meet at barriers in
-// global memory.  Status 3 when a barrier wait gave up.
+// global memory.  Status 3 when a barrier wait gave up (after `spin` polls of
+// 64 ns); absent >= 0 makes that rank of each group leave at once (the test of
+// the bounded waits), -1 normally.
 template <typename T>
-cudaError_t launch_mod_wide(const ModArgs &a, int ts, int G, cudaStream_t st);
+cudaError_t launch_mod_wide(const ModArgs &a, int ts, int G, long long spin, int absent, cudaStream_t st);
 template <typename T>
 int mod_wide_max_blocks(int ts, int num_sms);
 

@@ -198,3 +198,29 @@ def test_autotuned_single_system_matches_oracle(ctx):
     for _ in range(3):
         got = _run(ctx, 0, 0, 0, offsets, Y, idx, val, D0)
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-10)
+
+
+def test_wide_solve_bounded_wait_runs_out_and_context_stays_usable(ctx):
+    """A device-side wait made to run out: one block of each wide-solve group
+    leaves at once (SDL_OPT_WAIT_TEST), so the other blocks' first barrier can
+    never complete.  With a short limit (2^14 polls of 64 ns) they give up, the
+    call returns SDL_ETIMEOUT and leaves the atoms unchanged, and the next call
+    on the same context matches the oracle."""
+    offsets, Y, idx, val, D0 = _problem(314, [3000], 64, 256, 4, np.float64, unused=0)
+    ctx.set_option(sdl.OPT_MOD_SOLVE, 4)
+    ctx.set_option(sdl.OPT_MOD_TILE, 16)
+    ctx.set_option(sdl.OPT_CLUSTER, 8)
+    ctx.set_option(sdl.OPT_WAIT_LIMIT, 1 << 14)
+    ctx.set_option(sdl.OPT_WAIT_TEST, 1)
+    Dg = _t(D0.copy())
+    try:
+        with pytest.raises(sdl.SdlError) as err:
+            sdl.mod_update_batched(_t(Y), offsets, _t(idx), _t(val), Dg)
+        assert err.value.status == 3, err.value   # SDL_ETIMEOUT
+    finally:
+        ctx.set_option(sdl.OPT_WAIT_TEST, 0)
+        ctx.set_option(sdl.OPT_WAIT_LIMIT, 1 << 24)
+    np.testing.assert_array_equal(Dg.cpu().numpy(), D0)
+    want = _oracle_batched(offsets, Y, idx, val, D0)
+    got = _run(ctx, 4, 16, 8, offsets, Y, idx, val, D0)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-10)
