@@ -907,7 +907,8 @@ def run_denoise(args):
 
 def run_coding(args):
     """One OMP coding pass of 2^19 signals (m=256, K=512, s=8, noise 0.02, one
-    dictionary) with FP32 CUDA-core correlations, with BF16 tensor-core ones
+    dictionary) with FP32 CUDA-core correlations, with FP32-accurate
+    tensor-core ones (two-term TF32 split), with BF16 tensor-core ones
     (Batch-OMP selection) and with the BF16 residual form: the shape where the
     correlation GEMM is most of the arithmetic.  Printed as its own line; also
     the small case the tensor-core kernels are profiled on."""
@@ -925,7 +926,7 @@ def run_coding(args):
     ctx = sdl.context(0)
     stream = torch.cuda.current_stream(dev)
     out = {}
-    for name, prec, form in (("fp32", sdl.PREC_F32, 0), ("bf16", sdl.PREC_BF16, 1),
+    for name, prec, form in (("fp32", sdl.PREC_F32, 0), ("f32x3", sdl.PREC_F32X3, 0), ("bf16", sdl.PREC_BF16, 1),
                              ("bf16_residual_form", sdl.PREC_BF16, 2)):
         ctx.set_option(sdl.OPT_BF16_FORM, form)
         sdl.omp(D, Yg, s, prec=prec)

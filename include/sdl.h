@@ -62,7 +62,13 @@ typedef enum {
      FP32 accumulation; the Gram on the tensor cores from a two-term BF16 split
      of D (about 2^-16); coefficients recomputed in FP32 on the support from
      D_S^T y with one refinement step. */
-  SDL_PREC_BF16 = 2
+  SDL_PREC_BF16 = 2,
+  /* FP32 data; correlations and Gram on the tensor cores from a two-term TF32
+     split of both operands (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)),
+     hi hi^T + hi lo^T + lo hi^T with FP32 accumulation: within 3 2^-22 of each
+     |x_i z_i| plus the FP32 accumulation, the accuracy of the FP32 CUDA-core
+     sum; the OMP loop, refit and refinement step as for SDL_PREC_F32. */
+  SDL_PREC_F32X3 = 3
 } sdl_precision;
 
 typedef struct sdl_ctx sdl_ctx;
@@ -193,7 +199,9 @@ sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, 
  * m entries on the CUDA cores.  BF16: FP32 data split as d = hi + lo + r with
  * hi = bf16(d), lo = bf16(d - hi), and G = hi hi^T + hi lo^T + lo hi^T on the
  * tensor cores with FP32 accumulation, about 2^-16 of |d_i||d_j| from the
- * exact Gram (synchronises to read the tensor-core kernels' error word).
+ * exact Gram.  F32X3: the same three products from a two-term TF32 split
+ * (kind::tf32), within 3 2^-22 of |d_i||d_j| plus the FP32 accumulation.  BF16
+ * and F32X3 synchronise to read the tensor-core kernels' error word.
  * Errors: SDL_EINVAL for a bad shape or pointer, SDL_ETIMEOUT when a bounded
  * wait of the tensor-core kernel gave up. */
 sdl_status sdl_gram(sdl_ctx *ctx, sdl_precision prec, const void *D, int m, int K, int L, void *G);
@@ -374,10 +382,14 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     differently among atoms whose correlations tie to within BF16 rounding.
  *   SDL_OPT_WAIT_LIMIT: polls (64 ns apart) before a barrier wait of the wide
  *     solve gives up, default 2^24; the call then returns SDL_ETIMEOUT with the
- *     atoms unchanged and the context usable.
+ *     atoms unchanged and the context usable.  The same number, capped at
+ *     2^22, bounds the mbarrier waits of the TF32 tensor-core kernels
+ *     (SDL_PREC_F32X3).
  *   SDL_OPT_WAIT_TEST: 1 makes one block of every wide-solve group leave at
- *     once, so that the others' first barrier wait runs out: the test of the
- *     bounded waits (default 0).
+ *     once, so that the others' first barrier wait runs out, and the loader
+ *     role of the TF32 tensor-core kernels leave before its first copy, so
+ *     that the MMA issuer's first wait runs out: the tests of the bounded
+ *     waits (default 0).
  *   SDL_OPT_REPLACE: min_use of the atom replacement (sdl_replace_atoms) run
  *     after every MOD update of the training loops.  0 (default) = off, the
  *     paper's reading: unused atoms keep their value.  This option changes the

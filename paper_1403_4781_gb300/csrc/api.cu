@@ -307,7 +307,8 @@ bool aligned16(const void *p) { return p && ((uintptr_t)p & 15u) == 0; }
   } while (0)
 
 sdl_status check_prec(sdl_ctx *ctx, sdl_precision prec) {
-  if (prec == SDL_PREC_F64 || prec == SDL_PREC_F32 || prec == SDL_PREC_BF16) return SDL_OK;
+  if (prec == SDL_PREC_F64 || prec == SDL_PREC_F32 || prec == SDL_PREC_BF16 || prec == SDL_PREC_F32X3)
+    return SDL_OK;
   return set_error(ctx, SDL_EINVAL, "unknown precision");
 }
 
@@ -322,11 +323,14 @@ bool omp_split_f32(const sdl_ctx *ctx, int K, int m, int s) {
   return ctx->opt_omp_form != 1;
 }
 
-// Workspace of the BF16 tensor-core coding pass over n signals in L subsets:
-// the two BF16 images of D (hi, then lo), error word, and the correlation
-// scratch (one chunk of 128-signal tiles).  The FP32 Gram lives in the
-// caller's G.
-size_t tc_image_bytes(int L, int K, int m) { return (size_t)L * round16(K) * round16(m) * 2; }
+// Workspace of a tensor-core coding pass over n signals in L subsets: the two
+// images of D (hi, then lo; BF16 or the larger TF32 layout), error word, and
+// the correlation scratch (one chunk of 128-signal tiles).  The FP32 Gram
+// lives in the caller's G.
+size_t tc_image_bytes(int L, int K, int m) {
+  const size_t bf16 = (size_t)L * round16(K) * round16(m) * 2, x3 = x3_image_bytes(L, K, m);
+  return bf16 > x3 ? bf16 : x3;
+}
 size_t tc_a0_bytes(int L, int K, int64_t n) {
   const int64_t tiles = (n + 127) / 128 + L;
   return sizeof(float) * (size_t)omp_tc_chunk_tiles(K, tiles) * 128 * K;
@@ -361,6 +365,36 @@ cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t
   if (ctx->opt_bf16_form == 2 && omp_rtc_supported(oa.K, oa.m, oa.s))
     return timed(ctx, "omp_rtc", 1, [&] { return launch_omp_rtc(oa, sm); });
   return timed(ctx, "omp_tc", split_kernels(oa), [&] { return launch_omp_tc(oa, a0c, sm); });
+}
+
+// Bounds of the TF32 tensor-core kernels' mbarrier waits: SDL_OPT_WAIT_LIMIT
+// polls, capped at 2^22 (each poll may suspend the thread for a while);
+// SDL_OPT_WAIT_TEST makes their loader leave at once.
+X3Wait x3_wait(const sdl_ctx *ctx) {
+  const long long lim = ctx->opt_wait_limit < (1LL << 22) ? ctx->opt_wait_limit : (1LL << 22);
+  return X3Wait{(int)(lim > 0 ? lim : 1), ctx->opt_wait_test ? 1 : 0};
+}
+
+// One FP32-accurate tensor-core coding pass: TF32 hi and lo images of D (img
+// holds hi, then lo), Gram and correlations as three TF32 products on the
+// tensor cores, then the FP32 selection loop.
+cudaError_t run_omp_x3(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *err, float *a0c) {
+  cudaStream_t sm = ctx->stream;
+  void *lo = static_cast<unsigned char *>(img) + tc_image_bytes(oa.L, oa.K, oa.m);
+  oa.err = err;
+  oa.G = G;
+  cudaError_t e = timed(ctx, "x3_image", 1, [&] {
+    return launch_x3_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, img, lo, sm);
+  });
+  if (e != cudaSuccess) return e;
+  e = timed(ctx, "gram_x3", 1, [&] {
+    return launch_gram_x3(static_cast<const float *>(oa.D), img, lo, oa.K, oa.m, oa.L, G, err, ctx->num_sms,
+                          x3_wait(ctx), sm);
+  });
+  if (e != cudaSuccess) return e;
+  return timed(ctx, "omp_x3", split_kernels(oa), [&] {
+    return launch_omp_x3(oa, img, lo, a0c, ctx->num_sms, x3_wait(ctx), sm);
+  });
 }
 
 // Read back the error word of the tensor-core kernels (synchronises).
@@ -498,23 +532,26 @@ size_t train_ws_bytes(int L, int K, int m, int64_t n, int s, int iters) {
 // last round), MOD.  Synchronises once at the end to report a breakdown.
 template <typename T>
 sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, int L, int K, int s,
-                     double eps, int iters, T *D, double *xfro, double *rmse, bool bf16 = false) {
+                     double eps, int iters, T *D, double *xfro, double *rmse, sdl_precision tcp = SDL_PREC_F64) {
+  // tcp: SDL_PREC_BF16 or SDL_PREC_F32X3 run the coding passes on the tensor cores
+  const bool bf16 = sizeof(T) == 4 && tcp == SDL_PREC_BF16, x3 = sizeof(T) == 4 && tcp == SDL_PREC_F32X3;
+  const bool tc = bf16 || x3;
   const int64_t n = offsets[L];
   sdl_status st;
   OmpArgs oa{};
   int64_t *d_off = nullptr;
   int32_t *d_tiles = nullptr;
   int64_t tiles = 0;
-  const bool split = !bf16 && sizeof(T) == 4 && omp_split_f32(ctx, K, m, s);
-  const int tile = bf16 || split ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
+  const bool split = !tc && sizeof(T) == 4 && omp_split_f32(ctx, K, m, s);
+  const int tile = tc || split ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
   if (tile <= 0) return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
   if ((st = upload_plan(ctx, offsets, L, tile, &d_off, &d_tiles, &tiles)) != SDL_OK)
     return st;
-  void *img = bf16 ? ws_alloc(ctx, 2 * tc_image_bytes(L, K, m)) : nullptr;
-  int32_t *tc_err = bf16 ? static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4)) : nullptr;
-  float *a0c = bf16 || split ? static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n))) : nullptr;
-  if ((split && !a0c) || (bf16 && (!img || !tc_err || !a0c))) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
-  if (bf16) SDL_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int32_t), ctx->stream), "err clear");
+  void *img = tc ? ws_alloc(ctx, 2 * tc_image_bytes(L, K, m)) : nullptr;
+  int32_t *tc_err = tc ? static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4)) : nullptr;
+  float *a0c = tc || split ? static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n))) : nullptr;
+  if ((split && !a0c) || (tc && (!img || !tc_err || !a0c))) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  if (tc) SDL_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int32_t), ctx->stream), "err clear");
   T *G = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)L * K * K));
   int32_t *idx = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * s));
   T *val = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)n * s));
@@ -542,6 +579,8 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
       cudaError_t e;
       if (bf16) {
         e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c);
+      } else if (x3) {
+        e = run_omp_x3(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c);
       } else if (split) {
         SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
         e = timed(ctx, "omp_split", split_kernels(oa), [&] { return launch_omp_split_f32(oa, a0c, sm); });
@@ -579,11 +618,12 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
     if ((st = run_loop()) != SDL_OK) return st;
   } else {
     char kb[512];
-    snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d:%d",
-             sizeof(T), (int)bf16, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
+    snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d:%d:%d:%lld",
+             sizeof(T), (int)bf16 + 2 * (int)x3, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
              (void *)d_off, m, K, s, L, (long long)n, (long long)tiles, (long long)ma.total_tiles, eps, iters,
              ctx->opt_mod_solve, ctx->opt_tile, ctx->opt_cluster * 4 + ctx->opt_sm_blocks, ctx->opt_autotune,
-             (int)ctx->tuned.size(), (ctx->opt_replace * 4 + ctx->opt_omp_form) * 4 + ctx->opt_bf16_form);
+             (int)ctx->tuned.size(), (ctx->opt_replace * 4 + ctx->opt_omp_form) * 4 + ctx->opt_bf16_form,
+             ctx->opt_wait_test, ctx->opt_wait_limit);
     const std::string key(kb);
     auto hit = ctx->graphs.find(key);
     if (hit != ctx->graphs.end()) {
@@ -625,7 +665,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   }
   if (iters > 0) {
     if ((st = mod_status(ctx, worst, iters, d_max)) != SDL_OK) return st;
-    if (bf16) return tc_status(ctx, tc_err);
+    if (tc) return tc_status(ctx, tc_err);
   }
   return SDL_OK;
 }
@@ -706,9 +746,9 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
   int64_t *d_off = nullptr;
   int32_t *d_tiles = nullptr;
   int64_t tiles = 0;
-  const bool bf16 = prec == SDL_PREC_BF16;
+  const bool bf16 = prec == SDL_PREC_BF16, x3 = prec == SDL_PREC_F32X3;
   const bool split = prec == SDL_PREC_F32 && omp_split_f32(ctx, K, m, s);
-  const int tile = bf16 || split ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
+  const int tile = bf16 || x3 || split ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
   if (tile <= 0) return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
   if ((st = upload_plan(ctx, offsets, L, tile, &d_off, &d_tiles, &tiles)) != SDL_OK)
     return st;
@@ -717,16 +757,17 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
   a.D = D; a.G = G; a.Y = Y; a.offsets = d_off; a.tile_start = d_tiles; a.total_tiles = tiles;
   a.L = L; a.m = m; a.K = K; a.s = s; a.eps = eps;
   a.idx = idx; a.val = val; a.nnz = nnz; a.resid2 = resid2;
-  if (bf16) {
+  if (bf16 || x3) {
     void *img = ws_alloc(ctx, 2 * tc_image_bytes(L, K, m));
     int32_t *err = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
     float *a0c = static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n)));
     if (!img || !err || !a0c) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
     SDL_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream), "err clear");
-    cudaError_t e = run_omp_bf16(ctx, a, img, static_cast<float *>(G), err, a0c);
+    cudaError_t e = bf16 ? run_omp_bf16(ctx, a, img, static_cast<float *>(G), err, a0c)
+                         : run_omp_x3(ctx, a, img, static_cast<float *>(G), err, a0c);
     if (e == cudaErrorInvalidConfiguration)
       return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
-    SDL_CUDA(e, "omp bf16");
+    SDL_CUDA(e, bf16 ? "omp bf16" : "omp f32x3");
     return tc_status(ctx, err);
   }
   if (prec == SDL_PREC_F64) {
@@ -911,7 +952,7 @@ sdl_status sdl_local_train(sdl_ctx *ctx, sdl_precision prec, const void *Y, int 
   }
   if ((st = ws_reserve(ctx, train_ws_bytes<float>(L, K1, m, n, s1, iters))) != SDL_OK) return st;
   return train_run<float>(ctx, static_cast<const float *>(Y), m, offsets, L, K1, s1, eps, iters,
-                          static_cast<float *>(D_local), xfro, rmse, prec == SDL_PREC_BF16);
+                          static_cast<float *>(D_local), xfro, rmse, prec);
 }
 
 sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, const double *xfro, int m,
@@ -954,7 +995,7 @@ sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, cons
     SDL_CUDA(timed(ctx, "pick_init", 1, [&] { return launch_pick_init<float>(static_cast<const float *>(Yt), m, pick, K, static_cast<float *>(D),
                                      ctx->stream); }), "merge init");
   return train_run<float>(ctx, static_cast<const float *>(Yt), m, offsets, 1, K, s2, eps, iters,
-                          static_cast<float *>(D), xf_unused, rmse, prec == SDL_PREC_BF16);
+                          static_cast<float *>(D), xf_unused, rmse, prec);
 }
 
 sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t n, const void *D,
@@ -1008,6 +1049,16 @@ sdl_status sdl_gram(sdl_ctx *ctx, sdl_precision prec, const void *D, int m, int 
   if (!img || !err) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
   void *lo = static_cast<unsigned char *>(img) + tc_image_bytes(L, K, m);
   SDL_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), sm), "err clear");
+  if (prec == SDL_PREC_F32X3) {
+    SDL_CUDA(timed(ctx, "x3_image", 1, [&] {
+               return launch_x3_image(static_cast<const float *>(D), K, m, L, img, lo, sm);
+             }), "tf32 image");
+    SDL_CUDA(timed(ctx, "gram_x3", 1, [&] {
+               return launch_gram_x3(static_cast<const float *>(D), img, lo, K, m, L, static_cast<float *>(G), err,
+                                     ctx->num_sms, x3_wait(ctx), sm);
+             }), "gram x3");
+    return tc_status(ctx, err);
+  }
   SDL_CUDA(timed(ctx, "bf16_image", 1, [&] {
              return launch_bf16_image(static_cast<const float *>(D), K, m, L, img, lo, sm);
            }), "bf16 image");

@@ -164,6 +164,23 @@ cudaError_t launch_omp_split_f32(const OmpArgs &a, float *a0c, cudaStream_t st);
 // (used by launch_gram<float> when there are enough blocks to fill the GPU).
 cudaError_t launch_gram_f32_tiles(const float *D, int m, int K, int L, float *G, cudaStream_t st);
 int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles);
+// FP32-accurate tensor-core path (3 x TF32): hi = tf32(d), lo = tf32(d - hi)
+// images of D [L][round32(m)/32][round128(K)][32] (x3_image_bytes each), the
+// Gram and the correlations as hi hi^T + hi lo^T + lo hi^T with FP32
+// accumulation, then the FP32 selection kernel from the alpha0 scratch.
+// num_sms sizes the persistent grid; err as for the BF16 kernels; w bounds
+// every mbarrier wait (limit polls) and, with leave set, makes the loader role
+// leave at once so that the other roles' waits run out (a test).
+struct X3Wait {
+  int limit;
+  int leave;
+};
+size_t x3_image_bytes(int L, int K, int m);
+cudaError_t launch_x3_image(const float *D, int K, int m, int L, void *hi, void *lo, cudaStream_t st);
+cudaError_t launch_gram_x3(const float *D, const void *hi, const void *lo, int K, int m, int L, float *G,
+                           int32_t *err, int num_sms, const X3Wait &w, cudaStream_t st);
+cudaError_t launch_omp_x3(const OmpArgs &a, const void *hi, const void *lo, float *a0c, int num_sms,
+                          const X3Wait &w, cudaStream_t st);
 // Correlation features F = |D_t^T y| (FP32 FMA chains) of the 128-signal tiles
 // tile0 .. tile0+ntile-1 of the plan; signal row r goes to row r - row_base of F.
 cudaError_t launch_corr_features(const OmpArgs &a, int64_t tile0, int64_t ntile, int64_t row_base, float *F,

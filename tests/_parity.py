@@ -22,8 +22,11 @@ alpha0_j - g_j^T G_SS^-1 alpha0_S (Batch-OMP, Sec. 1 greedy choice): with
 alpha0 = D^T y off by delta, the compared value is off by
 delta_j - w_j^T delta_S, w_j = G_SS^-1 D_S^T d_j the coefficients of d_j on the
 prefix atoms.  |delta_j| <= e sum_i |d_ji y_i| with e = gamma_m for FP32
-products (u = 2^-24) and e = 2u_b + u_b^2 + gamma_m for BF16 operands
-(round to nearest, u_b = 2^-9, exact products, FP32 accumulation).
+products (u = 2^-24), e = 2u_b + u_b^2 + gamma_m for BF16 operands
+(round to nearest, u_b = 2^-9, exact products, FP32 accumulation), and
+e = 3 2^-22 + gamma_m(2^-23) for the two-term TF32 split (x = hi + lo, three
+products, FP32 accumulation whose rounding the tensor cores do not document:
+one unit 2^-23 per addition instead of half).
 """
 from __future__ import annotations
 
@@ -43,6 +46,21 @@ def fp32_gap_tol(m: int, ynorm: np.ndarray) -> np.ndarray:
     gamma_m = m u / (1 - m u), u = 2^-24; two correlations must move for their
     order to flip, so ties closer than 2 gamma_m ||y|| are undecidable in FP32."""
     return np.maximum(1e-6, 2 * gamma(m) * ynorm)
+
+
+def x3_unit(m: int) -> float:
+    """Relative error bound of a correlation from the two-term TF32 split: each
+    operand is hi + lo to within 2^-22 (hi = tf32(x) keeps 11 significant bits,
+    lo = tf32(x - hi) 11 more), the dropped lo lo term is below 2^-22 of the
+    product, so each of the m products is within 3 2^-22 of x_i z_i; the FP32
+    accumulation adds gamma_m with a unit of 2^-23."""
+    return 3 * 2.0 ** -22 + gamma(m, 2.0 ** -23)
+
+
+def x3_gap_tol(m: int, ynorm: np.ndarray) -> np.ndarray:
+    """The FP32 gap rule with the TF32-split bound: ties closer than
+    2 e ||y|| (e = x3_unit(m)) are undecidable on that path."""
+    return np.maximum(1e-6, 2 * x3_unit(m) * ynorm)
 
 
 def bf16_unit(m: int) -> float:
@@ -129,7 +147,7 @@ def _near_tie(D, y, gi, gn, oi, on, orc_gap_k, tol_a, tol_b, e, residual=False):
 
 
 def compare_codes(D, Y, gpu_idx, gpu_val, gpu_nnz, gpu_r2, orc, gap_tol, coef_rtol, r2_rtol=None, eps=None,
-                  max_excused=0.002):
+                  max_excused=0.002, e=None):
     """Returns a dict of counts; raises AssertionError on a real mismatch.
 
     D (K, m) and Y (n, m) are float64 numpy arrays of the inputs both sides saw.
@@ -139,7 +157,9 @@ def compare_codes(D, Y, gpu_idx, gpu_val, gpu_nnz, gpu_r2, orc, gap_tol, coef_rt
     is then a near-tie on the stop itself when the prefix's least-squares
     residual norm is eps to within 1e-4 eps.  At most max_excused of the
     signals may be excused near-ties (stop near-ties and rounding-level steps
-    are counted apart, as excused_eps and excused_rounding)."""
+    are counted apart, as excused_eps and excused_rounding).  e: the relative
+    bound of one correlation on the path (gamma_m for FP32 products, the
+    default; x3_unit for the TF32 split)."""
     n, s = gpu_idx.shape
     m = D.shape[1]
     gap_tol = np.broadcast_to(np.asarray(gap_tol, dtype=np.float64), (n,))
@@ -162,7 +182,7 @@ def compare_codes(D, Y, gpu_idx, gpu_val, gpu_nnz, gpu_r2, orc, gap_tol, coef_rt
         stats["coef_rel_max"] = float(rel.max())
     # differing supports: a near-tie in the oracle at which the GPU's atom was
     # near-maximal, and a valid code on its own support
-    e32 = gamma(m)
+    e32 = gamma(m) if e is None else e
     for i in np.nonzero(~same)[0]:
         gi, oi = gpu_idx[i], orc["idx"][i]
         kmin = int(min(gpu_nnz[i], orc["nnz"][i]))
