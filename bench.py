@@ -151,6 +151,8 @@ def algorithmic_work(p):
                       + p.N * omp_flops(K, p.s)),
         "omp_tc": ("alu", p.iters_local * p.N * omp_flops(K1, p.s1) + p.iters_merge * nm * omp_flops(K, p.s2)
                    + p.N * omp_flops(K, p.s)),
+        "omp_x3": ("alu", p.iters_local * p.N * omp_flops(K1, p.s1) + p.iters_merge * nm * omp_flops(K, p.s2)
+                   + p.N * omp_flops(K, p.s)),
         # residual form: D^T r of every step on the tensor cores (2 m K s per signal)
         "omp_rtc": ("tensor", 2 * m * (p.iters_local * p.N * K1 * p.s1 + p.iters_merge * nm * K * p.s2 + p.N * K * p.s)),
         "gram": ("alu", p.iters_local * L * 2 * K1 * K1 * m + p.iters_merge * 2 * K * K * m),
@@ -320,11 +322,11 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def step(*inp):
-        return forms.step(inp, sdl.PREC_BF16)
+    precs = {"f32x3": sdl.PREC_F32X3, "bf16": sdl.PREC_BF16, "fp32": sdl.PREC_F32}
+    chosen = args.chosen_prec
 
-    def step_fp32(*inp):
-        return forms.step(inp, sdl.PREC_F32)
+    def step(*inp):
+        return forms.step(inp, precs[chosen])
 
     # ---- chosen form, device-resident timed region: training loops replayed as
     # CUDA graphs (the first warm-up step runs eagerly and tunes, the next
@@ -345,23 +347,30 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
     rmse = float(np.sqrt(r2 / (p.m * p.N)))
     perr = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        perr = {"bf16": precision_error(p, host[0], D, fidx, fval, args.error_sample)}
+        perr = {chosen: precision_error(p, host[0], D, fidx, fval, args.error_sample)}
     del fidx, fval
 
-    # ---- the same form with FP32 CUDA-core coding passes (graphs as above)
-    fsteps = min(steps, 3)
-    for _ in range(3):
-        step_fp32(*inputs)
-    barrier()
-    fms, (fD, fout2, gidx, gval) = _timed_steps(step_fp32, inputs, fsteps, flush, stream)
-    ftot = max_over_ranks(float(sum(fms)), world, dev)
-    fr2, _ = fout2.cpu().tolist()
-    if perr is not None:
-        perr["fp32"] = precision_error(p, host[0], fD, gidx, gval, args.error_sample)
-    del gidx, gval
-    fp32_form = {"value": whole_job_rate(n_sig, world, fsteps, ftot), "unit": UNIT, "steps": fsteps,
-                 "ms_per_step": ftot / fsteps, "rmse_final": float(np.sqrt(fr2 / (p.m * p.N))),
-                 "form": "the chosen form with FP32 CUDA-core coding passes"}
+    # ---- the same form with the other coding precisions (graphs as above)
+    labels = {"fp32": "FP32 CUDA-core correlations and Gram",
+              "bf16": "BF16 tensor-core correlations and Gram (two-term split) with FP32 refits",
+              "f32x3": "FP32-accurate tensor-core correlations and Gram (two-term TF32 split)"}
+    alt_forms = {}
+    for alt in [a for a in ("fp32", "bf16", "f32x3") if a != chosen]:
+        fsteps = min(steps, 3)
+        for _ in range(3):
+            forms.step(inputs, precs[alt])
+        barrier()
+        fms, (fD, fout2, gidx, gval) = _timed_steps(lambda *inp: forms.step(inp, precs[alt]), inputs, fsteps,
+                                                    flush, stream)
+        ftot = max_over_ranks(float(sum(fms)), world, dev)
+        fr2, _ = fout2.cpu().tolist()
+        if perr is not None:
+            perr[alt] = precision_error(p, host[0], fD, gidx, gval, args.error_sample)
+        del gidx, gval
+        alt_forms[alt + "_form"] = {"value": whole_job_rate(n_sig, world, fsteps, ftot), "unit": UNIT,
+                                    "steps": fsteps, "ms_per_step": ftot / fsteps,
+                                    "rmse_final": float(np.sqrt(fr2 / (p.m * p.N))),
+                                    "form": "the chosen form with " + labels[alt]}
 
     # ---- the same steps eagerly with CUDA events around every launcher: the
     # per-kernel device times of the roofline and the breakdown (instrumented
@@ -414,7 +423,7 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
                  "chosen_speedup": (ptot / args.plain_steps) / (total_ms / steps),
                  "target_rmse": prmse * (1 + 1e-3),
                  "chosen_reaches_rmse": bool(rmse <= prmse * (1 + 1e-3)),
-                 "fp32_form_reaches_rmse": bool(fp32_form["rmse_final"] <= prmse * (1 + 1e-3))}
+                 **{k + "_reaches_rmse": bool(v["rmse_final"] <= prmse * (1 + 1e-3)) for k, v in alt_forms.items()}}
 
     # ---- roofline of the dominant kernel (device time measured inside the timed region)
     work = algorithmic_work(p)
@@ -441,19 +450,20 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
                 "timed": "instrumented eager pass over %d steps (%.2f ms/step)" % (psteps, prof_total_ms / psteps)}
     kernels = {k: {"ms_per_step": v[2] / psteps, "launches_per_step": v[0] / psteps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}
-    omp_names = ("omp", "omp_split", "gram", "omp_tc", "omp_rtc", "gram_tc", "bf16_image")
+    omp_names = ("omp", "omp_split", "gram", "omp_tc", "omp_rtc", "gram_tc", "bf16_image", "omp_x3", "gram_x3",
+                 "x3_image")
     omp_ms = sum(v[2] for k, v in prof.items() if k in omp_names) / psteps
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32x3": "tf32x3+f32+f64", "bf16": "bf16+f32+f64", "fp32": "f32+f64"}[chosen],
         "data": ("synthetic images (seeded piecewise-smooth fields + noise 0.1), 16x16 patches"
                  if name == "patches" else "synthetic (seeded; Sec. 3.1 data model)"),
         "config": workload_config(p, name, world),
         "form": "chosen: batched (all subsets of a phase per launch), training loops replayed as CUDA graphs, "
-                "autotuned FP64 MOD solve, BF16 tensor-core correlations and Gram with FP32 refits; "
-                "no proposer (see proposer_final_coding)",
+                "autotuned FP64 MOD solve, " + labels[chosen] + "; no proposer (see proposer_final_coding)",
         "signals_per_step": n_sig,
         "omp_stage": {"signals_per_s": n_sig / (omp_ms / 1e3) if omp_ms > 0 else None, "ms_per_step": omp_ms,
                       "kernels": [k for k in omp_names if k in prof],
@@ -463,7 +473,7 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
         "rmse_final": rmse,
         "mse_train_db": float(10 * np.log10(r2 / y2)),
         "plain": plain,
-        "fp32_form": fp32_form,
+        **alt_forms,
         "precision_error": perr,
         "e2e": {"value": whole_job_rate(n_sig, world, steps, e2e_total), "unit": UNIT, "steps": steps,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -502,7 +512,8 @@ def run_ours(args, rank, world, local_rank):
         ex = run_main(args, rank, world, local_rank, "splitmerge", extra_key=True)
         res["splitmerge_200k"] = {k: ex.get(k) for k in (
             "config", "value", "unit", "steps", "ms_per_step", "rmse_final", "oracle_rmse_final", "mse_train_db",
-            "plain", "fp32_form", "precision_error", "e2e", "roofline", "omp_stage", "cpu_baseline", "clocks")}
+            "plain", "fp32_form", "bf16_form", "f32x3_form", "precision_error", "e2e", "roofline", "omp_stage",
+            "cpu_baseline", "clocks")}
     if rank == 0 and world == 1 and not args.no_proposer:
         flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
         stream = torch.cuda.current_stream(dev)
@@ -1055,7 +1066,10 @@ def _oracle_phases(p, name, Y, n_sub, local_iters, merge_iters, final_n, threads
         Yt = (loc["D"] * loc["xfro"][:, None, None]).reshape(-1, p.m)
         mer = oracle.train(Yt, p.extra["D_merge0"], p.s2, merge_iters, nthreads=th)
     else:
-        pick = np.random.default_rng(0).choice(n_sub * p.K1, p.K, replace=False).astype(np.int32)
+        # the whole workload merges from the GPU's initial columns; a sample
+        # of fewer subsets from columns drawn among its own atoms
+        pick = (p.mpick.astype(np.int32) if n_sub == p.L else
+                np.random.default_rng(0).choice(n_sub * p.K1, p.K, replace=False).astype(np.int32))
         mer = oracle.merge(loc["D"], loc["xfro"], pick, p.K, p.s2, merge_iters, nthreads=th)
     out["merge"] = (merge_iters * n_sub * p.K1, time.perf_counter() - t0)
     t0 = time.perf_counter()
@@ -1164,6 +1178,8 @@ def main():
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposer sub-benchmarks")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 200,000-signal split-and-merge workload's extra key")
+    ap.add_argument("--chosen-prec", choices=["f32x3", "bf16", "fp32"], default="bf16",
+                    help="coding precision of the chosen form (the others are timed beside it)")
     ap.add_argument("--error-sample", type=int, default=2000,
                     help="signals of the final coding the oracle recodes for the precision error")
     ap.add_argument("--workload", choices=["patches", "splitmerge", "uneven-A", "uneven-B", "denoise", "coding",

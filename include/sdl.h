@@ -18,8 +18,10 @@
  *    every buffer it passes; the library never frees or retains them beyond the
  *    call.  Device pointers must be 16-byte aligned.
  *  - Element type: SDL_PREC_F64 uses double for D, Y, val and resid2; the other
- *    precisions use float.  Accumulators of the MOD normal equations and their
- *    Cholesky factor / solve are always FP64.
+ *    precisions use float.  Accumulators of the MOD normal equations are
+ *    always FP64; their Cholesky factor and solve are FP64, or for FP32 data an
+ *    FP32 pass whose error is checked against the FP64 residual per subset
+ *    (SDL_OPT_MOD_MIXED).
  *  - Every call enqueues its kernels on the context's stream and returns a
  *    status.  Calls that can report a device-side condition (Cholesky breakdown)
  *    synchronise that stream before returning.  A call may grow the context's
@@ -343,7 +345,22 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     SDL_OPT_CLUSTER blocks (0: the SM count over the number of subsets) of a
  *     cooperative launch anywhere on the GPU, meeting at barriers in global
  *     memory whose waits are bounded (SDL_ETIMEOUT when one gives up).  The
- *     automatic choice also times the wide form for fewer subsets than SMs / 16.
+ *     automatic choice also times the wide form for fewer subsets than SMs / 16
+ *     and, for FP32 data, the checked mixed-precision solve (SDL_OPT_MOD_MIXED).
+ *   SDL_OPT_MOD_MIXED: FP32 data only.  1 (default) = under SDL_OPT_MOD_SOLVE
+ *     0 the tiled factorisation and solve may run in FP32, followed by a check
+ *     of every subset's solution: 8 random-sign probes of the FP64 residual
+ *     D A - B, mapped through the FP32 factor, estimate each used atom's error
+ *     (Hutchinson); a subset whose estimates are all within 5e-6 of the atom's
+ *     norm (SDL_OPT_MOD_CHECK_TOL) is renormalised and kept, every other subset (and one whose FP32
+ *     squared pivot fell to 1e-3 of its diagonal) is solved again in FP64 as
+ *     it would have been alone, ridge retry included.  Chosen when the
+ *     autotuner times it faster than the FP64 candidates.  0 = FP64 only.
+ *   SDL_OPT_MOD_CHECK_TOL: the tolerance of that check in parts per 10^9 of
+ *     each atom's norm, 1 to 10^9, default 5000 (5e-6).  A smaller value sends
+ *     more subsets to the FP64 solve; 1 sends every one.
+ *     The result then differs from the FP64 solve's by the FP32 solve's
+ *     error, at most about 5e-6 of each atom (2e-5 is the FP32 atom tolerance).
  *   SDL_OPT_CLUSTER: cluster size, 0 = automatic (default); 4, 8 or 16 for
  *     option 1, 1 to 16 for option 3; blocks per subset for option 4.
  *   SDL_OPT_MOD_TILE: tile edge of the tiled solve: 0 = automatic (default),
@@ -406,7 +423,9 @@ typedef enum {
   SDL_OPT_OMP_FORM = 8,
   SDL_OPT_BF16_FORM = 9,
   SDL_OPT_WAIT_LIMIT = 10,
-  SDL_OPT_WAIT_TEST = 11
+  SDL_OPT_WAIT_TEST = 11,
+  SDL_OPT_MOD_MIXED = 12,
+  SDL_OPT_MOD_CHECK_TOL = 13
 } sdl_option;
 sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
 

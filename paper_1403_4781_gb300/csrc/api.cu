@@ -120,13 +120,15 @@ void prof_resolve(sdl_ctx *ctx) {
   cudaGetLastError();
 }
 
-// Cached number of clusters of the tiled solve that fit on the device at once.
+// Cached number of clusters of the tiled solve (f32: its FP32 pass) that fit
+// on the device at once.
 template <typename T>
-int tiled_occupancy(sdl_ctx *ctx, int ts, int C, int cap) {
-  const int64_t key = ((int64_t)(sizeof(T)) << 32) | ((int64_t)cap << 16) | ((int64_t)ts << 8) | C;
+int tiled_occupancy(sdl_ctx *ctx, int ts, int C, int cap, bool f32 = false) {
+  const int64_t key = ((int64_t)f32 << 40) | ((int64_t)(sizeof(T)) << 32) | ((int64_t)cap << 16) |
+                      ((int64_t)ts << 8) | C;
   auto it = ctx->occ.find(key);
   if (it != ctx->occ.end()) return it->second;
-  const int n = mod_tiled_max_clusters<T>(ts, C, cap);
+  const int n = mod_tiled_max_clusters<T>(ts, C, cap, f32);
   ctx->occ[key] = n;
   return n;
 }
@@ -136,7 +138,7 @@ int tiled_occupancy(sdl_ctx *ctx, int ts, int C, int cap) {
 // spread each subset over the largest cluster.  Many subsets: the largest
 // cluster for which every subset's cluster is resident at once.
 template <typename T>
-void pick_tiled(sdl_ctx *ctx, int L, int *ts, int *C) {
+void pick_tiled(sdl_ctx *ctx, int L, int *ts, int *C, bool f32 = false) {
   int t = ctx->opt_tile;
   int c = ctx->opt_cluster;
   if (t == 0) t = (int64_t)L * 8 <= ctx->num_sms ? 16 : 32;
@@ -144,7 +146,7 @@ void pick_tiled(sdl_ctx *ctx, int L, int *ts, int *C) {
     c = 1;
     const int cand[6] = {16, 8, 6, 4, 2, 1};
     for (int q = 0; q < 6; ++q) {
-      const int n = tiled_occupancy<T>(ctx, t, cand[q], 0);
+      const int n = tiled_occupancy<T>(ctx, t, cand[q], 0, f32);
       if (n >= L) { c = cand[q]; break; }
     }
   }
@@ -152,101 +154,149 @@ void pick_tiled(sdl_ctx *ctx, int L, int *ts, int *C) {
   *C = c;
 }
 
+// The checked mixed-precision solve of FP32 data: the FP32 pass (tile ts,
+// clusters of C), the check that renormalises the subsets it accepts, then the
+// FP64 solve of the subsets left to it (its shape from the shape rule; every
+// other subset's blocks leave at once).
+template <typename T>
+cudaError_t run_mixed(sdl_ctx *ctx, const ModArgs &ma, int ts, int C, bool timed_parts) {
+  if constexpr (sizeof(T) != 4) {   // FP32 data only
+    return cudaErrorNotSupported;
+  } else {
+  cudaStream_t sm = ctx->stream;
+  int ts64 = 32, C64 = 1;
+  pick_tiled<T>(ctx, ma.L, &ts64, &C64);
+  const bool single = ma.L == 1;
+  auto r32 = [&] { return launch_mod_tiled32<T>(ma, ts, C, 0, ctx->num_sms, sm); };
+  const float tau = (float)(ctx->opt_mod_check_ppb * 1e-9);
+  auto chk = [&] { return launch_mod_check<T>(ma, ts, tau, sm); };
+  auto r64 = [&] { return launch_mod_tiled<T>(ma, ts64, C64, 0, ctx->num_sms, sm, true); };
+  cudaError_t e;
+  if (!timed_parts) {
+    if ((e = r32()) != cudaSuccess) return e;
+    if ((e = chk()) != cudaSuccess) return e;
+    return r64();
+  }
+  if ((e = timed(ctx, single ? "mod_solve_fp32_single" : "mod_solve_fp32", 1, r32)) != cudaSuccess) return e;
+  if ((e = timed(ctx, "mod_check", 1, chk)) != cudaSuccess) return e;
+  return timed(ctx, single ? "mod_solve_fp64_single" : "mod_solve_fp64", 1, r64);
+  }
+}
+
+// Whether the checked FP32 pass applies to this call.
+template <typename T>
+bool mixed_allowed(const sdl_ctx *ctx, const ModArgs &ma) {
+  return sizeof(T) == 4 && ctx->opt_mod_mixed && ma.K <= 1024 && ma.m <= 256;
+}
+
 // Autotuner of the tiled solve: on the first call for a shape (element type,
 // subsets, K, m) that leaves the tile and cluster size automatic, every
 // candidate tile edge and cluster size is run on the caller's own inputs (the
 // solve reads A, B and the usage counts and rewrites only scratch, D and the
 // status, so repeated runs give the same result) and timed with CUDA events;
-// the fastest is cached in the context and run last.  (Capping the blocks per
-// SM to balance clusters over the SMs was measured slower at every shape tried:
-// the FP64 pipe wants the warps more than the balance, so it is not a
-// candidate.)  Skipped while the stream is being captured (the shape rule
-// above is used then) or when the option turns it off.
+// the fastest is cached in the context and run last.  For FP32 data the
+// candidates include the checked FP32 pass with each tile and cluster size
+// (timed with its check and the FP64 solve of what it leaves).  (Capping the
+// blocks per SM to balance clusters over the SMs was measured slower at every
+// shape tried: the FP64 pipe wants the warps more than the balance, so it is
+// not a candidate.)  Skipped while the stream is being captured (the shape
+// rule above is used then, with the checked FP32 pass where it applies) or
+// when the option turns it off.
 template <typename T>
 cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
   cudaStream_t sm = ctx->stream;
   int ts = 32, C = 1, cap = 0;
   const bool manual = ctx->opt_tile != 0 || ctx->opt_cluster != 0;
+  const bool mix_ok = mixed_allowed<T>(ctx, ma);
   const std::string key = std::to_string(sizeof(T)) + ":" + std::to_string(ma.L) + ":" + std::to_string(ma.K) +
-                          ":" + std::to_string(ma.m);
+                          ":" + std::to_string(ma.m) + ":" + std::to_string((int)mix_ok);
   auto it = ctx->tuned.find(key);
   cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(sm, &capst) != cudaSuccess) {
     cudaGetLastError();
     capst = cudaStreamCaptureStatusActive;
   }
-  int wide = 0;
+  int wide = 0, mixed = 0;
   if (!manual && it != ctx->tuned.end()) {
     ts = it->second.ts;
     C = it->second.C;
     cap = it->second.cap;
     wide = it->second.wide;
+    mixed = it->second.mixed;
   } else if (manual || !ctx->opt_autotune || capst != cudaStreamCaptureStatusNone) {
-    pick_tiled<T>(ctx, ma.L, &ts, &C);
+    mixed = mix_ok ? 1 : 0;
+    pick_tiled<T>(ctx, ma.L, &ts, &C, mixed != 0);
     if (manual) cap = ctx->opt_sm_blocks;
   } else {
-    int best_ts = 0, best_c = 0, best_cap = 0;
+    int best_ts = 0, best_c = 0, best_cap = 0, best_wide = 0, best_mixed = 0;
     float best = 3.4e38f;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // best of two timed runs of one candidate
+    auto time_it = [&](auto &&run) -> float {
+      float ms_best = 3.4e38f;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(e0, sm);
+        if (e == cudaSuccess) e = run();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, sm);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < ms_best) ms_best = ms;
+      }
+      return ms_best;
+    };
     const int tiles[2] = {16, 32};
     const int cls[7] = {1, 2, 3, 4, 6, 8, 16};
-    for (int a = 0; a < 2 && e == cudaSuccess; ++a)
-      for (int b = 0; b < 7 && e == cudaSuccess; ++b) {
-        const int t = tiles[a], c = cls[b], cp = 0;
-        // a subset's cluster must fit on the device; small clusters for few
-        // subsets leave most SMs idle and are not worth timing
-        if (tiled_occupancy<T>(ctx, t, c, cp) < 1) continue;
-        if ((int64_t)ma.L * c * 4 < ctx->num_sms && c < 16) continue;
-        float ms_best = 3.4e38f;
-        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-          e = cudaEventRecord(e0, sm);
-          if (e == cudaSuccess) e = launch_mod_tiled<T>(ma, t, c, cp, ctx->num_sms, sm);
-          if (e == cudaSuccess) ctx->launches += 1;
-          if (e == cudaSuccess) e = cudaEventRecord(e1, sm);
-          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-          float ms = 0.f;
-          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-          if (e == cudaSuccess && ms < ms_best) ms_best = ms;
+    for (int mx = mix_ok ? 1 : 0; mx >= 0 && e == cudaSuccess; --mx)
+      for (int a = 0; a < 2 && e == cudaSuccess; ++a)
+        for (int b = 0; b < 7 && e == cudaSuccess; ++b) {
+          const int t = tiles[a], c = cls[b], cp = 0;
+          // a subset's cluster must fit on the device; small clusters for few
+          // subsets leave most SMs idle and are not worth timing
+          if (tiled_occupancy<T>(ctx, t, c, cp, mx != 0) < 1) continue;
+          if ((int64_t)ma.L * c * 4 < ctx->num_sms && c < 16) continue;
+          const float ms = time_it([&] {
+            ctx->launches += mx ? 3 : 1;
+            return mx ? run_mixed<T>(ctx, ma, t, c, false) : launch_mod_tiled<T>(ma, t, c, cp, ctx->num_sms, sm);
+          });
+          if (e == cudaSuccess && ms < best) {
+            best = ms; best_ts = t; best_c = c; best_cap = cp; best_wide = 0; best_mixed = mx;
+          }
         }
-        if (e == cudaSuccess && ms_best < best) { best = ms_best; best_ts = t; best_c = c; best_cap = cp; }
-      }
     // few subsets: the wide form, each subset's tile tasks over G blocks
     // anywhere on the GPU (its largest cluster holds at most 16 SMs)
-    int best_wide = 0;
     if ((int64_t)ma.L * 16 < ctx->num_sms)
       for (int a = 0; a < 2 && e == cudaSuccess; ++a)
         for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
           const int t = tiles[a];
           const int G = (int)((int64_t)ctx->num_sms * (f == 0 ? 1 : (f == 1 ? 2 : 4)) / (2 * ma.L));
           if (G <= 16 || (int64_t)ma.L * G > mod_wide_max_blocks<T>(t, ctx->num_sms)) continue;
-          float ms_best = 3.4e38f;
-          for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-            e = cudaEventRecord(e0, sm);
-            if (e == cudaSuccess) e = launch_mod_wide<T>(ma, t, G, ctx->opt_wait_limit, -1, sm);
-            if (e == cudaSuccess) ctx->launches += 1;
-            if (e == cudaSuccess) e = cudaEventRecord(e1, sm);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e == cudaSuccess && ms < ms_best) ms_best = ms;
+          const float ms = time_it([&] {
+            ctx->launches += 1;
+            return launch_mod_wide<T>(ma, t, G, ctx->opt_wait_limit, -1, sm);
+          });
+          if (e == cudaSuccess && ms < best) {
+            best = ms; best_ts = t; best_c = G; best_cap = 0; best_wide = 1; best_mixed = 0;
           }
-          if (e == cudaSuccess && ms_best < best) { best = ms_best; best_ts = t; best_c = G; best_cap = 0; best_wide = 1; }
         }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return e;
     if (best_ts == 0) {
-      pick_tiled<T>(ctx, ma.L, &ts, &C);
+      mixed = mix_ok ? 1 : 0;
+      pick_tiled<T>(ctx, ma.L, &ts, &C, mixed != 0);
     } else {
       ts = best_ts;
       C = best_c;
       cap = best_cap;
       wide = best_wide;
+      mixed = best_mixed;
     }
-    ctx->tuned[key] = sdl_ctx::TunedSolve{ts, C, cap, wide};
+    ctx->tuned[key] = sdl_ctx::TunedSolve{ts, C, cap, wide, mixed};
   }
+  if (mixed) return run_mixed<T>(ctx, ma, ts, C, true);
   // the batched solve and the single-system (merge) solve are reported apart
   return timed(ctx, ma.L > 1 ? "mod_solve_fp64" : "mod_solve_fp64_single", 1, [&] {
     return wide ? launch_mod_wide<T>(ma, ts, C, ctx->opt_wait_limit, ctx->opt_wait_test ? 1 : -1, sm)
@@ -618,12 +668,13 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
     if ((st = run_loop()) != SDL_OK) return st;
   } else {
     char kb[512];
-    snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d:%d:%d:%lld",
+    snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d:%d:%d:%lld:%d",
              sizeof(T), (int)bf16 + 2 * (int)x3, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
              (void *)d_off, m, K, s, L, (long long)n, (long long)tiles, (long long)ma.total_tiles, eps, iters,
-             ctx->opt_mod_solve, ctx->opt_tile, ctx->opt_cluster * 4 + ctx->opt_sm_blocks, ctx->opt_autotune,
+             ctx->opt_mod_solve * 2 + ctx->opt_mod_mixed, ctx->opt_tile, ctx->opt_cluster * 4 + ctx->opt_sm_blocks,
+             ctx->opt_autotune,
              (int)ctx->tuned.size(), (ctx->opt_replace * 4 + ctx->opt_omp_form) * 4 + ctx->opt_bf16_form,
-             ctx->opt_wait_test, ctx->opt_wait_limit);
+             ctx->opt_wait_test, ctx->opt_wait_limit, ctx->opt_mod_check_ppb);
     const std::string key(kb);
     auto hit = ctx->graphs.find(key);
     if (hit != ctx->graphs.end()) {
@@ -1405,6 +1456,15 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
     case SDL_OPT_WAIT_TEST:
       if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_WAIT_TEST takes 0 or 1");
       ctx->opt_wait_test = (int)value;
+      return SDL_OK;
+    case SDL_OPT_MOD_CHECK_TOL:
+      if (value < 1 || value > 1000000000)
+        return set_error(ctx, SDL_EINVAL, "SDL_OPT_MOD_CHECK_TOL takes 1 to 10^9 (parts per 10^9)");
+      ctx->opt_mod_check_ppb = (int)value;
+      return SDL_OK;
+    case SDL_OPT_MOD_MIXED:
+      if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_MOD_MIXED takes 0 or 1");
+      ctx->opt_mod_mixed = (int)value;
       return SDL_OK;
     case SDL_OPT_BF16_FORM:
       if (value < 0 || value > 2) return set_error(ctx, SDL_EINVAL, "SDL_OPT_BF16_FORM takes 0, 1 or 2");

@@ -1,0 +1,249 @@
+// Check of the FP32 pass of the MOD solve (Sec. 1: D = Y X^T (X X^T)^-1) for
+// FP32 data, and the renormalisation of Sec. 3.1 of the subsets it accepts.
+//
+// The FP32 pass (mod_tiled_kernel with R = float) factors A = X X^T and
+// solves D A = B in FP32.  Its error E = D_32 - D is not known, but E A =
+// D_32 A - B is: for a probe u (m entries of +-1), u^T E = (u^T D_32 A - u^T B)
+// A^-1, whose FP64 residual costs two K x K and two m x K matrix-vector
+// products against the FP64 A and B, and whose A^-1 comes from the FP32 factor
+// (an estimate is all that is needed).  Entry j of u^T E is u . e_j, e_j the
+// error of atom j, and E[(u . e_j)^2] = |e_j|^2 over random signs (the
+// Hutchinson identity), so P probes give every atom's squared error up to a
+// chi-square factor with P degrees of freedom.  A subset is accepted when
+// every used atom's estimate is at most tau of its norm (tau = 5e-6, four
+// times below the FP32 atom tolerance of 2e-5 even for an estimate 16 times
+// too small, which happens with probability about 1e-8 at P = 8); then its
+// used atoms are renormalised and written.  Otherwise (and where the
+// factorisation broke down, or an atom's norm is zero or not finite) the
+// subset is marked for the FP64 solve, which then decides exactly as it would
+// have alone.
+//
+// One block per subset, 256 threads; thread j mod 256 owns atoms j.
+#include <math.h>
+
+#include "sdl_internal.cuh"
+
+namespace sdl {
+namespace {
+
+constexpr int kCThreads = 256;
+constexpr int kProbes = 8;
+constexpr int kCJ = 4;               // atoms per thread (K <= 1024)
+constexpr int kModDeferredC = 4;     // the status the FP32 pass and this check leave for the FP64 solve
+
+// +-1 of probe p at signal entry r of subset t: a 32-bit integer mix of the
+// three counters (xorshift-multiply rounds), its lowest bit as the sign.
+__device__ __forceinline__ float probe_sign(int t, int p, int r) {
+  uint32_t x = (uint32_t)r * 0x9E3779B1u ^ (uint32_t)(p + 1) * 0x85EBCA77u ^ (uint32_t)(t + 1) * 0xC2B2AE3Du;
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return (x & 1u) ? -1.f : 1.f;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__restrict__ A,
+                                                              const double *__restrict__ B,
+                                                              const int32_t *__restrict__ usage, int K, int m, int TS,
+                                                              const float *__restrict__ M, const float *__restrict__ V,
+                                                              T *D, int32_t *status, float tau) {
+  extern __shared__ double sh[];
+  __shared__ float Us[kProbes][256];
+  __shared__ double Ys[kProbes][32];
+  const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (status[t] == kModDeferredC) return;   // the FP32 factorisation broke down
+  const int R = (K + TS - 1) / TS;
+  const double *At = A + (size_t)t * K * K;
+  const double *Bt = B + (size_t)t * K * m;
+  const int32_t *ut = usage + (size_t)t * K;
+  const float *Lt = M + (size_t)t * (K + m) * K;   // lower triangle: the FP32 factor
+  const float *X = Lt + (size_t)K * K;              // row r: coordinate r of every atom
+  const float *Vt = V + (size_t)t * R * TS * TS;    // inverses of the diagonal factor tiles
+  double *Gs = sh;                     // [P][K]: u_p^T D_32
+  double *Rs = sh + kProbes * K;       // [P][K]: residual, then A^-1 applied in place
+
+  for (int e = tid; e < kProbes * m; e += kCThreads) Us[e / m][e % m] = probe_sign(t, e / m, e % m);
+  __syncthreads();
+
+  // G = U^T D_32 and the atoms' squared norms
+  double n2[kCJ];
+#pragma unroll
+  for (int q = 0; q < kCJ; ++q) {
+    const int j = tid + kCThreads * q;
+    n2[q] = 0.0;
+    if (j >= K) continue;
+    double g[kProbes] = {};
+    for (int r = 0; r < m; ++r) {
+      const double x = X[(size_t)r * K + j];
+      n2[q] = fma(x, x, n2[q]);
+#pragma unroll
+      for (int p = 0; p < kProbes; ++p) g[p] = fma((double)Us[p][r], x, g[p]);
+    }
+#pragma unroll
+    for (int p = 0; p < kProbes; ++p) Gs[p * K + j] = g[p];
+  }
+  __syncthreads();
+
+  // H = G A from the lower triangle of A: the part below the diagonal of
+  // column j by columns (row i's entries left of the diagonal, coalesced), the
+  // part on and right of it by rows (warp-per-row dot products into Rs)
+  double h[kCJ][kProbes];
+#pragma unroll
+  for (int q = 0; q < kCJ; ++q)
+#pragma unroll
+    for (int p = 0; p < kProbes; ++p) h[q][p] = 0.0;
+  for (int i = 1; i < K; ++i) {
+    const double *ai = At + (size_t)i * K;
+#pragma unroll
+    for (int q = 0; q < kCJ; ++q) {
+      const int j = tid + kCThreads * q;
+      if (j < i) {
+        const double a = __ldg(ai + j);
+#pragma unroll
+        for (int p = 0; p < kProbes; ++p) h[q][p] = fma(a, Gs[p * K + i], h[q][p]);
+      }
+    }
+  }
+  for (int i = warp; i < K; i += kCThreads / 32) {
+    const double *ai = At + (size_t)i * K;
+    double d[kProbes] = {};
+    for (int c = lane; c <= i; c += 32) {
+      const double a = __ldg(ai + c);
+#pragma unroll
+      for (int p = 0; p < kProbes; ++p) d[p] = fma(a, Gs[p * K + c], d[p]);
+    }
+#pragma unroll
+    for (int p = 0; p < kProbes; ++p)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d[p] += __shfl_xor_sync(0xffffffffu, d[p], o);
+    if (lane == 0)
+#pragma unroll
+      for (int p = 0; p < kProbes; ++p) Rs[p * K + i] = d[p];
+  }
+  __syncthreads();
+  // residual r_p = u_p^T D_32 A - u_p^T B (B is [K][m]: row j = atom j's column)
+#pragma unroll
+  for (int q = 0; q < kCJ; ++q) {
+    const int j = tid + kCThreads * q;
+    if (j >= K) continue;
+    double b[kProbes] = {};
+    const double *bj = Bt + (size_t)j * m;
+    for (int r = 0; r < m; ++r) {
+      const double v = __ldg(bj + r);
+#pragma unroll
+      for (int p = 0; p < kProbes; ++p) b[p] = fma((double)Us[p][r], v, b[p]);
+    }
+#pragma unroll
+    for (int p = 0; p < kProbes; ++p) Rs[p * K + j] += h[q][p] - b[p];
+  }
+  __syncthreads();
+
+  // z_p = r_p A^-1 = (L L^T)^-1 r_p: forward L y = r, then backward L^T z = y,
+  // tile by tile with the inverses of the diagonal factor tiles
+  for (int k = 0; k < R; ++k) {
+    const int k0 = k * TS, nb = K - k0 < TS ? K - k0 : TS;
+    if (tid < kProbes * TS) {
+      const int p = tid / TS, a = tid % TS;
+      double y = 0.0;
+      if (a < nb)
+        for (int c = 0; c <= a; ++c) y = fma((double)Vt[(size_t)k * TS * TS + a * TS + c], Rs[p * K + k0 + c], y);
+      Ys[p][a] = y;
+    }
+    __syncthreads();
+    if (tid < kProbes * TS) {
+      const int p = tid / TS, a = tid % TS;
+      if (a < nb) Rs[p * K + k0 + a] = Ys[p][a];
+    }
+    for (int i = k0 + nb + tid; i < K; i += kCThreads) {
+      const float *li = Lt + (size_t)i * K + k0;
+      double acc[kProbes] = {};
+      for (int c = 0; c < nb; ++c) {
+        const double l = li[c];
+#pragma unroll
+        for (int p = 0; p < kProbes; ++p) acc[p] = fma(l, Ys[p][c], acc[p]);
+      }
+#pragma unroll
+      for (int p = 0; p < kProbes; ++p) Rs[p * K + i] -= acc[p];
+    }
+    __syncthreads();
+  }
+  for (int k = R - 1; k >= 0; --k) {
+    const int k0 = k * TS, nb = K - k0 < TS ? K - k0 : TS;
+    if (tid < kProbes * TS) {
+      const int p = tid / TS, a = tid % TS;
+      double z = 0.0;
+      if (a < nb)
+        for (int c = a; c < nb; ++c) z = fma((double)Vt[(size_t)k * TS * TS + c * TS + a], Rs[p * K + k0 + c], z);
+      Ys[p][a] = z;
+    }
+    __syncthreads();
+    if (tid < kProbes * TS) {
+      const int p = tid / TS, a = tid % TS;
+      if (a < nb) Rs[p * K + k0 + a] = Ys[p][a];
+    }
+    for (int j = tid; j < k0; j += kCThreads) {
+      double acc[kProbes] = {};
+      for (int c = 0; c < nb; ++c) {
+        const double l = Lt[(size_t)(k0 + c) * K + j];
+#pragma unroll
+        for (int p = 0; p < kProbes; ++p) acc[p] = fma(l, Ys[p][c], acc[p]);
+      }
+#pragma unroll
+      for (int p = 0; p < kProbes; ++p) Rs[p * K + j] -= acc[p];
+    }
+    __syncthreads();
+  }
+
+  // every used atom's estimated error against tau of its norm
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < kCJ; ++q) {
+    const int j = tid + kCThreads * q;
+    if (j >= K || ut[j] == 0) continue;
+    double e2 = 0.0;
+#pragma unroll
+    for (int p = 0; p < kProbes; ++p) e2 = fma(Rs[p * K + j], Rs[p * K + j], e2);
+    e2 /= kProbes;
+    const double lim = (double)tau * (double)tau * n2[q];
+    if (!(n2[q] > 0.0) || !isfinite(n2[q]) || !(e2 <= lim)) ok = false;
+  }
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok) {
+    if (tid == 0) status[t] = kModDeferredC;
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < kCJ; ++q) {
+    const int j = tid + kCThreads * q;
+    if (j >= K || ut[j] == 0) continue;   // unused: keeps the previous atom
+    const double inv = 1.0 / sqrt(n2[q]);
+    T *dj = D + ((size_t)t * K + j) * m;
+    for (int r = 0; r < m; ++r) dj[r] = (T)((double)X[(size_t)r * K + j] * inv);
+  }
+  if (tid == 0) status[t] = 0;
+}
+
+}  // namespace
+
+size_t mod_check_smem(int K) { return sizeof(double) * 2 * kProbes * (size_t)K; }
+
+template <typename T>
+cudaError_t launch_mod_check(const ModArgs &a, int ts, float tau, cudaStream_t st) {
+  if (a.L <= 0) return cudaSuccess;
+  if (a.K > kCThreads * kCJ || a.m > 256 || (ts != 16 && ts != 32)) return cudaErrorInvalidValue;
+  const size_t smem = mod_check_smem(a.K);
+  cudaError_t e = cudaFuncSetAttribute(mod_check_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const float *M = reinterpret_cast<const float *>(a.Lf);
+  const float *V = M + (size_t)a.L * (a.K + a.m) * a.K;
+  mod_check_kernel<T><<<(unsigned)a.L, kCThreads, smem, st>>>(
+      static_cast<const double *>(a.A), static_cast<const double *>(a.B), a.usage, a.K, a.m, ts, M, V,
+      static_cast<T *>(a.D), a.status, tau);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_mod_check<float>(const ModArgs &, int, float, cudaStream_t);
+
+}  // namespace sdl

@@ -38,13 +38,15 @@ namespace {
 
 constexpr int kTThreads = 256;
 
-template <int TS>
+// R: the arithmetic type of the factorisation (double; float for the FP32
+// pass of the checked mixed-precision solve below).
+template <typename R, int TS>
 struct TiledSmem {
-  double a[TS][TS + 1];      // A operand; the diagonal factor during factor_diag
-  double b[TS][TS + 1];      // B operand; the inverse during factor_diag
-  double v[2][TS + 0][TS + 1];   // inverses of diagonal factors k (v[k & 1]), pushed by their owner
-  double invd[TS];
-  double dg[TS];
+  R a[TS][TS + 1];           // A operand; the diagonal factor during factor_diag
+  R b[TS][TS + 1];           // B operand; the inverse during factor_diag
+  R v[2][TS + 0][TS + 1];    // inverses of diagonal factors k (v[k & 1]), pushed by their owner
+  R invd[TS];
+  R dg[TS];
   int fail;
   int verdict[2];            // breakdown verdict of diagonal tile k (verdict[k & 1]), pushed by its owner
 };
@@ -66,37 +68,39 @@ struct TGeom {
 
 // A TS x TS operand in global memory: p[r * ld + c] for r < nr, c < nc, zero
 // elsewhere.
+template <typename R>
 struct Opnd {
-  const double *p;
+  const R *p;
   int ld, nr, nc;
 };
 
-template <int TS>
-__device__ __forceinline__ Opnd tile_of(const double *Mt, const TGeom &g, int i, int j) {
-  return Opnd{Mt + g.row(i, 0) * g.K + (int64_t)j * TS, g.K, g.rows_in(i), g.cols_in(j)};
+template <typename R, int TS>
+__device__ __forceinline__ Opnd<R> tile_of(const R *Mt, const TGeom &g, int i, int j) {
+  return Opnd<R>{Mt + g.row(i, 0) * g.K + (int64_t)j * TS, g.K, g.rows_in(i), g.cols_in(j)};
 }
 
 // One tile task: out (=|-=) A B^T with B staged as given (bt: from the
 // transpose of its source; bsm: B is the inverse held in shared memory).
+template <typename R>
 struct TileTask {
-  Opnd a, b, o;
+  Opnd<R> a, b, o;
   bool bt, bsm, sub, lower;
 };
 
 // Thread-to-element map shared by the loads, the products and the stores:
 // element u of this thread is (tid / TS + (256 / TS) u, tid mod TS).
-template <int TS>
-__device__ __forceinline__ void fetch(const Opnd &o, double (&r)[TS * TS / kTThreads]) {
+template <typename R, int TS>
+__device__ __forceinline__ void fetch(const Opnd<R> &o, R (&r)[TS * TS / kTThreads]) {
   constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
   const int cc = threadIdx.x % TS, r0 = threadIdx.x / TS;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int rr = r0 + RS * u;
-    r[u] = (rr < o.nr && cc < o.nc) ? __ldcg(o.p + (int64_t)rr * o.ld + cc) : 0.0;
+    r[u] = (rr < o.nr && cc < o.nc) ? __ldcg(o.p + (int64_t)rr * o.ld + cc) : R(0);
   }
 }
-template <int TS>
-__device__ __forceinline__ void commit(double (*S)[TS + 1], const double (&r)[TS * TS / kTThreads], bool t) {
+template <typename R, int TS>
+__device__ __forceinline__ void commit(R (*S)[TS + 1], const R (&r)[TS * TS / kTThreads], bool t) {
   constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
   const int cc = threadIdx.x % TS, r0 = threadIdx.x / TS;
 #pragma unroll
@@ -109,40 +113,39 @@ __device__ __forceinline__ void commit(double (*S)[TS + 1], const double (&r)[TS
 // For this thread's outputs (r_u, c): acc[u] = sum_q As[r_u][q] Bs[c][q], or,
 // with sub, acc[u] = old[u] - sum_q As[r_u][q] Bs[c][q] (the subtraction folded
 // into the fused multiply-adds).
-template <int TS>
-__device__ __forceinline__ void tile_product(const double (*As)[TS + 1], const double (*Bs)[TS + 1], bool sub,
-                                             const double (&old)[TS * TS / kTThreads],
-                                             double (&acc)[TS * TS / kTThreads]) {
+template <typename R, int TS>
+__device__ __forceinline__ void tile_product(const R (*As)[TS + 1], const R (*Bs)[TS + 1], bool sub,
+                                             const R (&old)[TS * TS / kTThreads], R (&acc)[TS * TS / kTThreads]) {
   constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
   const int c = threadIdx.x % TS, r0 = threadIdx.x / TS;
 #pragma unroll
-  for (int u = 0; u < U; ++u) acc[u] = sub ? old[u] : 0.0;
+  for (int u = 0; u < U; ++u) acc[u] = sub ? old[u] : R(0);
   if (sub) {
 #pragma unroll 8
     for (int q = 0; q < TS; ++q) {
-      const double bv = Bs[c][q];
+      const R bv = Bs[c][q];
 #pragma unroll
       for (int u = 0; u < U; ++u) acc[u] = fma(-As[r0 + RS * u][q], bv, acc[u]);
     }
   } else {
 #pragma unroll 8
     for (int q = 0; q < TS; ++q) {
-      const double bv = Bs[c][q];
+      const R bv = Bs[c][q];
 #pragma unroll
       for (int u = 0; u < U; ++u) acc[u] = fma(As[r0 + RS * u][q], bv, acc[u]);
     }
   }
 }
 
-template <int TS>
-__device__ __forceinline__ void put(const TileTask &t, const double (&acc)[TS * TS / kTThreads]) {
+template <typename R, int TS>
+__device__ __forceinline__ void put(const TileTask<R> &t, const R (&acc)[TS * TS / kTThreads]) {
   constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
   const int c = threadIdx.x % TS, r0 = threadIdx.x / TS;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int r = r0 + RS * u;
     if (r < t.o.nr && c < t.o.nc && (!t.lower || c <= r))
-      const_cast<double *>(t.o.p)[(int64_t)r * t.o.ld + c] = acc[u];
+      const_cast<R *>(t.o.p)[(int64_t)r * t.o.ld + c] = acc[u];
   }
 }
 
@@ -150,33 +153,33 @@ __device__ __forceinline__ void put(const TileTask &t, const double (&acc)[TS * 
 // output) of the next task are loaded into registers while the current one is
 // multiplied.  Tasks of one step never read a tile another task of the step
 // writes.  vs: the inverse used by tasks whose B operand is in shared memory.
-template <int TS, class Desc>
-__device__ __forceinline__ void run_step(TiledSmem<TS> &sm, const double (*vs)[TS + 1], int n, int first, int C,
+template <typename R, int TS, class Desc>
+__device__ __forceinline__ void run_step(TiledSmem<R, TS> &sm, const R (*vs)[TS + 1], int n, int first, int C,
                                          Desc desc) {
   constexpr int U = TS * TS / kTThreads;
   if (first >= n) return;
-  TileTask cur = desc(first);
-  double ra[U], rb[U], ro[U];
-  fetch<TS>(cur.a, ra);
-  if (!cur.bsm) fetch<TS>(cur.b, rb);
-  if (cur.sub) fetch<TS>(cur.o, ro);
+  TileTask<R> cur = desc(first);
+  R ra[U], rb[U], ro[U];
+  fetch<R, TS>(cur.a, ra);
+  if (!cur.bsm) fetch<R, TS>(cur.b, rb);
+  if (cur.sub) fetch<R, TS>(cur.o, ro);
   for (int q = first; q < n; q += C) {
     __syncthreads();
-    commit<TS>(sm.a, ra, false);
-    if (!cur.bsm) commit<TS>(sm.b, rb, cur.bt);
+    commit<R, TS>(sm.a, ra, false);
+    if (!cur.bsm) commit<R, TS>(sm.b, rb, cur.bt);
     __syncthreads();
     const bool more = q + C < n;
-    TileTask nxt = cur;
-    double rn[U];
+    TileTask<R> nxt = cur;
+    R rn[U];
     if (more) {
       nxt = desc(q + C);
-      fetch<TS>(nxt.a, ra);
-      if (!nxt.bsm) fetch<TS>(nxt.b, rb);
-      if (nxt.sub) fetch<TS>(nxt.o, rn);
+      fetch<R, TS>(nxt.a, ra);
+      if (!nxt.bsm) fetch<R, TS>(nxt.b, rb);
+      if (nxt.sub) fetch<R, TS>(nxt.o, rn);
     }
-    double acc[U];
-    tile_product<TS>(sm.a, cur.bsm ? vs : sm.b, cur.sub, ro, acc);
-    put<TS>(cur, acc);
+    R acc[U];
+    tile_product<R, TS>(sm.a, cur.bsm ? vs : sm.b, cur.sub, ro, acc);
+    put<R, TS>(cur, acc);
     if (more) {
       cur = nxt;
 #pragma unroll
@@ -185,21 +188,29 @@ __device__ __forceinline__ void run_step(TiledSmem<TS> &sm, const double (*vs)[T
   }
 }
 
-template <int TS>
-__device__ __forceinline__ void pivot(TiledSmem<TS> &sm, int c, double d) {
-  if (!(d > kModPivotRel * sm.dg[c]) || !(d > 0.0)) {
+// Breakdown rule of the factorisation in FP32: a squared pivot at most this
+// fraction of its diagonal leaves fewer than ~10 significant bits after
+// K-term FP32 updates, so such a subset goes to the FP64 solve instead.
+constexpr float kModPivotRel32 = 1e-3f;
+
+template <typename R>
+__device__ __forceinline__ R pivot_rel() { return sizeof(R) == 8 ? (R)kModPivotRel : (R)kModPivotRel32; }
+
+template <typename R, int TS>
+__device__ __forceinline__ void pivot(TiledSmem<R, TS> &sm, int c, R d) {
+  if (!(d > pivot_rel<R>() * sm.dg[c]) || !(d > R(0))) {
     sm.fail = 1;
     return;
   }
-  const double inv = rsqrt(d);
+  const R inv = rsqrt(d);
   sm.a[c][c] = d * inv;
   sm.invd[c] = inv;
 }
 
 // Factor the diagonal tile (k, k) into sm.a and invert the factor into sm.b
 // (zero above the diagonal, identity on padding).  Returns false on breakdown.
-template <int TS>
-__device__ bool factor_diag(TiledSmem<TS> &sm, const double *Mt, const TGeom &g, int k, const double *At,
+template <typename R, int TS>
+__device__ bool factor_diag(TiledSmem<R, TS> &sm, const R *Mt, const TGeom &g, int k, const double *At,
                             const int32_t *ut, double ridge) {
   const int tid = threadIdx.x;
   const int nb = g.cols_in(k);
@@ -207,14 +218,14 @@ __device__ bool factor_diag(TiledSmem<TS> &sm, const double *Mt, const TGeom &g,
   __syncthreads();
   for (int e = tid; e < TS * TS; e += kTThreads) {
     const int r = e / TS, c = e % TS;
-    double v;
-    if (r < nb && c < nb) v = c <= r ? __ldcg(Mt + (base + r) * g.K + base + c) : 0.0;
-    else v = r == c ? 1.0 : 0.0;
+    R v;
+    if (r < nb && c < nb) v = c <= r ? __ldcg(Mt + (base + r) * g.K + base + c) : R(0);
+    else v = r == c ? R(1) : R(0);
     sm.a[r][c] = v;
-    sm.b[r][c] = r == c ? 1.0 : 0.0;
+    sm.b[r][c] = r == c ? R(1) : R(0);
   }
   if (tid < TS)
-    sm.dg[tid] = tid < nb ? At[(base + tid) * g.K + base + tid] + (ut[base + tid] > 0 ? ridge : 0.0) : 1.0;
+    sm.dg[tid] = tid < nb ? (R)(At[(base + tid) * g.K + base + tid] + (ut[base + tid] > 0 ? ridge : 0.0)) : R(1);
   if (tid == 0) sm.fail = 0;
   __syncthreads();
   if (tid == 0) pivot(sm, 0, sm.a[0][0]);
@@ -233,7 +244,7 @@ __device__ bool factor_diag(TiledSmem<TS> &sm, const double *Mt, const TGeom &g,
     for (int e = tid; e < TS * TS; e += kTThreads) {
       const int r = e / TS, q = e % TS;
       if (q > c && q <= r) {
-        const double v = fma(-sm.a[r][c], sm.a[q][c], sm.a[r][q]);
+        const R v = fma(-sm.a[r][c], sm.a[q][c], sm.a[r][q]);
         if (r == c + 1 && q == c + 1) pivot(sm, c + 1, v);
         else sm.a[r][q] = v;
       }
@@ -245,29 +256,41 @@ __device__ bool factor_diag(TiledSmem<TS> &sm, const double *Mt, const TGeom &g,
   return true;
 }
 
-template <typename T, int TS>
+// Status of a subset whose FP32 pass (factorisation below, or the check of
+// its solution) left it to the FP64 solve.
+constexpr int kModDeferred = 4;
+
+// R = double: the FP64 solve with the ridge retry and the renormalisation; with
+// only_deferred set it solves only the subsets the FP32 pass left to it.
+// R = float: the FP32 pass of the checked mixed-precision solve: one attempt,
+// the unnormalised solution left in the scratch for the check, breakdown
+// recorded as kModDeferred (no ridge: the FP64 solve takes that subset).
+template <typename T, int TS, typename R>
 __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *__restrict__ A,
                                                                  const double *__restrict__ B,
                                                                  const int32_t *__restrict__ usage, int K, int m,
-                                                                 int C, int light, double *M, double *V, T *D,
-                                                                 int32_t *status, int32_t *status_max) {
+                                                                 int C, int light, int only_deferred, R *M, R *V,
+                                                                 T *D, int32_t *status, int32_t *status_max) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
-  __shared__ TiledSmem<TS> sm;
+  constexpr bool kF32 = sizeof(R) == 4;
+  __shared__ TiledSmem<R, TS> sm;
   __shared__ double red[2][kTThreads / 32];
   const int rank = (int)cl.block_rank();
   const int t = blockIdx.x / C;
+  // every block of the cluster reads the same word: all leave or none
+  if (only_deferred && status[t] != kModDeferred) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   TGeom g;
   g.K = K; g.m = m; g.TS = TS;
   g.R = (K + TS - 1) / TS;
   g.RT = g.R + (m + TS - 1) / TS;
-  const int R = g.R, RT = g.RT, Rm = RT - R;
+  const int R_ = g.R, RT = g.RT, Rm = RT - R_;
   const double *At = A + (size_t)t * K * K;
   const double *Bt = B + (size_t)t * K * m;
   const int32_t *ut = usage + (size_t)t * K;
-  double *Mt = M + (size_t)t * (K + m) * K;
-  double *Vt = V + (size_t)t * R * TS * TS;
+  R *Mt = M + (size_t)t * (K + m) * K;
+  R *Vt = V + (size_t)t * R_ * TS * TS;
 
   double tr = 0.0, nu = 0.0;
   for (int j = tid; j < K; j += kTThreads)
@@ -287,10 +310,10 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
   // inverse and verdict into every block of the cluster.
   double ridge = 0.0;
   auto own_diag = [&](int kk) {
-    const bool ok = factor_diag<TS>(sm, Mt, g, kk, At, ut, ridge);
+    const bool ok = factor_diag<R, TS>(sm, Mt, g, kk, At, ut, ridge);
     const int par = kk & 1;
     for (int r2 = 0; r2 < C; ++r2) {
-      double *dst = &cl.map_shared_rank(&sm.v[0][0][0], r2)[(size_t)par * TS * (TS + 1)];
+      R *dst = &cl.map_shared_rank(&sm.v[0][0][0], r2)[(size_t)par * TS * (TS + 1)];
       for (int e = tid; e < TS * TS; e += kTThreads) dst[(e / TS) * (TS + 1) + e % TS] = sm.b[e / TS][e % TS];
       if (tid == 0) cl.map_shared_rank(&sm.verdict[0], r2)[par] = ok ? 0 : 1;
     }
@@ -299,16 +322,17 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
 
   int st = 2;
   bool failed = true;
-  for (int attempt = 0; attempt < 2 && failed; ++attempt) {
+  // the FP32 pass makes one attempt: a breakdown goes to the FP64 solve
+  for (int attempt = 0; attempt < (kF32 ? 1 : 2) && failed; ++attempt) {
     ridge = attempt == 0 ? 0.0 : lambda;
     // M <- [lower(A) + ridge on used diagonal entries; B^T]
     const int64_t total = (int64_t)(K + m) * K;
     for (int64_t q = (int64_t)rank * kTThreads + tid; q < total; q += (int64_t)C * kTThreads) {
       const int r = (int)(q / K), c = (int)(q % K);
       if (r < K) {
-        if (c <= r) Mt[q] = At[(size_t)r * K + c] + ((r == c && ut[r] > 0) ? ridge : 0.0);
+        if (c <= r) Mt[q] = (R)(At[(size_t)r * K + c] + ((r == c && ut[r] > 0) ? ridge : 0.0));
       } else {
-        Mt[q] = Bt[(size_t)c * m + (r - K)];
+        Mt[q] = (R)Bt[(size_t)c * m + (r - K)];
       }
     }
     cl.sync();
@@ -316,13 +340,13 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
     if (rank == 0) own_diag(0);
     cl.sync();
     failed = false;
-    for (int k = 0; k < R; ++k) {
+    for (int k = 0; k < R_; ++k) {
       if (sm.verdict[k & 1]) { failed = true; break; }   // uniform: every block holds the pushed verdict
-      const double (*vk)[TS + 1] = sm.v[k & 1];
+      const R (*vk)[TS + 1] = sm.v[k & 1];
       // panel: tile (i, k) <- tile (i, k) V_k^T for every tile row below k
-      run_step<TS>(sm, vk, RT - k - 1, rank, C, [&](int q) {
-        const Opnd p = tile_of<TS>(Mt, g, k + 1 + q, k);
-        return TileTask{p, p, p, false, true, false, false};
+      run_step<R, TS>(sm, vk, RT - k - 1, rank, C, [&](int q) {
+        const Opnd<R> p = tile_of<R, TS>(Mt, g, k + 1 + q, k);
+        return TileTask<R>{p, p, p, false, true, false, false};
       });
       cl.sync();
       // trailing: tile (i, j) -= panel_i panel_j^T, k < j <= i, j a column of A.
@@ -330,17 +354,17 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
       // tasks), so task 0 is the next diagonal tile; its owner takes it first,
       // factors it at once and pushes the inverse while the other blocks go on
       // with their trailing tiles.
-      const int ntr = (R - k - 1) * (R - k) / 2 + Rm * (R - k - 1);
+      const int ntr = (R_ - k - 1) * (R_ - k) / 2 + Rm * (R_ - k - 1);
       auto trail = [&](int q) {
         int i = k + 1, w = 1;
         while (q >= w) {
           q -= w;
           ++i;
-          w = (i < R ? i : R - 1) - k;
+          w = (i < R_ ? i : R_ - 1) - k;
         }
         const int j = k + 1 + q;
-        return TileTask{tile_of<TS>(Mt, g, i, k), tile_of<TS>(Mt, g, j, k), tile_of<TS>(Mt, g, i, j), false, false,
-                        true, i == j};
+        return TileTask<R>{tile_of<R, TS>(Mt, g, i, k), tile_of<R, TS>(Mt, g, j, k), tile_of<R, TS>(Mt, g, i, j),
+                           false, false, true, i == j};
       };
       if (ntr > 0) {
         const int owner = (k + 1) % C;
@@ -348,19 +372,19 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
           // every block has an SM to itself: the owner's latency-bound diagonal
           // factorisation would lengthen the step, so it takes no other tile
           if (rank == owner) {
-            run_step<TS>(sm, vk, 1, 0, C, trail);
+            run_step<R, TS>(sm, vk, 1, 0, C, trail);
             __syncthreads();   // the updated diagonal tile is in global memory
             own_diag(k + 1);
           } else {
-            run_step<TS>(sm, vk, ntr, 1 + (rank - owner - 1 + C) % C, C - 1, trail);
+            run_step<R, TS>(sm, vk, ntr, 1 + (rank - owner - 1 + C) % C, C - 1, trail);
           }
         } else if (rank == owner) {
-          run_step<TS>(sm, vk, 1, 0, C, trail);
+          run_step<R, TS>(sm, vk, 1, 0, C, trail);
           __syncthreads();   // the updated diagonal tile is in global memory
           own_diag(k + 1);
-          run_step<TS>(sm, vk, ntr, C, C, trail);
+          run_step<R, TS>(sm, vk, ntr, C, C, trail);
         } else {
-          run_step<TS>(sm, vk, ntr, (rank - owner + C) % C, C, trail);
+          run_step<R, TS>(sm, vk, ntr, (rank - owner + C) % C, C, trail);
         }
       }
       cl.sync();
@@ -371,24 +395,25 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
 
   if (!failed) {
     // backward sweep on the right-hand-side rows: X^T = W L^{-1}
-    for (int k = R - 1; k >= 0; --k) {
-      run_step<TS>(sm, sm.v[0], Rm, rank, C, [&](int q) {
-        const Opnd w = tile_of<TS>(Mt, g, R + q, k);
-        return TileTask{w, Opnd{Vt + (size_t)k * TS * TS, TS, TS, TS}, w, true, false, false, false};
+    for (int k = R_ - 1; k >= 0; --k) {
+      run_step<R, TS>(sm, sm.v[0], Rm, rank, C, [&](int q) {
+        const Opnd<R> w = tile_of<R, TS>(Mt, g, R_ + q, k);
+        return TileTask<R>{w, Opnd<R>{Vt + (size_t)k * TS * TS, TS, TS, TS}, w, true, false, false, false};
       });
       cl.sync();
       if (k > 0)
-        run_step<TS>(sm, sm.v[0], Rm * k, rank, C, [&](int q) {
+        run_step<R, TS>(sm, sm.v[0], Rm * k, rank, C, [&](int q) {
           const int rb = q / k, i = q % k;
-          return TileTask{tile_of<TS>(Mt, g, R + rb, k), tile_of<TS>(Mt, g, k, i), tile_of<TS>(Mt, g, R + rb, i),
-                          true, false, true, false};
+          return TileTask<R>{tile_of<R, TS>(Mt, g, R_ + rb, k), tile_of<R, TS>(Mt, g, k, i),
+                             tile_of<R, TS>(Mt, g, R_ + rb, i), true, false, true, false};
         });
       cl.sync();
     }
-    // renormalise the used atoms (atom j = column j of the right-hand-side rows)
-    for (int j = rank * kTThreads + tid; j < K; j += C * kTThreads) {
+    // renormalise the used atoms (atom j = column j of the right-hand-side
+    // rows); the FP32 pass leaves that to the check
+    for (int j = rank * kTThreads + tid; j < K && !kF32; j += C * kTThreads) {
       if (ut[j] == 0) continue;   // unused: keeps the previous atom
-      const double *xj = Mt + (size_t)K * K + j;
+      const R *xj = Mt + (size_t)K * K + j;
       double n2 = 0.0;
       for (int r = 0; r < m; ++r) {
         const double v = __ldcg(xj + (size_t)r * K);
@@ -402,8 +427,12 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
     }
   }
   if (rank == 0 && tid == 0) {
-    status[t] = st;
-    if (status_max) atomicMax(status_max, st);
+    if (kF32) {
+      status[t] = failed ? kModDeferred : 0;   // folded by the check or the FP64 solve
+    } else {
+      status[t] = st;
+      if (status_max) atomicMax(status_max, st);
+    }
   }
 }
 
@@ -469,7 +498,7 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
                                                                 int G, double *M, double *V, WideSync *sync, T *D,
                                                                 int32_t *status, int32_t *status_max,
                                                                 long long spin, int absent) {
-  __shared__ TiledSmem<TS> sm;
+  __shared__ TiledSmem<double, TS> sm;
   __shared__ double red[2][kTThreads / 32];
   const int rank = blockIdx.x % G;
   const int t = blockIdx.x / G;
@@ -506,7 +535,7 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
   // factor diagonal tile kk; its inverse and verdict go to global memory
   double ridge = 0.0;
   auto own_diag = [&](int kk) {
-    const bool okd = factor_diag<TS>(sm, Mt, g, kk, At, ut, ridge);
+    const bool okd = factor_diag<double, TS>(sm, Mt, g, kk, At, ut, ridge);
     for (int e = tid; e < TS * TS; e += kTThreads) Vt[(size_t)kk * TS * TS + e] = sm.b[e / TS][e % TS];
     if (tid == 0) ws->verdict[kk & 1] = okd ? 0 : 1;
   };
@@ -538,9 +567,9 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
       if (vload(&ws->verdict[k & 1])) { failed = true; break; }   // the same value in every block
       load_inv(k);
       const double (*vk)[TS + 1] = sm.v[0];
-      run_step<TS>(sm, vk, RT - k - 1, rank, G, [&](int q) {
-        const Opnd p = tile_of<TS>(Mt, g, k + 1 + q, k);
-        return TileTask{p, p, p, false, true, false, false};
+      run_step<double, TS>(sm, vk, RT - k - 1, rank, G, [&](int q) {
+        const Opnd<double> p = tile_of<double, TS>(Mt, g, k + 1 + q, k);
+        return TileTask<double>{p, p, p, false, true, false, false};
       });
       if (!(alive = wide_sync(ws, G, spin))) break;
       const int ntr = (R - k - 1) * (R - k) / 2 + Rm * (R - k - 1);
@@ -552,7 +581,7 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
           w = (i < R ? i : R - 1) - k;
         }
         const int j = k + 1 + q;
-        return TileTask{tile_of<TS>(Mt, g, i, k), tile_of<TS>(Mt, g, j, k), tile_of<TS>(Mt, g, i, j), false, false,
+        return TileTask<double>{tile_of<double, TS>(Mt, g, i, k), tile_of<double, TS>(Mt, g, j, k), tile_of<double, TS>(Mt, g, i, j), false, false,
                         true, i == j};
       };
       if (ntr > 0) {
@@ -560,12 +589,12 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
         // other blocks in the group, takes no other tile; they share the rest
         const int owner = (k + 1) % G;
         if (rank == owner) {
-          run_step<TS>(sm, vk, 1, 0, G, trail);
+          run_step<double, TS>(sm, vk, 1, 0, G, trail);
           __syncthreads();   // the updated diagonal tile is in global memory
           own_diag(k + 1);
-          if (G == 1) run_step<TS>(sm, vk, ntr, 1, 1, trail);
+          if (G == 1) run_step<double, TS>(sm, vk, ntr, 1, 1, trail);
         } else {
-          run_step<TS>(sm, vk, ntr, 1 + (rank - owner - 1 + G) % G, G - 1, trail);
+          run_step<double, TS>(sm, vk, ntr, 1 + (rank - owner - 1 + G) % G, G - 1, trail);
         }
       }
       if (!(alive = wide_sync(ws, G, spin))) break;
@@ -577,15 +606,15 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
   if (!failed && alive) {
     // backward sweep on the right-hand-side rows: X^T = W L^{-1}
     for (int k = R - 1; k >= 0 && alive; --k) {
-      run_step<TS>(sm, sm.v[0], Rm, rank, G, [&](int q) {
-        const Opnd w = tile_of<TS>(Mt, g, R + q, k);
-        return TileTask{w, Opnd{Vt + (size_t)k * TS * TS, TS, TS, TS}, w, true, false, false, false};
+      run_step<double, TS>(sm, sm.v[0], Rm, rank, G, [&](int q) {
+        const Opnd<double> w = tile_of<double, TS>(Mt, g, R + q, k);
+        return TileTask<double>{w, Opnd<double>{Vt + (size_t)k * TS * TS, TS, TS, TS}, w, true, false, false, false};
       });
       if (!(alive = wide_sync(ws, G, spin))) break;
       if (k > 0)
-        run_step<TS>(sm, sm.v[0], Rm * k, rank, G, [&](int q) {
+        run_step<double, TS>(sm, sm.v[0], Rm * k, rank, G, [&](int q) {
           const int rb = q / k, i = q % k;
-          return TileTask{tile_of<TS>(Mt, g, R + rb, k), tile_of<TS>(Mt, g, k, i), tile_of<TS>(Mt, g, R + rb, i),
+          return TileTask<double>{tile_of<double, TS>(Mt, g, R + rb, k), tile_of<double, TS>(Mt, g, k, i), tile_of<double, TS>(Mt, g, R + rb, i),
                           true, false, true, false};
         });
       if (!(alive = wide_sync(ws, G, spin))) break;
@@ -627,23 +656,24 @@ size_t mod_tiled_scratch_doubles(int L, int K, int m) { return (size_t)L * (tile
 
 // Dynamic shared memory that keeps at most `cap` blocks on an SM (0: no cap):
 // more than 1/(cap + 1) of the SM's 228 KB with the static part included.
-template <int TS>
+template <typename R, int TS>
 static size_t cap_smem(int cap) {
   if (cap <= 0) return 0;
-  const size_t stat = sizeof(TiledSmem<TS>) + 2 * sizeof(double) * (kTThreads / 32) + 64;
+  const size_t stat = sizeof(TiledSmem<R, TS>) + 2 * sizeof(double) * (kTThreads / 32) + 64;
   const size_t want = (size_t)228 * 1024 / (size_t)(cap + 1) + 1024;
   return want > stat ? want - stat : 0;
 }
 
-template <typename T, int TS>
-static cudaError_t launch_tiled_ts(const ModArgs &a, int C, int cap, int num_sms, cudaStream_t st) {
-  auto kern = mod_tiled_kernel<T, TS>;
+template <typename T, int TS, typename R>
+static cudaError_t launch_tiled_ts(const ModArgs &a, int C, int cap, int num_sms, int only_deferred,
+                                   cudaStream_t st) {
+  auto kern = mod_tiled_kernel<T, TS, R>;
   cudaError_t e;
   if (C > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
-  const size_t dyn = cap_smem<TS>(cap);
+  const size_t dyn = cap_smem<R, TS>(cap);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -658,21 +688,22 @@ static cudaError_t launch_tiled_ts(const ModArgs &a, int C, int cap, int num_sms
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  double *M = a.Lf;
-  double *V = a.Lf + (size_t)a.L * (a.K + a.m) * a.K;
+  // the FP32 pass lays its scratch out in floats over the same bytes
+  R *M = reinterpret_cast<R *>(a.Lf);
+  R *V = M + (size_t)a.L * (a.K + a.m) * a.K;
   const int light = (int64_t)a.L * C <= num_sms ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, (const double *)a.A, (const double *)a.B, (const int32_t *)a.usage, a.K,
-                            a.m, C, light, M, V, static_cast<T *>(a.D), a.status, a.status_max);
+                            a.m, C, light, only_deferred, M, V, static_cast<T *>(a.D), a.status, a.status_max);
 }
 
-template <typename T>
-int mod_tiled_max_clusters(int ts, int C, int cap) {
-  auto kern = ts == 16 ? mod_tiled_kernel<T, 16> : mod_tiled_kernel<T, 32>;
+template <typename T, typename R>
+static int max_clusters_r(int ts, int C, int cap) {
+  auto kern = ts == 16 ? mod_tiled_kernel<T, 16, R> : mod_tiled_kernel<T, 32, R>;
   if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  const size_t dyn = ts == 16 ? cap_smem<16>(cap) : cap_smem<32>(cap);
+  const size_t dyn = ts == 16 ? cap_smem<R, 16>(cap) : cap_smem<R, 32>(cap);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -697,10 +728,26 @@ int mod_tiled_max_clusters(int ts, int C, int cap) {
 }
 
 template <typename T>
-cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, int num_sms, cudaStream_t st) {
+int mod_tiled_max_clusters(int ts, int C, int cap, bool f32) {
+  return f32 ? max_clusters_r<T, float>(ts, C, cap) : max_clusters_r<T, double>(ts, C, cap);
+}
+
+template <typename T>
+cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, int num_sms, cudaStream_t st,
+                             bool only_deferred) {
   if (a.L <= 0) return cudaSuccess;
   if (C < 1 || C > 16 || (ts != 16 && ts != 32) || cap < 0 || cap > 3) return cudaErrorInvalidValue;
-  return ts == 16 ? launch_tiled_ts<T, 16>(a, C, cap, num_sms, st) : launch_tiled_ts<T, 32>(a, C, cap, num_sms, st);
+  const int od = only_deferred ? 1 : 0;
+  return ts == 16 ? launch_tiled_ts<T, 16, double>(a, C, cap, num_sms, od, st)
+                  : launch_tiled_ts<T, 32, double>(a, C, cap, num_sms, od, st);
+}
+
+template <typename T>
+cudaError_t launch_mod_tiled32(const ModArgs &a, int ts, int C, int cap, int num_sms, cudaStream_t st) {
+  if (a.L <= 0) return cudaSuccess;
+  if (C < 1 || C > 16 || (ts != 16 && ts != 32) || cap < 0 || cap > 3) return cudaErrorInvalidValue;
+  return ts == 16 ? launch_tiled_ts<T, 16, float>(a, C, cap, num_sms, 0, st)
+                  : launch_tiled_ts<T, 32, float>(a, C, cap, num_sms, 0, st);
 }
 
 template <typename T, int TS>
@@ -748,9 +795,10 @@ template cudaError_t launch_mod_wide<float>(const ModArgs &, int, int, long long
 template cudaError_t launch_mod_wide<double>(const ModArgs &, int, int, long long, int, cudaStream_t);
 template int mod_wide_max_blocks<float>(int, int);
 template int mod_wide_max_blocks<double>(int, int);
-template cudaError_t launch_mod_tiled<float>(const ModArgs &, int, int, int, int, cudaStream_t);
-template cudaError_t launch_mod_tiled<double>(const ModArgs &, int, int, int, int, cudaStream_t);
-template int mod_tiled_max_clusters<float>(int, int, int);
-template int mod_tiled_max_clusters<double>(int, int, int);
+template cudaError_t launch_mod_tiled<float>(const ModArgs &, int, int, int, int, cudaStream_t, bool);
+template cudaError_t launch_mod_tiled<double>(const ModArgs &, int, int, int, int, cudaStream_t, bool);
+template cudaError_t launch_mod_tiled32<float>(const ModArgs &, int, int, int, int, cudaStream_t);
+template int mod_tiled_max_clusters<float>(int, int, int, bool);
+template int mod_tiled_max_clusters<double>(int, int, int, bool);
 
 }  // namespace sdl

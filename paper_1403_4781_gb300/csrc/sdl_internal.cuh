@@ -72,7 +72,8 @@ struct sdl_ctx {
   int opt_autotune = 1;          // time candidate launch shapes on first use
   struct TunedSolve {
     int ts, C, cap;
-    int wide;   // 1: the wide form with C blocks per subset
+    int wide;    // 1: the wide form with C blocks per subset
+    int mixed;   // 1: the checked FP32 pass (tile ts, cluster C), then the FP64 solve of what it left
   };
   std::map<std::string, TunedSolve> tuned;   // shape key -> chosen tile, cluster size, blocks-per-SM cap
   int opt_graph = 0;             // replay training loops as captured CUDA graphs
@@ -81,6 +82,8 @@ struct sdl_ctx {
   int opt_bf16_form = 0;         // BF16 OMP: 0 automatic, 1 Batch-OMP selection, 2 residual form
   long long opt_wait_limit = 1ll << 24;   // polls before a barrier wait of the wide solve gives up
   int opt_wait_test = 0;         // 1: one block of each wide-solve group leaves at once
+  int opt_mod_mixed = 1;         // FP32 data: 1 the checked FP32 pass of the tiled solve may run, 0 FP64 only
+  int opt_mod_check_ppb = 5000;  // tolerance of that check, parts per 10^9 of each atom's norm
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
@@ -229,10 +232,26 @@ int mod_tile_signals();
 // cap: at most that many blocks per SM (1..3, through padded dynamic shared
 // memory), 0 = as many as fit.  num_sms decides whether every block has an SM
 // to itself (then the block factoring a diagonal tile takes no trailing tile).
+// only_deferred: solve only the subsets whose status is 4 (left by the FP32
+// pass below), the others untouched.
 template <typename T>
-cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, int num_sms, cudaStream_t st);
+cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, int num_sms, cudaStream_t st,
+                             bool only_deferred = false);
+// The FP32 pass of the checked mixed-precision solve (FP32 data): the same
+// tiled factorisation and solve in FP32 over the same scratch (laid out in
+// floats), the unnormalised solution left there; status 0, or 4 where a
+// squared pivot fell to 1e-3 of its diagonal (then the FP64 solve takes it).
 template <typename T>
-int mod_tiled_max_clusters(int ts, int C, int cap);
+cudaError_t launch_mod_tiled32(const ModArgs &a, int ts, int C, int cap, int num_sms, cudaStream_t st);
+// The check of that pass: per subset, the error of every used atom estimated
+// from 8 random-sign probes of the FP64 residual D A - B mapped through the
+// FP32 factor; accepted subsets (every estimate at most tau of the atom's
+// norm) are renormalised and written with status 0, the others get status 4.
+// ts: the tile edge the FP32 pass ran with.  K <= 1024, m <= 256.
+template <typename T>
+cudaError_t launch_mod_check(const ModArgs &a, int ts, float tau, cudaStream_t st);
+template <typename T>
+int mod_tiled_max_clusters(int ts, int C, int cap, bool f32 = false);
 size_t mod_tiled_scratch_doubles(int L, int K, int m);
 // The wide form of the tiled solve for few subsets: the tile tasks of each
 // subset spread over G blocks of a cooperative launch that meet at barriers in
