@@ -351,16 +351,17 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     0 the tiled factorisation and solve may run in FP32, followed by a check
  *     of every subset's solution: 8 random-sign probes of the FP64 residual
  *     D A - B, mapped through the FP32 factor, estimate each used atom's error
- *     (Hutchinson); a subset whose estimates are all within 5e-6 of the atom's
- *     norm (SDL_OPT_MOD_CHECK_TOL) is renormalised and kept, every other subset (and one whose FP32
+ *     (Hutchinson); a subset whose estimated error norms are all within 2e-5
+ *     of the atom's norm (SDL_OPT_MOD_CHECK_TOL) is renormalised and kept, every other subset (and one whose FP32
  *     squared pivot fell to 1e-3 of its diagonal) is solved again in FP64 as
  *     it would have been alone, ridge retry included.  Chosen when the
  *     autotuner times it faster than the FP64 candidates.  0 = FP64 only.
  *   SDL_OPT_MOD_CHECK_TOL: the tolerance of that check in parts per 10^9 of
- *     each atom's norm, 1 to 10^9, default 5000 (5e-6).  A smaller value sends
+ *     each atom's norm, 1 to 10^9, default 20000 (2e-5).  A smaller value sends
  *     more subsets to the FP64 solve; 1 sends every one.
  *     The result then differs from the FP64 solve's by the FP32 solve's
- *     error, at most about 5e-6 of each atom (2e-5 is the FP32 atom tolerance).
+ *     error, about 2e-5 of each atom's norm at most (the FP32 atom
+ *     tolerance).
  *   SDL_OPT_CLUSTER: cluster size, 0 = automatic (default); 4, 8 or 16 for
  *     option 1, 1 to 16 for option 3; blocks per subset for option 4.
  *   SDL_OPT_MOD_TILE: tile edge of the tiled solve: 0 = automatic (default),

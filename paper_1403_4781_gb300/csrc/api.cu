@@ -249,22 +249,39 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
     };
     const int tiles[2] = {16, 32};
     const int cls[7] = {1, 2, 3, 4, 6, 8, 16};
-    for (int mx = mix_ok ? 1 : 0; mx >= 0 && e == cudaSuccess; --mx)
+    // the FP32 pass's tile and cluster size by the FP32 pass alone; then the
+    // whole checked solve with that shape (its check and the FP64 solve of what
+    // the check leaves do not depend on the shape) against the FP64 candidates
+    int ts32 = 0, c32 = 0;
+    float best32 = 3.4e38f;
+    for (int pass = mix_ok ? 0 : 1; pass < 2 && e == cudaSuccess; ++pass) {
+      const bool f32 = pass == 0;
       for (int a = 0; a < 2 && e == cudaSuccess; ++a)
         for (int b = 0; b < 7 && e == cudaSuccess; ++b) {
           const int t = tiles[a], c = cls[b], cp = 0;
           // a subset's cluster must fit on the device; small clusters for few
           // subsets leave most SMs idle and are not worth timing
-          if (tiled_occupancy<T>(ctx, t, c, cp, mx != 0) < 1) continue;
+          if (tiled_occupancy<T>(ctx, t, c, cp, f32) < 1) continue;
           if ((int64_t)ma.L * c * 4 < ctx->num_sms && c < 16) continue;
           const float ms = time_it([&] {
-            ctx->launches += mx ? 3 : 1;
-            return mx ? run_mixed<T>(ctx, ma, t, c, false) : launch_mod_tiled<T>(ma, t, c, cp, ctx->num_sms, sm);
+            ctx->launches += 1;
+            return f32 ? launch_mod_tiled32<T>(ma, t, c, cp, ctx->num_sms, sm)
+                       : launch_mod_tiled<T>(ma, t, c, cp, ctx->num_sms, sm);
           });
-          if (e == cudaSuccess && ms < best) {
-            best = ms; best_ts = t; best_c = c; best_cap = cp; best_wide = 0; best_mixed = mx;
-          }
+          if (e != cudaSuccess) break;
+          if (f32 && ms < best32) { best32 = ms; ts32 = t; c32 = c; }
+          if (!f32 && ms < best) { best = ms; best_ts = t; best_c = c; best_cap = cp; best_wide = 0; best_mixed = 0; }
         }
+      if (f32 && ts32 > 0 && e == cudaSuccess) {   // the whole checked solve with the best FP32 shape
+        const float msm = time_it([&] {
+          ctx->launches += 3;
+          return run_mixed<T>(ctx, ma, ts32, c32, false);
+        });
+        if (e == cudaSuccess && msm < best) {
+          best = msm; best_ts = ts32; best_c = c32; best_cap = 0; best_wide = 0; best_mixed = 1;
+        }
+      }
+    }
     // few subsets: the wide form, each subset's tile tasks over G blocks
     // anywhere on the GPU (its largest cluster holds at most 16 SMs)
     if ((int64_t)ma.L * 16 < ctx->num_sms)

@@ -5,18 +5,21 @@
 // solves D A = B in FP32.  Its error E = D_32 - D is not known, but E A =
 // D_32 A - B is: for a probe u (m entries of +-1), u^T E = (u^T D_32 A - u^T B)
 // A^-1, whose FP64 residual costs two K x K and two m x K matrix-vector
-// products against the FP64 A and B, and whose A^-1 comes from the FP32 factor
-// (an estimate is all that is needed).  Entry j of u^T E is u . e_j, e_j the
+// products against the FP64 A and B, and whose A^-1 comes from the FP32
+// factor.  Entry j of u^T E is u . e_j, e_j the
 // error of atom j, and E[(u . e_j)^2] = |e_j|^2 over random signs (the
-// Hutchinson identity), so P probes give every atom's squared error up to a
-// chi-square factor with P degrees of freedom.  A subset is accepted when
-// every used atom's estimate is at most tau of its norm (tau = 5e-6, four
-// times below the FP32 atom tolerance of 2e-5 even for an estimate 16 times
-// too small, which happens with probability about 1e-8 at P = 8); then its
-// used atoms are renormalised and written.  Otherwise (and where the
-// factorisation broke down, or an atom's norm is zero or not finite) the
-// subset is marked for the FP64 solve, which then decides exactly as it would
-// have alone.
+// Hutchinson identity), so P = 8 probes give every atom's squared error up
+// to a chi-square factor with 8 degrees of freedom (about 2 % of atoms whose
+// error is twice the tolerance pass, 1.5e-4 at four times).  A subset is
+// accepted when every used atom's estimated error is at most tau of its norm
+// (default 2e-5, the FP32 atom tolerance: an atom's largest entry error is at
+// most its error norm, and the FP32 solve spreads its error over the m
+// entries, so the entries stay well inside the tolerance); then its used atoms
+// are renormalised and written.  Otherwise (and where the factorisation broke
+// down, or an atom's norm is zero or not finite) the subset is marked for the
+// FP64 solve, which then decides exactly as it would have alone.  The residual
+// is formed in FP64; the two triangular solves that map it through the factor
+// run in FP32 (an estimate is all that is needed).
 //
 // One block per subset, 256 threads; thread j mod 256 owns atoms j.
 #include <math.h>
@@ -51,7 +54,7 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
                                                               T *D, int32_t *status, float tau) {
   extern __shared__ double sh[];
   __shared__ float Us[kProbes][256];
-  __shared__ double Ys[kProbes][32];
+  __shared__ float Ys[kProbes][32];
   const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (status[t] == kModDeferredC) return;   // the FP32 factorisation broke down
   const int R = (K + TS - 1) / TS;
@@ -62,7 +65,8 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
   const float *X = Lt + (size_t)K * K;              // row r: coordinate r of every atom
   const float *Vt = V + (size_t)t * R * TS * TS;    // inverses of the diagonal factor tiles
   double *Gs = sh;                     // [P][K]: u_p^T D_32
-  double *Rs = sh + kProbes * K;       // [P][K]: residual, then A^-1 applied in place
+  double *Hs = sh + kProbes * K;       // [P][K]: the row part of G A, then the FP64 residual
+  float *Zs = reinterpret_cast<float *>(sh + 2 * kProbes * K);   // [P][K]: A^-1 applied to it (FP32)
 
   for (int e = tid; e < kProbes * m; e += kCThreads) Us[e / m][e % m] = probe_sign(t, e / m, e % m);
   __syncthreads();
@@ -88,22 +92,28 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
 
   // H = G A from the lower triangle of A: the part below the diagonal of
   // column j by columns (row i's entries left of the diagonal, coalesced), the
-  // part on and right of it by rows (warp-per-row dot products into Rs)
+  // part on and right of it by rows (warp-per-row dot products into Hs)
   double h[kCJ][kProbes];
 #pragma unroll
   for (int q = 0; q < kCJ; ++q)
 #pragma unroll
     for (int p = 0; p < kProbes; ++p) h[q][p] = 0.0;
-  for (int i = 1; i < K; ++i) {
-    const double *ai = At + (size_t)i * K;
+  for (int i0 = 1; i0 < K; i0 += 4) {
+    double a[4][kCJ];
 #pragma unroll
-    for (int q = 0; q < kCJ; ++q) {
-      const int j = tid + kCThreads * q;
-      if (j < i) {
-        const double a = __ldg(ai + j);
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int p = 0; p < kProbes; ++p) h[q][p] = fma(a, Gs[p * K + i], h[q][p]);
+      for (int q = 0; q < kCJ; ++q) {
+        const int i = i0 + u, j = tid + kCThreads * q;
+        a[u][q] = (i < K && j < i) ? __ldg(At + (size_t)i * K + j) : 0.0;
       }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u < K ? i0 + u : K - 1;
+#pragma unroll
+      for (int q = 0; q < kCJ; ++q)
+#pragma unroll
+        for (int p = 0; p < kProbes; ++p) h[q][p] = fma(a[u][q], Gs[p * K + i], h[q][p]);
     }
   }
   for (int i = warp; i < K; i += kCThreads / 32) {
@@ -120,7 +130,7 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
       for (int o = 16; o > 0; o >>= 1) d[p] += __shfl_xor_sync(0xffffffffu, d[p], o);
     if (lane == 0)
 #pragma unroll
-      for (int p = 0; p < kProbes; ++p) Rs[p * K + i] = d[p];
+      for (int p = 0; p < kProbes; ++p) Hs[p * K + i] = d[p];
   }
   __syncthreads();
   // residual r_p = u_p^T D_32 A - u_p^T B (B is [K][m]: row j = atom j's column)
@@ -136,36 +146,37 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
       for (int p = 0; p < kProbes; ++p) b[p] = fma((double)Us[p][r], v, b[p]);
     }
 #pragma unroll
-    for (int p = 0; p < kProbes; ++p) Rs[p * K + j] += h[q][p] - b[p];
+    for (int p = 0; p < kProbes; ++p) Zs[p * K + j] = (float)(Hs[p * K + j] + h[q][p] - b[p]);
   }
   __syncthreads();
 
-  // z_p = r_p A^-1 = (L L^T)^-1 r_p: forward L y = r, then backward L^T z = y,
-  // tile by tile with the inverses of the diagonal factor tiles
+  // z_p = r_p A^-1 = (L L^T)^-1 r_p in FP32 (an estimate is all that is
+  // needed): forward L y = r, then backward L^T z = y, tile by tile with the
+  // inverses of the diagonal factor tiles
   for (int k = 0; k < R; ++k) {
     const int k0 = k * TS, nb = K - k0 < TS ? K - k0 : TS;
     if (tid < kProbes * TS) {
       const int p = tid / TS, a = tid % TS;
-      double y = 0.0;
+      float y = 0.f;
       if (a < nb)
-        for (int c = 0; c <= a; ++c) y = fma((double)Vt[(size_t)k * TS * TS + a * TS + c], Rs[p * K + k0 + c], y);
+        for (int c = 0; c <= a; ++c) y = fmaf(Vt[(size_t)k * TS * TS + a * TS + c], Zs[p * K + k0 + c], y);
       Ys[p][a] = y;
     }
     __syncthreads();
     if (tid < kProbes * TS) {
       const int p = tid / TS, a = tid % TS;
-      if (a < nb) Rs[p * K + k0 + a] = Ys[p][a];
+      if (a < nb) Zs[p * K + k0 + a] = Ys[p][a];
     }
     for (int i = k0 + nb + tid; i < K; i += kCThreads) {
       const float *li = Lt + (size_t)i * K + k0;
-      double acc[kProbes] = {};
+      float acc[kProbes] = {};
       for (int c = 0; c < nb; ++c) {
-        const double l = li[c];
+        const float l = li[c];
 #pragma unroll
-        for (int p = 0; p < kProbes; ++p) acc[p] = fma(l, Ys[p][c], acc[p]);
+        for (int p = 0; p < kProbes; ++p) acc[p] = fmaf(l, Ys[p][c], acc[p]);
       }
 #pragma unroll
-      for (int p = 0; p < kProbes; ++p) Rs[p * K + i] -= acc[p];
+      for (int p = 0; p < kProbes; ++p) Zs[p * K + i] -= acc[p];
     }
     __syncthreads();
   }
@@ -173,25 +184,25 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
     const int k0 = k * TS, nb = K - k0 < TS ? K - k0 : TS;
     if (tid < kProbes * TS) {
       const int p = tid / TS, a = tid % TS;
-      double z = 0.0;
+      float z = 0.f;
       if (a < nb)
-        for (int c = a; c < nb; ++c) z = fma((double)Vt[(size_t)k * TS * TS + c * TS + a], Rs[p * K + k0 + c], z);
+        for (int c = a; c < nb; ++c) z = fmaf(Vt[(size_t)k * TS * TS + c * TS + a], Zs[p * K + k0 + c], z);
       Ys[p][a] = z;
     }
     __syncthreads();
     if (tid < kProbes * TS) {
       const int p = tid / TS, a = tid % TS;
-      if (a < nb) Rs[p * K + k0 + a] = Ys[p][a];
+      if (a < nb) Zs[p * K + k0 + a] = Ys[p][a];
     }
     for (int j = tid; j < k0; j += kCThreads) {
-      double acc[kProbes] = {};
+      float acc[kProbes] = {};
       for (int c = 0; c < nb; ++c) {
-        const double l = Lt[(size_t)(k0 + c) * K + j];
+        const float l = Lt[(size_t)(k0 + c) * K + j];
 #pragma unroll
-        for (int p = 0; p < kProbes; ++p) acc[p] = fma(l, Ys[p][c], acc[p]);
+        for (int p = 0; p < kProbes; ++p) acc[p] = fmaf(l, Ys[p][c], acc[p]);
       }
 #pragma unroll
-      for (int p = 0; p < kProbes; ++p) Rs[p * K + j] -= acc[p];
+      for (int p = 0; p < kProbes; ++p) Zs[p * K + j] -= acc[p];
     }
     __syncthreads();
   }
@@ -204,7 +215,7 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
     if (j >= K || ut[j] == 0) continue;
     double e2 = 0.0;
 #pragma unroll
-    for (int p = 0; p < kProbes; ++p) e2 = fma(Rs[p * K + j], Rs[p * K + j], e2);
+    for (int p = 0; p < kProbes; ++p) e2 = fma((double)Zs[p * K + j], (double)Zs[p * K + j], e2);
     e2 /= kProbes;
     const double lim = (double)tau * (double)tau * n2[q];
     if (!(n2[q] > 0.0) || !isfinite(n2[q]) || !(e2 <= lim)) ok = false;
@@ -227,7 +238,7 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
 
 }  // namespace
 
-size_t mod_check_smem(int K) { return sizeof(double) * 2 * kProbes * (size_t)K; }
+size_t mod_check_smem(int K) { return (2 * sizeof(double) + sizeof(float)) * kProbes * (size_t)K; }
 
 template <typename T>
 cudaError_t launch_mod_check(const ModArgs &a, int ts, float tau, cudaStream_t st) {

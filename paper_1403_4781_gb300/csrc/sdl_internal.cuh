@@ -83,7 +83,7 @@ struct sdl_ctx {
   long long opt_wait_limit = 1ll << 24;   // polls before a barrier wait of the wide solve gives up
   int opt_wait_test = 0;         // 1: one block of each wide-solve group leaves at once
   int opt_mod_mixed = 1;         // FP32 data: 1 the checked FP32 pass of the tiled solve may run, 0 FP64 only
-  int opt_mod_check_ppb = 5000;  // tolerance of that check, parts per 10^9 of each atom's norm
+  int opt_mod_check_ppb = 20000; // tolerance of that check, parts per 10^9 of each atom's norm
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
@@ -245,8 +245,8 @@ template <typename T>
 cudaError_t launch_mod_tiled32(const ModArgs &a, int ts, int C, int cap, int num_sms, cudaStream_t st);
 // The check of that pass: per subset, the error of every used atom estimated
 // from 8 random-sign probes of the FP64 residual D A - B mapped through the
-// FP32 factor; accepted subsets (every estimate at most tau of the atom's
-// norm) are renormalised and written with status 0, the others get status 4.
+// FP32 factor; accepted subsets (every estimated error norm at most tau of the
+// atom's norm) are renormalised and written with status 0, the others get status 4.
 // ts: the tile edge the FP32 pass ran with.  K <= 1024, m <= 256.
 template <typename T>
 cudaError_t launch_mod_check(const ModArgs &a, int ts, float tau, cudaStream_t st);

@@ -4,7 +4,7 @@ then unit columns, Sec. 3.1) and against the FP64 solve.
 
 The FP32 pass factors and solves in FP32; a check estimates every used atom's
 error from random-sign probes of the FP64 residual and hands any subset whose
-estimate exceeds 5e-6 of the atom's norm (or whose FP32 squared pivot fell to
+estimated error norm exceeds 2e-5 of the atom's norm (or whose FP32 squared pivot fell to
 1e-3 of its diagonal) to the FP64 solve.  Tolerances: every atom within 2e-5
 absolute of the oracle's (the FP32 atom tolerance); unused atoms bit-exact;
 a subset the check hands on matches the FP64 solve's result to 1e-6 (the same
@@ -35,7 +35,7 @@ def ctx():
     c.set_option(sdl.OPT_MOD_TILE, 0)
     c.set_option(sdl.OPT_AUTOTUNE, 1)
     c.set_option(sdl.OPT_MOD_MIXED, 1)
-    c.set_option(sdl.OPT_MOD_CHECK_TOL, 5000)
+    c.set_option(sdl.OPT_MOD_CHECK_TOL, 20000)
     c.profile(False)
 
 
@@ -139,7 +139,7 @@ def test_check_at_tiny_tolerance_sends_every_subset_to_fp64(ctx, K, m):
     fp64, _ = _run(ctx, 0, 32, 2, offsets, Y, idx, val, D0)
     ctx.set_option(sdl.OPT_MOD_CHECK_TOL, 1)
     strict, prof = _run(ctx, 1, 32, 2, offsets, Y, idx, val, D0)
-    ctx.set_option(sdl.OPT_MOD_CHECK_TOL, 5000)
+    ctx.set_option(sdl.OPT_MOD_CHECK_TOL, 20000)
     assert "mod_check" in prof
     np.testing.assert_allclose(strict, fp64, rtol=0, atol=1e-6)
     kept, _ = _run(ctx, 1, 32, 2, offsets, Y, idx, val, D0)
