@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kCThreads = 256;
 constexpr int kProbes = 8;
-constexpr int kCJ = 4;               // atoms per thread (K <= 1024)
+constexpr int kCJMax = 4;            // atoms per thread at most (K <= 1024)
 constexpr int kModDeferredC = 4;     // the status the FP32 pass and this check leave for the FP64 solve
 
 // +-1 of probe p at signal entry r of subset t: a 32-bit integer mix of the
@@ -46,7 +46,58 @@ __device__ __forceinline__ float probe_sign(int t, int p, int r) {
   return (x & 1u) ? -1.f : 1.f;
 }
 
-template <typename T>
+// Double-float arithmetic on the FP32 pipes (this part's FP64 pipe, conversions
+// included, runs at 1/64 of its FP32 rate): a value is a compensated sum s + c,
+// each addition an error-free TwoSum (Knuth) whose rounding error goes into c,
+// each product of two hi + lo pairs exact in its hi * hi part (the FMA
+// residual, Dekker/Kahan) with the cross terms added to c.  Explicit _rn
+// operations keep the compiler from contracting the sums into FMAs.
+struct DF {
+  float s, c;
+};
+__device__ __forceinline__ void df_add(DF &a, float t) {
+  const float s = __fadd_rn(a.s, t);
+  const float bb = __fsub_rn(s, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(t, bb));
+  a.s = s;
+  a.c = __fadd_rn(a.c, err);
+}
+__device__ __forceinline__ void df_add_prod(DF &a, float xh, float xl, float yh, float yl) {
+  const float p = __fmul_rn(xh, yh);
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  df_add(a, p);
+  a.c = __fadd_rn(a.c, e);
+}
+__device__ __forceinline__ DF df_merge(DF a, DF b) {
+  df_add(a, b.s);
+  a.c = __fadd_rn(a.c, b.c);
+  return a;
+}
+// A double as hi + lo floats by integer operations on its bits: hi its sign,
+// exponent and top 23 fraction bits, lo the other 29 fraction bits (rounded to
+// 24).  Values outside the float range count as zero (|a| < 2^-126; the
+// normal equations' entries are far above it).
+__device__ __forceinline__ void split_d(double a, float &hi, float &lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int fe = e - 1023 + 127;
+  if (fe <= 0 || fe >= 255) {
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));
+  const int le = e - 1075 + 127;   // 2^(e - 1075), the weight of the lowest fraction bit
+  const float l = le > 0 ? __fmul_rn(__uint2float_rn((unsigned)(b & 0x1FFFFFFFull)), __uint_as_float((unsigned)le << 23))
+                         : 0.f;
+  lo = sign ? -l : l;
+}
+
+// CJ: atoms per thread (K <= 256 CJ).
+template <typename T, int CJ>
 __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__restrict__ A,
                                                               const double *__restrict__ B,
                                                               const int32_t *__restrict__ usage, int K, int m, int TS,
@@ -64,89 +115,121 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
   const float *Lt = M + (size_t)t * (K + m) * K;   // lower triangle: the FP32 factor
   const float *X = Lt + (size_t)K * K;              // row r: coordinate r of every atom
   const float *Vt = V + (size_t)t * R * TS * TS;    // inverses of the diagonal factor tiles
-  double *Gs = sh;                     // [P][K]: u_p^T D_32
-  double *Hs = sh + kProbes * K;       // [P][K]: the row part of G A, then the FP64 residual
-  float *Zs = reinterpret_cast<float *>(sh + 2 * kProbes * K);   // [P][K]: A^-1 applied to it (FP32)
+  float *Gh = reinterpret_cast<float *>(sh);   // [P][K]: u_p^T D_32 as hi + lo
+  float *Gl = Gh + kProbes * K;
+  float *Hs = Gl + kProbes * K;                // [P][K]: the row part of G A, compensated sum
+  float *Hc = Hs + kProbes * K;
+  float *Zs = Hc + kProbes * K;                // [P][K]: the residual, then A^-1 applied to it
 
   for (int e = tid; e < kProbes * m; e += kCThreads) Us[e / m][e % m] = probe_sign(t, e / m, e % m);
   __syncthreads();
 
-  // G = U^T D_32 and the atoms' squared norms
-  double n2[kCJ];
+  // G = U^T D_32 (hi + lo pairs) and the atoms' squared norms
+  float n2[CJ];
 #pragma unroll
-  for (int q = 0; q < kCJ; ++q) {
+  for (int q = 0; q < CJ; ++q) {
     const int j = tid + kCThreads * q;
-    n2[q] = 0.0;
+    n2[q] = 0.f;
     if (j >= K) continue;
-    double g[kProbes] = {};
-    for (int r = 0; r < m; ++r) {
-      const double x = X[(size_t)r * K + j];
-      n2[q] = fma(x, x, n2[q]);
+    DF g[kProbes];
 #pragma unroll
-      for (int p = 0; p < kProbes; ++p) g[p] = fma((double)Us[p][r], x, g[p]);
+    for (int p = 0; p < kProbes; ++p) g[p] = DF{0.f, 0.f};
+    for (int r = 0; r < m; ++r) {
+      const float x = X[(size_t)r * K + j];
+      n2[q] = fmaf(x, x, n2[q]);
+#pragma unroll
+      for (int p = 0; p < kProbes; ++p) df_add(g[p], Us[p][r] < 0.f ? -x : x);
     }
 #pragma unroll
-    for (int p = 0; p < kProbes; ++p) Gs[p * K + j] = g[p];
+    for (int p = 0; p < kProbes; ++p) {
+      const float hi = __fadd_rn(g[p].s, g[p].c);
+      Gh[p * K + j] = hi;
+      Gl[p * K + j] = __fsub_rn(g[p].c, __fsub_rn(hi, g[p].s));
+    }
   }
   __syncthreads();
 
   // H = G A from the lower triangle of A: the part below the diagonal of
   // column j by columns (row i's entries left of the diagonal, coalesced), the
-  // part on and right of it by rows (warp-per-row dot products into Hs)
-  double h[kCJ][kProbes];
+  // part on and right of it by rows (warp-per-row sums into Hs, Hc)
+  DF h[CJ][kProbes];
 #pragma unroll
-  for (int q = 0; q < kCJ; ++q)
+  for (int q = 0; q < CJ; ++q)
 #pragma unroll
-    for (int p = 0; p < kProbes; ++p) h[q][p] = 0.0;
-  for (int i0 = 1; i0 < K; i0 += 4) {
-    double a[4][kCJ];
+    for (int p = 0; p < kProbes; ++p) h[q][p] = DF{0.f, 0.f};
+  for (int i0 = 1; i0 < K; i0 += 8) {
+    double a[8][CJ];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 8; ++u)
 #pragma unroll
-      for (int q = 0; q < kCJ; ++q) {
+      for (int q = 0; q < CJ; ++q) {
         const int i = i0 + u, j = tid + kCThreads * q;
         a[u][q] = (i < K && j < i) ? __ldg(At + (size_t)i * K + j) : 0.0;
       }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int i = i0 + u < K ? i0 + u : K - 1;
 #pragma unroll
-      for (int q = 0; q < kCJ; ++q)
+      for (int q = 0; q < CJ; ++q) {
+        float ah, al;
+        split_d(a[u][q], ah, al);
 #pragma unroll
-        for (int p = 0; p < kProbes; ++p) h[q][p] = fma(a[u][q], Gs[p * K + i], h[q][p]);
+        for (int p = 0; p < kProbes; ++p) df_add_prod(h[q][p], ah, al, Gh[p * K + i], Gl[p * K + i]);
+      }
     }
   }
   for (int i = warp; i < K; i += kCThreads / 32) {
     const double *ai = At + (size_t)i * K;
-    double d[kProbes] = {};
-    for (int c = lane; c <= i; c += 32) {
-      const double a = __ldg(ai + c);
+    DF d[kProbes];
 #pragma unroll
-      for (int p = 0; p < kProbes; ++p) d[p] = fma(a, Gs[p * K + c], d[p]);
+    for (int p = 0; p < kProbes; ++p) d[p] = DF{0.f, 0.f};
+    for (int c = lane; c <= i; c += 32) {
+      float ah, al;
+      split_d(__ldg(ai + c), ah, al);
+#pragma unroll
+      for (int p = 0; p < kProbes; ++p) df_add_prod(d[p], ah, al, Gh[p * K + c], Gl[p * K + c]);
     }
 #pragma unroll
     for (int p = 0; p < kProbes; ++p)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) d[p] += __shfl_xor_sync(0xffffffffu, d[p], o);
+      for (int o = 16; o > 0; o >>= 1) {
+        const DF other{__shfl_xor_sync(0xffffffffu, d[p].s, o), __shfl_xor_sync(0xffffffffu, d[p].c, o)};
+        d[p] = df_merge(d[p], other);
+      }
     if (lane == 0)
 #pragma unroll
-      for (int p = 0; p < kProbes; ++p) Hs[p * K + i] = d[p];
+      for (int p = 0; p < kProbes; ++p) {
+        Hs[p * K + i] = d[p].s;
+        Hc[p * K + i] = d[p].c;
+      }
   }
   __syncthreads();
-  // residual r_p = u_p^T D_32 A - u_p^T B (B is [K][m]: row j = atom j's column)
+  // residual r_p = u_p^T D_32 A - u_p^T B (B is [K][m]: row j = atom j's
+  // column); the large parts cancel exactly in the float differences of the
+  // compensated sums, their corrections carry the rest
 #pragma unroll
-  for (int q = 0; q < kCJ; ++q) {
+  for (int q = 0; q < CJ; ++q) {
     const int j = tid + kCThreads * q;
     if (j >= K) continue;
-    double b[kProbes] = {};
+    DF bv[kProbes];
+#pragma unroll
+    for (int p = 0; p < kProbes; ++p) bv[p] = DF{0.f, 0.f};
     const double *bj = Bt + (size_t)j * m;
     for (int r = 0; r < m; ++r) {
-      const double v = __ldg(bj + r);
+      float bh, bl;
+      split_d(__ldg(bj + r), bh, bl);
 #pragma unroll
-      for (int p = 0; p < kProbes; ++p) b[p] = fma((double)Us[p][r], v, b[p]);
+      for (int p = 0; p < kProbes; ++p) {
+        const bool neg = Us[p][r] < 0.f;
+        df_add(bv[p], neg ? -bh : bh);
+        bv[p].c = __fadd_rn(bv[p].c, neg ? -bl : bl);
+      }
     }
 #pragma unroll
-    for (int p = 0; p < kProbes; ++p) Zs[p * K + j] = (float)(Hs[p * K + j] + h[q][p] - b[p]);
+    for (int p = 0; p < kProbes; ++p) {
+      const DF hp = df_merge(h[q][p], DF{Hs[p * K + j], Hc[p * K + j]});
+      Zs[p * K + j] = __fadd_rn(__fsub_rn(hp.s, bv[p].s), __fsub_rn(hp.c, bv[p].c));
+    }
   }
   __syncthreads();
 
@@ -210,15 +293,15 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
   // every used atom's estimated error against tau of its norm
   bool ok = true;
 #pragma unroll
-  for (int q = 0; q < kCJ; ++q) {
+  for (int q = 0; q < CJ; ++q) {
     const int j = tid + kCThreads * q;
     if (j >= K || ut[j] == 0) continue;
     double e2 = 0.0;
 #pragma unroll
     for (int p = 0; p < kProbes; ++p) e2 = fma((double)Zs[p * K + j], (double)Zs[p * K + j], e2);
     e2 /= kProbes;
-    const double lim = (double)tau * (double)tau * n2[q];
-    if (!(n2[q] > 0.0) || !isfinite(n2[q]) || !(e2 <= lim)) ok = false;
+    const double lim = (double)tau * (double)tau * (double)n2[q];
+    if (!(n2[q] > 0.f) || !isfinite(n2[q]) || !(e2 <= lim)) ok = false;
   }
   ok = __syncthreads_and(ok) != 0;
   if (!ok) {
@@ -226,10 +309,16 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
     return;
   }
 #pragma unroll
-  for (int q = 0; q < kCJ; ++q) {
+  for (int q = 0; q < CJ; ++q) {
     const int j = tid + kCThreads * q;
     if (j >= K || ut[j] == 0) continue;   // unused: keeps the previous atom
-    const double inv = 1.0 / sqrt(n2[q]);
+    // the norm again in FP64 for the scale (one pass over the atom)
+    double s2 = 0.0;
+    for (int r = 0; r < m; ++r) {
+      const double x = X[(size_t)r * K + j];
+      s2 = fma(x, x, s2);
+    }
+    const double inv = 1.0 / sqrt(s2);
     T *dj = D + ((size_t)t * K + j) * m;
     for (int r = 0; r < m; ++r) dj[r] = (T)((double)X[(size_t)r * K + j] * inv);
   }
@@ -238,20 +327,20 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
 
 }  // namespace
 
-size_t mod_check_smem(int K) { return (2 * sizeof(double) + sizeof(float)) * kProbes * (size_t)K; }
+size_t mod_check_smem(int K) { return 5 * sizeof(float) * kProbes * (size_t)K; }
 
 template <typename T>
 cudaError_t launch_mod_check(const ModArgs &a, int ts, float tau, cudaStream_t st) {
   if (a.L <= 0) return cudaSuccess;
-  if (a.K > kCThreads * kCJ || a.m > 256 || (ts != 16 && ts != 32)) return cudaErrorInvalidValue;
+  if (a.K > kCThreads * kCJMax || a.m > 256 || (ts != 16 && ts != 32)) return cudaErrorInvalidValue;
   const size_t smem = mod_check_smem(a.K);
-  cudaError_t e = cudaFuncSetAttribute(mod_check_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = a.K <= 2 * kCThreads ? mod_check_kernel<T, 2> : mod_check_kernel<T, 4>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const float *M = reinterpret_cast<const float *>(a.Lf);
   const float *V = M + (size_t)a.L * (a.K + a.m) * a.K;
-  mod_check_kernel<T><<<(unsigned)a.L, kCThreads, smem, st>>>(
-      static_cast<const double *>(a.A), static_cast<const double *>(a.B), a.usage, a.K, a.m, ts, M, V,
-      static_cast<T *>(a.D), a.status, tau);
+  kern<<<(unsigned)a.L, kCThreads, smem, st>>>(static_cast<const double *>(a.A), static_cast<const double *>(a.B),
+                                               a.usage, a.K, a.m, ts, M, V, static_cast<T *>(a.D), a.status, tau);
   return cudaGetLastError();
 }
 
