@@ -974,11 +974,13 @@ def run_coding(args):
 def run_mod_local(args):
     """The local MOD update of the image-patch workload's shape, alone: 256
     subsets, K1=512 atoms, m=256, codes of s1=4 from the overcomplete DCT
-    (2,048 patches per subset: the FP64 solve's cost does not depend on n).
-    The third call is bracketed by cudaProfilerStart/Stop, so a profiler
-    started with profiling off captures exactly one accumulation and one solve
-    in the bench's launch configuration.  The small case the FP64 solve is
-    profiled on; printed as its own line."""
+    (2,048 patches per subset: the solve's cost does not depend on n).  The
+    third call of the default (checked mixed-precision) solve is bracketed by
+    cudaProfilerStart/Stop, so a profiler started with profiling off captures
+    exactly one accumulation, the FP32 pass, its check and the FP64 pass of
+    what the check left, in the bench's launch configuration.  Then the FP64
+    solve alone (SDL_OPT_MOD_MIXED 0) for comparison.  The small case the MOD
+    kernels are profiled on; printed as its own line."""
     import torch
 
     import paper_1403_4781_gb300 as sdl
@@ -988,65 +990,36 @@ def run_mod_local(args):
     Yp = sdl.split(torch.from_numpy(p.Y).to(dev), torch.from_numpy(p.perm).to(dev))
     D = torch.from_numpy(np.broadcast_to(p.extra["D_local0"], (p.L, p.K1, p.m)).copy()).to(dev)
     idx, val, _, _ = sdl.omp_batched(D, Yp, p.offsets, p.s1, prec=sdl.PREC_BF16, with_resid=False)
-    for _ in range(2):   # the first call tunes the solve
-        sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
-    torch.cuda.synchronize()
-    torch.cuda.profiler.start()
-    sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
-    torch.cuda.synchronize()
-    torch.cuda.profiler.stop()
     ctx = sdl.context(0)
-    ctx.profile(True)
-    ctx.profile_reset()
-    sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
-    prof = ctx.profile_read()
-    ctx.profile(False)
     flops = p.L * (p.K1 ** 3 / 3 + 2 * p.K1 ** 2 * p.m)
-    ms = prof["mod_solve_fp64"][2]
-    print(json.dumps({"metric": METRIC, "workload": f"mod_local_L{p.L}_K{p.K1}_m{p.m}_s{p.s1}",
-                      "solve_ms": ms, "solve_tflops": flops / (ms / 1e3) / 1e12,
-                      "fp64_frac": flops / (ms / 1e3) / FP64_PEAK_FLOPS,
-                      "kernels": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}),
-          flush=True)
-
-
-# ------------------------------------------------------------ CPU oracle ------
-def run_mod_local(args):
-    """The local MOD update of the image-patch workload's shape, alone: 256
-    subsets, K1=512 atoms, m=256, codes of s1=4 from the overcomplete DCT
-    (2,048 patches per subset: the FP64 solve's cost does not depend on n).
-    The third call is bracketed by cudaProfilerStart/Stop, so a profiler
-    started with profiling off captures exactly one accumulation and one solve
-    in the bench's launch configuration.  The small case the FP64 solve is
-    profiled on; printed as its own line."""
-    import torch
-
-    import paper_1403_4781_gb300 as sdl
-
-    dev = torch.device("cuda", 0)
-    p = si.config4(n_images=32, per_image=16384, L=256)
-    Yp = sdl.split(torch.from_numpy(p.Y).to(dev), torch.from_numpy(p.perm).to(dev))
-    D = torch.from_numpy(np.broadcast_to(p.extra["D_local0"], (p.L, p.K1, p.m)).copy()).to(dev)
-    idx, val, _, _ = sdl.omp_batched(D, Yp, p.offsets, p.s1, prec=sdl.PREC_BF16, with_resid=False)
-    for _ in range(2):   # the first call tunes the solve
+    out = {}
+    for mixed in (1, 0):
+        ctx.set_option(sdl.OPT_MOD_MIXED, mixed)
+        for _ in range(2):   # the first call tunes the solve
+            sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
+        torch.cuda.synchronize()
+        if mixed:
+            torch.cuda.profiler.start()
+            sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+        ctx.profile(True)
+        ctx.profile_reset()
         sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
-    torch.cuda.synchronize()
-    torch.cuda.profiler.start()
-    sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
-    torch.cuda.synchronize()
-    torch.cuda.profiler.stop()
-    ctx = sdl.context(0)
-    ctx.profile(True)
-    ctx.profile_reset()
-    sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    flops = p.L * (p.K1 ** 3 / 3 + 2 * p.K1 ** 2 * p.m)
-    ms = prof["mod_solve_fp64"][2]
-    print(json.dumps({"metric": METRIC, "workload": f"mod_local_L{p.L}_K{p.K1}_m{p.m}_s{p.s1}",
-                      "solve_ms": ms, "solve_tflops": flops / (ms / 1e3) / 1e12,
-                      "fp64_frac": flops / (ms / 1e3) / FP64_PEAK_FLOPS,
-                      "kernels": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}),
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        kern = {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}
+        if mixed:
+            ms32 = prof["mod_solve_fp32"][2]
+            out["mixed"] = {"fp32_pass_ms": ms32, "fp32_pass_tflops": flops / (ms32 / 1e3) / 1e12,
+                            "fp32_frac": flops / (ms32 / 1e3) / FP32_PEAK_FLOPS,
+                            "check_ms": prof["mod_check"][2], "kernels": kern}
+        else:
+            ms = prof["mod_solve_fp64"][2]
+            out["fp64"] = {"solve_ms": ms, "solve_tflops": flops / (ms / 1e3) / 1e12,
+                           "fp64_frac": flops / (ms / 1e3) / FP64_PEAK_FLOPS, "kernels": kern}
+    ctx.set_option(sdl.OPT_MOD_MIXED, 1)
+    print(json.dumps({"metric": METRIC, "workload": f"mod_local_L{p.L}_K{p.K1}_m{p.m}_s{p.s1}", **out}),
           flush=True)
 
 

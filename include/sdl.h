@@ -62,8 +62,9 @@ typedef enum {
   SDL_PREC_F32 = 1,
   /* FP32 data; correlations from BF16 operands on the tensor cores with
      FP32 accumulation; the Gram on the tensor cores from a two-term BF16 split
-     of D (about 2^-16); coefficients recomputed in FP32 on the support from
-     D_S^T y with one refinement step. */
+     of D (about 2^-16); coefficients on the support corrected by one FP32
+     refinement step (residual from D_S and y in FP32), which removes the BF16
+     rounding they inherit from the correlations. */
   SDL_PREC_BF16 = 2,
   /* FP32 data; correlations and Gram on the tensor cores from a two-term TF32
      split of both operands (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)),

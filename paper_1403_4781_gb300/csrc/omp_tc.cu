@@ -12,10 +12,9 @@
 // loop from there with little shared memory per block.  The Gram is formed
 // from a two-term BF16 split of D (hi + lo, three products), accurate to about
 // 2^-16 where one BF16 product would give 2^-8, so the selection's Cholesky
-// factor of G_SS also serves the refit of the coefficients on the support from
-// D_S^T y in FP32, whose refinement step (residuals from D_S and y in FP32)
-// removes the factor's remaining error: the BF16 rounding of alpha0 affects
-// only which atoms are chosen.
+// factor of G_SS also serves the correction step of the coefficients on the
+// support (residuals from D_S and y in FP32), which removes the BF16 rounding
+// they inherit from alpha0: that rounding affects only which atoms are chosen.
 #include "omp_common.cuh"
 #include "tc_ptx.cuh"
 
@@ -478,7 +477,12 @@ cudaError_t launch_omp_tc(const OmpArgs &a, float *a0c, cudaStream_t st) {
     const int64_t nt = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
     corr_tc_kernel<<<(unsigned)nt, kCorrThreads, csm, st>>>(a, cl, a0c, g0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = select_dispatch<true>(a, a0c, g0, nt, st)) != cudaSuccess) return e;
+    // the coefficients from alpha0 on the support carry its BF16 rounding; the
+    // selection loop's FP32 correction step (residual from D_S and y in FP32,
+    // solved with the factor of the FP32 Gram, within 2^-16 of the exact one)
+    // removes it to about 2^-16 kappa(G_SS) of that rounding, so no separate
+    // refit from D_S^T y is needed
+    if ((e = select_dispatch<false>(a, a0c, g0, nt, st)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

@@ -12,7 +12,7 @@ the oracle's only at a step where the oracle's top-two gap, and the amount by
 which the GPU's atom trails the oracle's under the oracle's own residual, are
 both below 1.25 (E_o + E_g), E the per-atom bound (tests/_parity.py); each test
 caps the share of signals that differ.  Whatever support the GPU chose, its
-coefficients are refitted in FP32 on that support from D and y, so they must
+coefficients are corrected in FP32 on that support (residual from D and y), so they must
 equal the exact least-squares fit on that support within the BF16 coefficient
 tolerance 2e-2, and the reported residual must be that fit's residual.
 """
