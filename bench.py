@@ -971,6 +971,41 @@ def run_coding(args):
     print(json.dumps(res), flush=True)
 
 
+def run_coding_final(args):
+    """The image-patch workload's final coding shape alone: 2^20 patches coded
+    with s=16 against the 1024-atom overcomplete DCT (256 x 1024), with BF16,
+    FP32-accurate (F32X3) and FP32 CUDA-core correlations.  The small case the
+    s=16 selection kernel is profiled on; printed as its own line."""
+    import torch
+
+    import paper_1403_4781_gb300 as sdl
+
+    dev = torch.device("cuda", 0)
+    p = si.config4(n_images=64, per_image=16384, L=64)
+    Y = torch.from_numpy(p.Y).to(dev)
+    D = torch.from_numpy(p.extra["D_merge0"]).to(dev)
+    s = p.extra["s_final"]
+    ctx = sdl.context(0)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, prec in (("bf16", sdl.PREC_BF16), ("f32x3", sdl.PREC_F32X3), ("fp32", sdl.PREC_F32)):
+        sdl.omp(D, Y, s, prec=prec, with_resid=False)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sdl.omp(D, Y, s, prec=prec, with_resid=False)
+        e1.record(stream)
+        e1.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        ms = e0.elapsed_time(e1)
+        out[name] = {"signals_per_s": p.N / (ms / 1e3), "ms": ms,
+                     "kernels": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}
+    print(json.dumps({"metric": METRIC, "workload": f"coding_final_m256_K1024_s{s}_n{p.N}", **out}), flush=True)
+
+
 def run_mod_local(args):
     """The local MOD update of the image-patch workload's shape, alone: 256
     subsets, K1=512 atoms, m=256, codes of s1=4 from the overcomplete DCT
@@ -1167,6 +1202,7 @@ def main():
     ap.add_argument("--error-sample", type=int, default=2000,
                     help="signals of the final coding the oracle recodes for the precision error")
     ap.add_argument("--workload", choices=["patches", "splitmerge", "uneven-A", "uneven-B", "denoise", "coding",
+                                           "coding-final",
                                            "conditioned", "mod-local"],
                     default="patches",
                     help="the main line's workload (patches or splitmerge), or a parity workload measured alone")
@@ -1182,7 +1218,7 @@ def main():
         run_ours(args, rank, world, local_rank)
     elif rank == 0:
         {"denoise": run_denoise, "coding": run_coding, "conditioned": run_conditioned,
-         "mod-local": run_mod_local}.get(
+         "mod-local": run_mod_local, "coding-final": run_coding_final}.get(
             args.workload, lambda a: run_uneven(a, args.workload[-1]))(args)
 
 

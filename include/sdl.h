@@ -191,7 +191,8 @@ sdl_status sdl_merge(sdl_ctx *ctx, sdl_precision prec, const void *D_local, cons
                      int iters, void *D, double *rmse);
 
 /* Table 1's MSE_train ingredients: out2 device double [2] receives
- * ||Y - D X||_F^2 and ||Y||_F^2 for ELL codes X. */
+ * ||Y - D X||_F^2 and ||Y||_F^2 for ELL codes X (s entries per signal, -1
+ * pads).  m <= 256, s <= 32, as for sdl_omp; SDL_EINVAL otherwise. */
 sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, int64_t n,
                         const void *D, int K, const int32_t *idx, const void *val, int s,
                         double *out2);

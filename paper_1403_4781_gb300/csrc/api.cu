@@ -1072,7 +1072,8 @@ sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, 
   ctx->err.clear();
   sdl_status st;
   if ((st = check_prec(ctx, prec)) != SDL_OK) return st;
-  SDL_REQUIRE(m >= 1 && n >= 0 && K >= 1 && s >= 1, "bad sizes");
+  SDL_REQUIRE(m >= 1 && m <= kMaxM && n >= 0 && K >= 1 && s >= 1 && s <= kMaxS,
+              "bad sizes (m in [1, 256], s in [1, 32])");
   SDL_REQUIRE(aligned16(out2) && aligned16(D) && (n == 0 || (aligned16(Y) && aligned16(idx) && aligned16(val))),
               "device pointers must be non-NULL and 16-byte aligned");
   DeviceGuard g(ctx->device);

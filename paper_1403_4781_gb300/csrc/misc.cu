@@ -149,23 +149,47 @@ __global__ void __launch_bounds__(256) residual_kernel(const T *__restrict__ Y, 
     // FP32 data: the residual entry y - sum_k d x_k and the two energies in
     // compensated FP32 (each product split exactly by an FMA), about 48
     // significant bits, on the FP32 pipe rather than the narrow FP64 one
+    // The signal's code sits in the lanes (lane k: entry k, s <= 32) and
+    // reaches the warp by shuffles; lane l holds entries l + 32 u (m <= 256) of
+    // the residual, so every atom's column loads once, coalesced.
     CSum cr, cy;
+    constexpr int MU = 8;
     for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
-      for (int r = lane; r < m; r += 32) {
-        const float y = (float)Y[(size_t)i * m + r];
-        CSum v;
-        v.hi = y;
-        for (int k = 0; k < s; ++k) {
-          const int j = idx[(size_t)i * s + k];
-          if (j >= 0) {
-            const float d = (float)D[(size_t)j * m + r], x = (float)val[(size_t)i * s + k];
+      int jl = -1;
+      float xl = 0.f;
+      if (lane < s) {
+        jl = idx[(size_t)i * s + lane];
+        xl = (float)val[(size_t)i * s + lane];
+      }
+      CSum v[MU];
+      float yv[MU];
+#pragma unroll
+      for (int u = 0; u < MU; ++u) {
+        const int r = lane + 32 * u;
+        yv[u] = r < m ? (float)Y[(size_t)i * m + r] : 0.f;
+        v[u].hi = yv[u];
+      }
+      for (int k = 0; k < s; ++k) {
+        const int j = __shfl_sync(0xffffffffu, jl, k);
+        const float x = __shfl_sync(0xffffffffu, xl, k);
+        if (j < 0) continue;   // warp-uniform
+        const T *dj = D + (size_t)j * m;
+#pragma unroll
+        for (int u = 0; u < MU; ++u) {
+          const int r = lane + 32 * u;
+          if (r < m) {
+            const float d = (float)dj[r];
             const float p = d * x;
-            v.add(-p, -fmaf(d, x, -p));
+            v[u].add(-p, -fmaf(d, x, -p));
           }
         }
-        const float h = v.hi, l = v.lo, p2 = h * h;
+      }
+#pragma unroll
+      for (int u = 0; u < MU; ++u) {
+        if (lane + 32 * u >= m) continue;
+        const float h = v[u].hi, l = v[u].lo, p2 = h * h;
         cr.add(p2, fmaf(h, h, -p2) + 2.f * h * l);
-        cy.add_sq(y);
+        cy.add_sq(yv[u]);
       }
     }
     r2 = cr.value();
