@@ -973,8 +973,9 @@ def run_coding(args):
 
 def run_coding_final(args):
     """The image-patch workload's final coding shape alone: 2^20 patches coded
-    with s=16 against the 1024-atom overcomplete DCT (256 x 1024), with BF16,
-    FP32-accurate (F32X3) and FP32 CUDA-core correlations.  The small case the
+    with s=16 against the 1024-atom overcomplete DCT (256 x 1024), with BF16
+    correlations (Batch-OMP selection and the residual form), FP32-accurate
+    (F32X3) and FP32 CUDA-core ones.  The small case the
     s=16 selection kernel is profiled on; printed as its own line."""
     import torch
 
@@ -988,7 +989,9 @@ def run_coding_final(args):
     ctx = sdl.context(0)
     stream = torch.cuda.current_stream(dev)
     out = {}
-    for name, prec in (("bf16", sdl.PREC_BF16), ("f32x3", sdl.PREC_F32X3), ("fp32", sdl.PREC_F32)):
+    for name, prec, form in (("bf16", sdl.PREC_BF16, 1), ("bf16_residual_form", sdl.PREC_BF16, 2),
+                             ("f32x3", sdl.PREC_F32X3, 0), ("fp32", sdl.PREC_F32, 0)):
+        ctx.set_option(sdl.OPT_BF16_FORM, form)
         sdl.omp(D, Y, s, prec=prec, with_resid=False)
         torch.cuda.synchronize()
         ctx.profile(True)
@@ -1003,6 +1006,7 @@ def run_coding_final(args):
         ms = e0.elapsed_time(e1)
         out[name] = {"signals_per_s": p.N / (ms / 1e3), "ms": ms,
                      "kernels": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}
+    ctx.set_option(sdl.OPT_BF16_FORM, 0)
     print(json.dumps({"metric": METRIC, "workload": f"coding_final_m256_K1024_s{s}_n{p.N}", **out}), flush=True)
 
 

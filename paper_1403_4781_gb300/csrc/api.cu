@@ -396,14 +396,16 @@ bool omp_split_f32(const sdl_ctx *ctx, int K, int m, int s) {
 // lives in the caller's G.
 size_t tc_image_bytes(int L, int K, int m) {
   const size_t bf16 = (size_t)L * round16(K) * round16(m) * 2, x3 = x3_image_bytes(L, K, m);
-  return bf16 > x3 ? bf16 : x3;
+  const size_t rtc = rtc_image_bytes(L, K, m);
+  const size_t mx = bf16 > x3 ? bf16 : x3;
+  return mx > rtc ? mx : rtc;
 }
 size_t tc_a0_bytes(int L, int K, int64_t n) {
   const int64_t tiles = (n + 127) / 128 + L;
   return sizeof(float) * (size_t)omp_tc_chunk_tiles(K, tiles) * 128 * K;
 }
 size_t tc_ws_bytes(int L, int K, int m, int64_t n) {
-  return round256(2 * tc_image_bytes(L, K, m)) + round256(sizeof(int32_t) * 4) + round256(tc_a0_bytes(L, K, n));
+  return round256(3 * tc_image_bytes(L, K, m)) + round256(sizeof(int32_t) * 4) + round256(tc_a0_bytes(L, K, n));
 }
 
 // Kernels of one two-kernel coding pass: a correlation and a selection launch
@@ -429,8 +431,15 @@ cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t
   if (e != cudaSuccess) return e;
   e = timed(ctx, "gram_tc", 1, [&] { return launch_gram_tc(img, lo, oa.K, oa.m, oa.L, G, err, sm); });
   if (e != cudaSuccess) return e;
-  if (ctx->opt_bf16_form == 2 && omp_rtc_supported(oa.K, oa.m, oa.s))
-    return timed(ctx, "omp_rtc", 1, [&] { return launch_omp_rtc(oa, sm); });
+  if (ctx->opt_bf16_form == 2 && omp_rtc_supported(oa.K, oa.m, oa.s)) {
+    // the residual form's own image (256-atom x 64-entry slabs) in the third slot
+    void *rimg = static_cast<unsigned char *>(img) + 2 * tc_image_bytes(oa.L, oa.K, oa.m);
+    e = timed(ctx, "rtc_image", 1, [&] {
+      return launch_rtc_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, rimg, sm);
+    });
+    if (e != cudaSuccess) return e;
+    return timed(ctx, "omp_rtc", 1, [&] { return launch_omp_rtc(oa, rimg, sm); });
+  }
   return timed(ctx, "omp_tc", split_kernels(oa), [&] { return launch_omp_tc(oa, a0c, sm); });
 }
 
@@ -614,7 +623,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   if (tile <= 0) return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
   if ((st = upload_plan(ctx, offsets, L, tile, &d_off, &d_tiles, &tiles)) != SDL_OK)
     return st;
-  void *img = tc ? ws_alloc(ctx, 2 * tc_image_bytes(L, K, m)) : nullptr;
+  void *img = tc ? ws_alloc(ctx, 3 * tc_image_bytes(L, K, m)) : nullptr;
   int32_t *tc_err = tc ? static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4)) : nullptr;
   float *a0c = tc || split ? static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n))) : nullptr;
   if ((split && !a0c) || (tc && (!img || !tc_err || !a0c))) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
@@ -826,7 +835,7 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
   a.L = L; a.m = m; a.K = K; a.s = s; a.eps = eps;
   a.idx = idx; a.val = val; a.nnz = nnz; a.resid2 = resid2;
   if (bf16 || x3) {
-    void *img = ws_alloc(ctx, 2 * tc_image_bytes(L, K, m));
+    void *img = ws_alloc(ctx, 3 * tc_image_bytes(L, K, m));
     int32_t *err = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
     float *a0c = static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n)));
     if (!img || !err || !a0c) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");

@@ -154,7 +154,11 @@ int omp_tc_tile_signals(int K, int m, int s);
 // images and FP32 Gram): D^T r of every step by tcgen05 into TMEM, picks,
 // Cholesky rows and FP32 residuals per signal.  Shapes: s <= 16, m <= 256.
 bool omp_rtc_supported(int K, int m, int s);
-cudaError_t launch_omp_rtc(const OmpArgs &a, cudaStream_t st);
+// Its BF16 image of D: [L][round64(m)/64][round256(K)][64], 256-atom x 64-entry
+// slabs (rtc_image_bytes(L, K, m) bytes).
+size_t rtc_image_bytes(int L, int K, int m);
+cudaError_t launch_rtc_image(const float *D, int K, int m, int L, void *img, cudaStream_t st);
+cudaError_t launch_omp_rtc(const OmpArgs &a, const void *img, cudaStream_t st);
 // The selection kernel over 128-signal tiles tile0 .. tile0+ntile-1 whose
 // alpha0 rows are in a0c (FP32 data).  exact: alpha0 came from BF16 products,
 // so the coefficients are refitted from D_S^T y.
