@@ -358,6 +358,10 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     squared pivot fell to 1e-3 of its diagonal) is solved again in FP64 as
  *     it would have been alone, ridge retry included.  Chosen when the
  *     autotuner times it faster than the FP64 candidates.  0 = FP64 only.
+ *   SDL_OPT_A0_CHUNK_MB: the two-kernel coding passes (FP32, BF16, F32X3)
+ *     write the correlations alpha0 of 128-signal tiles to a workspace scratch
+ *     and run the selection from there, chunk by chunk: the chunk's size in
+ *     MB, 1 to 1024, or 0 (default) for the automatic size.
  *   SDL_OPT_MOD_CHECK_TOL: the tolerance of that check in parts per 10^9 of
  *     each atom's norm, 1 to 10^9, default 20000 (2e-5).  A smaller value sends
  *     more subsets to the FP64 solve; 1 sends every one.
@@ -428,7 +432,8 @@ typedef enum {
   SDL_OPT_WAIT_LIMIT = 10,
   SDL_OPT_WAIT_TEST = 11,
   SDL_OPT_MOD_MIXED = 12,
-  SDL_OPT_MOD_CHECK_TOL = 13
+  SDL_OPT_MOD_CHECK_TOL = 13,
+  SDL_OPT_A0_CHUNK_MB = 14
 } sdl_option;
 sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
 

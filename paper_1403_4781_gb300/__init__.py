@@ -99,7 +99,7 @@ OPT_MOD_SOLVE, OPT_CLUSTER, OPT_MOD_TILE, OPT_AUTOTUNE, OPT_GRAPH, OPT_SM_BLOCKS
 OPT_OMP_FORM = 8
 OPT_BF16_FORM = 9
 OPT_WAIT_LIMIT, OPT_WAIT_TEST = 10, 11
-OPT_MOD_MIXED, OPT_MOD_CHECK_TOL = 12, 13
+OPT_MOD_MIXED, OPT_MOD_CHECK_TOL, OPT_A0_CHUNK_MB = 12, 13, 14
 
 
 def lib() -> ctypes.CDLL:

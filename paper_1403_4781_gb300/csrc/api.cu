@@ -411,7 +411,7 @@ size_t tc_ws_bytes(int L, int K, int m, int64_t n) {
 // Kernels of one two-kernel coding pass: a correlation and a selection launch
 // per chunk of the scratch.
 int split_kernels(const OmpArgs &oa) {
-  const int64_t chunk = omp_tc_chunk_tiles(oa.K, oa.total_tiles);
+  const int64_t chunk = omp_tc_chunk_tiles(oa.K, oa.total_tiles, oa.a0_cap);
   return oa.total_tiles > 0 ? 2 * (int)((oa.total_tiles + chunk - 1) / chunk) : 0;
 }
 
@@ -637,6 +637,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   if (!G || !idx || !val || !nnz || !res2 || !worst)
     return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
   oa.D = D; oa.G = G; oa.Y = Y; oa.offsets = d_off; oa.tile_start = d_tiles; oa.total_tiles = tiles;
+  oa.a0_cap = (int64_t)ctx->opt_a0_chunk_mb << 20;
   oa.L = L; oa.m = m; oa.K = K; oa.s = s; oa.eps = eps;
   oa.idx = idx; oa.val = val; oa.nnz = nnz; oa.resid2 = res2;
   ModArgs ma{};
@@ -700,7 +701,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
              ctx->opt_mod_solve * 2 + ctx->opt_mod_mixed, ctx->opt_tile, ctx->opt_cluster * 4 + ctx->opt_sm_blocks,
              ctx->opt_autotune,
              (int)ctx->tuned.size(), (ctx->opt_replace * 4 + ctx->opt_omp_form) * 4 + ctx->opt_bf16_form,
-             ctx->opt_wait_test, ctx->opt_wait_limit, ctx->opt_mod_check_ppb);
+             ctx->opt_wait_test, ctx->opt_wait_limit, ctx->opt_mod_check_ppb * 2048 + ctx->opt_a0_chunk_mb);
     const std::string key(kb);
     auto hit = ctx->graphs.find(key);
     if (hit != ctx->graphs.end()) {
@@ -832,6 +833,7 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
   void *G = ws_alloc(ctx, elem_size(prec) * (size_t)L * K * K);
   if (!G) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
   a.D = D; a.G = G; a.Y = Y; a.offsets = d_off; a.tile_start = d_tiles; a.total_tiles = tiles;
+  a.a0_cap = (int64_t)ctx->opt_a0_chunk_mb << 20;
   a.L = L; a.m = m; a.K = K; a.s = s; a.eps = eps;
   a.idx = idx; a.val = val; a.nnz = nnz; a.resid2 = resid2;
   if (bf16 || x3) {
@@ -1271,6 +1273,7 @@ sdl_status sdl_corr_features(sdl_ctx *ctx, const float *D, int m, int K, const f
   int64_t tiles = 0;
   if ((st = upload_plan(ctx, offsets, L, 128, &d_off, &d_tiles, &tiles)) != SDL_OK) return st;
   a.D = D; a.Y = Y; a.offsets = d_off; a.tile_start = d_tiles; a.total_tiles = tiles;
+  a.a0_cap = (int64_t)ctx->opt_a0_chunk_mb << 20;
   a.L = L; a.m = m; a.K = K;
   SDL_CUDA(timed(ctx, "corr_features", 1, [&] { return launch_corr_features(a, 0, tiles, 0, F, ctx->stream); }),
            "correlation features");
@@ -1350,6 +1353,7 @@ sdl_status sdl_omp_proposed_batched(sdl_ctx *ctx, sdl_proposer *p, int features,
     };
     OmpArgs fa{};
     fa.D = D; fa.Y = Y; fa.offsets = d_off; fa.tile_start = d_tiles; fa.total_tiles = tiles;
+    fa.a0_cap = (int64_t)ctx->opt_a0_chunk_mb << 20;
     fa.L = L; fa.m = m; fa.K = K;
     for (int64_t g0 = 0; g0 < tiles; g0 += kChunkTiles) {
       const int64_t g1 = tiles - g0 < kChunkTiles ? tiles : g0 + kChunkTiles;
@@ -1483,6 +1487,10 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
     case SDL_OPT_WAIT_TEST:
       if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_WAIT_TEST takes 0 or 1");
       ctx->opt_wait_test = (int)value;
+      return SDL_OK;
+    case SDL_OPT_A0_CHUNK_MB:
+      if (value < 0 || value > 1024) return set_error(ctx, SDL_EINVAL, "SDL_OPT_A0_CHUNK_MB takes 0 to 1024");
+      ctx->opt_a0_chunk_mb = (int)value;
       return SDL_OK;
     case SDL_OPT_MOD_CHECK_TOL:
       if (value < 1 || value > 1000000000)

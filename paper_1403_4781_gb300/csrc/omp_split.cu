@@ -198,7 +198,7 @@ cudaError_t launch_corr_features(const OmpArgs &a, int64_t tile0, int64_t ntile,
 
 cudaError_t launch_omp_split_f32(const OmpArgs &a, float *a0c, cudaStream_t st) {
   if (a.total_tiles <= 0) return cudaSuccess;
-  const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles);
+  const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles, a.a0_cap);
   for (int64_t g0 = 0; g0 < a.total_tiles; g0 += chunk) {
     const int64_t nt = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
     const int nb = (a.K + kGN - 1) / kGN;

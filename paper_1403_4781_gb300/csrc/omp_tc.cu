@@ -457,10 +457,11 @@ int omp_tc_tile_signals(int K, int m, int s) {
   return 128;
 }
 
-// Tiles per chunk of the alpha0 scratch (at most 1 GiB, at least one tile).
-int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles) {
+// Tiles per chunk of the alpha0 scratch (at most cap bytes, 0: 1 GiB; at least
+// one tile).
+int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles, int64_t cap) {
   const int64_t per = (int64_t)128 * K * (int64_t)sizeof(float);
-  int64_t c = ((int64_t)1 << 30) / per;
+  int64_t c = (cap > 0 ? cap : ((int64_t)1 << 30)) / per;
   if (c < 1) c = 1;
   return c < total_tiles ? c : (total_tiles > 0 ? total_tiles : 1);
 }
@@ -472,7 +473,7 @@ cudaError_t launch_omp_tc(const OmpArgs &a, float *a0c, cudaStream_t st) {
   if (csm > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
   if (e != cudaSuccess) return e;
-  const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles);
+  const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles, a.a0_cap);
   for (int64_t g0 = 0; g0 < a.total_tiles; g0 += chunk) {
     const int64_t nt = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
     corr_tc_kernel<<<(unsigned)nt, kCorrThreads, csm, st>>>(a, cl, a0c, g0);

@@ -454,7 +454,7 @@ cudaError_t launch_omp_x3(const OmpArgs &a, const void *hi, const void *lo, floa
                           const X3Wait &w, cudaStream_t st) {
   if (a.total_tiles <= 0) return cudaSuccess;
   X3Job j = x3_job(a, hi, lo, a0c, a.err, w);
-  const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles);
+  const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles, a.a0_cap);
   for (int64_t g0 = 0; g0 < a.total_tiles; g0 += chunk) {
     j.tile0 = g0;
     j.ntile = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;

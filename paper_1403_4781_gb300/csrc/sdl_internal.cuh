@@ -84,6 +84,7 @@ struct sdl_ctx {
   int opt_wait_test = 0;         // 1: one block of each wide-solve group leaves at once
   int opt_mod_mixed = 1;         // FP32 data: 1 the checked FP32 pass of the tiled solve may run, 0 FP64 only
   int opt_mod_check_ppb = 20000; // tolerance of that check, parts per 10^9 of each atom's norm
+  int opt_a0_chunk_mb = 0;       // alpha0 scratch chunk of the two-kernel coding passes, MB (0: automatic)
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
@@ -132,6 +133,7 @@ struct OmpArgs {
   const void *Dimg;       // [L][Kp][mp] BF16 canonical K-major image of D
   int Kp, mp;             // K and m rounded up to multiples of 16
   int32_t *err;           // device word: bit 0 set when a bounded wait gave up
+  int64_t a0_cap;         // bytes of one alpha0 scratch chunk (0: 1 GiB)
 };
 template <typename T>
 cudaError_t launch_omp(const OmpArgs &a, int num_sms, cudaStream_t st);
@@ -170,7 +172,8 @@ cudaError_t launch_omp_split_f32(const OmpArgs &a, float *a0c, cudaStream_t st);
 // G_t = D_t D_t^T with the correlation GEMM's 128 x 128 register-tiled blocks
 // (used by launch_gram<float> when there are enough blocks to fill the GPU).
 cudaError_t launch_gram_f32_tiles(const float *D, int m, int K, int L, float *G, cudaStream_t st);
-int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles);
+// Tiles per chunk of the alpha0 scratch: at most cap bytes (0: 1 GiB), at least one tile.
+int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles, int64_t cap = 0);
 // FP32-accurate tensor-core path (3 x TF32): hi = tf32(d), lo = tf32(d - hi)
 // images of D [L][round32(m)/32][round128(K)][32] (x3_image_bytes each), the
 // Gram and the correlations as hi hi^T + hi lo^T + lo hi^T with FP32
