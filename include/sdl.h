@@ -397,12 +397,15 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *   SDL_OPT_BF16_FORM: BF16 OMP kernels.  0 = automatic (default): form 1.
  *     1 = Batch-OMP form: alpha0 =
  *     D^T y of 128-signal tiles on the tensor cores into a workspace scratch,
- *     then the selection kernel's running correlations through the Gram.
- *     2 = residual form: one kernel recomputes D^T r of a 128-signal tile at
- *     every step on the tensor cores (accumulators in tensor memory) and forms
- *     the residuals and right-hand sides in FP32 (s <= 16 and m <= 256; other
- *     shapes run form 1).  Both refit the coefficients
- *     on the chosen support in FP32 with one refinement step; they may choose
+ *     then the selection kernel's running correlations through the FP32 Gram.
+ *     3 = the same with the running update's K-wide Gram columns read from a
+ *     half-precision copy (2^-11 of each entry, below the correlations' own
+ *     BF16 rounding; the Cholesky entries stay FP32): half the bytes of those
+ *     reads.  2 = residual form: one kernel recomputes D^T r of a
+ *     128-signal tile at every step on the tensor cores (accumulators in tensor
+ *     memory) and forms the residuals and right-hand sides in FP32 (s <= 16 and
+ *     m <= 256; other shapes run form 1).  All correct the coefficients on the
+ *     chosen support in FP32 with one refinement step; they may choose
  *     differently among atoms whose correlations tie to within BF16 rounding.
  *   SDL_OPT_WAIT_LIMIT: polls (64 ns apart) before a barrier wait of the wide
  *     solve gives up, default 2^24; the call then returns SDL_ETIMEOUT with the

@@ -404,8 +404,11 @@ size_t tc_a0_bytes(int L, int K, int64_t n) {
   const int64_t tiles = (n + 127) / 128 + L;
   return sizeof(float) * (size_t)omp_tc_chunk_tiles(K, tiles) * 128 * K;
 }
+// Half-precision copy of the Gram for the BF16 pass's running update.
+size_t tc_g16_bytes(int L, int K) { return (size_t)L * K * K * 2; }
 size_t tc_ws_bytes(int L, int K, int m, int64_t n) {
-  return round256(3 * tc_image_bytes(L, K, m)) + round256(sizeof(int32_t) * 4) + round256(tc_a0_bytes(L, K, n));
+  return round256(3 * tc_image_bytes(L, K, m)) + round256(sizeof(int32_t) * 4) + round256(tc_a0_bytes(L, K, n)) +
+         round256(tc_g16_bytes(L, K));
 }
 
 // Kernels of one two-kernel coding pass: a correlation and a selection launch
@@ -417,7 +420,10 @@ int split_kernels(const OmpArgs &oa) {
 
 // One BF16 coding pass: BF16 images of D (img holds hi, then lo), Gram and
 // correlations on the tensor cores, selection loop, FP32 refit on the support.
-cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *err, float *a0c) {
+cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *err, float *a0c, void *G16) {
+  // only form 3 reads the half-precision Gram copy in the running update
+  if (ctx->opt_bf16_form != 3) G16 = nullptr;
+  oa.G16 = G16;
   cudaStream_t sm = ctx->stream;
   void *lo = static_cast<unsigned char *>(img) + tc_image_bytes(oa.L, oa.K, oa.m);
   oa.Dimg = img;
@@ -429,7 +435,7 @@ cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t
     return launch_bf16_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, img, lo, sm);
   });
   if (e != cudaSuccess) return e;
-  e = timed(ctx, "gram_tc", 1, [&] { return launch_gram_tc(img, lo, oa.K, oa.m, oa.L, G, err, sm); });
+  e = timed(ctx, "gram_tc", 1, [&] { return launch_gram_tc(img, lo, oa.K, oa.m, oa.L, G, err, sm, G16); });
   if (e != cudaSuccess) return e;
   if (ctx->opt_bf16_form == 2 && omp_rtc_supported(oa.K, oa.m, oa.s)) {
     // the residual form's own image (256-atom x 64-entry slabs) in the third slot
@@ -626,7 +632,9 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   void *img = tc ? ws_alloc(ctx, 3 * tc_image_bytes(L, K, m)) : nullptr;
   int32_t *tc_err = tc ? static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4)) : nullptr;
   float *a0c = tc || split ? static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n))) : nullptr;
-  if ((split && !a0c) || (tc && (!img || !tc_err || !a0c))) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+  void *g16 = bf16 && ctx->opt_bf16_form == 3 ? ws_alloc(ctx, tc_g16_bytes(L, K)) : nullptr;
+  if ((split && !a0c) || (tc && (!img || !tc_err || !a0c)) || (bf16 && ctx->opt_bf16_form == 3 && !g16))
+    return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
   if (tc) SDL_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int32_t), ctx->stream), "err clear");
   T *G = static_cast<T *>(ws_alloc(ctx, sizeof(T) * (size_t)L * K * K));
   int32_t *idx = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * (size_t)n * s));
@@ -655,7 +663,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
     for (int it = 0; it < iters; ++it) {
       cudaError_t e;
       if (bf16) {
-        e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c);
+        e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c, g16);
       } else if (x3) {
         e = run_omp_x3(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c);
       } else if (split) {
@@ -840,9 +848,11 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
     void *img = ws_alloc(ctx, 3 * tc_image_bytes(L, K, m));
     int32_t *err = static_cast<int32_t *>(ws_alloc(ctx, sizeof(int32_t) * 4));
     float *a0c = static_cast<float *>(ws_alloc(ctx, tc_a0_bytes(L, K, n)));
-    if (!img || !err || !a0c) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
+    void *g16 = bf16 && ctx->opt_bf16_form == 3 ? ws_alloc(ctx, tc_g16_bytes(L, K)) : nullptr;
+    if (!img || !err || !a0c || (bf16 && ctx->opt_bf16_form == 3 && !g16))
+      return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
     SDL_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream), "err clear");
-    cudaError_t e = bf16 ? run_omp_bf16(ctx, a, img, static_cast<float *>(G), err, a0c)
+    cudaError_t e = bf16 ? run_omp_bf16(ctx, a, img, static_cast<float *>(G), err, a0c, g16)
                          : run_omp_x3(ctx, a, img, static_cast<float *>(G), err, a0c);
     if (e == cudaErrorInvalidConfiguration)
       return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
@@ -1502,7 +1512,7 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
       ctx->opt_mod_mixed = (int)value;
       return SDL_OK;
     case SDL_OPT_BF16_FORM:
-      if (value < 0 || value > 2) return set_error(ctx, SDL_EINVAL, "SDL_OPT_BF16_FORM takes 0, 1 or 2");
+      if (value < 0 || value > 3) return set_error(ctx, SDL_EINVAL, "SDL_OPT_BF16_FORM takes 0 to 3");
       ctx->opt_bf16_form = (int)value;
       return SDL_OK;
     case SDL_OPT_GRAPH:

@@ -3,6 +3,7 @@
 // and the per-warp Batch-OMP selection loop with its refinement on the support.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "sdl_internal.cuh"
@@ -167,6 +168,40 @@ __device__ __forceinline__ void span_load(const double *p, double (&v)[KPL], uin
   }
 }
 
+// This lane's entries of a row whose every group exists and is 16-byte
+// aligned: unconditional vector loads (no per-group tests).
+template <int KPL>
+__device__ __forceinline__ void span_load_full(const float *p, float (&v)[KPL]) {
+#pragma unroll
+  for (int c = 0; c < KPL; c += 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p + 128 * (c >> 2));
+    v[c] = t.x; v[c + 1] = t.y; v[c + 2] = t.z; v[c + 3] = t.w;
+  }
+}
+
+// This lane's entries of a half-precision row (four consecutive atoms per group
+// load as one 8-byte vector when vec), widened to FP32.
+template <int KPL>
+__device__ __forceinline__ void span_load_h(const __half *p, float (&v)[KPL], uint32_t valid, bool vec) {
+#pragma unroll
+  for (int c = 0; c < KPL; c += 4) {
+    const __half *q = p + 128 * (c >> 2);
+    if (vec) {
+      if ((valid >> c) & 1u) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(q);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+        v[c] = a.x; v[c + 1] = a.y; v[c + 2] = b.x; v[c + 3] = b.y;
+      } else {
+        v[c] = v[c + 1] = v[c + 2] = v[c + 3] = 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[c + e] = (valid >> (c + e)) & 1u ? __half2float(q[e]) : 0.f;
+    }
+  }
+}
+
 // The selection loop (Sec. 1 greedy choice, Batch-OMP form), refinement on the
 // support and the ELL write-out for signals sig_begin .. sig_begin+sig_count-1
 // of a tile, run by one warp.
@@ -179,6 +214,9 @@ __device__ __forceinline__ void span_load(const double *p, double (&v)[KPL], uin
 //          the most later updates)
 //   EXACT  alpha0 came from reduced-precision products: the refit takes D_S^T y
 //          in T instead of alpha0 on the support
+//   H16    (FP32 only) the running update alpha -= G[:, S] dx reads a
+//          half-precision copy of G (G16t; the shared-memory cache gc holds
+//          half columns too), the Cholesky entries still come from the FP32 Gt
 // Lane l owns the atoms lane_atom(l, c), c < KPL: its correlations and the
 // matching entries of each G column load as 16-byte vectors.
 // Per step the correlations are kept as a running vector alpha = alpha0 -
@@ -186,10 +224,13 @@ __device__ __forceinline__ void span_load(const double *p, double (&v)[KPL], uin
 // the change of every coefficient.  The forward-solved vector z = L^{-1}
 // alpha0_S grows by one entry per step, (alpha0_j - w^T z) / l for the new
 // factor row [w^T, l], so only x = L^{-T} z is solved again.
-template <typename T, int KPL, int MU, bool EXACT>
+template <typename T, int KPL, int MU, bool EXACT, bool H16 = false>
 __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase, int ypitch, int sig_begin,
                                   int sig_count, int nsig, int64_t row0, const T *__restrict__ Dt,
-                                  const T *__restrict__ Gt, T *Ls, T *gc, int lp, int gcn) {
+                                  const T *__restrict__ Gt, T *Ls, void *gcv, int lp, int gcn,
+                                  const __half *__restrict__ G16t = nullptr) {
+  T *gc = static_cast<T *>(gcv);
+  __half *gc16 = static_cast<__half *>(gcv);
   constexpr int M32 = MU;
   const int K = a.K, m = a.m, s = a.s;
   const int lane = threadIdx.x & 31;
@@ -201,6 +242,9 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
     if (lane_atom(lane, c) < K) valid |= 1u << c;
   const bool vec = (K & 3) == 0;   // 16-byte aligned rows of alpha0 and G (warp-uniform)
   const int j0 = 4 * lane;         // this lane's first atom
+  // every entry of this lane exists (K a multiple of 128 makes it every lane):
+  // rows load without per-group tests
+  const bool full = sizeof(T) == 4 && vec && valid == (KPL >= 32 ? 0xffffffffu : ((1u << KPL) - 1u));
 
   for (int q = 0; q < sig_count; ++q) {
     const int sig = sig_begin + q;
@@ -209,7 +253,12 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
     const T *ysig = ybase + (size_t)sig * ypitch;
     const T *arow = a0 + (size_t)sig * K;
     T av[KPL];   // running correlations of this lane's atoms
-    span_load<KPL>(arow + j0, av, valid, vec);
+    if constexpr (sizeof(T) == 4) {
+      if (full) span_load_full<KPL>(arow + j0, av);
+      else span_load<KPL>(arow + j0, av, valid, vec);
+    } else {
+      span_load<KPL>(arow + j0, av, valid, vec);
+    }
 
     T yn2 = T(0);
 #pragma unroll
@@ -239,10 +288,22 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
       // updates of later steps only, so the last step reads it from L2
       const T *gcol = Gt + (size_t)best * K;
       if (k < gcn && k + 1 < s) {
-        T *dst = gc + (size_t)k * K;
-        for (int j = lane; j < K; j += 32) dst[j] = gcol[j];
-        __syncwarp();
-        gcol = dst;
+        if constexpr (H16) {   // the update's half column; the FP32 entries below stay in L2
+          const __half *src = G16t + (size_t)best * K;
+          __half *dst = gc16 + (size_t)k * K;
+          if (vec) {
+            for (int j = 4 * lane; j < K; j += 128)
+              *reinterpret_cast<uint2 *>(dst + j) = *reinterpret_cast<const uint2 *>(src + j);
+          } else {
+            for (int j = lane; j < K; j += 32) dst[j] = src[j];
+          }
+          __syncwarp();
+        } else {
+          T *dst = gc + (size_t)k * K;
+          for (int j = lane; j < K; j += 32) dst[j] = gcol[j];
+          __syncwarp();
+          gcol = dst;
+        }
       }
       // progressive Cholesky: L w = G[S, best]; new row [w^T, sqrt(g_bb - w^T w)]
       const T gS = lane < k ? gcol[Sl] : T(0);
@@ -267,9 +328,20 @@ __device__ void code_warp_signals(const OmpArgs &a, const T *a0, const T *ybase,
         const T dl = xn - xl;
         for (int p = 0; p < k; ++p) {
           const T dp = __shfl_sync(0xffffffffu, dl, p);
-          const T *gp = p < gcn ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
           T g[KPL];
-          span_load<KPL>(gp + j0, g, valid, vec);
+          if constexpr (H16) {
+            const __half *gp = p < gcn ? gc16 + (size_t)p * K
+                                       : G16t + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
+            span_load_h<KPL>(gp + j0, g, valid, vec);
+          } else {
+            const T *gp = p < gcn ? gc + (size_t)p * K : Gt + (size_t)__shfl_sync(0xffffffffu, Sl, p) * K;
+            if constexpr (sizeof(T) == 4) {
+              if (full) span_load_full<KPL>(gp + j0, g);
+              else span_load<KPL>(gp + j0, g, valid, vec);
+            } else {
+              span_load<KPL>(gp + j0, g, valid, vec);
+            }
+          }
 #pragma unroll
           for (int c = 0; c < KPL; ++c) av[c] = fma(-g[c], dp, av[c]);
         }

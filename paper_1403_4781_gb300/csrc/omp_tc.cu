@@ -67,7 +67,8 @@ constexpr int kGramNG = 128;
 
 __global__ void __launch_bounds__(128) gram_tc_kernel(const unsigned char *__restrict__ hi,
                                                       const unsigned char *__restrict__ lo, int K, int Kp, int mp,
-                                                      bool all4, float *__restrict__ G, int32_t *err) {
+                                                      bool all4, float *__restrict__ G, int32_t *err,
+                                                      __half *__restrict__ G16) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int t = blockIdx.z, bx = blockIdx.x, by = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -158,10 +159,14 @@ __global__ void __launch_bounds__(128) gram_tc_kernel(const unsigned char *__res
       tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + c0, v);
       if (row < K) {
         float *grow = G + ((size_t)t * K + row) * K;
+        __half *hrow = G16 ? G16 + ((size_t)t * K + row) * K : nullptr;
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
           const int col = kGramNG * by + c0 + e;
-          if (col < K) grow[col] = v[e];
+          if (col < K) {
+            grow[col] = v[e];
+            if (hrow) hrow[col] = __float2half_rn(v[e]);
+          }
         }
       }
     }
@@ -348,7 +353,7 @@ struct SelLayout {
 // fit the shared memory one block gets at the occupancy its registers allow
 // (the first picks' columns: column p is re-read by the s - 1 - p later
 // updates, so caching the first few saves most of the L2 reads).
-inline SelLayout sel_layout(int K, int s, int regs) {
+inline SelLayout sel_layout(int K, int s, int regs, bool h16) {
   const int rr = (regs + 7) & ~7;
   int blocks = 65536 / (kSelThreads * (rr > 0 ? rr : 8));
   blocks = blocks < 1 ? 1 : (blocks > 8 ? 8 : blocks);
@@ -356,7 +361,7 @@ inline SelLayout sel_layout(int K, int s, int regs) {
   SelLayout L{};
   L.lp = odd_pitch(s);
   const size_t ls = align16(sizeof(float) * (size_t)8 * s * L.lp);
-  const size_t col = sizeof(float) * (size_t)8 * K;   // one column for every warp
+  const size_t col = (h16 ? 2 : sizeof(float)) * (size_t)8 * K;   // one column for every warp
   const int fit = budget > ls ? (int)((budget - ls) / col) : 0;
   L.gcn = fit < s - 1 ? fit : (s > 1 ? s - 1 : 0);
   size_t off = 0;
@@ -366,7 +371,7 @@ inline SelLayout sel_layout(int K, int s, int regs) {
   return L;
 }
 
-template <int KPL, int MU, bool EXACT>
+template <int KPL, int MU, bool EXACT, bool H16>
 __global__ void __launch_bounds__(kSelThreads, KPL <= 8 ? 4 : (KPL <= 16 ? 3 : 2)) omp_select_kernel(OmpArgs a, SelLayout lay, const float *a0c,
                                                                  int64_t tile0) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -383,37 +388,41 @@ __global__ void __launch_bounds__(kSelThreads, KPL <= 8 ? 4 : (KPL <= 16 ? 3 : 2
   const float *__restrict__ Gt = static_cast<const float *>(a.G) + (size_t)t * K * K;
   const float *a0 = a0c + ((size_t)(g - tile0) * 128 + quarter * 32) * K;
   float *Ls = reinterpret_cast<float *>(smem + lay.ls) + (size_t)warp * s * lay.lp;
-  float *gc = lay.gcn > 0 ? reinterpret_cast<float *>(smem + lay.gc) + (size_t)warp * lay.gcn * K : nullptr;
-  code_warp_signals<float, KPL, MU, EXACT>(a, a0, static_cast<const float *>(a.Y) + (size_t)row0 * m, m, warp * 4, 4,
-                                          nsig, row0, Dt, Gt, Ls, gc, lay.lp, lay.gcn);
+  void *gc = nullptr;
+  if (lay.gcn > 0)
+    gc = H16 ? static_cast<void *>(reinterpret_cast<__half *>(smem + lay.gc) + (size_t)warp * lay.gcn * K)
+             : static_cast<void *>(reinterpret_cast<float *>(smem + lay.gc) + (size_t)warp * lay.gcn * K);
+  const __half *G16t = H16 ? static_cast<const __half *>(a.G16) + (size_t)t * K * K : nullptr;
+  code_warp_signals<float, KPL, MU, EXACT, H16>(a, a0, static_cast<const float *>(a.Y) + (size_t)row0 * m, m,
+                                               warp * 4, 4, nsig, row0, Dt, Gt, Ls, gc, lay.lp, lay.gcn, G16t);
 }
 
-template <int KPL, int MU, bool EXACT>
+template <int KPL, int MU, bool EXACT, bool H16>
 cudaError_t launch_select(const OmpArgs &a, const float *a0c, int64_t tile0, int64_t ntile, cudaStream_t st) {
-  auto kern = omp_select_kernel<KPL, MU, EXACT>;
+  auto kern = omp_select_kernel<KPL, MU, EXACT, H16>;
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
-  const SelLayout lay = sel_layout(a.K, a.s, fa.numRegs);
+  const SelLayout lay = sel_layout(a.K, a.s, fa.numRegs, H16);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)(ntile * 4), kSelThreads, lay.total, st>>>(a, lay, a0c, tile0);
   return cudaGetLastError();
 }
 
-template <bool EXACT>
+template <bool EXACT, bool H16>
 cudaError_t select_dispatch(const OmpArgs &a, const float *a0c, int64_t g0, int64_t nt, cudaStream_t st) {
   const int kpl = (a.K + 31) / 32;
   if (a.m <= 64) {
-    return kpl <= 4 ? launch_select<4, 2, EXACT>(a, a0c, g0, nt, st)
-         : kpl <= 8 ? launch_select<8, 2, EXACT>(a, a0c, g0, nt, st)
-         : kpl <= 16 ? launch_select<16, 2, EXACT>(a, a0c, g0, nt, st)
-                     : launch_select<32, 2, EXACT>(a, a0c, g0, nt, st);
+    return kpl <= 4 ? launch_select<4, 2, EXACT, H16>(a, a0c, g0, nt, st)
+         : kpl <= 8 ? launch_select<8, 2, EXACT, H16>(a, a0c, g0, nt, st)
+         : kpl <= 16 ? launch_select<16, 2, EXACT, H16>(a, a0c, g0, nt, st)
+                     : launch_select<32, 2, EXACT, H16>(a, a0c, g0, nt, st);
   }
-  return kpl <= 4 ? launch_select<4, 8, EXACT>(a, a0c, g0, nt, st)
-       : kpl <= 8 ? launch_select<8, 8, EXACT>(a, a0c, g0, nt, st)
-       : kpl <= 16 ? launch_select<16, 8, EXACT>(a, a0c, g0, nt, st)
-                   : launch_select<32, 8, EXACT>(a, a0c, g0, nt, st);
+  return kpl <= 4 ? launch_select<4, 8, EXACT, H16>(a, a0c, g0, nt, st)
+       : kpl <= 8 ? launch_select<8, 8, EXACT, H16>(a, a0c, g0, nt, st)
+       : kpl <= 16 ? launch_select<16, 8, EXACT, H16>(a, a0c, g0, nt, st)
+                   : launch_select<32, 8, EXACT, H16>(a, a0c, g0, nt, st);
 }
 
 }  // namespace
@@ -430,7 +439,7 @@ cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, vo
 }
 
 cudaError_t launch_gram_tc(const void *hi, const void *lo, int K, int m, int L, float *G, int32_t *err,
-                           cudaStream_t st) {
+                           cudaStream_t st, void *G16) {
   if (L <= 0) return cudaSuccess;
   const int Kp = round16(K), mp = round16(m);
   const size_t tile = (size_t)128 * mp * 2;
@@ -441,13 +450,16 @@ cudaError_t launch_gram_tc(const void *hi, const void *lo, int K, int m, int L, 
   if (e != cudaSuccess) return e;
   dim3 grid((Kp + 127) / 128, (Kp + kGramNG - 1) / kGramNG, L);
   gram_tc_kernel<<<grid, 128, smem, st>>>(static_cast<const unsigned char *>(hi),
-                                          static_cast<const unsigned char *>(lo), K, Kp, mp, all4, G, err);
+                                          static_cast<const unsigned char *>(lo), K, Kp, mp, all4, G, err,
+                                          static_cast<__half *>(G16));
   return cudaGetLastError();
 }
 
 cudaError_t launch_omp_select(const OmpArgs &a, const float *a0c, int64_t tile0, int64_t ntile, bool exact,
-                              cudaStream_t st) {
-  return exact ? select_dispatch<true>(a, a0c, tile0, ntile, st) : select_dispatch<false>(a, a0c, tile0, ntile, st);
+                              cudaStream_t st, bool h16) {
+  if (exact) return select_dispatch<true, false>(a, a0c, tile0, ntile, st);
+  return h16 && a.G16 ? select_dispatch<false, true>(a, a0c, tile0, ntile, st)
+                      : select_dispatch<false, false>(a, a0c, tile0, ntile, st);
 }
 
 int omp_tc_tile_signals(int K, int m, int s) {
@@ -483,7 +495,7 @@ cudaError_t launch_omp_tc(const OmpArgs &a, float *a0c, cudaStream_t st) {
     // solved with the factor of the FP32 Gram, within 2^-16 of the exact one)
     // removes it to about 2^-16 kappa(G_SS) of that rounding, so no separate
     // refit from D_S^T y is needed
-    if ((e = select_dispatch<false>(a, a0c, g0, nt, st)) != cudaSuccess) return e;
+    if ((e = launch_omp_select(a, a0c, g0, nt, false, st, a.G16 != nullptr)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

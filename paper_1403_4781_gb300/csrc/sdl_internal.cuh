@@ -79,7 +79,8 @@ struct sdl_ctx {
   int opt_graph = 0;             // replay training loops as captured CUDA graphs
   int opt_replace = 0;           // atom replacement after every MOD update: min_use (0 = off)
   int opt_omp_form = 0;          // FP32 OMP: 0 automatic, 1 fused kernel, 2 correlation GEMM + selection
-  int opt_bf16_form = 0;         // BF16 OMP: 0 automatic, 1 Batch-OMP selection, 2 residual form
+  int opt_bf16_form = 0;         // BF16 OMP: 0 automatic, 1 Batch-OMP selection, 2 residual form,
+                                 // 3 Batch-OMP with a half-precision Gram copy in the running update
   long long opt_wait_limit = 1ll << 24;   // polls before a barrier wait of the wide solve gives up
   int opt_wait_test = 0;         // 1: one block of each wide-solve group leaves at once
   int opt_mod_mixed = 1;         // FP32 data: 1 the checked FP32 pass of the tiled solve may run, 0 FP64 only
@@ -134,6 +135,7 @@ struct OmpArgs {
   int Kp, mp;             // K and m rounded up to multiples of 16
   int32_t *err;           // device word: bit 0 set when a bounded wait gave up
   int64_t a0_cap;         // bytes of one alpha0 scratch chunk (0: 1 GiB)
+  const void *G16;        // BF16 path: half-precision copy of G for the running update (or null)
 };
 template <typename T>
 cudaError_t launch_omp(const OmpArgs &a, int num_sms, cudaStream_t st);
@@ -145,8 +147,9 @@ inline int round16(int x) { return (x + 15) & ~15; }
 cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, void *lo_img, cudaStream_t st);
 // G = hi hi^T + hi lo^T + lo hi^T per dictionary on the tensor cores (FP32
 // accumulation, about 2^-16 relative to the exact Gram of D).
+// G16 (or null): a half-precision copy of G written beside it.
 cudaError_t launch_gram_tc(const void *hi, const void *lo, int K, int m, int L, float *G, int32_t *err,
-                           cudaStream_t st);
+                           cudaStream_t st, void *G16 = nullptr);
 // Correlations of 128-signal tiles on the tensor cores into the scratch a0c
 // (omp_tc_chunk_tiles tiles of 128 x K floats at a time), then the selection
 // loop from there.
@@ -164,8 +167,9 @@ cudaError_t launch_omp_rtc(const OmpArgs &a, const void *img, cudaStream_t st);
 // The selection kernel over 128-signal tiles tile0 .. tile0+ntile-1 whose
 // alpha0 rows are in a0c (FP32 data).  exact: alpha0 came from BF16 products,
 // so the coefficients are refitted from D_S^T y.
+// h16: the running update reads the half copy a.G16 of the Gram.
 cudaError_t launch_omp_select(const OmpArgs &a, const float *a0c, int64_t tile0, int64_t ntile, bool exact,
-                              cudaStream_t st);
+                              cudaStream_t st, bool h16 = false);
 // FP32 OMP in two kernels: FFMA correlation GEMM of 128-signal tiles into a0c,
 // then the selection kernel (same plan and scratch as the BF16 path).
 cudaError_t launch_omp_split_f32(const OmpArgs &a, float *a0c, cudaStream_t st);

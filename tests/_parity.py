@@ -84,15 +84,24 @@ def step_correlations(D, y, S):
     return c, W, r
 
 
-def corr_error_bound(D, y, S, W, e, r=None):
+U16 = 2.0 ** -11
+
+
+def corr_error_bound(D, y, S, W, e, r=None, h16=False):
     """Per-atom bound on the error of the correlation the GPU compares at a
     step with prefix S.  Running correlations (Batch-OMP): e (a_j + |w_j|^T a_S),
-    a_j = sum_i |d_ji y_i|.  Recomputed from the residual (r given): e b_j,
-    b_j = sum_i |d_ji r_i|."""
+    a_j = sum_i |d_ji y_i|; with h16 the running update reads a half-precision
+    copy of G (round to nearest, u = 2^-11 per entry), which adds
+    u sum_p |G_jp x_p|, x the prefix's coefficients.  Recomputed from the
+    residual (r given): e b_j, b_j = sum_i |d_ji r_i|."""
     if r is not None:
         return e * (np.abs(D) @ np.abs(r))
     a = np.abs(D) @ np.abs(y)
-    return e * (a + (np.abs(W).T @ a[list(S)] if len(S) else 0.0))
+    E = e * (a + (np.abs(W).T @ a[list(S)] if len(S) else 0.0))
+    if h16 and len(S):
+        x, *_ = np.linalg.lstsq(D[list(S)].T, y, rcond=None)
+        E = E + U16 * (np.abs(D @ D[list(S)].T) @ np.abs(x))
+    return E
 
 
 def _first_difference(gi, gn, oi, on):
@@ -102,7 +111,7 @@ def _first_difference(gi, gn, oi, on):
     return k, g, o
 
 
-def _near_tie(D, y, gi, gn, oi, on, orc_gap_k, tol_a, tol_b, e, residual=False):
+def _near_tie(D, y, gi, gn, oi, on, orc_gap_k, tol_a, tol_b, e, residual=False, h16=False):
     """Checks (a) with tolerance tol_a(E, o, g) and (b) with tol_b(E, o, g) at
     the first differing step (E: the per-atom bound there, of the residual form
     when `residual`); returns whether that step is at rounding level (the
@@ -110,7 +119,7 @@ def _near_tie(D, y, gi, gn, oi, on, orc_gap_k, tol_a, tol_b, e, residual=False):
     k, g, o = _first_difference(gi, gn, oi, on)
     S = [int(v) for v in gi[:k]]
     c, W, r = step_correlations(D, y, S)
-    E = corr_error_bound(D, y, S, W, e, r if residual else None)
+    E = corr_error_bound(D, y, S, W, e, r if residual else None, h16=h16 and not residual)
     if o >= 0 and g >= 0:
         assert orc_gap_k < tol_a(E, o, g), (
             f"support differs at step {k} (gpu {gi.tolist()} orc {oi.tolist()}) but the oracle gap there is "
@@ -217,7 +226,8 @@ def compare_codes(D, Y, gpu_idx, gpu_val, gpu_nnz, gpu_r2, orc, gap_tol, coef_rt
     return stats
 
 
-def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0.05, residual=False, eps=None):
+def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0.05, residual=False, eps=None,
+                     h16=False):
     """BF16-operand correlations (tcgen05) with FP32 refits: every code is valid
     on its own support (exact least squares within coef_rtol, the reported
     residual that fit's); a support may differ from the oracle's only at a step
@@ -227,7 +237,9 @@ def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0
     the signals may differ at steps that are not at rounding level.
     residual: the path recomputed D^T r from the BF16-rounded residual at every
     step, so E is the residual form's bound e sum_i |d_ji r_i| (tighter as the
-    residual shrinks).  eps: the error-constrained stop; a code that agrees
+    residual shrinks).  h16: the Batch-OMP form's running update read a
+    half-precision copy of the Gram (form 3), whose rounding adds
+    2^-11 sum_p |G_jp x_p| to E.  eps: the error-constrained stop; a code that agrees
     with the oracle's on their common prefix but stops at another length is a
     near-tie on the stop itself when the prefix's least-squares residual norm
     is eps to within 1e-4 eps (counted with the rounding-level ones).  Returns
@@ -262,7 +274,8 @@ def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0
             kk, _, _ = _first_difference(idx[i], k, orc["idx"][i], int(orc["nnz"][i]))
             gk = orc["gap"][i][kk] if kk < s else np.inf
             tol = lambda E, o, g: 1.25 * (E[o] + E[g])  # noqa: E731
-            if _near_tie(D64, Y64[i], idx[i], k, orc["idx"][i], int(orc["nnz"][i]), gk, tol, tol, e16, residual):
+            if _near_tie(D64, Y64[i], idx[i], k, orc["idx"][i], int(orc["nnz"][i]), gk, tol, tol, e16, residual,
+                         h16):
                 rounding += 1
             else:
                 excused += 1

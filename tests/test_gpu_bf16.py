@@ -46,12 +46,13 @@ def _problem(seed, m, K, n, s, sigma):
     return D0, Y
 
 
-@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("form", [1, 2, 3])
 @pytest.mark.parametrize("m,K,n,s", [(64, 256, 4133, 6), (64, 128, 700, 5), (144, 512, 1500, 10),
                                      (30, 60, 333, 6), (256, 1024, 300, 16)])
 def test_bf16_omp_matches_oracle(m, K, n, s, form):
-    """Both BF16 forms (1: Batch-OMP selection from alpha0; 2: residual form)
-    under the Batch-OMP rule, whose bound covers both."""
+    """The BF16 forms (1: Batch-OMP selection from alpha0; 3: the same with a
+    half-precision Gram copy in the running update; 2: residual form) under the
+    Batch-OMP rule with the half-precision term, whose bound covers all three."""
     D, Y = _problem(400 + m + K, m, K, n, min(s, 6), 0.01)
     ctx = sdl.context(0)
     ctx.set_option(sdl.OPT_BF16_FORM, form)
@@ -62,7 +63,7 @@ def test_bf16_omp_matches_oracle(m, K, n, s, form):
         ctx.set_option(sdl.OPT_BF16_FORM, 0)
     orc = oracle.omp(D.astype(np.float64), Y.astype(np.float64), s)
     excused, rounding = check_bf16_codes(D, Y, idx.cpu().numpy(), val.cpu().numpy(), nnz.cpu().numpy(),
-                                         r2.cpu().numpy(), orc, max_excused=CAPS[(m, K)])
+                                         r2.cpu().numpy(), orc, max_excused=CAPS[(m, K)], h16=True)
     # near-tie picks cost little: mean residual energy within 5 % of the oracle's
     # (measured 2.7 % at m=30, K=60 where ties are most frequent)
     assert r2.cpu().numpy().astype(np.float64).mean() <= 1.05 * orc["resid2"].mean() + 1e-9
@@ -84,7 +85,9 @@ def test_bf16_gram_and_correlation_exact_on_bf16_representable_inputs():
     D = (rng.integers(-8, 9, size=(K, m)) / 8.0).astype(np.float32)
     Y = (rng.integers(-8, 9, size=(n, m)) / 8.0).astype(np.float32)
     ctx = sdl.context(0)
-    ctx.set_option(sdl.OPT_BF16_FORM, 1)   # the Batch-OMP form: alpha0 and G exact on these inputs
+    # the Batch-OMP form with the FP32 Gram throughout: alpha0 and G exact on
+    # these inputs (form 3's half-precision copy of G would not be: |G| reaches 64)
+    ctx.set_option(sdl.OPT_BF16_FORM, 1)
     try:
         idx, val, nnz, r2 = (x.cpu().numpy() for x in sdl.omp(_t(D), _t(Y), s, prec=sdl.PREC_BF16))
     finally:
