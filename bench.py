@@ -12,8 +12,9 @@ One step = split gather -> initial atoms -> local training -> scaled stack +
 merge training -> final coding -> residual.
 
 The chosen form (batched launches, training loops replayed as CUDA graphs,
-autotuned FP64 MOD solve, BF16 tensor-core correlations and Gram with FP32
-refits) is timed against the plain form (the same algorithm with one launch
+autotuned MOD solve: a checked FP32 solve with FP64 re-solves where the check
+fails, BF16 tensor-core correlations and Gram with an FP32 correction step) is
+timed against the plain form (the same algorithm with one launch
 sequence per subset, FP32 CUDA-core correlations, no graphs), both to the
 RMSE they reach.  The split-and-merge FP32 workload of 200,000 signals
 (m=64, K=256, L=100 x 2,000) is measured in the same run as an extra key, and
@@ -360,7 +361,7 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
 
     # ---- the same form with the other coding precisions (graphs as above)
     labels = {"fp32": "FP32 CUDA-core correlations and Gram",
-              "bf16": "BF16 tensor-core correlations and Gram (two-term split) with FP32 refits",
+              "bf16": "BF16 tensor-core correlations and Gram (two-term split) with an FP32 correction step",
               "f32x3": "FP32-accurate tensor-core correlations and Gram (two-term TF32 split)"}
     alt_forms = {}
     for alt in [a for a in ("fp32", "bf16", "f32x3") if a != chosen]:
@@ -474,7 +475,7 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
                  if name == "patches" else "synthetic (seeded; Sec. 3.1 data model)"),
         "config": workload_config(p, name, world),
         "form": "chosen: batched (all subsets of a phase per launch), training loops replayed as CUDA graphs, "
-                "autotuned FP64 MOD solve, " + labels[chosen] + "; no proposer (see proposer_final_coding)",
+                "autotuned MOD solve (checked FP32 solve, FP64 where the check fails or is faster), " + labels[chosen] + "; no proposer (see proposer_final_coding)",
         "signals_per_step": n_sig,
         "omp_stage": {"signals_per_s": n_sig / (omp_ms / 1e3) if omp_ms > 0 else None, "ms_per_step": omp_ms,
                       "kernels": [k for k in omp_names if k in prof],

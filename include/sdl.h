@@ -380,7 +380,13 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     every candidate on the call's own inputs with CUDA events (this
  *     synchronises the stream once) and keeps the fastest for the context;
  *     calls made while the stream is being captured use a rule on the shape
- *     instead.  0 = always use that rule (and forget tuned shapes).
+ *     instead.  The same holds for the selection launch of the two-kernel
+ *     coding passes (FP32 form 2, BF16 form 1 or 3, F32X3) where
+ *     SDL_OPT_SEL_SPW and SDL_OPT_SEL_GCACHE are both 0 and the call has at
+ *     least two 128-signal tiles per SM: the first call for a shape
+ *     (precision, number of subsets, K, m, s, tiles rounded down to a power of
+ *     two) runs the whole pass once per selection shape and keeps the fastest.
+ *     0 = always use that rule (and forget tuned shapes).
  *   SDL_OPT_GRAPH: 1 = the training loops of sdl_local_train and sdl_merge run
  *     as CUDA graphs: the first call with a given set of buffers, sizes and
  *     options runs eagerly, the second captures the iterations and launches
@@ -407,15 +413,23 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     m <= 256; other shapes run form 1).  All correct the coefficients on the
  *     chosen support in FP32 with one refinement step; they may choose
  *     differently among atoms whose correlations tie to within BF16 rounding.
+ *   SDL_OPT_SEL_SPW: signals per warp of the selection launch of the
+ *     two-kernel coding passes: 1, 2 or 4, or 0 (default) for automatic (the
+ *     autotuner's choice, else 4).
+ *   SDL_OPT_SEL_GCACHE: the Gram columns of the support that each warp of
+ *     that launch caches in shared memory: 1 = as many as fit, 2 = none, 0
+ *     (default) = automatic (the autotuner's choice, else as many as fit).
+ *     Neither option changes the result.
  *   SDL_OPT_WAIT_LIMIT: polls (64 ns apart) before a barrier wait of the wide
  *     solve gives up, default 2^24; the call then returns SDL_ETIMEOUT with the
  *     atoms unchanged and the context usable.  The same number, capped at
- *     2^22, bounds the mbarrier waits of the TF32 tensor-core kernels
- *     (SDL_PREC_F32X3).
+ *     2^22, bounds the mbarrier waits of the persistent tensor-core
+ *     correlation and Gram kernels (SDL_PREC_BF16 correlations,
+ *     SDL_PREC_F32X3).
  *   SDL_OPT_WAIT_TEST: 1 makes one block of every wide-solve group leave at
  *     once, so that the others' first barrier wait runs out, and the loader
- *     role of the TF32 tensor-core kernels leave before its first copy, so
- *     that the MMA issuer's first wait runs out: the tests of the bounded
+ *     role of the persistent tensor-core kernels leave before its first copy,
+ *     so that the MMA issuer's first wait runs out: the tests of the bounded
  *     waits (default 0).
  *   SDL_OPT_REPLACE: min_use of the atom replacement (sdl_replace_atoms) run
  *     after every MOD update of the training loops.  0 (default) = off, the
@@ -436,7 +450,9 @@ typedef enum {
   SDL_OPT_WAIT_TEST = 11,
   SDL_OPT_MOD_MIXED = 12,
   SDL_OPT_MOD_CHECK_TOL = 13,
-  SDL_OPT_A0_CHUNK_MB = 14
+  SDL_OPT_A0_CHUNK_MB = 14,
+  SDL_OPT_SEL_SPW = 15,
+  SDL_OPT_SEL_GCACHE = 16
 } sdl_option;
 sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value);
 

@@ -100,6 +100,7 @@ OPT_OMP_FORM = 8
 OPT_BF16_FORM = 9
 OPT_WAIT_LIMIT, OPT_WAIT_TEST = 10, 11
 OPT_MOD_MIXED, OPT_MOD_CHECK_TOL, OPT_A0_CHUNK_MB = 12, 13, 14
+OPT_SEL_SPW, OPT_SEL_GCACHE = 15, 16
 
 
 def lib() -> ctypes.CDLL:

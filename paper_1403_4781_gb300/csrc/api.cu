@@ -418,43 +418,115 @@ int split_kernels(const OmpArgs &oa) {
   return oa.total_tiles > 0 ? 2 * (int)((oa.total_tiles + chunk - 1) / chunk) : 0;
 }
 
-// One BF16 coding pass: BF16 images of D (img holds hi, then lo), Gram and
-// correlations on the tensor cores, selection loop, FP32 refit on the support.
-cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *err, float *a0c, void *G16) {
-  // only form 3 reads the half-precision Gram copy in the running update
-  if (ctx->opt_bf16_form != 3) G16 = nullptr;
-  oa.G16 = G16;
-  cudaStream_t sm = ctx->stream;
-  void *lo = static_cast<unsigned char *>(img) + tc_image_bytes(oa.L, oa.K, oa.m);
-  oa.Dimg = img;
-  oa.Kp = round16(oa.K);
-  oa.mp = round16(oa.m);
-  oa.err = err;
-  oa.G = G;
-  cudaError_t e = timed(ctx, "bf16_image", 1, [&] {
-    return launch_bf16_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, img, lo, sm);
-  });
-  if (e != cudaSuccess) return e;
-  e = timed(ctx, "gram_tc", 1, [&] { return launch_gram_tc(img, lo, oa.K, oa.m, oa.L, G, err, sm, G16); });
-  if (e != cudaSuccess) return e;
-  if (ctx->opt_bf16_form == 2 && omp_rtc_supported(oa.K, oa.m, oa.s)) {
-    // the residual form's own image (256-atom x 64-entry slabs) in the third slot
-    void *rimg = static_cast<unsigned char *>(img) + 2 * tc_image_bytes(oa.L, oa.K, oa.m);
-    e = timed(ctx, "rtc_image", 1, [&] {
-      return launch_rtc_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, rimg, sm);
-    });
-    if (e != cudaSuccess) return e;
-    return timed(ctx, "omp_rtc", 1, [&] { return launch_omp_rtc(oa, rimg, sm); });
+// Autotuner of the selection launch of the two-kernel coding passes: on the
+// first call of a shape (tag, subsets, K, m, s, whether eps stops early, tiles
+// rounded down to a power of two) with at least two 128-signal tiles per SM,
+// the whole pass (correlations and selection, run()) is run once per selection
+// shape (4, 2 or 1 signals per warp; the G-column cache as large as fits, or
+// none) and timed with CUDA events, the pass of under 20 ms twice (best of
+// two); the fastest shape is cached in the context.  Every shape computes the
+// same codes (each signal's arithmetic and its order do not depend on it), so
+// the timing runs cost only time.  Options set by hand, a stream being
+// captured, or SDL_OPT_AUTOTUNE = 0: the cached shape, else 4 signals per warp
+// and the cache as large as fits.
+template <class Run>
+cudaError_t tune_select(sdl_ctx *ctx, OmpArgs &oa, const char *tag, Run &&run) {
+  const int gc_of[3] = {0, 0, -1};
+  oa.sel_spw = ctx->opt_sel_spw != 0 ? ctx->opt_sel_spw : 4;
+  oa.sel_gcn = gc_of[ctx->opt_sel_gcache];
+  if (ctx->opt_sel_spw != 0 || ctx->opt_sel_gcache != 0) return cudaSuccess;
+  int lg = 0;
+  while (lg < 62 && ((int64_t)2 << lg) <= oa.total_tiles) ++lg;
+  const std::string key = std::string(tag) + ":" + std::to_string(oa.L) + ":" + std::to_string(oa.K) + ":" +
+                          std::to_string(oa.m) + ":" + std::to_string(oa.s) + ":" +
+                          std::to_string(oa.eps > 0 ? 1 : 0) + ":" + std::to_string(lg);
+  auto it = ctx->tuned_sel.find(key);
+  if (it != ctx->tuned_sel.end()) {
+    oa.sel_spw = it->second.spw;
+    oa.sel_gcn = it->second.gcn;
+    return cudaSuccess;
   }
-  return timed(ctx, "omp_tc", split_kernels(oa), [&] { return launch_omp_tc(oa, a0c, sm); });
+  cudaStream_t sm = ctx->stream;
+  cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(sm, &capst) != cudaSuccess) {
+    cudaGetLastError();
+    capst = cudaStreamCaptureStatusActive;
+  }
+  if (!ctx->opt_autotune || capst != cudaStreamCaptureStatusNone || oa.total_tiles < 2 * (int64_t)ctx->num_sms)
+    return cudaSuccess;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int spws[3] = {4, 2, 1}, gcns[2] = {0, -1};
+  int best_spw = 4, best_gcn = 0;
+  float best = 3.4e38f;
+  for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      oa.sel_spw = spws[a];
+      oa.sel_gcn = gcns[b];
+      float ms_best = 3.4e38f;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(e0, sm);
+        if (e == cudaSuccess) e = run();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, sm);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < ms_best) ms_best = ms;
+        if (ms_best >= 20.f) break;
+      }
+      if (e == cudaSuccess && ms_best < best) {
+        best = ms_best;
+        best_spw = spws[a];
+        best_gcn = gcns[b];
+      }
+    }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  oa.sel_spw = best_spw;
+  oa.sel_gcn = best_gcn;
+  if (e == cudaSuccess) ctx->tuned_sel[key] = sdl_ctx::TunedSelect{best_spw, best_gcn};
+  return e;
 }
 
-// Bounds of the TF32 tensor-core kernels' mbarrier waits: SDL_OPT_WAIT_LIMIT
+// Bounds of the tensor-core kernels' mbarrier waits: SDL_OPT_WAIT_LIMIT
 // polls, capped at 2^22 (each poll may suspend the thread for a while);
 // SDL_OPT_WAIT_TEST makes their loader leave at once.
 X3Wait x3_wait(const sdl_ctx *ctx) {
   const long long lim = ctx->opt_wait_limit < (1LL << 22) ? ctx->opt_wait_limit : (1LL << 22);
   return X3Wait{(int)(lim > 0 ? lim : 1), ctx->opt_wait_test ? 1 : 0};
+}
+
+// One BF16 coding pass: BF16 images of D (img holds hi, lo and the slab
+// image), Gram and correlations on the tensor cores, selection loop with its
+// FP32 correction step on the support.
+cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *err, float *a0c, void *G16) {
+  // only form 3 reads the half-precision Gram copy in the running update
+  if (ctx->opt_bf16_form != 3) G16 = nullptr;
+  oa.G16 = G16;
+  cudaStream_t sm = ctx->stream;
+  // slots: the hi and lo images of the split Gram, then the slab image that
+  // the correlation kernel and the residual form read
+  void *lo = static_cast<unsigned char *>(img) + tc_image_bytes(oa.L, oa.K, oa.m);
+  void *simg = static_cast<unsigned char *>(img) + 2 * tc_image_bytes(oa.L, oa.K, oa.m);
+  oa.err = err;
+  oa.G = G;
+  cudaError_t e = timed(ctx, "bf16_image", 2, [&] {
+    cudaError_t r = launch_bf16_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, img, lo, sm);
+    return r != cudaSuccess ? r : launch_rtc_image(static_cast<const float *>(oa.D), oa.K, oa.m, oa.L, simg, sm);
+  });
+  if (e != cudaSuccess) return e;
+  e = timed(ctx, "gram_tc", 1, [&] { return launch_gram_tc(img, lo, oa.K, oa.m, oa.L, G, err, sm, G16); });
+  if (e != cudaSuccess) return e;
+  if (ctx->opt_bf16_form == 2 && omp_rtc_supported(oa.K, oa.m, oa.s))
+    return timed(ctx, "omp_rtc", 1, [&] { return launch_omp_rtc(oa, simg, sm); });
+  auto pass = [&] { return launch_omp_tc(oa, simg, a0c, ctx->num_sms, x3_wait(ctx), sm); };
+  e = tune_select(ctx, oa, G16 ? "bf16h" : "bf16", [&] {
+    ctx->launches += split_kernels(oa);
+    return pass();
+  });
+  if (e != cudaSuccess) return e;
+  return timed(ctx, "omp_tc", split_kernels(oa), pass);
 }
 
 // One FP32-accurate tensor-core coding pass: TF32 hi and lo images of D (img
@@ -474,9 +546,26 @@ cudaError_t run_omp_x3(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *
                           x3_wait(ctx), sm);
   });
   if (e != cudaSuccess) return e;
-  return timed(ctx, "omp_x3", split_kernels(oa), [&] {
-    return launch_omp_x3(oa, img, lo, a0c, ctx->num_sms, x3_wait(ctx), sm);
+  auto pass = [&] { return launch_omp_x3(oa, img, lo, a0c, ctx->num_sms, x3_wait(ctx), sm); };
+  e = tune_select(ctx, oa, "x3", [&] {
+    ctx->launches += split_kernels(oa);
+    return pass();
   });
+  if (e != cudaSuccess) return e;
+  return timed(ctx, "omp_x3", split_kernels(oa), pass);
+}
+
+// The FP32 two-kernel coding pass (correlation GEMM, then the selection
+// kernel) with the tuned selection launch; the Gram is the caller's.
+cudaError_t run_omp_split(sdl_ctx *ctx, OmpArgs &oa, float *a0c) {
+  cudaStream_t sm = ctx->stream;
+  auto pass = [&] { return launch_omp_split_f32(oa, a0c, sm); };
+  cudaError_t e = tune_select(ctx, oa, "f32", [&] {
+    ctx->launches += split_kernels(oa);
+    return pass();
+  });
+  if (e != cudaSuccess) return e;
+  return timed(ctx, "omp_split", split_kernels(oa), pass);
 }
 
 // Read back the error word of the tensor-core kernels (synchronises).
@@ -668,7 +757,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
         e = run_omp_x3(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c);
       } else if (split) {
         SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
-        e = timed(ctx, "omp_split", split_kernels(oa), [&] { return launch_omp_split_f32(oa, a0c, sm); });
+        e = run_omp_split(ctx, oa, a0c);
       } else {
         SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
         e = timed(ctx, "omp", 1, [&] { return launch_omp<T>(oa, ctx->num_sms, sm); });
@@ -703,13 +792,14 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
     if ((st = run_loop()) != SDL_OK) return st;
   } else {
     char kb[512];
-    snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d:%d:%d:%lld:%d",
+    snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d:%d:%d:%lld:%d:%d:%d",
              sizeof(T), (int)bf16 + 2 * (int)x3, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
              (void *)d_off, m, K, s, L, (long long)n, (long long)tiles, (long long)ma.total_tiles, eps, iters,
              ctx->opt_mod_solve * 2 + ctx->opt_mod_mixed, ctx->opt_tile, ctx->opt_cluster * 4 + ctx->opt_sm_blocks,
              ctx->opt_autotune,
              (int)ctx->tuned.size(), (ctx->opt_replace * 4 + ctx->opt_omp_form) * 4 + ctx->opt_bf16_form,
-             ctx->opt_wait_test, ctx->opt_wait_limit, ctx->opt_mod_check_ppb * 2048 + ctx->opt_a0_chunk_mb);
+             ctx->opt_wait_test, ctx->opt_wait_limit, ctx->opt_mod_check_ppb * 2048 + ctx->opt_a0_chunk_mb,
+             ctx->opt_sel_spw * 4 + ctx->opt_sel_gcache, (int)ctx->tuned_sel.size());
     const std::string key(kb);
     auto hit = ctx->graphs.find(key);
     if (hit != ctx->graphs.end()) {
@@ -871,8 +961,7 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
     if (!a0c) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
     SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<float>(static_cast<const float *>(D), m, K, L, static_cast<float *>(G),
                                 ctx->stream); }), "gram");
-    SDL_CUDA(timed(ctx, "omp_split", split_kernels(a), [&] { return launch_omp_split_f32(a, a0c, ctx->stream); }),
-             "omp");
+    SDL_CUDA(run_omp_split(ctx, a, a0c), "omp");
   } else {
     SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<float>(static_cast<const float *>(D), m, K, L, static_cast<float *>(G),
                                 ctx->stream); }), "gram");
@@ -1475,7 +1564,10 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
     case SDL_OPT_AUTOTUNE:
       if (value != 0 && value != 1) return set_error(ctx, SDL_EINVAL, "SDL_OPT_AUTOTUNE takes 0 or 1");
       ctx->opt_autotune = (int)value;
-      if (!value) ctx->tuned.clear();
+      if (!value) {
+        ctx->tuned.clear();
+        ctx->tuned_sel.clear();
+      }
       return SDL_OK;
     case SDL_OPT_SM_BLOCKS:
       if (value < 0 || value > 3) return set_error(ctx, SDL_EINVAL, "SDL_OPT_SM_BLOCKS takes 0 to 3");
@@ -1501,6 +1593,15 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
     case SDL_OPT_A0_CHUNK_MB:
       if (value < 0 || value > 1024) return set_error(ctx, SDL_EINVAL, "SDL_OPT_A0_CHUNK_MB takes 0 to 1024");
       ctx->opt_a0_chunk_mb = (int)value;
+      return SDL_OK;
+    case SDL_OPT_SEL_SPW:
+      if (value != 0 && value != 1 && value != 2 && value != 4)
+        return set_error(ctx, SDL_EINVAL, "SDL_OPT_SEL_SPW takes 0, 1, 2 or 4");
+      ctx->opt_sel_spw = (int)value;
+      return SDL_OK;
+    case SDL_OPT_SEL_GCACHE:
+      if (value < 0 || value > 2) return set_error(ctx, SDL_EINVAL, "SDL_OPT_SEL_GCACHE takes 0, 1 or 2");
+      ctx->opt_sel_gcache = (int)value;
       return SDL_OK;
     case SDL_OPT_MOD_CHECK_TOL:
       if (value < 1 || value > 1000000000)

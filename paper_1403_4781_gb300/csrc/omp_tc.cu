@@ -179,168 +179,325 @@ __global__ void __launch_bounds__(128) gram_tc_kernel(const unsigned char *__res
 }
 
 // ---- correlations: alpha0 = Y D^T of 128-signal tiles into global memory ----
-// One block per tile of 128 signals (the MMA's M), 8 warps.  The signal tile is
-// converted to a BF16 K-major image once (16-byte loads, eight warps so many
-// loads are in flight); dictionary tiles of 128 atoms stream in by bulk copies
-// into two buffers, and their products go to two TMEM accumulators, so the MMA
-// of tile nt+1 runs while tile nt is read out.  Warps w and w + 4 read the TMEM
-// lanes of rows 32 (w mod 4) .. + 31, each half of the columns.  Row r of the
-// tile's alpha0 block (atoms in order) is written to a0 + r * K.
-constexpr int kCorrThreads = 256;
-constexpr int kCorrNT = 128;
+// A persistent block per SM runs work items in turn: an item is a tile of 128
+// signals (the MMA's M) against one pass of 256 atoms (the MMA's N and one
+// 256-column TMEM accumulator).  The dictionary comes from its slab image
+// ([L][mp/64][Kp][64] BF16, Kp = K rounded up to 256: the 256 atoms x 64
+// entries of one pass and block are one contiguous 32 KB slab).  Four roles
+// meet only at mbarriers:
+//   warps 0-3  convert the tile's signal entries, 64 at a time, from FP32 into
+//              a 16 KB BF16 block image (three buffers); thread (w, lane) takes
+//              row lane & 7 of 8-row groups w, w + 4, w + 8, w + 12 and entry
+//              groups lane >> 3 and + 4, so a quarter-warp's 16-byte stores
+//              fill 128 contiguous bytes (no bank conflict); the next block's
+//              loads fly while the thread waits for a free buffer;
+//   warp 8     streams the pass's slabs into four stages by bulk copies;
+//   warp 9     issues per block four 128 x 256 x 16 MMAs into the item's
+//              accumulator (two, alternating by item), freeing each stage and
+//              signal buffer by tcgen05.commit;
+//   warps 4-7  read a finished accumulator out while the next item's products
+//              run into the other one: warp 4 + q owns TMEM lanes (tile rows)
+//              32 q .. 32 q + 31, passes each 32-column slice through a padded
+//              transpose buffer and stores it as four 128-byte row segments per
+//              instruction.
+// Every wait is bounded: a role that gives up sets the block's fail flag and
+// the error word; the others leave at their next check or bounded wait, the
+// loader waits for its copies in flight, the issuer for its products, and the
+// tensor memory is freed.
+constexpr int kC16Threads = 320;
+constexpr int kC16NT = 256;                                 // atoms per item
+constexpr int kC16KB = 64;                                  // signal entries per block
+constexpr int kC16Stages = 4;                               // dictionary slab stages
+constexpr int kC16ABuf = 3;                                 // signal block buffers
+constexpr uint32_t kC16Slab = (uint32_t)kC16NT * kC16KB * 2;   // 32 KB
+constexpr uint32_t kC16ABlk = 128u * kC16KB * 2;               // 16 KB
+constexpr int kC16Pitch = 36;   // floats per row of a read-out transpose buffer (32 + 4: no bank conflict)
 
-struct CorrLayout {
-  size_t aim, bim, bar, total;
+inline int round64c(int x) { return (x + 63) & ~63; }
+inline int round256c(int x) { return (x + 255) & ~255; }
+
+struct C16Job {
+  OmpArgs a;                 // K, m, L, Y and the tile plan
+  const unsigned char *img;  // slab image of D
+  float *out;                // alpha0 scratch: row (g - tile0) * 128 + r of tile g
+  int64_t tile0, ntile;
+  int nblk, Kp, npass;       // 64-entry blocks, K rounded up to 256, items per tile
+  int32_t *err;
+  int wait_limit;            // polls of a bounded wait
+  int leave;                 // 1: the loader leaves at once (a test of the bounded waits)
 };
 
-inline CorrLayout corr_layout(int mp) {
-  CorrLayout L{};
-  size_t off = 0;
-  L.aim = off; off += (size_t)128 * mp * 2;
-  L.bim = off; off += (size_t)2 * kCorrNT * mp * 2;
-  L.bar = off; off += 64;
-  L.total = off;
-  return L;
+struct C16Tile {
+  int t;              // dictionary
+  const float *rows;  // row 0 of the tile (pitch m)
+  int nrow;           // valid rows
+  float *out;         // output row 0 (pitch K)
+};
+
+__device__ __forceinline__ C16Tile c16_tile(const C16Job &j, int64_t g) {
+  C16Tile T;
+  T.t = find_subset(j.a.tile_start, j.a.L, g);
+  const int64_t row0 = j.a.offsets[T.t] + (g - j.a.tile_start[T.t]) * (int64_t)128;
+  const int64_t left = j.a.offsets[T.t + 1] - row0;
+  T.rows = static_cast<const float *>(j.a.Y) + (size_t)row0 * j.a.m;
+  T.nrow = left < 128 ? (int)left : 128;
+  T.out = j.out + (size_t)(g - j.tile0) * 128 * j.a.K;
+  return T;
 }
 
-__global__ void __launch_bounds__(kCorrThreads) corr_tc_kernel(OmpArgs a, CorrLayout lay, float *a0c, int64_t tile0) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  const int K = a.K, m = a.m, mp = a.mp, Kp = a.Kp;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t g = tile0 + blockIdx.x;
-  const int t = find_subset(a.tile_start, a.L, g);
-  const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)128;
-  const int64_t rows_left = a.offsets[t + 1] - row0;
-  const int nsig = rows_left < 128 ? (int)rows_left : 128;
-  const float *__restrict__ Y = static_cast<const float *>(a.Y);
-  const unsigned char *sub = static_cast<const unsigned char *>(a.Dimg) + (size_t)t * Kp * mp * 2;
-  unsigned char *Aim = smem + lay.aim;
-  unsigned char *Bim = smem + lay.bim;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + lay.bar);   // [0,1] loads, [2,3] MMA commits
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 4);
-  int *fail = reinterpret_cast<int *>(bar + 5);
-  constexpr int NT = kCorrNT;
-  const size_t btile = (size_t)NT * mp * 2;
-  const int ntiles = (K + NT - 1) / NT;
-  auto tile_bytes = [&](int nt) { return (uint32_t)min(NT, Kp - nt * NT) * (uint32_t)mp * 2u; };
+struct C16Bars {
+  uint64_t full_b[kC16Stages], empty_b[kC16Stages];
+  uint64_t full_a[kC16ABuf], empty_a[kC16ABuf];
+  uint64_t acc_full[2], acc_empty[2];
+  uint64_t done;
+  uint32_t tslot;
+  int fail;
+};
 
-  if (warp == 0) tc::tmem_alloc(tslot, 2 * NT);
+constexpr size_t kC16A = 0;                                             // signal block buffers
+constexpr size_t kC16B = kC16A + kC16ABuf * (size_t)kC16ABlk;           // slab stages
+constexpr size_t kC16T = kC16B + kC16Stages * (size_t)kC16Slab;         // read-out transpose buffers
+constexpr size_t kC16Bar = kC16T + 4 * 32 * kC16Pitch * sizeof(float);
+constexpr size_t kC16Smem = kC16Bar + sizeof(C16Bars);
+
+__global__ void __launch_bounds__(kC16Threads, 1) corr16_kernel(C16Job j) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  C16Bars *bars = reinterpret_cast<C16Bars *>(smem + kC16Bar);
+  volatile int *fail = &bars->fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K = j.a.K, m = j.a.m, nblk = j.nblk;
+  const int64_t nitem = j.ntile * j.npass;
+
+  if (warp == 9) tc::tmem_alloc(&bars->tslot, 2 * kC16NT);
   if (tid == 0) {
-    for (int q = 0; q < 4; ++q) tc::mbar_init(&bar[q], 1);
+    for (int q = 0; q < kC16Stages; ++q) {
+      tc::mbar_init(&bars->full_b[q], 1);
+      tc::mbar_init(&bars->empty_b[q], 1);
+    }
+    for (int q = 0; q < kC16ABuf; ++q) {
+      tc::mbar_init(&bars->full_a[q], 128);
+      tc::mbar_init(&bars->empty_a[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&bars->acc_full[q], 1);
+      tc::mbar_init(&bars->acc_empty[q], 128);
+    }
+    tc::mbar_init(&bars->done, 1);
+    bars->fail = 0;
     tc::mbar_fence_init();
-    *fail = 0;
-    for (int nt = 0; nt < 2 && nt < ntiles; ++nt) {
-      tc::mbar_expect_tx(&bar[nt], tile_bytes(nt));
-      tc::bulk_g2s(Bim + nt * btile, sub + (size_t)nt * NT * mp * 2, tile_bytes(nt), &bar[nt]);
-    }
   }
-  // signal tile -> BF16 A image (rows beyond the tile are zero); item q is
-  // entries 8 kc .. 8 kc + 7 of row r
-  const int kc8 = mp >> 3;
-  const bool vec = (m & 3) == 0;   // 16-byte aligned rows
-  constexpr int kU = 4;            // items whose loads are in flight together
-  for (int q0 = tid; q0 < 128 * kc8; q0 += kU * kCorrThreads) {
-    float f[kU][8];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int q = q0 + u * kCorrThreads;
-      const int r = q / kc8, k0 = (q - r * kc8) * 8;
-      const float *yr = Y + (size_t)(row0 + r) * m + k0;
-      if (q < 128 * kc8 && r < nsig && vec && k0 + 8 <= m) {
-        const float4 u0 = *reinterpret_cast<const float4 *>(yr);
-        const float4 u1 = *reinterpret_cast<const float4 *>(yr + 4);
-        f[u][0] = u0.x; f[u][1] = u0.y; f[u][2] = u0.z; f[u][3] = u0.w;
-        f[u][4] = u1.x; f[u][5] = u1.y; f[u][6] = u1.z; f[u][7] = u1.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) f[u][e] = (q < 128 * kc8 && r < nsig && k0 + e < m) ? yr[e] : 0.f;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int q = q0 + u * kCorrThreads;
-      if (q >= 128 * kc8) break;
-      const int r = q / kc8, kc = q - r * kc8;
-      uint32_t packed[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        __nv_bfloat162 b2 = __floats2bfloat162_rn(f[u][2 * e], f[u][2 * e + 1]);
-        packed[e] = *reinterpret_cast<uint32_t *>(&b2);
-      }
-      *reinterpret_cast<uint4 *>(Aim + tc::image_offset(r, kc * 8, mp)) =
-          make_uint4(packed[0], packed[1], packed[2], packed[3]);
-    }
-  }
-  tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t tbase = *tslot;
-  const uint32_t idesc = tc::idesc_bf16(128, NT);
-  const uint32_t sbo = (uint32_t)kc8 * 128;
-  // tile nt's product into TMEM columns (nt & 1) * 128 (thread 0)
-  auto issue = [&](int nt) {
-    const int b = nt & 1;
-    if (!tc::mbar_wait(&bar[b], (nt >> 1) & 1, kWaitLimit)) { *fail = 1; return; }
-    tc::fence_after();
-    const uint32_t bsm = tc::smem_u32(Bim + b * btile);
-    for (int ks = 0; ks < (mp >> 4); ++ks)
-      tc::mma_bf16(tbase + (uint32_t)(b * NT), tc::smem_desc(tc::smem_u32(Aim) + ks * 256, 128, sbo),
-                   tc::smem_desc(bsm + ks * 256, 128, sbo), idesc, ks > 0);
-    tc::mma_commit(&bar[2 + b]);
+  const uint32_t tbase = bars->tslot;
+  auto give_up = [&]() {
+    *fail = 1;
+    if (j.err) atomicOr(j.err, 1);
   };
-  if (tid == 0) issue(0);
-  const int quarter = warp & 3, half = warp >> 2;   // TMEM lanes 32 quarter .. + 31
-  const int row = 32 * quarter + lane;
-  float *arow = a0c + ((size_t)(g - tile0) * 128 + row) * K;
-  int nt = 0;
-  for (; nt < ntiles; ++nt) {
-    const int b = nt & 1;
-    if (tid == 0 && nt + 1 < ntiles && !*fail) issue(nt + 1);
-    if (!tc::mbar_wait(&bar[2 + b], (nt >> 1) & 1, kWaitLimit)) *fail = 1;
-    __syncthreads();
-    if (*fail) break;
-    tc::fence_after();
-    for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += 32) {
-      float v[32];
-      tc::tmem_ld32(tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * NT + c0), v);
-      const int col0 = nt * NT + c0;
-      if (row < nsig) {
-        if (col0 + 32 <= K && (K & 3) == 0) {
+
+  if (warp < 4) {
+    // ---- converters
+    const int rr = lane & 7, gq = lane >> 3;
+    const bool vec = (m & 3) == 0 && (reinterpret_cast<uintptr_t>(j.a.Y) & 15) == 0;
+    float4 v[4][2][2];   // [row group i][entry group gq + 4 h][half]
+    auto load = [&](const C16Tile &T, int b) {
 #pragma unroll
-          for (int e = 0; e < 32; e += 4)
-            *reinterpret_cast<float4 *>(arow + col0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-        } else {
+      for (int i = 0; i < 4; ++i) {
+        const int r = 8 * (warp + 4 * i) + rr;
 #pragma unroll
-          for (int e = 0; e < 32; ++e)
-            if (col0 + e < K) arow[col0 + e] = v[e];
+        for (int h = 0; h < 2; ++h) {
+          const int k = b * kC16KB + 8 * (gq + 4 * h);
+          const float *src = T.rows + (size_t)r * m + k;
+          const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (r >= T.nrow || k >= m) {
+            v[i][h][0] = z;
+            v[i][h][1] = z;
+          } else if (vec) {   // k + 4 <= m; entries k + 4 .. exist only if k + 8 <= m
+            v[i][h][0] = __ldg(reinterpret_cast<const float4 *>(src));
+            v[i][h][1] = k + 8 <= m ? __ldg(reinterpret_cast<const float4 *>(src + 4)) : z;
+          } else {
+            float e[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) e[q] = k + q < m ? src[q] : 0.f;
+            v[i][h][0] = make_float4(e[0], e[1], e[2], e[3]);
+            v[i][h][1] = make_float4(e[4], e[5], e[6], e[7]);
+          }
         }
       }
+    };
+    uint32_t cnt = 0;   // blocks converted
+    bool stop = false;
+    if ((int64_t)blockIdx.x < nitem) load(c16_tile(j, j.tile0 + blockIdx.x / j.npass), 0);
+    for (int64_t it = blockIdx.x; it < nitem && !stop; it += gridDim.x) {
+      const C16Tile T = c16_tile(j, j.tile0 + it / j.npass);
+      for (int b = 0; b < nblk; ++b) {
+        const int ab = (int)(cnt % kC16ABuf);
+        const uint32_t use = cnt / kC16ABuf;
+        if (use >= 1 && !tc::mbar_wait(&bars->empty_a[ab], (use - 1) & 1, j.wait_limit)) {
+          give_up();
+          stop = true;
+          break;
+        }
+        if (*fail) {
+          stop = true;
+          break;
+        }
+        unsigned char *A = smem + kC16A + (size_t)ab * kC16ABlk;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float4 x = v[i][h][0], y = v[i][h][1];
+            const __nv_bfloat162 p0 = __floats2bfloat162_rn(x.x, x.y), p1 = __floats2bfloat162_rn(x.z, x.w);
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(y.x, y.y), p3 = __floats2bfloat162_rn(y.z, y.w);
+            const uint32_t off = (uint32_t)((warp + 4 * i) * 1024 + (gq + 4 * h) * 128 + rr * 16);
+            *reinterpret_cast<uint4 *>(A + off) =
+                make_uint4(*reinterpret_cast<const uint32_t *>(&p0), *reinterpret_cast<const uint32_t *>(&p1),
+                           *reinterpret_cast<const uint32_t *>(&p2), *reinterpret_cast<const uint32_t *>(&p3));
+          }
+        }
+        tc::fence_proxy_async();
+        tc::mbar_arrive(&bars->full_a[ab]);
+        ++cnt;
+        if (b + 1 < nblk)
+          load(T, b + 1);
+        else if (it + gridDim.x < nitem)
+          load(c16_tile(j, j.tile0 + (it + gridDim.x) / j.npass), 0);
+      }
     }
-    tc::fence_before();
-    __syncthreads();   // buffer b (TMEM columns and B image) is free again
-    if (tid == 0 && nt + 2 < ntiles) {
-      tc::mbar_expect_tx(&bar[b], tile_bytes(nt + 2));
-      tc::bulk_g2s(Bim + b * btile, sub + (size_t)(nt + 2) * NT * mp * 2, tile_bytes(nt + 2), &bar[b]);
+  } else if (warp < 8) {
+    // ---- read-out: warp 4 + q owns TMEM lanes (tile rows) 32 q .. 32 q + 31
+    const int q = warp & 3;
+    float *tb = reinterpret_cast<float *>(smem + kC16T) + (size_t)q * 32 * kC16Pitch;
+    const bool vst = (K & 3) == 0;
+    const int sub = lane >> 3, c4 = 4 * (lane & 7);   // write phase: row 4 jj + sub, columns c4 .. c4 + 3
+    uint32_t cnt = 0;
+    for (int64_t it = blockIdx.x; it < nitem; it += gridDim.x, ++cnt) {
+      const int acc = cnt & 1;
+      const bool got = tc::mbar_wait(&bars->acc_full[acc], (cnt >> 1) & 1, j.wait_limit);
+      if (!__all_sync(0xffffffffu, got)) {   // the TMEM loads below need the whole warp
+        give_up();
+        break;
+      }
+      if (__any_sync(0xffffffffu, *fail != 0)) break;
+      tc::fence_after();
+      const C16Tile T = c16_tile(j, j.tile0 + it / j.npass);
+      const int c0 = (int)(it % j.npass) * kC16NT;
+      const int ncol = K - c0 < kC16NT ? K - c0 : kC16NT;
+      for (int c = 0; c < ncol; c += 32) {
+        float x[32];
+        tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kC16NT + c), x);
+#pragma unroll
+        for (int e = 0; e < 32; e += 4)
+          *reinterpret_cast<float4 *>(tb + lane * kC16Pitch + e) = make_float4(x[e], x[e + 1], x[e + 2], x[e + 3]);
+        __syncwarp();
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int rl = 4 * jj + sub, row = 32 * q + rl, col = c + c4;
+          const float4 y = *reinterpret_cast<const float4 *>(tb + rl * kC16Pitch + c4);
+          if (row >= T.nrow) continue;
+          float *o = T.out + (size_t)row * K + c0 + col;
+          if (vst && col + 4 <= ncol) {
+            *reinterpret_cast<float4 *>(o) = y;
+          } else {
+            if (col < ncol) o[0] = y.x;
+            if (col + 1 < ncol) o[1] = y.y;
+            if (col + 2 < ncol) o[2] = y.z;
+            if (col + 3 < ncol) o[3] = y.w;
+          }
+        }
+        __syncwarp();
+      }
+      tc::fence_before();
+      tc::mbar_arrive(&bars->acc_empty[acc]);
     }
-  }
-  if (*fail) {
-    // wait (bounded) for the bulk copies still in flight before the shared
-    // memory is given back: loads of tiles nt .. nt + 1 may be outstanding
-    if (tid == 0) {
-      for (int q = nt; q < nt + 2 && q < ntiles; ++q) tc::mbar_wait(&bar[q & 1], (q >> 1) & 1, kWaitLimit);
-      if (a.err) atomicOr(a.err, 1);
+  } else if (warp == 8) {
+    // ---- loader: the pass's slabs (32 KB each) into the stages
+    if (lane == 0 && !j.leave) {
+      uint32_t c = 0;   // slabs issued
+      bool stop = false;
+      for (int64_t it = blockIdx.x; it < nitem && !stop; it += gridDim.x) {
+        const int64_t g = j.tile0 + it / j.npass;
+        const int t = find_subset(j.a.tile_start, j.a.L, g);
+        const int p = (int)(it % j.npass);
+        for (int b = 0; b < nblk; ++b) {
+          const int s = (int)(c % kC16Stages);
+          const uint32_t u = c / kC16Stages;
+          if (u >= 1 && !tc::mbar_wait(&bars->empty_b[s], (u - 1) & 1, j.wait_limit)) {
+            give_up();
+            stop = true;
+            break;
+          }
+          if (*fail) {
+            stop = true;
+            break;
+          }
+          const size_t src = ((size_t)t * nblk + b) * (size_t)j.Kp * kC16KB * 2 + (size_t)p * kC16Slab;
+          tc::mbar_expect_tx(&bars->full_b[s], kC16Slab);
+          tc::bulk_g2s(smem + kC16B + (size_t)s * kC16Slab, j.img + src, kC16Slab, &bars->full_b[s]);
+          ++c;
+        }
+      }
+      // the shared memory outlives no copy: wait (bounded) for the last slab
+      // issued into every stage
+      for (int s = 0; s < kC16Stages; ++s)
+        if (c > (uint32_t)s) tc::mbar_wait(&bars->full_b[s], ((c - 1 - s) / kC16Stages) & 1, j.wait_limit);
+    }
+  } else {
+    // ---- issuer: four 128 x 256 x 16 products per block into the item's accumulator
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16(128, kC16NT);
+      const uint32_t abase = tc::smem_u32(smem + kC16A), bbase = tc::smem_u32(smem + kC16B);
+      uint32_t c = 0, nbk = 0, cnt = 0;
+      bool stop = false;
+      for (int64_t it = blockIdx.x; it < nitem && !stop; it += gridDim.x, ++cnt) {
+        const int acc = cnt & 1;
+        if (cnt >= 2 && !tc::mbar_wait(&bars->acc_empty[acc], ((cnt >> 1) - 1) & 1, j.wait_limit)) {
+          give_up();
+          break;
+        }
+        tc::fence_after();
+        const uint32_t d = tbase + (uint32_t)(acc * kC16NT);
+        for (int b = 0; b < nblk; ++b) {
+          const int ab = (int)(nbk % kC16ABuf), s = (int)(c % kC16Stages);
+          if (*fail || !tc::mbar_wait(&bars->full_a[ab], (nbk / kC16ABuf) & 1, j.wait_limit) ||
+              !tc::mbar_wait(&bars->full_b[s], (c / kC16Stages) & 1, j.wait_limit)) {
+            if (!*fail) give_up();
+            stop = true;
+            break;
+          }
+          tc::fence_after();
+          const uint32_t a_s = abase + (uint32_t)ab * kC16ABlk, b_s = bbase + (uint32_t)s * kC16Slab;
+#pragma unroll
+          for (int ks = 0; ks < kC16KB / 16; ++ks) {
+            const uint32_t o = (uint32_t)ks * 256;
+            tc::mma_bf16(d, tc::smem_desc(a_s + o, 128, 1024), tc::smem_desc(b_s + o, 128, 1024), idesc,
+                         b > 0 || ks > 0);
+          }
+          tc::mma_commit(&bars->empty_b[s]);
+          tc::mma_commit(&bars->empty_a[ab]);
+          ++c;
+          ++nbk;
+        }
+        if (stop) break;
+        tc::mma_commit(&bars->acc_full[acc]);
+      }
+      // every product issued has finished before the tensor memory is freed
+      tc::mma_commit(&bars->done);
+      if (!tc::mbar_wait(&bars->done, 0, j.wait_limit)) give_up();
     }
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, 2 * NT);
+  tc::fence_after();
+  if (warp == 9) tc::tmem_dealloc(tbase, 2 * kC16NT);
 }
 
 // ---- selection: the Batch-OMP loop and exact refit from alpha0 in global memory
-// A block covers a quarter (32 signals, 4 per warp) of a 128-signal tile; shared
-// memory holds only the per-warp factors and, when it fits, the G-column cache,
-// so many blocks share an SM to hide the loop's latency.
+// A block of 8 warps covers 8 spw signals of a 128-signal tile (spw signals per
+// warp, 16 / spw blocks per tile); shared memory holds only the per-warp
+// factors and, when it fits, the G-column cache, so many blocks share an SM to
+// hide the loop's latency.
 constexpr int kSelThreads = 256;
 
 struct SelLayout {
@@ -352,8 +509,9 @@ struct SelLayout {
 // Per-warp factor scratch, then as many of the support's G columns per warp as
 // fit the shared memory one block gets at the occupancy its registers allow
 // (the first picks' columns: column p is re-read by the s - 1 - p later
-// updates, so caching the first few saves most of the L2 reads).
-inline SelLayout sel_layout(int K, int s, int regs, bool h16) {
+// updates, so caching the first few saves most of the L2 reads), at most cap
+// columns when cap > 0 and none when cap < 0.
+inline SelLayout sel_layout(int K, int s, int regs, bool h16, int cap) {
   const int rr = (regs + 7) & ~7;
   int blocks = 65536 / (kSelThreads * (rr > 0 ? rr : 8));
   blocks = blocks < 1 ? 1 : (blocks > 8 ? 8 : blocks);
@@ -362,7 +520,9 @@ inline SelLayout sel_layout(int K, int s, int regs, bool h16) {
   L.lp = odd_pitch(s);
   const size_t ls = align16(sizeof(float) * (size_t)8 * s * L.lp);
   const size_t col = (h16 ? 2 : sizeof(float)) * (size_t)8 * K;   // one column for every warp
-  const int fit = budget > ls ? (int)((budget - ls) / col) : 0;
+  int fit = budget > ls ? (int)((budget - ls) / col) : 0;
+  if (cap < 0) fit = 0;
+  else if (cap > 0 && fit > cap) fit = cap;
   L.gcn = fit < s - 1 ? fit : (s > 1 ? s - 1 : 0);
   size_t off = 0;
   L.ls = off; off += ls;
@@ -371,22 +531,26 @@ inline SelLayout sel_layout(int K, int s, int regs, bool h16) {
   return L;
 }
 
+// Signals per warp of the selection kernel: 1, 2 or 4 (default 4).
+inline int sel_spw(const OmpArgs &a) { return a.sel_spw == 1 || a.sel_spw == 2 ? a.sel_spw : 4; }
+
 template <int KPL, int MU, bool EXACT, bool H16>
 __global__ void __launch_bounds__(kSelThreads, KPL <= 8 ? 4 : (KPL <= 16 ? 3 : 2)) omp_select_kernel(OmpArgs a, SelLayout lay, const float *a0c,
-                                                                 int64_t tile0) {
+                                                                 int64_t tile0, int spw) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int K = a.K, m = a.m, s = a.s;
   const int warp = threadIdx.x >> 5;
-  const int64_t g = tile0 + blockIdx.x / 4;
-  const int quarter = blockIdx.x & 3;
+  const int bpt = 16 / spw, nb = 8 * spw;   // blocks per tile, signals per block
+  const int64_t g = tile0 + blockIdx.x / bpt;
+  const int part = blockIdx.x % bpt;
   const int t = find_subset(a.tile_start, a.L, g);
-  const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)128 + quarter * 32;
+  const int64_t row0 = a.offsets[t] + (g - a.tile_start[t]) * (int64_t)128 + part * nb;
   const int64_t rows_left = a.offsets[t + 1] - row0;
   if (rows_left <= 0) return;   // whole block: nothing below is a block-wide barrier
-  const int nsig = rows_left < 32 ? (int)rows_left : 32;
+  const int nsig = rows_left < nb ? (int)rows_left : nb;
   const float *__restrict__ Dt = static_cast<const float *>(a.D) + (size_t)t * K * m;
   const float *__restrict__ Gt = static_cast<const float *>(a.G) + (size_t)t * K * K;
-  const float *a0 = a0c + ((size_t)(g - tile0) * 128 + quarter * 32) * K;
+  const float *a0 = a0c + ((size_t)(g - tile0) * 128 + part * nb) * K;
   float *Ls = reinterpret_cast<float *>(smem + lay.ls) + (size_t)warp * s * lay.lp;
   void *gc = nullptr;
   if (lay.gcn > 0)
@@ -394,7 +558,7 @@ __global__ void __launch_bounds__(kSelThreads, KPL <= 8 ? 4 : (KPL <= 16 ? 3 : 2
              : static_cast<void *>(reinterpret_cast<float *>(smem + lay.gc) + (size_t)warp * lay.gcn * K);
   const __half *G16t = H16 ? static_cast<const __half *>(a.G16) + (size_t)t * K * K : nullptr;
   code_warp_signals<float, KPL, MU, EXACT, H16>(a, a0, static_cast<const float *>(a.Y) + (size_t)row0 * m, m,
-                                               warp * 4, 4, nsig, row0, Dt, Gt, Ls, gc, lay.lp, lay.gcn, G16t);
+                                               warp * spw, spw, nsig, row0, Dt, Gt, Ls, gc, lay.lp, lay.gcn, G16t);
 }
 
 template <int KPL, int MU, bool EXACT, bool H16>
@@ -403,10 +567,11 @@ cudaError_t launch_select(const OmpArgs &a, const float *a0c, int64_t tile0, int
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
-  const SelLayout lay = sel_layout(a.K, a.s, fa.numRegs, H16);
+  const SelLayout lay = sel_layout(a.K, a.s, fa.numRegs, H16, a.sel_gcn);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)(ntile * 4), kSelThreads, lay.total, st>>>(a, lay, a0c, tile0);
+  const int spw = sel_spw(a);
+  kern<<<(unsigned)(ntile * (16 / spw)), kSelThreads, lay.total, st>>>(a, lay, a0c, tile0, spw);
   return cudaGetLastError();
 }
 
@@ -478,24 +643,37 @@ int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles, int64_t cap) {
   return c < total_tiles ? c : (total_tiles > 0 ? total_tiles : 1);
 }
 
-cudaError_t launch_omp_tc(const OmpArgs &a, float *a0c, cudaStream_t st) {
+cudaError_t launch_omp_tc(const OmpArgs &a, const void *img, float *a0c, int num_sms, const X3Wait &w,
+                          cudaStream_t st) {
   if (a.total_tiles <= 0) return cudaSuccess;
-  const CorrLayout cl = corr_layout(a.mp);
-  const size_t csm = tc::smem_for_tmem(cl.total, 2 * kCorrNT);
-  if (csm > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+  const size_t smem = tc::smem_for_tmem(kC16Smem, 2 * kC16NT);   // all 512 TMEM columns: one block per SM
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(corr16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  C16Job j{};
+  j.a = a;
+  j.img = static_cast<const unsigned char *>(img);
+  j.out = a0c;
+  j.nblk = round64c(a.m) / kC16KB;
+  j.Kp = round256c(a.K);
+  j.npass = (a.K + kC16NT - 1) / kC16NT;
+  j.err = a.err;
+  j.wait_limit = w.limit > 0 ? w.limit : 1;
+  j.leave = w.leave;
+  const int64_t sms = num_sms > 0 ? num_sms : 1;
   const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles, a.a0_cap);
   for (int64_t g0 = 0; g0 < a.total_tiles; g0 += chunk) {
-    const int64_t nt = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
-    corr_tc_kernel<<<(unsigned)nt, kCorrThreads, csm, st>>>(a, cl, a0c, g0);
+    j.tile0 = g0;
+    j.ntile = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
+    const int64_t nitem = j.ntile * j.npass;
+    corr16_kernel<<<(unsigned)(nitem < sms ? nitem : sms), kC16Threads, smem, st>>>(j);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the coefficients from alpha0 on the support carry its BF16 rounding; the
     // selection loop's FP32 correction step (residual from D_S and y in FP32,
     // solved with the factor of the FP32 Gram, within 2^-16 of the exact one)
     // removes it to about 2^-16 kappa(G_SS) of that rounding, so no separate
     // refit from D_S^T y is needed
-    if ((e = launch_omp_select(a, a0c, g0, nt, false, st, a.G16 != nullptr)) != cudaSuccess) return e;
+    if ((e = launch_omp_select(a, a0c, g0, j.ntile, false, st, a.G16 != nullptr)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

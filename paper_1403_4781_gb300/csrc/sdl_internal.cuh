@@ -86,6 +86,12 @@ struct sdl_ctx {
   int opt_mod_mixed = 1;         // FP32 data: 1 the checked FP32 pass of the tiled solve may run, 0 FP64 only
   int opt_mod_check_ppb = 20000; // tolerance of that check, parts per 10^9 of each atom's norm
   int opt_a0_chunk_mb = 0;       // alpha0 scratch chunk of the two-kernel coding passes, MB (0: automatic)
+  int opt_sel_spw = 0;           // selection launch: signals per warp (0 automatic, 1, 2, 4)
+  int opt_sel_gcache = 0;        // selection launch: G-column cache (0 automatic, 1 as fits, 2 none)
+  struct TunedSelect {
+    int spw, gcn;
+  };
+  std::map<std::string, TunedSelect> tuned_sel;   // coding-pass shape key -> selection launch shape
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
@@ -130,16 +136,26 @@ struct OmpArgs {
   void *val;
   int32_t *nnz;
   void *resid2;           // may be null
-  // tensor-core (BF16) path only
-  const void *Dimg;       // [L][Kp][mp] BF16 canonical K-major image of D
-  int Kp, mp;             // K and m rounded up to multiples of 16
+  // tensor-core paths only
   int32_t *err;           // device word: bit 0 set when a bounded wait gave up
   int64_t a0_cap;         // bytes of one alpha0 scratch chunk (0: 1 GiB)
   const void *G16;        // BF16 path: half-precision copy of G for the running update (or null)
+  // shape of the two-kernel selection launch (the autotuner's knobs; the
+  // results do not depend on them): signals per warp (1, 2 or 4; 0: 4) and
+  // the G columns cached per warp (0: as many as fit, -1: none, k: at most k)
+  int sel_spw, sel_gcn;
 };
 template <typename T>
 cudaError_t launch_omp(const OmpArgs &a, int num_sms, cudaStream_t st);
 int omp_tile_signals();
+
+// Bounds of the tensor-core kernels' mbarrier waits: limit polls each; with
+// leave set the loader role leaves at once, so that the other roles' waits run
+// out (a test).
+struct X3Wait {
+  int limit;
+  int leave;
+};
 
 // BF16 tensor-core path (tcgen05 + TMEM, operands fed by bulk TMA copies).
 inline int round16(int x) { return (x + 15) & ~15; }
@@ -151,16 +167,19 @@ cudaError_t launch_bf16_image(const float *D, int K, int m, int L, void *img, vo
 cudaError_t launch_gram_tc(const void *hi, const void *lo, int K, int m, int L, float *G, int32_t *err,
                            cudaStream_t st, void *G16 = nullptr);
 // Correlations of 128-signal tiles on the tensor cores into the scratch a0c
-// (omp_tc_chunk_tiles tiles of 128 x K floats at a time), then the selection
-// loop from there.
-cudaError_t launch_omp_tc(const OmpArgs &a, float *a0c, cudaStream_t st);
+// (omp_tc_chunk_tiles tiles of 128 x K floats at a time) by a persistent kernel
+// (num_sms blocks at most) reading the slab image img of D (launch_rtc_image),
+// then the selection loop from there.
+cudaError_t launch_omp_tc(const OmpArgs &a, const void *img, float *a0c, int num_sms, const X3Wait &w,
+                          cudaStream_t st);
 int omp_tc_tile_signals(int K, int m, int s);
 // Residual-form OMP on the tensor cores (same 128-signal tiles, same BF16
 // images and FP32 Gram): D^T r of every step by tcgen05 into TMEM, picks,
 // Cholesky rows and FP32 residuals per signal.  Shapes: s <= 16, m <= 256.
 bool omp_rtc_supported(int K, int m, int s);
-// Its BF16 image of D: [L][round64(m)/64][round256(K)][64], 256-atom x 64-entry
-// slabs (rtc_image_bytes(L, K, m) bytes).
+// The slab image of D that it and the correlation kernel read:
+// [L][round64(m)/64][round256(K)][64] BF16, 256-atom x 64-entry slabs
+// (rtc_image_bytes(L, K, m) bytes).
 size_t rtc_image_bytes(int L, int K, int m);
 cudaError_t launch_rtc_image(const float *D, int K, int m, int L, void *img, cudaStream_t st);
 cudaError_t launch_omp_rtc(const OmpArgs &a, const void *img, cudaStream_t st);
@@ -183,12 +202,7 @@ int64_t omp_tc_chunk_tiles(int K, int64_t total_tiles, int64_t cap = 0);
 // Gram and the correlations as hi hi^T + hi lo^T + lo hi^T with FP32
 // accumulation, then the FP32 selection kernel from the alpha0 scratch.
 // num_sms sizes the persistent grid; err as for the BF16 kernels; w bounds
-// every mbarrier wait (limit polls) and, with leave set, makes the loader role
-// leave at once so that the other roles' waits run out (a test).
-struct X3Wait {
-  int limit;
-  int leave;
-};
+// every mbarrier wait.
 size_t x3_image_bytes(int L, int K, int m);
 cudaError_t launch_x3_image(const float *D, int K, int m, int L, void *hi, void *lo, cudaStream_t st);
 cudaError_t launch_gram_x3(const float *D, const void *hi, const void *lo, int K, int m, int L, float *G,

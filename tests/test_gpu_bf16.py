@@ -142,3 +142,51 @@ def test_bf16_local_training_per_iteration():
         Dm, *_ = oracle.mod(Yp[a:b].astype(np.float64), idx[a:b], val[a:b].astype(np.float64),
                             Dl[t].astype(np.float64), True)
         np.testing.assert_allclose(after[t], Dm, rtol=0, atol=2e-5, err_msg=f"subset {t}")
+
+
+def test_bf16_bounded_waits_run_out_and_context_stays_usable():
+    """The loader role of the persistent BF16 correlation kernel leaves before
+    its first copy (SDL_OPT_WAIT_TEST), so the MMA issuer's first wait for a
+    dictionary slab can never complete: with a short limit every role gives
+    up, the call returns SDL_ETIMEOUT, and the next call on the same context
+    meets the BF16 bar against the oracle (the signals hold 4 atoms and are
+    coded with s = 4: a fifth pick would rank noise correlations that tie
+    within the BF16 bound on several percent of them)."""
+    ctx = sdl.context(0)
+    D, Y = _problem(413, 64, 256, 700, 4, 0.02)
+    ctx.set_option(sdl.OPT_WAIT_LIMIT, 1 << 12)
+    ctx.set_option(sdl.OPT_WAIT_TEST, 1)
+    try:
+        with pytest.raises(sdl.SdlError) as err:
+            sdl.omp(_t(D), _t(Y), 4, prec=sdl.PREC_BF16)
+            torch.cuda.synchronize()
+        assert err.value.status == 3, err.value   # SDL_ETIMEOUT
+    finally:
+        ctx.set_option(sdl.OPT_WAIT_TEST, 0)
+        ctx.set_option(sdl.OPT_WAIT_LIMIT, 1 << 24)
+    idx, val, nnz, r2 = (x.cpu().numpy() for x in sdl.omp(_t(D), _t(Y), 4, prec=sdl.PREC_BF16))
+    orc = oracle.omp(D.astype(np.float64), Y.astype(np.float64), 4)
+    check_bf16_codes(D, Y, idx, val, nnz, r2, orc, max_excused=0.04)
+
+
+@pytest.mark.parametrize("m,K,sizes", [(100, 700, [129, 1, 300]), (192, 1000, [257, 3]), (17, 33, [640, 5])])
+def test_bf16_correlation_passes_and_ragged_edges(m, K, sizes):
+    """Shapes that exercise every edge of the persistent correlation kernel:
+    several 256-atom passes per tile with a partial last pass (K = 700, 1000,
+    33), signal lengths that are not multiples of 4 or 64 (scalar loads, a
+    partial last 64-entry block), K not a multiple of 4 (scalar stores), and
+    tiles with 1-129 valid rows over uneven subsets; codes under the BF16 rule
+    against the oracle, subset by subset."""
+    rng = np.random.default_rng(414 + m)
+    s = 4
+    L = len(sizes)
+    Ds = np.stack([si.unit_gaussian_atoms(rng, m, K) for _ in range(L)]).astype(np.float32)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    Y = np.concatenate([si.sparse_signals(rng, Ds[t].astype(np.float64), n, s, 0.01, dtype=np.float32)[0]
+                        for t, n in enumerate(sizes)])
+    idx, val, nnz, r2 = (x.cpu().numpy() for x in sdl.omp_batched(_t(Ds), _t(Y), offsets, s, prec=sdl.PREC_BF16))
+    for t in range(L):
+        a, b = offsets[t], offsets[t + 1]
+        orc = oracle.omp(Ds[t].astype(np.float64), Y[a:b].astype(np.float64), s)
+        ex, ro = check_bf16_codes(Ds[t], Y[a:b], idx[a:b], val[a:b], nnz[a:b], r2[a:b], orc, max_excused=0.05)
+        print(f"m={m} K={K} subset {t} ({b - a} signals): {ex} differ at near-ties, {ro} at rounding-level steps")
