@@ -1014,7 +1014,8 @@ def run_coding_final(args):
 def run_mod_local(args):
     """The local MOD update of the image-patch workload's shape, alone: 256
     subsets, K1=512 atoms, m=256, codes of s1=4 from the overcomplete DCT
-    (2,048 patches per subset: the solve's cost does not depend on n).  The
+    (by default 32 synthetic images of 16,384 patches, 2,048 per subset: the
+    solve's cost does not depend on n; --mod-local-images sets the image count).  The
     third call of the default (checked mixed-precision) solve is bracketed by
     cudaProfilerStart/Stop, so a profiler started with profiling off captures
     exactly one accumulation, the FP32 pass, its check and the FP64 pass of
@@ -1026,7 +1027,7 @@ def run_mod_local(args):
     import paper_1403_4781_gb300 as sdl
 
     dev = torch.device("cuda", 0)
-    p = si.config4(n_images=32, per_image=16384, L=256)
+    p = si.config4(n_images=args.mod_local_images, per_image=16384, L=256)
     Yp = sdl.split(torch.from_numpy(p.Y).to(dev), torch.from_numpy(p.perm).to(dev))
     D = torch.from_numpy(np.broadcast_to(p.extra["D_local0"], (p.L, p.K1, p.m)).copy()).to(dev)
     idx, val, _, _ = sdl.omp_batched(D, Yp, p.offsets, p.s1, prec=sdl.PREC_BF16, with_resid=False)
@@ -1059,7 +1060,7 @@ def run_mod_local(args):
             out["fp64"] = {"solve_ms": ms, "solve_tflops": flops / (ms / 1e3) / 1e12,
                            "fp64_frac": flops / (ms / 1e3) / FP64_PEAK_FLOPS, "kernels": kern}
     ctx.set_option(sdl.OPT_MOD_MIXED, 1)
-    print(json.dumps({"metric": METRIC, "workload": f"mod_local_L{p.L}_K{p.K1}_m{p.m}_s{p.s1}", **out}),
+    print(json.dumps({"metric": METRIC, "workload": f"mod_local_L{p.L}_K{p.K1}_m{p.m}_s{p.s1}_N{p.Y.shape[0]}", **out}),
           flush=True)
 
 
@@ -1211,6 +1212,8 @@ def main():
                                            "conditioned", "mod-local"],
                     default="patches",
                     help="the main line's workload (patches or splitmerge), or a parity workload measured alone")
+    ap.add_argument("--mod-local-images", type=int, default=32,
+                    help="--workload mod-local: synthetic images of 16,384 patches (256 at full size)")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed steps of the per-subset plain form (0 skips it)")
     args = ap.parse_args()
