@@ -371,7 +371,8 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *   SDL_OPT_CLUSTER: cluster size, 0 = automatic (default); 4, 8 or 16 for
  *     option 1, 1 to 16 for option 3; blocks per subset for option 4.
  *   SDL_OPT_MOD_TILE: tile edge of the tiled solve: 0 = automatic (default),
- *     16 or 32.
+ *     16, 32 or 64 (64: the FP32 pass of the checked solve, with 4 x 4
+ *     register micro-tiles; an FP64 solve then takes 32).
  *   SDL_OPT_SM_BLOCKS: with the tile or cluster size set by hand, at most this
  *     many blocks of the tiled solve per SM (1 to 3; 0 = as many as fit, the
  *     default).  The autotuner also tries a cap of 2.

@@ -142,6 +142,7 @@ void pick_tiled(sdl_ctx *ctx, int L, int *ts, int *C, bool f32 = false) {
   int t = ctx->opt_tile;
   int c = ctx->opt_cluster;
   if (t == 0) t = (int64_t)L * 8 <= ctx->num_sms ? 16 : 32;
+  if (t == 64 && !f32) t = 32;   // 64 x 64 tiles: the FP32 pass only
   if (c == 0) {
     c = 1;
     const int cand[6] = {16, 8, 6, 4, 2, 1};
@@ -247,7 +248,7 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
       }
       return ms_best;
     };
-    const int tiles[2] = {16, 32};
+    const int tiles[3] = {16, 32, 64};   // 64: the FP32 pass only
     const int cls[7] = {1, 2, 3, 4, 6, 8, 16};
     // the FP32 pass's tile and cluster size by the FP32 pass alone; then the
     // whole checked solve with that shape (its check and the FP64 solve of what
@@ -256,7 +257,7 @@ cudaError_t run_tiled_tuned(sdl_ctx *ctx, const ModArgs &ma) {
     float best32 = 3.4e38f;
     for (int pass = mix_ok ? 0 : 1; pass < 2 && e == cudaSuccess; ++pass) {
       const bool f32 = pass == 0;
-      for (int a = 0; a < 2 && e == cudaSuccess; ++a)
+      for (int a = 0; a < (f32 ? 3 : 2) && e == cudaSuccess; ++a)
         for (int b = 0; b < 7 && e == cudaSuccess; ++b) {
           const int t = tiles[a], c = cls[b], cp = 0;
           // a subset's cluster must fit on the device; small clusters for few
@@ -1557,8 +1558,8 @@ sdl_status sdl_set_option(sdl_ctx *ctx, int option, int64_t value) {
       ctx->opt_cluster = (int)value;
       return SDL_OK;
     case SDL_OPT_MOD_TILE:
-      if (value != 0 && value != 16 && value != 32)
-        return set_error(ctx, SDL_EINVAL, "SDL_OPT_MOD_TILE takes 0, 16 or 32");
+      if (value != 0 && value != 16 && value != 32 && value != 64)
+        return set_error(ctx, SDL_EINVAL, "SDL_OPT_MOD_TILE takes 0, 16, 32 or 64");
       ctx->opt_tile = (int)value;
       return SDL_OK;
     case SDL_OPT_AUTOTUNE:

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
                                                               T *D, int32_t *status, float tau) {
   extern __shared__ double sh[];
   __shared__ float Us[kProbes][256];
-  __shared__ float Ys[kProbes][32];
+  __shared__ float Ys[kProbes][64];
   const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (status[t] == kModDeferredC) return;   // the FP32 factorisation broke down
   const int R = (K + TS - 1) / TS;
@@ -238,16 +238,16 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
   // inverses of the diagonal factor tiles
   for (int k = 0; k < R; ++k) {
     const int k0 = k * TS, nb = K - k0 < TS ? K - k0 : TS;
-    if (tid < kProbes * TS) {
-      const int p = tid / TS, a = tid % TS;
+    for (int e = tid; e < kProbes * TS; e += kCThreads) {
+      const int p = e / TS, a = e % TS;
       float y = 0.f;
       if (a < nb)
         for (int c = 0; c <= a; ++c) y = fmaf(Vt[(size_t)k * TS * TS + a * TS + c], Zs[p * K + k0 + c], y);
       Ys[p][a] = y;
     }
     __syncthreads();
-    if (tid < kProbes * TS) {
-      const int p = tid / TS, a = tid % TS;
+    for (int e = tid; e < kProbes * TS; e += kCThreads) {
+      const int p = e / TS, a = e % TS;
       if (a < nb) Zs[p * K + k0 + a] = Ys[p][a];
     }
     for (int i = k0 + nb + tid; i < K; i += kCThreads) {
@@ -265,16 +265,16 @@ __global__ void __launch_bounds__(kCThreads) mod_check_kernel(const double *__re
   }
   for (int k = R - 1; k >= 0; --k) {
     const int k0 = k * TS, nb = K - k0 < TS ? K - k0 : TS;
-    if (tid < kProbes * TS) {
-      const int p = tid / TS, a = tid % TS;
+    for (int e = tid; e < kProbes * TS; e += kCThreads) {
+      const int p = e / TS, a = e % TS;
       float z = 0.f;
       if (a < nb)
         for (int c = a; c < nb; ++c) z = fmaf(Vt[(size_t)k * TS * TS + c * TS + a], Zs[p * K + k0 + c], z);
       Ys[p][a] = z;
     }
     __syncthreads();
-    if (tid < kProbes * TS) {
-      const int p = tid / TS, a = tid % TS;
+    for (int e = tid; e < kProbes * TS; e += kCThreads) {
+      const int p = e / TS, a = e % TS;
       if (a < nb) Zs[p * K + k0 + a] = Ys[p][a];
     }
     for (int j = tid; j < k0; j += kCThreads) {
@@ -332,7 +332,7 @@ size_t mod_check_smem(int K) { return 5 * sizeof(float) * kProbes * (size_t)K; }
 template <typename T>
 cudaError_t launch_mod_check(const ModArgs &a, int ts, float tau, cudaStream_t st) {
   if (a.L <= 0) return cudaSuccess;
-  if (a.K > kCThreads * kCJMax || a.m > 256 || (ts != 16 && ts != 32)) return cudaErrorInvalidValue;
+  if (a.K > kCThreads * kCJMax || a.m > 256 || (ts != 16 && ts != 32 && ts != 64)) return cudaErrorInvalidValue;
   const size_t smem = mod_check_smem(a.K);
   auto kern = a.K <= 2 * kCThreads ? mod_check_kernel<T, 2> : mod_check_kernel<T, 4>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

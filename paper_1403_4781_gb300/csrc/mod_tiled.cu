@@ -38,15 +38,28 @@ namespace {
 
 constexpr int kTThreads = 256;
 
+// The FP32 pass's 64 x 64 tiles (R = float, TS = 64) multiply 4 x 4 register
+// micro-tiles from transposed operands (A^T and B^T rows in shared memory, two
+// 16-byte loads per 16 FMAs), where the other tiles' products read 1.25
+// shared-memory words per FMA; their rows are padded to 68 floats so that the
+// 16-byte loads stay aligned.
+template <typename R, int TS>
+constexpr bool kMicro = sizeof(R) == 4 && TS == 64;
+template <typename R, int TS>
+constexpr int kPitch = kMicro<R, TS> ? TS + 4 : TS + 1;
+
 // R: the arithmetic type of the factorisation (double; float for the FP32
-// pass of the checked mixed-precision solve below).
+// pass of the checked mixed-precision solve below).  The micro-tiled products
+// hold a and b transposed, and v as the transposes of the inverses.
 template <typename R, int TS>
 struct TiledSmem {
-  R a[TS][TS + 1];           // A operand; the diagonal factor during factor_diag
-  R b[TS][TS + 1];           // B operand; the inverse during factor_diag
-  R v[2][TS + 0][TS + 1];    // inverses of diagonal factors k (v[k & 1]), pushed by their owner
+  static constexpr int P = kPitch<R, TS>;
+  R a[TS][P];                // A operand; the diagonal factor during factor_diag
+  R b[TS][P];                // B operand; the inverse during factor_diag
+  R v[2][TS][P];             // inverses of diagonal factors k (v[k & 1]), pushed by their owner
   R invd[TS];
   R dg[TS];
+  R col[TS];                 // factor_diag: the scaled column of the current step
   int fail;
   int verdict[2];            // breakdown verdict of diagonal tile k (verdict[k & 1]), pushed by its owner
 };
@@ -100,7 +113,7 @@ __device__ __forceinline__ void fetch(const Opnd<R> &o, R (&r)[TS * TS / kTThrea
   }
 }
 template <typename R, int TS>
-__device__ __forceinline__ void commit(R (*S)[TS + 1], const R (&r)[TS * TS / kTThreads], bool t) {
+__device__ __forceinline__ void commit(R (*S)[kPitch<R, TS>], const R (&r)[TS * TS / kTThreads], bool t) {
   constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
   const int cc = threadIdx.x % TS, r0 = threadIdx.x / TS;
 #pragma unroll
@@ -114,7 +127,7 @@ __device__ __forceinline__ void commit(R (*S)[TS + 1], const R (&r)[TS * TS / kT
 // with sub, acc[u] = old[u] - sum_q As[r_u][q] Bs[c][q] (the subtraction folded
 // into the fused multiply-adds).
 template <typename R, int TS>
-__device__ __forceinline__ void tile_product(const R (*As)[TS + 1], const R (*Bs)[TS + 1], bool sub,
+__device__ __forceinline__ void tile_product(const R (*As)[kPitch<R, TS>], const R (*Bs)[kPitch<R, TS>], bool sub,
                                              const R (&old)[TS * TS / kTThreads], R (&acc)[TS * TS / kTThreads]) {
   constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
   const int c = threadIdx.x % TS, r0 = threadIdx.x / TS;
@@ -137,6 +150,76 @@ __device__ __forceinline__ void tile_product(const R (*As)[TS + 1], const R (*Bs
   }
 }
 
+// The micro-tiled map (R = float, TS = 64): thread (warp w, lane l) owns
+// output rows 4 ri .. 4 ri + 3 and columns 4 ci .. 4 ci + 3, ri = 4 (w / 2) +
+// l / 8, ci = 8 (w mod 2) + l mod 8, element (a, b) in slot 4 a + b; a warp's
+// 16-byte operand loads then touch 4 (A) and 8 (B) distinct chunks of one
+// shared-memory row.
+__device__ __forceinline__ int micro_ri() { return ((threadIdx.x >> 6) << 2) + ((threadIdx.x & 31) >> 3); }
+__device__ __forceinline__ int micro_ci() { return (((threadIdx.x >> 5) & 1) << 3) + (threadIdx.x & 7); }
+
+// Output tile elements in the micro map (zero outside the tile).
+__device__ __forceinline__ void fetch_micro(const Opnd<float> &o, float (&r)[16]) {
+  const int r0 = 4 * micro_ri(), c0 = 4 * micro_ci();
+  const bool vec = (o.ld & 3) == 0 && ((reinterpret_cast<uintptr_t>(o.p) & 15) == 0) && c0 + 4 <= o.nc;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int rr = r0 + a;
+    if (rr < o.nr && vec) {
+      const float4 v = __ldcg(reinterpret_cast<const float4 *>(o.p + (int64_t)rr * o.ld + c0));
+      r[4 * a] = v.x; r[4 * a + 1] = v.y; r[4 * a + 2] = v.z; r[4 * a + 3] = v.w;
+    } else {
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        r[4 * a + b] = (rr < o.nr && c0 + b < o.nc) ? __ldcg(o.p + (int64_t)rr * o.ld + c0 + b) : 0.f;
+    }
+  }
+}
+
+// acc = (old -) A B^T over the tile's 64 products, As[q][r] = A(r, q) and
+// Bs[q][c] = B(c, q).
+__device__ __forceinline__ void tile_product_micro(const float (*As)[68], const float (*Bs)[68], bool sub,
+                                                   const float (&old)[16], float (&acc)[16]) {
+  const int r0 = 4 * micro_ri(), c0 = 4 * micro_ci();
+#pragma unroll
+  for (int u = 0; u < 16; ++u) acc[u] = sub ? old[u] : 0.f;
+  // with sub, B enters negated: acc = old - sum_q a_q b_q^T
+  const float sg = sub ? -1.f : 1.f;
+#pragma unroll 1
+  for (int q = 0; q < 64; ++q) {
+    const float4 av = *reinterpret_cast<const float4 *>(&As[q][r0]);
+    const float4 bv = *reinterpret_cast<const float4 *>(&Bs[q][c0]);
+    const float a[4] = {av.x, av.y, av.z, av.w};
+    const float b[4] = {sg * bv.x, sg * bv.y, sg * bv.z, sg * bv.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[4 * i + k] = fmaf(a[i], b[k], acc[4 * i + k]);
+  }
+}
+
+__device__ __forceinline__ void put_micro(const TileTask<float> &t, const float (&acc)[16]) {
+  const int r0 = 4 * micro_ri(), c0 = 4 * micro_ci();
+  float *base = const_cast<float *>(t.o.p);
+  const bool vec = (t.o.ld & 3) == 0 && ((reinterpret_cast<uintptr_t>(base) & 15) == 0) && c0 + 4 <= t.o.nc &&
+                   !(t.lower && c0 + 3 > r0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int rr = r0 + a;
+    if (rr >= t.o.nr) continue;
+    if (vec && (!t.lower || c0 + 3 <= rr)) {
+      *reinterpret_cast<float4 *>(base + (int64_t)rr * t.o.ld + c0) =
+          make_float4(acc[4 * a], acc[4 * a + 1], acc[4 * a + 2], acc[4 * a + 3]);
+    } else {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = c0 + b;
+        if (c < t.o.nc && (!t.lower || c <= rr)) base[(int64_t)rr * t.o.ld + c] = acc[4 * a + b];
+      }
+    }
+  }
+}
+
 template <typename R, int TS>
 __device__ __forceinline__ void put(const TileTask<R> &t, const R (&acc)[TS * TS / kTThreads]) {
   constexpr int U = TS * TS / kTThreads, RS = kTThreads / TS;
@@ -154,19 +237,27 @@ __device__ __forceinline__ void put(const TileTask<R> &t, const R (&acc)[TS * TS
 // multiplied.  Tasks of one step never read a tile another task of the step
 // writes.  vs: the inverse used by tasks whose B operand is in shared memory.
 template <typename R, int TS, class Desc>
-__device__ __forceinline__ void run_step(TiledSmem<R, TS> &sm, const R (*vs)[TS + 1], int n, int first, int C,
+__device__ __forceinline__ void run_step(TiledSmem<R, TS> &sm, const R (*vs)[kPitch<R, TS>], int n, int first, int C,
                                          Desc desc) {
   constexpr int U = TS * TS / kTThreads;
+  constexpr bool MI = kMicro<R, TS>;
   if (first >= n) return;
+  // the output tile's old values in the product's map
+  auto fetch_o = [&](const Opnd<R> &o, R (&r)[U]) {
+    if constexpr (MI) fetch_micro(o, r);
+    else fetch<R, TS>(o, r);
+  };
   TileTask<R> cur = desc(first);
   R ra[U], rb[U], ro[U];
   fetch<R, TS>(cur.a, ra);
   if (!cur.bsm) fetch<R, TS>(cur.b, rb);
-  if (cur.sub) fetch<R, TS>(cur.o, ro);
+  if (!MI && cur.sub) fetch_o(cur.o, ro);
   for (int q = first; q < n; q += C) {
     __syncthreads();
-    commit<R, TS>(sm.a, ra, false);
-    if (!cur.bsm) commit<R, TS>(sm.b, rb, cur.bt);
+    // the micro-tiled product reads A^T and B^T (B^T is the staged source
+    // itself when B comes from the transpose of its source)
+    commit<R, TS>(sm.a, ra, MI);
+    if (!cur.bsm) commit<R, TS>(sm.b, rb, MI ? !cur.bt : cur.bt);
     __syncthreads();
     const bool more = q + C < n;
     TileTask<R> nxt = cur;
@@ -175,15 +266,23 @@ __device__ __forceinline__ void run_step(TiledSmem<R, TS> &sm, const R (*vs)[TS 
       nxt = desc(q + C);
       fetch<R, TS>(nxt.a, ra);
       if (!nxt.bsm) fetch<R, TS>(nxt.b, rb);
-      if (nxt.sub) fetch<R, TS>(nxt.o, rn);
+      if (!MI && nxt.sub) fetch_o(nxt.o, rn);
     }
+    // the micro-tiled tasks load their old outputs here (registers)
+    if (MI && cur.sub) fetch_o(cur.o, ro);
     R acc[U];
-    tile_product<R, TS>(sm.a, cur.bsm ? vs : sm.b, cur.sub, ro, acc);
-    put<R, TS>(cur, acc);
+    if constexpr (MI) {
+      tile_product_micro(sm.a, cur.bsm ? vs : sm.b, cur.sub, ro, acc);
+      put_micro(cur, acc);
+    } else {
+      tile_product<R, TS>(sm.a, cur.bsm ? vs : sm.b, cur.sub, ro, acc);
+      put<R, TS>(cur, acc);
+    }
     if (more) {
       cur = nxt;
+      if (!MI)
 #pragma unroll
-      for (int u = 0; u < U; ++u) ro[u] = rn[u];
+        for (int u = 0; u < U; ++u) ro[u] = rn[u];
     }
   }
 }
@@ -236,7 +335,11 @@ __device__ bool factor_diag(TiledSmem<R, TS> &sm, const R *Mt, const TGeom &g, i
   // below are subtracted in the same phase as the trailing update.
   for (int c = 0; c < TS; ++c) {
     if (sm.fail) break;   // uniform: read after a barrier
-    if (tid > c && tid < TS) sm.a[tid][c] *= sm.invd[c];
+    if (tid > c && tid < TS) {
+      const R l = sm.a[tid][c] * sm.invd[c];
+      sm.a[tid][c] = l;
+      sm.col[tid] = l;   // read below from consecutive words
+    }
     if (tid >= TS && tid - TS <= c) sm.b[c][tid - TS] *= sm.invd[c];
     __syncthreads();
     // rank-1 update of the trailing triangle (the thread that updates the next
@@ -244,11 +347,11 @@ __device__ bool factor_diag(TiledSmem<R, TS> &sm, const R *Mt, const TGeom &g, i
     for (int e = tid; e < TS * TS; e += kTThreads) {
       const int r = e / TS, q = e % TS;
       if (q > c && q <= r) {
-        const R v = fma(-sm.a[r][c], sm.a[q][c], sm.a[r][q]);
+        const R v = fma(-sm.col[r], sm.col[q], sm.a[r][q]);
         if (r == c + 1 && q == c + 1) pivot(sm, c + 1, v);
         else sm.a[r][q] = v;
       }
-      if (r > c && q <= c) sm.b[r][q] = fma(-sm.a[r][c], sm.b[c][q], sm.b[r][q]);
+      if (r > c && q <= c) sm.b[r][q] = fma(-sm.col[r], sm.b[c][q], sm.b[r][q]);
     }
     __syncthreads();
   }
@@ -266,7 +369,7 @@ constexpr int kModDeferred = 4;
 // the unnormalised solution left in the scratch for the check, breakdown
 // recorded as kModDeferred (no ridge: the FP64 solve takes that subset).
 template <typename T, int TS, typename R>
-__global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *__restrict__ A,
+__global__ void __launch_bounds__(kTThreads, kMicro<R, TS> ? 2 : 3) mod_tiled_kernel(const double *__restrict__ A,
                                                                  const double *__restrict__ B,
                                                                  const int32_t *__restrict__ usage, int K, int m,
                                                                  int C, int light, int only_deferred, R *M, R *V,
@@ -274,7 +377,9 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   constexpr bool kF32 = sizeof(R) == 4;
-  __shared__ TiledSmem<R, TS> sm;
+  constexpr int P = kPitch<R, TS>;
+  extern __shared__ __align__(16) unsigned char tiled_dyn[];
+  TiledSmem<R, TS> &sm = *reinterpret_cast<TiledSmem<R, TS> *>(tiled_dyn);
   __shared__ double red[2][kTThreads / 32];
   const int rank = (int)cl.block_rank();
   const int t = blockIdx.x / C;
@@ -313,8 +418,12 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
     const bool ok = factor_diag<R, TS>(sm, Mt, g, kk, At, ut, ridge);
     const int par = kk & 1;
     for (int r2 = 0; r2 < C; ++r2) {
-      R *dst = &cl.map_shared_rank(&sm.v[0][0][0], r2)[(size_t)par * TS * (TS + 1)];
-      for (int e = tid; e < TS * TS; e += kTThreads) dst[(e / TS) * (TS + 1) + e % TS] = sm.b[e / TS][e % TS];
+      R *dst = &cl.map_shared_rank(&sm.v[0][0][0], r2)[(size_t)par * TS * P];
+      for (int e = tid; e < TS * TS; e += kTThreads) {
+        const int r = e / TS, c = e % TS;
+        if (kMicro<R, TS>) dst[c * P + r] = sm.b[r][c];   // the micro-tiled product reads V^T
+        else dst[r * P + c] = sm.b[r][c];
+      }
       if (tid == 0) cl.map_shared_rank(&sm.verdict[0], r2)[par] = ok ? 0 : 1;
     }
     for (int e = tid; e < TS * TS; e += kTThreads) Vt[(size_t)kk * TS * TS + e] = sm.b[e / TS][e % TS];
@@ -342,7 +451,7 @@ __global__ void __launch_bounds__(kTThreads, 3) mod_tiled_kernel(const double *_
     failed = false;
     for (int k = 0; k < R_; ++k) {
       if (sm.verdict[k & 1]) { failed = true; break; }   // uniform: every block holds the pushed verdict
-      const R (*vk)[TS + 1] = sm.v[k & 1];
+      const R (*vk)[P] = sm.v[k & 1];
       // panel: tile (i, k) <- tile (i, k) V_k^T for every tile row below k
       run_step<R, TS>(sm, vk, RT - k - 1, rank, C, [&](int q) {
         const Opnd<R> p = tile_of<R, TS>(Mt, g, k + 1 + q, k);
@@ -646,22 +755,25 @@ __global__ void __launch_bounds__(kTThreads, 2) mod_wide_kernel(const double *__
 
 }  // namespace
 
-// Scratch per subset: M ((K + m) x K), room for the inverses of either tile
+// Scratch per subset: M ((K + m) x K), room for the inverses of every tile
 // edge, and the wide form's barrier words (4 doubles).
 static size_t tiled_sub_doubles(int K, int m) {
   const int R = (K + 15) / 16;   // the smaller tile needs the most inverse blocks
-  return (size_t)(K + m) * K + (size_t)R * 16 * 16 + (size_t)((K + 31) / 32) * 32 * 32;
+  return (size_t)(K + m) * K + (size_t)R * 16 * 16 + (size_t)((K + 31) / 32) * 32 * 32 +
+         (size_t)((K + 63) / 64) * 64 * 64 / 2;   // the FP32 pass's 64 x 64 inverses (floats)
 }
 size_t mod_tiled_scratch_doubles(int L, int K, int m) { return (size_t)L * (tiled_sub_doubles(K, m) + 4); }
 
-// Dynamic shared memory that keeps at most `cap` blocks on an SM (0: no cap):
-// more than 1/(cap + 1) of the SM's 228 KB with the static part included.
+// Dynamic shared memory of the tiled kernel: its tile buffers, grown where a
+// cap of at most `cap` blocks per SM is asked for (0: no cap) to more than
+// 1/(cap + 1) of the SM's 228 KB with the static part included.
 template <typename R, int TS>
 static size_t cap_smem(int cap) {
-  if (cap <= 0) return 0;
-  const size_t stat = sizeof(TiledSmem<R, TS>) + 2 * sizeof(double) * (kTThreads / 32) + 64;
+  const size_t need = sizeof(TiledSmem<R, TS>);
+  if (cap <= 0) return need;
+  const size_t stat = 2 * sizeof(double) * (kTThreads / 32) + 64;
   const size_t want = (size_t)228 * 1024 / (size_t)(cap + 1) + 1024;
-  return want > stat ? want - stat : 0;
+  return want > stat + need ? want - stat : need;
 }
 
 template <typename T, int TS, typename R>
@@ -696,14 +808,14 @@ static cudaError_t launch_tiled_ts(const ModArgs &a, int C, int cap, int num_sms
                             a.m, C, light, only_deferred, M, V, static_cast<T *>(a.D), a.status, a.status_max);
 }
 
-template <typename T, typename R>
-static int max_clusters_r(int ts, int C, int cap) {
-  auto kern = ts == 16 ? mod_tiled_kernel<T, 16, R> : mod_tiled_kernel<T, 32, R>;
+template <typename T, typename R, int TS>
+static int max_clusters_ts(int C, int cap) {
+  auto kern = mod_tiled_kernel<T, TS, R>;
   if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  const size_t dyn = ts == 16 ? cap_smem<R, 16>(cap) : cap_smem<R, 32>(cap);
+  const size_t dyn = cap_smem<R, TS>(cap);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -729,7 +841,12 @@ static int max_clusters_r(int ts, int C, int cap) {
 
 template <typename T>
 int mod_tiled_max_clusters(int ts, int C, int cap, bool f32) {
-  return f32 ? max_clusters_r<T, float>(ts, C, cap) : max_clusters_r<T, double>(ts, C, cap);
+  if (f32)
+    return ts == 16 ? max_clusters_ts<T, float, 16>(C, cap)
+         : ts == 32 ? max_clusters_ts<T, float, 32>(C, cap)
+         : ts == 64 ? max_clusters_ts<T, float, 64>(C, cap) : 0;
+  return ts == 16 ? max_clusters_ts<T, double, 16>(C, cap)
+       : ts == 32 ? max_clusters_ts<T, double, 32>(C, cap) : 0;
 }
 
 template <typename T>
@@ -745,9 +862,10 @@ cudaError_t launch_mod_tiled(const ModArgs &a, int ts, int C, int cap, int num_s
 template <typename T>
 cudaError_t launch_mod_tiled32(const ModArgs &a, int ts, int C, int cap, int num_sms, cudaStream_t st) {
   if (a.L <= 0) return cudaSuccess;
-  if (C < 1 || C > 16 || (ts != 16 && ts != 32) || cap < 0 || cap > 3) return cudaErrorInvalidValue;
+  if (C < 1 || C > 16 || (ts != 16 && ts != 32 && ts != 64) || cap < 0 || cap > 3) return cudaErrorInvalidValue;
   return ts == 16 ? launch_tiled_ts<T, 16, float>(a, C, cap, num_sms, 0, st)
-                  : launch_tiled_ts<T, 32, float>(a, C, cap, num_sms, 0, st);
+       : ts == 32 ? launch_tiled_ts<T, 32, float>(a, C, cap, num_sms, 0, st)
+                  : launch_tiled_ts<T, 64, float>(a, C, cap, num_sms, 0, st);
 }
 
 template <typename T, int TS>

@@ -78,9 +78,12 @@ def _run(ctx, mixed, ts, C, offsets, Y, idx, val, D0, autotune=0):
     return Dg.cpu().numpy(), prof
 
 
-@pytest.mark.parametrize("K,m,s", [(60, 30, 4), (97, 33, 5), (256, 64, 6), (512, 256, 4)])
-@pytest.mark.parametrize("ts,C", [(16, 1), (16, 4), (32, 2), (32, 16)])
+@pytest.mark.parametrize("K,m,s", [(60, 30, 4), (97, 33, 5), (256, 64, 6), (512, 256, 4), (130, 70, 3)])
+@pytest.mark.parametrize("ts,C", [(16, 1), (16, 4), (32, 2), (32, 16), (64, 1), (64, 4), (64, 16)])
 def test_mixed_matches_oracle(ctx, ts, C, K, m, s):
+    """The FP32 pass with every tile edge (64: the 4 x 4 register micro-tiled
+    products, with K and m that leave partial tiles and rows not a multiple of
+    4) and cluster size, checked and renormalised, against the oracle."""
     offsets, Y, idx, val, D0 = _problem(900 + K, [3 * K, 5 * K, 4 * K], m, K, s)
     want = _oracle(offsets, Y, idx, val, D0)
     got, prof = _run(ctx, 1, ts, C, offsets, Y, idx, val, D0)
@@ -89,11 +92,12 @@ def test_mixed_matches_oracle(ctx, ts, C, K, m, s):
     np.testing.assert_allclose(got, want, rtol=0, atol=2e-5)
 
 
-def test_mixed_single_system_K1024(ctx):
+@pytest.mark.parametrize("ts", [32, 64])
+def test_mixed_single_system_K1024(ctx, ts):
     """One subset, K=1024, m=256 (the image-patch merge shape), clusters of 16."""
     offsets, Y, idx, val, D0 = _problem(910, [6000], 256, 1024, 4, unused=0)
     want = _oracle(offsets, Y, idx, val, D0)
-    got, prof = _run(ctx, 1, 32, 16, offsets, Y, idx, val, D0)
+    got, prof = _run(ctx, 1, ts, 16, offsets, Y, idx, val, D0)
     assert "mod_solve_fp32_single" in prof, prof
     np.testing.assert_allclose(got, want, rtol=0, atol=2e-5)
 
@@ -113,7 +117,8 @@ def _near_dependent(seed, rho, n=3000, m=48, K=64):
     return offsets, Y, idx, val, D0
 
 
-def test_breakdown_goes_to_fp64(ctx):
+@pytest.mark.parametrize("ts", [16, 64])
+def test_breakdown_goes_to_fp64(ctx, ts):
     """In subset 1 the squared pivot of atom 1 is about 1e-5 of its diagonal:
     the FP32 factorisation breaks down (below 1e-3) and that subset comes out
     of the FP64 solve: within 1e-6 of the FP64-only run (the two runs differ
@@ -121,7 +126,7 @@ def test_breakdown_goes_to_fp64(ctx):
     rounding of the atoms); the whole result within 2e-5 of the oracle."""
     offsets, Y, idx, val, D0 = _near_dependent(920, 1e-5)
     want = _oracle(offsets, Y, idx, val, D0)
-    mixed, prof = _run(ctx, 1, 16, 2, offsets, Y, idx, val, D0)
+    mixed, prof = _run(ctx, 1, ts, 2, offsets, Y, idx, val, D0)
     fp64, prof64 = _run(ctx, 0, 16, 2, offsets, Y, idx, val, D0)
     assert "mod_check" in prof and "mod_check" not in prof64
     np.testing.assert_allclose(mixed[1], fp64[1], rtol=0, atol=1e-6)
