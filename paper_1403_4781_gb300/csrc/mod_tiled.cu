@@ -177,24 +177,40 @@ __device__ __forceinline__ void fetch_micro(const Opnd<float> &o, float (&r)[16]
 }
 
 // acc = (old -) A B^T over the tile's 64 products, As[q][r] = A(r, q) and
-// Bs[q][c] = B(c, q).
+// Bs[q][c] = B(c, q).  The products are summed from zero and old is added
+// last, so that its loads (issued just before) complete under the products.
 __device__ __forceinline__ void tile_product_micro(const float (*As)[68], const float (*Bs)[68], bool sub,
                                                    const float (&old)[16], float (&acc)[16]) {
   const int r0 = 4 * micro_ri(), c0 = 4 * micro_ci();
 #pragma unroll
-  for (int u = 0; u < 16; ++u) acc[u] = sub ? old[u] : 0.f;
-  // with sub, B enters negated: acc = old - sum_q a_q b_q^T
-  const float sg = sub ? -1.f : 1.f;
+  for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+  // two copies of the loop, so that the sign is the FMA's own operand modifier
+  if (sub) {
 #pragma unroll 1
-  for (int q = 0; q < 64; ++q) {
-    const float4 av = *reinterpret_cast<const float4 *>(&As[q][r0]);
-    const float4 bv = *reinterpret_cast<const float4 *>(&Bs[q][c0]);
-    const float a[4] = {av.x, av.y, av.z, av.w};
-    const float b[4] = {sg * bv.x, sg * bv.y, sg * bv.z, sg * bv.w};
+    for (int q = 0; q < 64; ++q) {
+      const float4 av = *reinterpret_cast<const float4 *>(&As[q][r0]);
+      const float4 bv = *reinterpret_cast<const float4 *>(&Bs[q][c0]);
+      const float a[4] = {av.x, av.y, av.z, av.w};
+      const float b[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[4 * i + k] = fmaf(a[i], b[k], acc[4 * i + k]);
+        for (int k = 0; k < 4; ++k) acc[4 * i + k] = fmaf(-a[i], b[k], acc[4 * i + k]);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc[u] = old[u] + acc[u];
+  } else {
+#pragma unroll 1
+    for (int q = 0; q < 64; ++q) {
+      const float4 av = *reinterpret_cast<const float4 *>(&As[q][r0]);
+      const float4 bv = *reinterpret_cast<const float4 *>(&Bs[q][c0]);
+      const float a[4] = {av.x, av.y, av.z, av.w};
+      const float b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[4 * i + k] = fmaf(a[i], b[k], acc[4 * i + k]);
+    }
   }
 }
 
