@@ -543,10 +543,10 @@ def proposer_bench(sdl, dev, flush, stream):
     D0 64 x 256, s = 6, noise 0.01): labels from plain OMP on the training
     signals, Adam training (timed), then proposer-assisted OMP (top-2s
     candidates, restricted OMP, plain OMP where ||r|| > 8.5 sigma) against plain
-    OMP on fresh signals.  Sizes are reduced from the 1M / 1M pairs of the
-    workload to keep the run short; they are stated in the output."""
+    OMP on fresh signals: 2^20 training pairs and 2^20 fresh evaluation
+    signals, the workload's 1M / 1M (stated in the output)."""
     import torch
-    n_train, n_eval, epochs, B = 1 << 19, 1 << 19, 4, 4096
+    n_train, n_eval, epochs, B = 1 << 20, 1 << 20, 4, 4096
     c = si.config3(n_train=n_train, n_eval=n_eval)
     D = torch.from_numpy(c["D0"]).to(dev)
     Ytr = torch.from_numpy(c["Ytr"]).to(dev)
@@ -1060,6 +1060,29 @@ def run_mod_local(args):
             out["fp64"] = {"solve_ms": ms, "solve_tflops": flops / (ms / 1e3) / 1e12,
                            "fp64_frac": flops / (ms / 1e3) / FP64_PEAK_FLOPS, "kernels": kern}
     ctx.set_option(sdl.OPT_MOD_MIXED, 1)
+    if args.mod_sweep:
+        # the FP32 pass with the tile edge and cluster size set by hand (best of 3 calls)
+        sweep = {}
+        ctx.set_option(sdl.OPT_AUTOTUNE, 0)
+        try:
+            for ts in (32, 64):
+                for C in (1, 2, 4, 8, 16):
+                    ctx.set_option(sdl.OPT_MOD_TILE, ts)
+                    ctx.set_option(sdl.OPT_CLUSTER, C)
+                    sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
+                    ctx.profile(True)
+                    best = float("inf")
+                    for _ in range(3):
+                        ctx.profile_reset()
+                        sdl.mod_update_batched(Yp, p.offsets, idx, val, D.clone())
+                        best = min(best, ctx.profile_read()["mod_solve_fp32"][2])
+                    ctx.profile(False)
+                    sweep[f"tile{ts}_cluster{C}"] = round(best, 3)
+        finally:
+            ctx.set_option(sdl.OPT_MOD_TILE, 0)
+            ctx.set_option(sdl.OPT_CLUSTER, 0)
+            ctx.set_option(sdl.OPT_AUTOTUNE, 1)
+        out["fp32_pass_ms_by_shape"] = sweep
     print(json.dumps({"metric": METRIC, "workload": f"mod_local_L{p.L}_K{p.K1}_m{p.m}_s{p.s1}_N{p.Y.shape[0]}", **out}),
           flush=True)
 
@@ -1214,6 +1237,8 @@ def main():
                     help="the main line's workload (patches or splitmerge), or a parity workload measured alone")
     ap.add_argument("--mod-local-images", type=int, default=32,
                     help="--workload mod-local: synthetic images of 16,384 patches (256 at full size)")
+    ap.add_argument("--mod-sweep", action="store_true",
+                    help="--workload mod-local: also time the FP32 pass at every tile edge and cluster size")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed steps of the per-subset plain form (0 skips it)")
     args = ap.parse_args()

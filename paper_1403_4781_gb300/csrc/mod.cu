@@ -191,9 +191,10 @@ __global__ void __launch_bounds__(256) mod_accum_kernel(ModArgs a) {
 // ---- 3 (FP32 signals): A and B from the CSC entries, warps over entry ranges --
 // Each warp takes 32 s consecutive CSC entries of a subset (atom-major, so a
 // range spans few atoms).  B[:, j] = sum x_ij y_i is accumulated per run of
-// equal atoms in double-single precision on the FP32 pipe -- each product x y of
-// two floats is split exactly into p + e by an FMA, then added with TwoSum, so
-// about 48 significant bits are kept -- and added to B in FP64 when the atom
+// equal atoms by compensated summation on the FP32 pipe -- each product x y of
+// two floats is split exactly into p + e by an FMA, p is added with TwoSum and
+// the errors are collected in a second float, so the run's sum is good to
+// about 2^-48 of its terms' magnitudes -- and added to B in FP64 when the atom
 // changes.  Every entry (i, j) adds x_ij x_ij2 (exact in FP64) to A[j][j2] for
 // the atoms j2 <= j of its signal, so A's lower triangle is complete.  A and B
 // start at zero; unused atoms get their identity row and previous value after.
@@ -201,16 +202,19 @@ struct DSum {
   float hi, lo;
 };
 
+// hi is the plain FP32 running sum; every rounding error it makes (TwoSum,
+// exact) and every product's low part e go into lo, which stays about 2^-24 of
+// the sum's magnitude per term, so its own rounding is negligible (compensated
+// summation, no renormalisation per term).  Explicit _rn operations keep the
+// compiler from contracting the sums with the product.
 __device__ __forceinline__ void ds_add_product(DSum &a, float x, float y) {
-  const float p = x * y;
+  const float p = __fmul_rn(x, y);
   const float e = fmaf(x, y, -p);          // x y = p + e exactly
-  const float s = a.hi + p;                // TwoSum(a.hi, p) = s + err
-  const float bb = s - a.hi;
-  const float err = (a.hi - (s - bb)) + (p - bb);
-  const float lo = a.lo + (e + err);
-  const float hi = s + lo;                  // renormalise
-  a.lo = lo - (hi - s);
-  a.hi = hi;
+  const float s = __fadd_rn(a.hi, p);      // TwoSum(a.hi, p) = s + err exactly
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(e, err));
 }
 
 template <int MU>
