@@ -398,13 +398,23 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
     D_host = torch.empty((p.K, p.m), dtype=torch.float32).pin_memory()
     out_host = torch.empty((2,), dtype=torch.float64).pin_memory()
 
+    # The inputs are copied into device buffers allocated once (a caller streaming
+    # batches would do the same), so every step presents the same pointers and
+    # the cached training-loop graphs apply; warm-up as for the device-resident
+    # steps.
+    dev_in = tuple(None if a is None else torch.empty(a.shape, dtype=a.dtype, device=dev) for a in host_t)
+
     def step_e2e(*inp_h):
-        Dd, o2, _, _ = step(*(None if a is None else a.to(dev, non_blocking=True) for a in inp_h))
+        for b, a in zip(dev_in, inp_h):
+            if a is not None:
+                b.copy_(a, non_blocking=True)
+        Dd, o2, _, _ = step(*dev_in)
         D_host.copy_(Dd, non_blocking=True)
         out_host.copy_(o2, non_blocking=True)
         return Dd, o2
 
-    step_e2e(*host_t)
+    for _ in range(max(warmup, 3)):
+        step_e2e(*host_t)
     barrier()
     e2e_ms, _ = _timed_steps(step_e2e, host_t, steps, flush, stream)
     e2e_total = max_over_ranks(float(sum(e2e_ms)), world, dev)
