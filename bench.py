@@ -472,8 +472,8 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
                 "timed": "instrumented eager pass over %d steps (%.2f ms/step)" % (psteps, prof_total_ms / psteps)}
     kernels = {k: {"ms_per_step": v[2] / psteps, "launches_per_step": v[0] / psteps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}
-    omp_names = ("omp", "omp_split", "gram", "omp_tc", "omp_rtc", "gram_tc", "bf16_image", "omp_x3", "gram_x3",
-                 "x3_image")
+    omp_names = ("omp", "omp_split", "gram", "omp_tc", "omp_rtc", "gram_tc", "bf16_image", "omp_x3", "omp_tf32",
+                 "gram_x3", "x3_image")
     omp_ms = sum(v[2] for k, v in prof.items() if k in omp_names) / psteps
 
     res = {
@@ -941,7 +941,8 @@ def run_denoise(args):
 def run_coding(args):
     """One OMP coding pass of 2^19 signals (m=256, K=512, s=8, noise 0.02, one
     dictionary) with FP32 CUDA-core correlations, with FP32-accurate
-    tensor-core ones (two-term TF32 split), with BF16 tensor-core ones
+    tensor-core ones (two-term TF32 split), with single-product TF32 ones,
+    with BF16 tensor-core ones
     (Batch-OMP selection) and with the BF16 residual form: the shape where the
     correlation GEMM is most of the arithmetic.  Printed as its own line; also
     the small case the tensor-core kernels are profiled on."""
@@ -959,8 +960,8 @@ def run_coding(args):
     ctx = sdl.context(0)
     stream = torch.cuda.current_stream(dev)
     out = {}
-    for name, prec, form in (("fp32", sdl.PREC_F32, 0), ("f32x3", sdl.PREC_F32X3, 0), ("bf16", sdl.PREC_BF16, 1),
-                             ("bf16_residual_form", sdl.PREC_BF16, 2)):
+    for name, prec, form in (("fp32", sdl.PREC_F32, 0), ("f32x3", sdl.PREC_F32X3, 0), ("tf32", sdl.PREC_TF32, 0),
+                             ("bf16", sdl.PREC_BF16, 1), ("bf16_residual_form", sdl.PREC_BF16, 2)):
         ctx.set_option(sdl.OPT_BF16_FORM, form)
         sdl.omp(D, Yg, s, prec=prec)
         torch.cuda.synchronize()
@@ -985,8 +986,8 @@ def run_coding(args):
 def run_coding_final(args):
     """The image-patch workload's final coding shape alone: 2^20 patches coded
     with s=16 against the 1024-atom overcomplete DCT (256 x 1024), with BF16
-    correlations (Batch-OMP selection and the residual form), FP32-accurate
-    (F32X3) and FP32 CUDA-core ones.  The small case the
+    correlations (Batch-OMP selection and the residual form), single-product
+    TF32, FP32-accurate (F32X3) and FP32 CUDA-core ones.  The small case the
     s=16 selection kernel is profiled on; printed as its own line."""
     import torch
 
@@ -1001,7 +1002,7 @@ def run_coding_final(args):
     stream = torch.cuda.current_stream(dev)
     out = {}
     for name, prec, form in (("bf16", sdl.PREC_BF16, 1), ("bf16_residual_form", sdl.PREC_BF16, 2),
-                             ("f32x3", sdl.PREC_F32X3, 0), ("fp32", sdl.PREC_F32, 0)):
+                             ("tf32", sdl.PREC_TF32, 0), ("f32x3", sdl.PREC_F32X3, 0), ("fp32", sdl.PREC_F32, 0)):
         ctx.set_option(sdl.OPT_BF16_FORM, form)
         sdl.omp(D, Y, s, prec=prec, with_resid=False)
         torch.cuda.synchronize()

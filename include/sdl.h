@@ -71,7 +71,13 @@ typedef enum {
      hi hi^T + hi lo^T + lo hi^T with FP32 accumulation: within 3 2^-22 of each
      |x_i z_i| plus the FP32 accumulation, the accuracy of the FP32 CUDA-core
      sum; the OMP loop, refit and refinement step as for SDL_PREC_F32. */
-  SDL_PREC_F32X3 = 3
+  SDL_PREC_F32X3 = 3,
+  /* FP32 data; correlations from one TF32 product on the tensor cores
+     (kind::tf32, each operand rounded to 11 significant bits: within 2 2^-11
+     of each |x_i z_i| plus the FP32 accumulation), the Gram from the
+     three-product split as for SDL_PREC_F32X3; coefficients on the support
+     corrected by one FP32 refinement step, as for SDL_PREC_BF16. */
+  SDL_PREC_TF32 = 4
 } sdl_precision;
 
 typedef struct sdl_ctx sdl_ctx;
@@ -204,8 +210,9 @@ sdl_status sdl_residual(sdl_ctx *ctx, sdl_precision prec, const void *Y, int m, 
  * hi = bf16(d), lo = bf16(d - hi), and G = hi hi^T + hi lo^T + lo hi^T on the
  * tensor cores with FP32 accumulation, about 2^-16 of |d_i||d_j| from the
  * exact Gram.  F32X3: the same three products from a two-term TF32 split
- * (kind::tf32), within 3 2^-22 of |d_i||d_j| plus the FP32 accumulation.  BF16
- * and F32X3 synchronise to read the tensor-core kernels' error word.
+ * (kind::tf32), within 3 2^-22 of |d_i||d_j| plus the FP32 accumulation; TF32
+ * forms the same three-product Gram.  BF16, F32X3 and TF32 synchronise to read
+ * the tensor-core kernels' error word.
  * Errors: SDL_EINVAL for a bad shape or pointer, SDL_ETIMEOUT when a bounded
  * wait of the tensor-core kernel gave up. */
 sdl_status sdl_gram(sdl_ctx *ctx, sdl_precision prec, const void *D, int m, int K, int L, void *G);
@@ -426,7 +433,7 @@ sdl_status sdl_omp_noalloc(void *stream, const float *D, int m, int K, const flo
  *     atoms unchanged and the context usable.  The same number, capped at
  *     2^22, bounds the mbarrier waits of the persistent tensor-core
  *     correlation and Gram kernels (SDL_PREC_BF16 correlations,
- *     SDL_PREC_F32X3).
+ *     SDL_PREC_F32X3, SDL_PREC_TF32).
  *   SDL_OPT_WAIT_TEST: 1 makes one block of every wide-solve group leave at
  *     once, so that the others' first barrier wait runs out, and the loader
  *     role of the persistent tensor-core kernels leave before its first copy,

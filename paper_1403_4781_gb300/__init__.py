@@ -21,12 +21,12 @@ import threading
 from . import _build
 
 __all__ = [
-    "PREC_F64", "PREC_F32", "PREC_BF16", "PREC_F32X3", "SdlError", "lib", "library_path", "declared_symbols",
+    "PREC_F64", "PREC_F32", "PREC_BF16", "PREC_F32X3", "PREC_TF32", "SdlError", "lib", "library_path", "declared_symbols",
     "Context", "context", "omp", "omp_batched", "mod_update", "mod_update_batched", "split",
     "init_dict", "local_train", "merge", "residual", "recovery", "Proposer",
 ]
 
-PREC_F64, PREC_F32, PREC_BF16, PREC_F32X3 = 0, 1, 2, 3
+PREC_F64, PREC_F32, PREC_BF16, PREC_F32X3, PREC_TF32 = 0, 1, 2, 3, 4
 _STATUS = {0: "SDL_OK", 1: "SDL_EINVAL", 2: "SDL_ENOTPD", 3: "SDL_ETIMEOUT", 4: "SDL_ECUDA",
            5: "SDL_ENOMEM", 6: "SDL_ERANGE"}
 

@@ -375,7 +375,8 @@ bool aligned16(const void *p) { return p && ((uintptr_t)p & 15u) == 0; }
   } while (0)
 
 sdl_status check_prec(sdl_ctx *ctx, sdl_precision prec) {
-  if (prec == SDL_PREC_F64 || prec == SDL_PREC_F32 || prec == SDL_PREC_BF16 || prec == SDL_PREC_F32X3)
+  if (prec == SDL_PREC_F64 || prec == SDL_PREC_F32 || prec == SDL_PREC_BF16 || prec == SDL_PREC_F32X3 ||
+      prec == SDL_PREC_TF32)
     return SDL_OK;
   return set_error(ctx, SDL_EINVAL, "unknown precision");
 }
@@ -532,8 +533,10 @@ cudaError_t run_omp_bf16(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t
 
 // One FP32-accurate tensor-core coding pass: TF32 hi and lo images of D (img
 // holds hi, then lo), Gram and correlations as three TF32 products on the
-// tensor cores, then the FP32 selection loop.
-cudaError_t run_omp_x3(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *err, float *a0c) {
+// tensor cores, then the FP32 selection loop.  single: the correlations from
+// one TF32 product (SDL_PREC_TF32), the Gram still from three.
+cudaError_t run_omp_x3(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *err, float *a0c,
+                       bool single) {
   cudaStream_t sm = ctx->stream;
   void *lo = static_cast<unsigned char *>(img) + tc_image_bytes(oa.L, oa.K, oa.m);
   oa.err = err;
@@ -547,13 +550,13 @@ cudaError_t run_omp_x3(sdl_ctx *ctx, OmpArgs &oa, void *img, float *G, int32_t *
                           x3_wait(ctx), sm);
   });
   if (e != cudaSuccess) return e;
-  auto pass = [&] { return launch_omp_x3(oa, img, lo, a0c, ctx->num_sms, x3_wait(ctx), sm); };
-  e = tune_select(ctx, oa, "x3", [&] {
+  auto pass = [&] { return launch_omp_x3(oa, img, lo, a0c, ctx->num_sms, x3_wait(ctx), sm, single); };
+  e = tune_select(ctx, oa, single ? "tf32" : "x3", [&] {
     ctx->launches += split_kernels(oa);
     return pass();
   });
   if (e != cudaSuccess) return e;
-  return timed(ctx, "omp_x3", split_kernels(oa), pass);
+  return timed(ctx, single ? "omp_tf32" : "omp_x3", split_kernels(oa), pass);
 }
 
 // The FP32 two-kernel coding pass (correlation GEMM, then the selection
@@ -705,8 +708,10 @@ size_t train_ws_bytes(int L, int K, int m, int64_t n, int s, int iters) {
 template <typename T>
 sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, int L, int K, int s,
                      double eps, int iters, T *D, double *xfro, double *rmse, sdl_precision tcp = SDL_PREC_F64) {
-  // tcp: SDL_PREC_BF16 or SDL_PREC_F32X3 run the coding passes on the tensor cores
-  const bool bf16 = sizeof(T) == 4 && tcp == SDL_PREC_BF16, x3 = sizeof(T) == 4 && tcp == SDL_PREC_F32X3;
+  // tcp: SDL_PREC_BF16, SDL_PREC_F32X3 or SDL_PREC_TF32 run the coding passes on the tensor cores
+  const bool bf16 = sizeof(T) == 4 && tcp == SDL_PREC_BF16;
+  const bool tf32 = sizeof(T) == 4 && tcp == SDL_PREC_TF32;
+  const bool x3 = sizeof(T) == 4 && (tcp == SDL_PREC_F32X3 || tf32);
   const bool tc = bf16 || x3;
   const int64_t n = offsets[L];
   sdl_status st;
@@ -755,7 +760,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
       if (bf16) {
         e = run_omp_bf16(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c, g16);
       } else if (x3) {
-        e = run_omp_x3(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c);
+        e = run_omp_x3(ctx, oa, img, reinterpret_cast<float *>(G), tc_err, a0c, tf32);
       } else if (split) {
         SDL_CUDA(timed(ctx, "gram", 1, [&] { return launch_gram<T>(D, m, K, L, G, sm); }), "gram");
         e = run_omp_split(ctx, oa, a0c);
@@ -794,7 +799,7 @@ sdl_status train_run(sdl_ctx *ctx, const T *Y, int m, const int64_t *offsets, in
   } else {
     char kb[512];
     snprintf(kb, sizeof(kb), "%zu:%d:%p:%p:%p:%p:%p:%p:%d:%d:%d:%d:%lld:%lld:%lld:%a:%d:%d:%d:%d:%d:%d:%d:%d:%lld:%d:%d:%d",
-             sizeof(T), (int)bf16 + 2 * (int)x3, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
+             sizeof(T), (int)bf16 + 2 * (int)x3 + 4 * (int)tf32, (const void *)Y, (void *)D, (void *)xfro, (void *)rmse, (void *)ctx->ws.base,
              (void *)d_off, m, K, s, L, (long long)n, (long long)tiles, (long long)ma.total_tiles, eps, iters,
              ctx->opt_mod_solve * 2 + ctx->opt_mod_mixed, ctx->opt_tile, ctx->opt_cluster * 4 + ctx->opt_sm_blocks,
              ctx->opt_autotune,
@@ -923,7 +928,7 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
   int64_t *d_off = nullptr;
   int32_t *d_tiles = nullptr;
   int64_t tiles = 0;
-  const bool bf16 = prec == SDL_PREC_BF16, x3 = prec == SDL_PREC_F32X3;
+  const bool bf16 = prec == SDL_PREC_BF16, x3 = prec == SDL_PREC_F32X3 || prec == SDL_PREC_TF32;
   const bool split = prec == SDL_PREC_F32 && omp_split_f32(ctx, K, m, s);
   const int tile = bf16 || x3 || split ? omp_tc_tile_signals(K, m, s) : omp_tile_signals();
   if (tile <= 0) return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
@@ -944,10 +949,10 @@ sdl_status sdl_omp_batched(sdl_ctx *ctx, sdl_precision prec, const void *D, int 
       return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
     SDL_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream), "err clear");
     cudaError_t e = bf16 ? run_omp_bf16(ctx, a, img, static_cast<float *>(G), err, a0c, g16)
-                         : run_omp_x3(ctx, a, img, static_cast<float *>(G), err, a0c);
+                         : run_omp_x3(ctx, a, img, static_cast<float *>(G), err, a0c, prec == SDL_PREC_TF32);
     if (e == cudaErrorInvalidConfiguration)
       return set_error(ctx, SDL_EINVAL, "shape too large for the tensor-core OMP kernel");
-    SDL_CUDA(e, bf16 ? "omp bf16" : "omp f32x3");
+    SDL_CUDA(e, bf16 ? "omp bf16" : (prec == SDL_PREC_TF32 ? "omp tf32" : "omp f32x3"));
     return tc_status(ctx, err);
   }
   if (prec == SDL_PREC_F64) {
@@ -1229,7 +1234,7 @@ sdl_status sdl_gram(sdl_ctx *ctx, sdl_precision prec, const void *D, int m, int 
   if (!img || !err) return set_error(ctx, SDL_ENOMEM, "workspace carve-up failed");
   void *lo = static_cast<unsigned char *>(img) + tc_image_bytes(L, K, m);
   SDL_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), sm), "err clear");
-  if (prec == SDL_PREC_F32X3) {
+  if (prec == SDL_PREC_F32X3 || prec == SDL_PREC_TF32) {   // TF32: the same FP32-accurate split Gram
     SDL_CUDA(timed(ctx, "x3_image", 1, [&] {
                return launch_x3_image(static_cast<const float *>(D), K, m, L, img, lo, sm);
              }), "tf32 image");

@@ -1,4 +1,5 @@
-// FP32-accurate tensor-core correlations and Gram for OMP (SDL_PREC_F32X3).
+// FP32-accurate tensor-core correlations and Gram for OMP (SDL_PREC_F32X3),
+// and the single-product TF32 correlations (SDL_PREC_TF32).
 //
 // OMP's first step ranks alpha0 = D^T y (Sec. 1) and the Batch-OMP update
 // reads G = D^T D; the FP32 path forms both with FMA chains on the CUDA cores.
@@ -9,6 +10,11 @@
 // 3 2^-22 of each |x_i z_i|, below the FP32 sum's own rounding bound (m 2^-24
 // at m >= 64), so the selection that follows (the FP32 selection kernel with
 // its refit and refinement step on the support) meets the FP32 parity bar.
+// The TF32 precision (SDL_PREC_TF32) takes the correlations from hi hi^T
+// alone (one product; each operand rounded to 11 significant bits, so within
+// 2 2^-11 of each |x_i z_i|) and keeps the three-product Gram, whose factor
+// lets the selection's FP32 correction step on the support remove that
+// rounding from the coefficients.
 //
 // Layout.  Operands are K-major canonical images of 32-bit elements without
 // swizzle: core matrices of 8 rows x 16 bytes (four elements), 128 bytes apart
@@ -160,7 +166,9 @@ constexpr size_t kX3Bar = kX3B + 2 * kX3Stages * (size_t)kX3Slab;
 constexpr size_t kX3Smem = kX3Bar + sizeof(X3Bars);
 
 
-template <bool GRAM>
+// NP = 3: the three products of the split; NP = 1: hi hi^T alone (one TF32
+// product, SDL_PREC_TF32), the lo images neither formed nor loaded.
+template <bool GRAM, int NP>
 __global__ void __launch_bounds__(kX3Threads, 1) corr_x3_kernel(X3Job j) {
   extern __shared__ __align__(1024) unsigned char smem[];
   X3Bars *bars = reinterpret_cast<X3Bars *>(smem + kX3Bar);
@@ -238,10 +246,12 @@ __global__ void __launch_bounds__(kX3Threads, 1) corr_x3_kernel(X3Job j) {
         for (int i = 0; i < 8; ++i) {
           const uint32_t off = x3_offset(rbase + 16 * i, 4 * q4);
           const float4 h = make_float4(tf32_rn(v[i].x), tf32_rn(v[i].y), tf32_rn(v[i].z), tf32_rn(v[i].w));
-          const float4 l = make_float4(tf32_rn(v[i].x - h.x), tf32_rn(v[i].y - h.y), tf32_rn(v[i].z - h.z),
-                                       tf32_rn(v[i].w - h.w));
           *reinterpret_cast<float4 *>(Ah + off) = h;
-          *reinterpret_cast<float4 *>(Al + off) = l;
+          if (NP == 3) {
+            const float4 l = make_float4(tf32_rn(v[i].x - h.x), tf32_rn(v[i].y - h.y), tf32_rn(v[i].z - h.z),
+                                         tf32_rn(v[i].w - h.w));
+            *reinterpret_cast<float4 *>(Al + off) = l;
+          }
         }
         tc::fence_proxy_async();
         tc::mbar_arrive(&bars->full_a[ab]);
@@ -314,9 +324,9 @@ __global__ void __launch_bounds__(kX3Threads, 1) corr_x3_kernel(X3Job j) {
             }
             const size_t src = slab + (size_t)(p * kX3Pass + ch * kX3NT) * kX3KB * 4;
             unsigned char *dst = smem + kX3B + (size_t)s * 2 * kX3Slab;
-            tc::mbar_expect_tx(&bars->full_b[s], 2 * kX3Slab);
+            tc::mbar_expect_tx(&bars->full_b[s], (NP == 3 ? 2 : 1) * kX3Slab);
             tc::bulk_g2s(dst, j.hi + src, kX3Slab, &bars->full_b[s]);
-            tc::bulk_g2s(dst + kX3Slab, j.lo + src, kX3Slab, &bars->full_b[s]);
+            if (NP == 3) tc::bulk_g2s(dst + kX3Slab, j.lo + src, kX3Slab, &bars->full_b[s]);
             ++c;
           }
         }
@@ -365,8 +375,10 @@ __global__ void __launch_bounds__(kX3Threads, 1) corr_x3_kernel(X3Job j) {
               const uint64_t dah = tc::smem_desc(ahi + o, 128, 1024), dal = tc::smem_desc(alo + o, 128, 1024);
               const uint64_t dbh = tc::smem_desc(bhi + o, 128, 1024), dbl = tc::smem_desc(blo + o, 128, 1024);
               mma_tf32(d, dah, dbh, idesc, b > 0 || ks > 0);
-              mma_tf32(d, dah, dbl, idesc, true);
-              mma_tf32(d, dal, dbh, idesc, true);
+              if (NP == 3) {
+                mma_tf32(d, dah, dbl, idesc, true);
+                mma_tf32(d, dal, dbh, idesc, true);
+              }
             }
             tc::mma_commit(&bars->empty_b[s]);
             ++c;
@@ -389,11 +401,11 @@ __global__ void __launch_bounds__(kX3Threads, 1) corr_x3_kernel(X3Job j) {
   if (warp == 9) tc::tmem_dealloc(tbase, 2 * kX3Pass);
 }
 
-template <bool GRAM>
+template <bool GRAM, int NP>
 cudaError_t launch_x3(const X3Job &j, int num_sms, cudaStream_t st) {
   const int64_t nitem = j.ntile * j.npass;
   if (nitem <= 0) return cudaSuccess;
-  auto kern = corr_x3_kernel<GRAM>;
+  auto kern = corr_x3_kernel<GRAM, NP>;
   // the block takes all 512 TMEM columns: one block per SM
   const size_t smem = tc::smem_for_tmem(kX3Smem, 2 * kX3Pass);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
@@ -447,18 +459,18 @@ cudaError_t launch_gram_x3(const float *D, const void *hi, const void *lo, int K
   X3Job j = x3_job(a, hi, lo, G, err, w);
   j.tile0 = 0;
   j.ntile = (int64_t)L * j.tpd;
-  return launch_x3<true>(j, num_sms, st);
+  return launch_x3<true, 3>(j, num_sms, st);
 }
 
 cudaError_t launch_omp_x3(const OmpArgs &a, const void *hi, const void *lo, float *a0c, int num_sms,
-                          const X3Wait &w, cudaStream_t st) {
+                          const X3Wait &w, cudaStream_t st, bool single) {
   if (a.total_tiles <= 0) return cudaSuccess;
   X3Job j = x3_job(a, hi, lo, a0c, a.err, w);
   const int64_t chunk = omp_tc_chunk_tiles(a.K, a.total_tiles, a.a0_cap);
   for (int64_t g0 = 0; g0 < a.total_tiles; g0 += chunk) {
     j.tile0 = g0;
     j.ntile = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
-    cudaError_t e = launch_x3<false>(j, num_sms, st);
+    cudaError_t e = single ? launch_x3<false, 1>(j, num_sms, st) : launch_x3<false, 3>(j, num_sms, st);
     if (e != cudaSuccess) return e;
     if ((e = launch_omp_select(a, a0c, g0, j.ntile, false, st)) != cudaSuccess) return e;
   }

@@ -207,8 +207,10 @@ size_t x3_image_bytes(int L, int K, int m);
 cudaError_t launch_x3_image(const float *D, int K, int m, int L, void *hi, void *lo, cudaStream_t st);
 cudaError_t launch_gram_x3(const float *D, const void *hi, const void *lo, int K, int m, int L, float *G,
                            int32_t *err, int num_sms, const X3Wait &w, cudaStream_t st);
+// single: the correlations from hi hi^T alone, one TF32 product (SDL_PREC_TF32;
+// the Gram stays the three-product split).
 cudaError_t launch_omp_x3(const OmpArgs &a, const void *hi, const void *lo, float *a0c, int num_sms,
-                          const X3Wait &w, cudaStream_t st);
+                          const X3Wait &w, cudaStream_t st, bool single = false);
 // Correlation features F = |D_t^T y| (FP32 FMA chains) of the 128-signal tiles
 // tile0 .. tile0+ntile-1 of the plan; signal row r goes to row r - row_base of F.
 cudaError_t launch_corr_features(const OmpArgs &a, int64_t tile0, int64_t ntile, int64_t row_base, float *F,

@@ -63,6 +63,15 @@ def x3_gap_tol(m: int, ynorm: np.ndarray) -> np.ndarray:
     return np.maximum(1e-6, 2 * x3_unit(m) * ynorm)
 
 
+def tf32_unit(m: int) -> float:
+    """Relative error bound of one TF32-operand correlation term sum: each
+    operand rounded to nearest with 11 significant bits (unit 2^-11), the
+    product of the two exact, the FP32 accumulation of the tensor cores with a
+    unit of 2^-23 per addition (their rounding of the sum is not documented)."""
+    u = 2.0 ** -11
+    return 2 * u + u * u + gamma(m, 2.0 ** -23) * (1 + 2 * u)
+
+
 def bf16_unit(m: int) -> float:
     """Relative error bound of one BF16-operand correlation term sum."""
     return 2 * UB16 + UB16 ** 2 + gamma(m) * (1 + 2 * UB16)
@@ -227,7 +236,7 @@ def compare_codes(D, Y, gpu_idx, gpu_val, gpu_nnz, gpu_r2, orc, gap_tol, coef_rt
 
 
 def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0.05, residual=False, eps=None,
-                     h16=False):
+                     h16=False, unit=None):
     """BF16-operand correlations (tcgen05) with FP32 refits: every code is valid
     on its own support (exact least squares within coef_rtol, the reported
     residual that fit's); a support may differ from the oracle's only at a step
@@ -242,12 +251,13 @@ def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0
     2^-11 sum_p |G_jp x_p| to E.  eps: the error-constrained stop; a code that agrees
     with the oracle's on their common prefix but stops at another length is a
     near-tie on the stop itself when the prefix's least-squares residual norm
-    is eps to within 1e-4 eps (counted with the rounding-level ones).  Returns
-    (signals that differ there, signals that differ at rounding-level steps or
-    at the stop)."""
+    is eps to within 1e-4 eps (counted with the rounding-level ones).  unit:
+    the per-term bound e in place of the BF16 one (tf32_unit for one TF32
+    product).  Returns (signals that differ there, signals that differ at
+    rounding-level steps or at the stop)."""
     D64, Y64 = D.astype(np.float64), Y.astype(np.float64)
     n, s = idx.shape
-    e16 = bf16_unit(D.shape[1])
+    e16 = bf16_unit(D.shape[1]) if unit is None else unit
     excused = rounding = 0
     for i in range(n):
         k = int(nnz[i])
@@ -280,7 +290,7 @@ def check_bf16_codes(D, Y, idx, val, nnz, r2, orc, coef_rtol=2e-2, max_excused=0
             else:
                 excused += 1
     assert excused <= max(2, max_excused * n), (
-        f"{excused} of {n} BF16 supports differ at near-ties, above the cap {max_excused:.2%} "
+        f"{excused} of {n} supports differ at near-ties, above the cap {max_excused:.2%} "
         f"({rounding} more at rounding-level steps)")
     return excused, rounding
 

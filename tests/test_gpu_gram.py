@@ -11,13 +11,16 @@ unit atoms (Cauchy-Schwarz), plus the FP32 accumulation's gamma_m.  The test
 allows 4 2^-16 + gamma_m, room for an accumulation order the tensor cores do
 not document.  A single BF16 product (the split's hi hi^T alone) would be
 off by about 2^-8: the bound fails for it, which the last test checks with
-numpy on the host."""
+numpy on the host.  F32X3 and TF32 (the TF32 precision takes its Gram from the
+same split): the two-term TF32 split, within 3 2^-22 per product plus the
+FP32 accumulation (tests/_parity.py: x3_unit), doubled."""
 import numpy as np
 import pytest
 import torch
 
 import paper_1403_4781_gb300 as sdl
 import sdl_inputs as si
+from _parity import x3_unit
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -36,7 +39,7 @@ SHAPES = [(64, 256, 3), (144, 512, 2), (30, 60, 4), (256, 1024, 1), (8, 16, 5), 
 
 
 @pytest.mark.parametrize("m,K,L", SHAPES)
-@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16", "f32x3", "tf32"])
 def test_gram_matches_fp64_product(m, K, L, prec):
     rng = np.random.default_rng(800 + m + K + L)
     D = np.stack([si.unit_gaussian_atoms(rng, m, K) for _ in range(L)])
@@ -45,8 +48,10 @@ def test_gram_matches_fp64_product(m, K, L, prec):
     else:
         D = D.astype(np.float32)
         Dd = D
-        tol = _gamma(m) if prec == "f32" else 4 * 2.0 ** -16 + _gamma(m)
-        p = sdl.PREC_F32 if prec == "f32" else sdl.PREC_BF16
+        # F32X3 and TF32 share the two-term TF32 split Gram: 3 2^-22 per product
+        # plus the accumulation (x3_unit), doubled for an undocumented order
+        tol = {"f32": _gamma(m), "bf16": 4 * 2.0 ** -16 + _gamma(m)}.get(prec, 2 * x3_unit(m))
+        p = {"f32": sdl.PREC_F32, "bf16": sdl.PREC_BF16, "f32x3": sdl.PREC_F32X3, "tf32": sdl.PREC_TF32}[prec]
     G = sdl.gram(_t(Dd), prec=p).cpu().numpy().astype(np.float64)
     D64 = D.astype(np.float64)
     want = np.einsum("lkm,ljm->lkj", D64, D64)

@@ -7,7 +7,7 @@ splits).  Exact products of TF32 values fit a double, so the sums below are
 exact but for FP64 rounding far below the bound."""
 import numpy as np
 
-from _parity import x3_unit
+from _parity import tf32_unit, x3_unit
 
 
 def tf32_rna(x):
@@ -44,3 +44,25 @@ def test_split_error_within_bound_and_single_product_outside():
         # and errs about 2^10 times more than the split
         assert (np.abs(one - exact) > 3 * 2.0 ** -22 * scale).any()
         assert np.abs(one - exact).max() > 300 * np.abs(split - exact).max()
+
+
+def test_single_tf32_product_within_its_own_bound_and_tight():
+    """The single-product TF32 precision's bound (tests/_parity.py: tf32_unit):
+    each operand rounded to 11 significant bits misses x z by at most
+    (2 2^-11 + 2^-22) |x z|, so every correlation's error is within
+    tf32_unit(m) sum_i |x_i z_i|; one operand pair, x = z = 1 + 2^-11 + 2^-13
+    (rounded up to 1 + 2^-10), reaches 1.5 2^-11 of |x z|, so the bound's
+    leading term 2 2^-11 is tight to a factor 4/3."""
+    rng = np.random.default_rng(8)
+    for m in (8, 64, 256):
+        X = rng.standard_normal((400, m)).astype(np.float32)
+        Z = rng.standard_normal((300, m)).astype(np.float32)
+        Z /= np.linalg.norm(Z, axis=1, keepdims=True)
+        f = lambda a, b: a.astype(np.float64) @ b.astype(np.float64).T
+        err = np.abs(f(tf32_rna(X), tf32_rna(Z)) - f(X, Z))
+        scale = np.abs(X.astype(np.float64)) @ np.abs(Z.astype(np.float64)).T
+        assert (err <= tf32_unit(m) * scale).all()
+    xs = np.float32(1.0 + 2.0 ** -11 + 2.0 ** -13)
+    assert float(tf32_rna(np.array([xs]))[0]) == 1.0 + 2.0 ** -10
+    p_err = abs(float(tf32_rna(np.array([xs]))[0]) ** 2 - float(xs) ** 2) / float(xs) ** 2
+    assert 1.4 * 2.0 ** -11 < p_err <= 2 * 2.0 ** -11 + 2.0 ** -22
