@@ -162,6 +162,8 @@ def algorithmic_work(p):
                    + p.N * omp_flops(K, p.s)),
         "omp_x3": ("alu", p.iters_local * p.N * omp_flops(K1, p.s1) + p.iters_merge * nm * omp_flops(K, p.s2)
                    + p.N * omp_flops(K, p.s)),
+        "omp_tf32": ("alu", p.iters_local * p.N * omp_flops(K1, p.s1) + p.iters_merge * nm * omp_flops(K, p.s2)
+                     + p.N * omp_flops(K, p.s)),
         # residual form: D^T r of every step on the tensor cores (2 m K s per signal)
         "omp_rtc": ("tensor", 2 * m * (p.iters_local * p.N * K1 * p.s1 + p.iters_merge * nm * K * p.s2 + p.N * K * p.s)),
         "gram": ("alu", p.iters_local * L * 2 * K1 * K1 * m + p.iters_merge * 2 * K * K * m),
@@ -331,7 +333,7 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
             dist.barrier()
         torch.cuda.synchronize()
 
-    precs = {"f32x3": sdl.PREC_F32X3, "bf16": sdl.PREC_BF16, "fp32": sdl.PREC_F32}
+    precs = {"f32x3": sdl.PREC_F32X3, "bf16": sdl.PREC_BF16, "fp32": sdl.PREC_F32, "tf32": sdl.PREC_TF32}
     chosen = args.chosen_prec
 
     def step(*inp):
@@ -362,9 +364,10 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
     # ---- the same form with the other coding precisions (graphs as above)
     labels = {"fp32": "FP32 CUDA-core correlations and Gram",
               "bf16": "BF16 tensor-core correlations and Gram (two-term split) with an FP32 correction step",
-              "f32x3": "FP32-accurate tensor-core correlations and Gram (two-term TF32 split)"}
+              "f32x3": "FP32-accurate tensor-core correlations and Gram (two-term TF32 split)",
+              "tf32": "single-product TF32 tensor-core correlations, the TF32-split Gram, an FP32 correction step"}
     alt_forms = {}
-    for alt in [a for a in ("fp32", "bf16", "f32x3") if a != chosen]:
+    for alt in [a for a in ("fp32", "bf16", "tf32", "f32x3") if a != chosen]:
         fsteps = min(steps, 3)
         for _ in range(3):
             forms.step(inputs, precs[alt])
@@ -480,7 +483,7 @@ def run_main(args, rank, world, local_rank, name, extra_key=False):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f32x3": "tf32x3+f32+f64", "bf16": "bf16+f32+f64", "fp32": "f32+f64"}[chosen],
+        "dtype": {"f32x3": "tf32x3+f32+f64", "bf16": "bf16+f32+f64", "fp32": "f32+f64", "tf32": "tf32+f32+f64"}[chosen],
         "data": ("synthetic images (seeded piecewise-smooth fields + noise 0.1), 16x16 patches"
                  if name == "patches" else "synthetic (seeded; Sec. 3.1 data model)"),
         "config": workload_config(p, name, world),
@@ -534,7 +537,7 @@ def run_ours(args, rank, world, local_rank):
         ex = run_main(args, rank, world, local_rank, "splitmerge", extra_key=True)
         res["splitmerge_200k"] = {k: ex.get(k) for k in (
             "config", "value", "unit", "steps", "ms_per_step", "rmse_final", "oracle_rmse_final", "mse_train_db",
-            "plain", "fp32_form", "bf16_form", "f32x3_form", "precision_error", "e2e", "roofline", "omp_stage",
+            "plain", "fp32_form", "bf16_form", "tf32_form", "f32x3_form", "precision_error", "e2e", "roofline", "omp_stage",
             "cpu_baseline", "clocks")}
     if rank == 0 and world == 1 and not args.no_proposer:
         flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
@@ -1237,7 +1240,7 @@ def main():
     ap.add_argument("--no-proposer", action="store_true", help="skip the proposer sub-benchmarks")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 200,000-signal split-and-merge workload's extra key")
-    ap.add_argument("--chosen-prec", choices=["f32x3", "bf16", "fp32"], default="bf16",
+    ap.add_argument("--chosen-prec", choices=["f32x3", "bf16", "tf32", "fp32"], default="bf16",
                     help="coding precision of the chosen form (the others are timed beside it)")
     ap.add_argument("--error-sample", type=int, default=2000,
                     help="signals of the final coding the oracle recodes for the precision error")

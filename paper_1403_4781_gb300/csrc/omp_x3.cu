@@ -205,15 +205,20 @@ __global__ void __launch_bounds__(kX3Threads, 1) corr_x3_kernel(X3Job j) {
   auto chunks_of = [&](int p) { return K - p * kX3Pass > kX3NT ? 2 : 1; };
 
   if (warp < 4) {
-    // ---- converters: rows (tid >> 3) + 16 i, entries 4 (tid & 7) .. + 3 of each block
-    const int q4 = tid & 7, rbase = tid >> 3;
-    const bool vec = (m & 3) == 0;
+    // ---- converters: item u of thread (warp, lane) is row 8 (warp + 4 (u / 2)) +
+    // (lane & 7) and entries 4 ((lane >> 3) + 4 (u & 1)) .. + 3 of each block,
+    // so the eight lanes of a quarter-warp store 128 contiguous bytes (rows 0-7
+    // of one core matrix: no bank conflict)
+    const int rr = lane & 7, gq = lane >> 3;
+    auto row_of = [&](int u) { return 8 * (warp + 4 * (u >> 1)) + rr; };
+    auto grp_of = [&](int u) { return gq + 4 * (u & 1); };
+    const bool vec = (m & 3) == 0 &&
+                     (reinterpret_cast<uintptr_t>(GRAM ? j.a.D : j.a.Y) & 15) == 0;   // 16-byte rows
     float4 v[8];
     auto load = [&](const X3Tile &T, int b) {
-      const int k = b * kX3KB + 4 * q4;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int r = rbase + 16 * i;
+        const int r = row_of(i), k = b * kX3KB + 4 * grp_of(i);
         const float *src = T.rows + (size_t)r * m + k;
         if (r >= T.nrow || k >= m) {
           v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(kX3Threads, 1) corr_x3_kernel(X3Job j) {
         unsigned char *Al = Ah + kX3Slab;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const uint32_t off = x3_offset(rbase + 16 * i, 4 * q4);
+          const uint32_t off = x3_offset(row_of(i), 4 * grp_of(i));
           const float4 h = make_float4(tf32_rn(v[i].x), tf32_rn(v[i].y), tf32_rn(v[i].z), tf32_rn(v[i].w));
           *reinterpret_cast<float4 *>(Ah + off) = h;
           if (NP == 3) {
