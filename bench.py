@@ -784,6 +784,21 @@ def conditioned_bench(sdl, dev, flush, stream):
             "proposed_pass_kernel_ms": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}
 
 
+def run_proposer(args):
+    """The learned-proposer workload (config of 2^20 training and 2^20
+    evaluation pairs, m=64, K=256, s=6) alone, printed as its own line."""
+    import torch
+
+    import paper_1403_4781_gb300 as sdl
+
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    res = {"metric": METRIC, "workload": "proposer_m64_K256_s6_train1048576_eval1048576",
+           "data": "synthetic (seeded; Sec. 3.1 data model)",
+           **proposer_bench(sdl, dev, flush, torch.cuda.current_stream(dev))}
+    print(json.dumps(res), flush=True)
+
+
 def run_conditioned(args):
     """The dictionary-conditioned proposer workload alone, printed as its own line."""
     import torch
@@ -1246,7 +1261,7 @@ def main():
                     help="signals of the final coding the oracle recodes for the precision error")
     ap.add_argument("--workload", choices=["patches", "splitmerge", "uneven-A", "uneven-B", "denoise", "coding",
                                            "coding-final",
-                                           "conditioned", "mod-local"],
+                                           "conditioned", "proposer", "mod-local"],
                     default="patches",
                     help="the main line's workload (patches or splitmerge), or a parity workload measured alone")
     ap.add_argument("--mod-local-images", type=int, default=32,
@@ -1264,7 +1279,7 @@ def main():
     elif args.workload in WORKLOADS:
         run_ours(args, rank, world, local_rank)
     elif rank == 0:
-        {"denoise": run_denoise, "coding": run_coding, "conditioned": run_conditioned,
+        {"denoise": run_denoise, "coding": run_coding, "conditioned": run_conditioned, "proposer": run_proposer,
          "mod-local": run_mod_local, "coding-final": run_coding_final}.get(
             args.workload, lambda a: run_uneven(a, args.workload[-1]))(args)
 
