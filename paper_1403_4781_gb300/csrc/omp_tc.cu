@@ -179,22 +179,24 @@ __global__ void __launch_bounds__(128) gram_tc_kernel(const unsigned char *__res
 }
 
 // ---- correlations: alpha0 = Y D^T of 128-signal tiles into global memory ----
-// A persistent block per SM runs work items in turn: an item is a tile of 128
-// signals (the MMA's M) against one pass of 256 atoms (the MMA's N and one
-// 256-column TMEM accumulator).  The dictionary comes from its slab image
+// A persistent block per SM runs its tiles of 128 signals (the MMA's M) in
+// turn, each as ceil(K / 256) work items: one pass of 256 atoms (the MMA's N
+// and one 256-column TMEM accumulator) each.  The dictionary comes from its slab image
 // ([L][mp/64][Kp][64] BF16, Kp = K rounded up to 256: the 256 atoms x 64
 // entries of one pass and block are one contiguous 32 KB slab).  Four roles
 // meet only at mbarriers:
-//   warps 0-3  convert the tile's signal entries, 64 at a time, from FP32 into
-//              a 16 KB BF16 block image (three buffers); thread (w, lane) takes
-//              row lane & 7 of 8-row groups w, w + 4, w + 8, w + 12 and entry
-//              groups lane >> 3 and + 4, so a quarter-warp's 16-byte stores
-//              fill 128 contiguous bytes (no bank conflict); the next block's
-//              loads fly while the thread waits for a free buffer;
-//   warp 8     streams the pass's slabs into four stages by bulk copies;
+//   warps 0-3  convert each tile's signal entries once, 64 at a time, from
+//              FP32 into 16 KB BF16 block images (two sets of four, one set per
+//              tile, alternating, so a tile's image serves all of its passes);
+//              thread (w, lane) takes row lane & 7 of 8-row groups w, w + 4,
+//              w + 8, w + 12 and entry groups lane >> 3 and + 4, so a
+//              quarter-warp's 16-byte stores fill 128 contiguous bytes (no bank
+//              conflict); the next block's loads fly while the thread waits for
+//              a free set;
+//   warp 8     streams each pass's slabs into two stages by bulk copies;
 //   warp 9     issues per block four 128 x 256 x 16 MMAs into the item's
-//              accumulator (two, alternating by item), freeing each stage and
-//              signal buffer by tcgen05.commit;
+//              accumulator (two, alternating by item), freeing each stage by
+//              tcgen05.commit and a tile's image set after its last pass;
 //   warps 4-7  read a finished accumulator out while the next item's products
 //              run into the other one: warp 4 + q owns TMEM lanes (tile rows)
 //              32 q .. 32 q + 31, passes each 32-column slice through a padded
@@ -207,8 +209,8 @@ __global__ void __launch_bounds__(128) gram_tc_kernel(const unsigned char *__res
 constexpr int kC16Threads = 320;
 constexpr int kC16NT = 256;                                 // atoms per item
 constexpr int kC16KB = 64;                                  // signal entries per block
-constexpr int kC16Stages = 4;                               // dictionary slab stages
-constexpr int kC16ABuf = 3;                                 // signal block buffers
+constexpr int kC16Stages = 2;                               // dictionary slab stages
+constexpr int kC16ABlks = 4;                                // signal blocks per image set (m <= 256)
 constexpr uint32_t kC16Slab = (uint32_t)kC16NT * kC16KB * 2;   // 32 KB
 constexpr uint32_t kC16ABlk = 128u * kC16KB * 2;               // 16 KB
 constexpr int kC16Pitch = 36;   // floats per row of a read-out transpose buffer (32 + 4: no bank conflict)
@@ -247,15 +249,15 @@ __device__ __forceinline__ C16Tile c16_tile(const C16Job &j, int64_t g) {
 
 struct C16Bars {
   uint64_t full_b[kC16Stages], empty_b[kC16Stages];
-  uint64_t full_a[kC16ABuf], empty_a[kC16ABuf];
+  uint64_t full_a[2][kC16ABlks], empty_a[2];
   uint64_t acc_full[2], acc_empty[2];
   uint64_t done;
   uint32_t tslot;
   int fail;
 };
 
-constexpr size_t kC16A = 0;                                             // signal block buffers
-constexpr size_t kC16B = kC16A + kC16ABuf * (size_t)kC16ABlk;           // slab stages
+constexpr size_t kC16A = 0;                                             // two signal image sets
+constexpr size_t kC16B = kC16A + 2 * kC16ABlks * (size_t)kC16ABlk;      // slab stages
 constexpr size_t kC16T = kC16B + kC16Stages * (size_t)kC16Slab;         // read-out transpose buffers
 constexpr size_t kC16Bar = kC16T + 4 * 32 * kC16Pitch * sizeof(float);
 constexpr size_t kC16Smem = kC16Bar + sizeof(C16Bars);
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(kC16Threads, 1) corr16_kernel(C16Job j) {
   volatile int *fail = &bars->fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = j.a.K, m = j.a.m, nblk = j.nblk;
-  const int64_t nitem = j.ntile * j.npass;
+  const int npass = j.npass;
 
   if (warp == 9) tc::tmem_alloc(&bars->tslot, 2 * kC16NT);
   if (tid == 0) {
@@ -274,8 +276,8 @@ __global__ void __launch_bounds__(kC16Threads, 1) corr16_kernel(C16Job j) {
       tc::mbar_init(&bars->full_b[q], 1);
       tc::mbar_init(&bars->empty_b[q], 1);
     }
-    for (int q = 0; q < kC16ABuf; ++q) {
-      tc::mbar_init(&bars->full_a[q], 128);
+    for (int q = 0; q < 2; ++q) {
+      for (int b = 0; b < kC16ABlks; ++b) tc::mbar_init(&bars->full_a[q][b], 128);
       tc::mbar_init(&bars->empty_a[q], 1);
     }
     for (int q = 0; q < 2; ++q) {
@@ -325,24 +327,23 @@ __global__ void __launch_bounds__(kC16Threads, 1) corr16_kernel(C16Job j) {
         }
       }
     };
-    uint32_t cnt = 0;   // blocks converted
     bool stop = false;
-    if ((int64_t)blockIdx.x < nitem) load(c16_tile(j, j.tile0 + blockIdx.x / j.npass), 0);
-    for (int64_t it = blockIdx.x; it < nitem && !stop; it += gridDim.x) {
-      const C16Tile T = c16_tile(j, j.tile0 + it / j.npass);
+    if ((int64_t)blockIdx.x < j.ntile) load(c16_tile(j, j.tile0 + blockIdx.x), 0);
+    uint32_t tk = 0;   // tiles converted
+    for (int64_t tt = blockIdx.x; tt < j.ntile && !stop; tt += gridDim.x, ++tk) {
+      const C16Tile T = c16_tile(j, j.tile0 + tt);
+      const int set = (int)(tk & 1);
+      // the products of every pass of the tile two back read this set
+      if (tk >= 2 && !tc::mbar_wait(&bars->empty_a[set], ((tk >> 1) - 1) & 1, j.wait_limit)) {
+        give_up();
+        break;
+      }
       for (int b = 0; b < nblk; ++b) {
-        const int ab = (int)(cnt % kC16ABuf);
-        const uint32_t use = cnt / kC16ABuf;
-        if (use >= 1 && !tc::mbar_wait(&bars->empty_a[ab], (use - 1) & 1, j.wait_limit)) {
-          give_up();
-          stop = true;
-          break;
-        }
         if (*fail) {
           stop = true;
           break;
         }
-        unsigned char *A = smem + kC16A + (size_t)ab * kC16ABlk;
+        unsigned char *A = smem + kC16A + (size_t)(set * kC16ABlks + b) * kC16ABlk;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
 #pragma unroll
@@ -357,12 +358,11 @@ __global__ void __launch_bounds__(kC16Threads, 1) corr16_kernel(C16Job j) {
           }
         }
         tc::fence_proxy_async();
-        tc::mbar_arrive(&bars->full_a[ab]);
-        ++cnt;
+        tc::mbar_arrive(&bars->full_a[set][b]);
         if (b + 1 < nblk)
           load(T, b + 1);
-        else if (it + gridDim.x < nitem)
-          load(c16_tile(j, j.tile0 + (it + gridDim.x) / j.npass), 0);
+        else if (tt + gridDim.x < j.ntile)
+          load(c16_tile(j, j.tile0 + tt + gridDim.x), 0);
       }
     }
   } else if (warp < 8) {
@@ -371,8 +371,11 @@ __global__ void __launch_bounds__(kC16Threads, 1) corr16_kernel(C16Job j) {
     float *tb = reinterpret_cast<float *>(smem + kC16T) + (size_t)q * 32 * kC16Pitch;
     const bool vst = (K & 3) == 0;
     const int sub = lane >> 3, c4 = 4 * (lane & 7);   // write phase: row 4 jj + sub, columns c4 .. c4 + 3
-    uint32_t cnt = 0;
-    for (int64_t it = blockIdx.x; it < nitem; it += gridDim.x, ++cnt) {
+    uint32_t cnt = 0;   // items read out
+    const int64_t nit = ((j.ntile - blockIdx.x + gridDim.x - 1) / gridDim.x) * npass;   // this block's items
+    for (int64_t k = 0; k < nit; ++k, ++cnt) {
+      const int64_t tt = blockIdx.x + (k / npass) * (int64_t)gridDim.x;
+      const int p = (int)(k % npass);
       const int acc = cnt & 1;
       const bool got = tc::mbar_wait(&bars->acc_full[acc], (cnt >> 1) & 1, j.wait_limit);
       if (!__all_sync(0xffffffffu, got)) {   // the TMEM loads below need the whole warp
@@ -381,8 +384,8 @@ __global__ void __launch_bounds__(kC16Threads, 1) corr16_kernel(C16Job j) {
       }
       if (__any_sync(0xffffffffu, *fail != 0)) break;
       tc::fence_after();
-      const C16Tile T = c16_tile(j, j.tile0 + it / j.npass);
-      const int c0 = (int)(it % j.npass) * kC16NT;
+      const C16Tile T = c16_tile(j, j.tile0 + tt);
+      const int c0 = p * kC16NT;
       const int ncol = K - c0 < kC16NT ? K - c0 : kC16NT;
       for (int c = 0; c < ncol; c += 32) {
         float x[32];
@@ -416,10 +419,11 @@ __global__ void __launch_bounds__(kC16Threads, 1) corr16_kernel(C16Job j) {
     if (lane == 0 && !j.leave) {
       uint32_t c = 0;   // slabs issued
       bool stop = false;
-      for (int64_t it = blockIdx.x; it < nitem && !stop; it += gridDim.x) {
-        const int64_t g = j.tile0 + it / j.npass;
+      const int64_t nit = ((j.ntile - blockIdx.x + gridDim.x - 1) / gridDim.x) * npass;
+      for (int64_t k = 0; k < nit && !stop; ++k) {
+        const int64_t g = j.tile0 + blockIdx.x + (k / npass) * (int64_t)gridDim.x;
         const int t = find_subset(j.a.tile_start, j.a.L, g);
-        const int p = (int)(it % j.npass);
+        const int p = (int)(k % npass);
         for (int b = 0; b < nblk; ++b) {
           const int s = (int)(c % kC16Stages);
           const uint32_t u = c / kC16Stages;
@@ -448,39 +452,45 @@ __global__ void __launch_bounds__(kC16Threads, 1) corr16_kernel(C16Job j) {
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16(128, kC16NT);
       const uint32_t abase = tc::smem_u32(smem + kC16A), bbase = tc::smem_u32(smem + kC16B);
-      uint32_t c = 0, nbk = 0, cnt = 0;
+      uint32_t c = 0, cnt = 0, tk = 0;   // slabs, items, tiles
       bool stop = false;
-      for (int64_t it = blockIdx.x; it < nitem && !stop; it += gridDim.x, ++cnt) {
-        const int acc = cnt & 1;
-        if (cnt >= 2 && !tc::mbar_wait(&bars->acc_empty[acc], ((cnt >> 1) - 1) & 1, j.wait_limit)) {
-          give_up();
-          break;
-        }
-        tc::fence_after();
-        const uint32_t d = tbase + (uint32_t)(acc * kC16NT);
-        for (int b = 0; b < nblk; ++b) {
-          const int ab = (int)(nbk % kC16ABuf), s = (int)(c % kC16Stages);
-          if (*fail || !tc::mbar_wait(&bars->full_a[ab], (nbk / kC16ABuf) & 1, j.wait_limit) ||
-              !tc::mbar_wait(&bars->full_b[s], (c / kC16Stages) & 1, j.wait_limit)) {
-            if (!*fail) give_up();
+      for (int64_t tt = blockIdx.x; tt < j.ntile && !stop; tt += gridDim.x, ++tk) {
+        const int set = (int)(tk & 1);
+        const uint32_t par = (tk >> 1) & 1;
+        for (int p = 0; p < npass && !stop; ++p, ++cnt) {
+          const int acc = cnt & 1;
+          if (cnt >= 2 && !tc::mbar_wait(&bars->acc_empty[acc], ((cnt >> 1) - 1) & 1, j.wait_limit)) {
+            give_up();
             stop = true;
             break;
           }
           tc::fence_after();
-          const uint32_t a_s = abase + (uint32_t)ab * kC16ABlk, b_s = bbase + (uint32_t)s * kC16Slab;
+          const uint32_t d = tbase + (uint32_t)(acc * kC16NT);
+          for (int b = 0; b < nblk; ++b) {
+            const int s = (int)(c % kC16Stages);
+            if (*fail || !tc::mbar_wait(&bars->full_a[set][b], par, j.wait_limit) ||
+                !tc::mbar_wait(&bars->full_b[s], (c / kC16Stages) & 1, j.wait_limit)) {
+              if (!*fail) give_up();
+              stop = true;
+              break;
+            }
+            tc::fence_after();
+            const uint32_t a_s = abase + (uint32_t)(set * kC16ABlks + b) * kC16ABlk, b_s = bbase + (uint32_t)s * kC16Slab;
 #pragma unroll
-          for (int ks = 0; ks < kC16KB / 16; ++ks) {
-            const uint32_t o = (uint32_t)ks * 256;
-            tc::mma_bf16(d, tc::smem_desc(a_s + o, 128, 1024), tc::smem_desc(b_s + o, 128, 1024), idesc,
-                         b > 0 || ks > 0);
+            for (int ks = 0; ks < kC16KB / 16; ++ks) {
+              const uint32_t o = (uint32_t)ks * 256;
+              tc::mma_bf16(d, tc::smem_desc(a_s + o, 128, 1024), tc::smem_desc(b_s + o, 128, 1024), idesc,
+                           b > 0 || ks > 0);
+            }
+            tc::mma_commit(&bars->empty_b[s]);
+            ++c;
           }
-          tc::mma_commit(&bars->empty_b[s]);
-          tc::mma_commit(&bars->empty_a[ab]);
-          ++c;
-          ++nbk;
+          if (stop) break;
+          tc::mma_commit(&bars->acc_full[acc]);
         }
         if (stop) break;
-        tc::mma_commit(&bars->acc_full[acc]);
+        // every pass of the tile has read its image set
+        tc::mma_commit(&bars->empty_a[set]);
       }
       // every product issued has finished before the tensor memory is freed
       tc::mma_commit(&bars->done);
@@ -657,6 +667,7 @@ cudaError_t launch_omp_tc(const OmpArgs &a, const void *img, float *a0c, int num
   j.nblk = round64c(a.m) / kC16KB;
   j.Kp = round256c(a.K);
   j.npass = (a.K + kC16NT - 1) / kC16NT;
+  if (j.nblk > kC16ABlks) return cudaErrorInvalidValue;   // m <= 256: a tile's image fits one set
   j.err = a.err;
   j.wait_limit = w.limit > 0 ? w.limit : 1;
   j.leave = w.leave;
@@ -665,8 +676,7 @@ cudaError_t launch_omp_tc(const OmpArgs &a, const void *img, float *a0c, int num
   for (int64_t g0 = 0; g0 < a.total_tiles; g0 += chunk) {
     j.tile0 = g0;
     j.ntile = a.total_tiles - g0 < chunk ? a.total_tiles - g0 : chunk;
-    const int64_t nitem = j.ntile * j.npass;
-    corr16_kernel<<<(unsigned)(nitem < sms ? nitem : sms), kC16Threads, smem, st>>>(j);
+    corr16_kernel<<<(unsigned)(j.ntile < sms ? j.ntile : sms), kC16Threads, smem, st>>>(j);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the coefficients from alpha0 on the support carry its BF16 rounding; the
     // selection loop's FP32 correction step (residual from D_S and y in FP32,
